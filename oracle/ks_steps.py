@@ -1,0 +1,232 @@
+"""Step model of the four Kronecker-substitution variants -- TEST INFRASTRUCTURE ONLY.
+
+Each variant is run on Python integers, following the steps of Harvey's
+Sec. 3 in the paper's order and notation, in any base: the evaluation point is
+X = base^N, so base 2 gives the method itself and base 10 replays the paper's
+worked examples (Sec. 1, and the examples of Sec. 3.2, 3.3 and 3.4).  Every
+intermediate (evaluations, products, combined halves, the digits u_i and
+w_i, and the reconstruction's alpha_i, beta_i, delta_i, epsilon_i) is returned
+so that tests can pin it.
+
+Readings of the paper used here (the paper is silent or garbled on them):
+
+* Unequal lengths: Lh = Lf + Lg - 1 replaces 2L - 1, and
+  e = ceil(log_base min(Lf, Lg)) bounds the number of terms per h_k.
+* Reversal: rev f(x) = x^(Lf-1) f(1/x), i.e. the coefficient list reversed.
+  The four-point variant's reversed pair is taken as rev f(+-X) rev g(+-X) =
+  rev h(+-X); this reproduces the printed values of the Sec. 3.4 example,
+  whose sign of 10^6 f(-10^-2) differs from the displayed sum formula of
+  Sec. 2.4 by (-1)^(L-1).
+* Four-point pairing: when Lh is even, the even-index half of rev h holds the
+  odd coefficients of h, so the even coefficients come from (E, OR) and the
+  odd ones from (O, ER).
+* Signed coefficients (the paper treats non-negative ones only): bias each
+  coefficient by c = 2^(b-1) to make it non-negative, multiply, and subtract
+  c (f U_g + U_f g) + c^2 U_f U_g, with U the all-ones polynomial.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+
+def ceil_log(n: int, base: int) -> int:
+    """Smallest e >= 0 with base^e >= n."""
+    e, p = 0, 1
+    while p < n:
+        p *= base
+        e += 1
+    return e
+
+
+def variant_N(variant: int, b: int, e: int) -> int:
+    """The evaluation exponent N of each variant (Sec. 3.1-3.4)."""
+    if variant == 1:
+        return 2 * b + e                      # Sec. 3.1
+    if variant in (2, 3):
+        return b + (e + 1) // 2               # Sec. 3.3 and Sec. 3.2
+    if variant == 4:
+        return (2 * b + e + 3) // 4           # Sec. 3.4
+    raise ValueError("variant must be 1..4")
+
+
+def evaluate(coeffs: list[int], X: int) -> int:
+    """sum_i c_i X^i (Horner), for any integer X, positive or negative."""
+    v = 0
+    for c in reversed(coeffs):
+        v = v * X + c
+    return v
+
+
+def digit(v: int, i: int, X: int) -> int:
+    """The i-th base-X digit of the non-negative integer v."""
+    return (v // X ** i) % X
+
+
+def even_odd(coeffs: list[int]) -> tuple[list[int], list[int]]:
+    return coeffs[0::2], coeffs[1::2]
+
+
+def eval_pm(coeffs: list[int], X: int) -> tuple[int, int]:
+    """f(X) and f(-X) from the even and odd parts, as Sec. 3.3 describes:
+    f(+-X) = f0(X^2) +- X f1(X^2), each part packed at spacing 2N without overlap."""
+    f0, f1 = even_odd(coeffs)
+    e = evaluate(f0, X * X)
+    o = X * evaluate(f1, X * X)
+    return e + o, e - o
+
+
+@dataclass
+class Recovery:
+    h: list[int]
+    alpha: list[int]
+    beta: list[int]
+    delta: list[int]
+    eps: list[int]
+    u: list[int]
+    w: list[int]
+
+
+def recover(fwd: int, rev: int, n: int, X: int) -> Recovery:
+    """Reciprocal reconstruction of Sec. 3.2 (eqs. for digits u_i, w_i and carries).
+
+    fwd = sum_{i<n} c_i X^i and rev = sum_{i<n} c_{n-1-i} X^i, with
+    0 <= c_i < X (X - 1).  Returns c_0..c_{n-1} and the intermediates.
+    Digits: fwd = sum_{i=0}^{n} u_i X^i;  rev = sum_{i=0}^{n} w_{n-i} X^i.
+    """
+    if n < 1:
+        raise ValueError("need at least one coefficient")
+    u = [digit(fwd, i, X) for i in range(n + 1)]
+    w = [digit(rev, n - j, X) for j in range(n + 1)]
+    alpha = [0] * n
+    beta = [0] * n
+    delta = [0] * n
+    eps = [0] * n
+    alpha[0] = u[0]
+    a_prev = 0                                # alpha_{-1}
+    for j in range(n - 1):
+        # epsilon_j: carry out of alpha_j + beta_{j+1} + eps_{j+1} in rev
+        eps[j] = 1 if alpha[j] > w[j + 1] else 0
+        beta[j] = (w[j] - a_prev - eps[j]) % X
+        alpha[j + 1] = (u[j + 1] - beta[j] - delta[j]) % X
+        t = beta[j] + alpha[j + 1] + delta[j] - u[j + 1]
+        assert t % X == 0
+        delta[j + 1] = t // X
+        a_prev = alpha[j]
+    beta[n - 1] = (w[n - 1] - a_prev - 0) % X   # eps_{n-1} = 0
+    h = [alpha[i] + X * beta[i] for i in range(n)]
+    return Recovery(h, alpha, beta, delta, eps, u, w)
+
+
+@dataclass
+class Run:
+    variant: int
+    X: int
+    h: list[int]
+    evals: dict = field(default_factory=dict)
+    products: dict = field(default_factory=dict)
+    halves: dict = field(default_factory=dict)
+    recoveries: list = field(default_factory=list)
+
+
+def ks1(f: list[int], g: list[int], X: int) -> Run:
+    """Standard substitution (Sec. 3.1): one product at X, coefficients read off base X."""
+    F, G = evaluate(f, X), evaluate(g, X)
+    P = F * G
+    lh = len(f) + len(g) - 1
+    h = [digit(P, k, X) for k in range(lh)]
+    return Run(1, X, h, {"F": F, "G": G}, {"P": P})
+
+
+def ks2(f: list[int], g: list[int], X: int) -> Run:
+    """Negated points (Sec. 3.3): products at +X and -X; even coefficients from
+    (P+ + P-)/2 = h0(X^2), odd ones from (P+ - P-)/2 = X h1(X^2)."""
+    Fp, Fm = eval_pm(f, X)
+    Gp, Gm = eval_pm(g, X)
+    Pp, Pm = Fp * Gp, Fm * Gm
+    assert (Pp + Pm) % 2 == 0 and (Pp - Pm) % (2 * X) == 0
+    E = (Pp + Pm) // 2
+    Oh = (Pp - Pm) // 2
+    lh = len(f) + len(g) - 1
+    Y = X * X
+    h = [0] * lh
+    for k in range(lh):
+        h[k] = digit(E, k // 2, Y) if k % 2 == 0 else digit(Oh // X, k // 2, Y)
+    return Run(2, X, h, {"F+": Fp, "F-": Fm, "G+": Gp, "G-": Gm},
+               {"P+": Pp, "P-": Pm}, {"E": E, "XO": Oh})
+
+
+def ks3(f: list[int], g: list[int], X: int) -> Run:
+    """Reciprocal points (Sec. 3.2): P = f(X) g(X) and R = rev f(X) rev g(X)
+    = X^(Lh-1) h(1/X); the coefficients come from the reconstruction."""
+    F, G = evaluate(f, X), evaluate(g, X)
+    Fr, Gr = evaluate(f[::-1], X), evaluate(g[::-1], X)
+    P, R = F * G, Fr * Gr
+    lh = len(f) + len(g) - 1
+    rec = recover(P, R, lh, X)
+    return Run(3, X, rec.h, {"F": F, "G": G, "Fr": Fr, "Gr": Gr}, {"P": P, "R": R},
+               recoveries=[rec])
+
+
+def ks4(f: list[int], g: list[int], X: int) -> Run:
+    """Four points (Sec. 3.4): products at +-X and, reversed, at +-1/X; the
+    combined halves at Y = X^2 feed two runs of the Sec. 3.2 reconstruction,
+    one for the even-index and one for the odd-index coefficients."""
+    Fp, Fm = eval_pm(f, X)
+    Gp, Gm = eval_pm(g, X)
+    Frp, Frm = eval_pm(f[::-1], X)
+    Grp, Grm = eval_pm(g[::-1], X)
+    Pp, Pm, Rp, Rm = Fp * Gp, Fm * Gm, Frp * Grp, Frm * Grm
+    for a, b in ((Pp, Pm), (Rp, Rm)):
+        assert (a + b) % 2 == 0 and (a - b) % (2 * X) == 0
+    E, O = (Pp + Pm) // 2, (Pp - Pm) // (2 * X)
+    ER, OR = (Rp + Rm) // 2, (Rp - Rm) // (2 * X)
+    lh = len(f) + len(g) - 1
+    n0, n1 = (lh + 1) // 2, lh // 2
+    Y = X * X
+    even_pair = (E, ER) if lh % 2 == 1 else (E, OR)
+    odd_pair = (O, OR) if lh % 2 == 1 else (O, ER)
+    rec0 = recover(even_pair[0], even_pair[1], n0, Y)
+    recs = [rec0]
+    h = [0] * lh
+    h[0::2] = rec0.h
+    if n1 > 0:
+        rec1 = recover(odd_pair[0], odd_pair[1], n1, Y)
+        recs.append(rec1)
+        h[1::2] = rec1.h
+    return Run(4, X, h,
+               {"F+": Fp, "F-": Fm, "Fr+": Frp, "Fr-": Frm,
+                "G+": Gp, "G-": Gm, "Gr+": Grp, "Gr-": Grm},
+               {"P+": Pp, "P-": Pm, "R+": Rp, "R-": Rm},
+               {"E": E, "O": O, "ER": ER, "OR": OR,
+                "XO": (Pp - Pm) // 2, "XOR": (Rp - Rm) // 2},
+               recs)
+
+
+VARIANTS = {1: ks1, 2: ks2, 3: ks3, 4: ks4}
+
+
+def ks_mul_unsigned(f: list[int], g: list[int], b: int, variant: int, base: int = 2) -> Run:
+    """Runs one variant with the paper's N for coefficients of at most b base-digits."""
+    if min(f) < 0 or min(g) < 0:
+        raise ValueError("the paper's variants take non-negative coefficients")
+    e = ceil_log(min(len(f), len(g)), base)
+    N = variant_N(variant, b, e)
+    return VARIANTS[variant](f, g, base ** N)
+
+
+def ks_mul_signed(f: list[int], g: list[int], b: int, variant: int) -> list[int]:
+    """Signed coefficients in [-2^(b-1), 2^(b-1)) by the bias reading (see module doc)."""
+    c = 1 << (b - 1)
+    fb = [x + c for x in f]
+    gb = [x + c for x in g]
+    hb = ks_mul_unsigned(fb, gb, b, variant).h
+    lf, lg = len(f), len(g)
+    out = []
+    for k in range(lf + lg - 1):
+        lo, hi = max(0, k - lg + 1), min(k, lf - 1)
+        wf = sum(f[lo:hi + 1])                       # (f * U_g)_k
+        lo2, hi2 = max(0, k - lf + 1), min(k, lg - 1)
+        wg = sum(g[lo2:hi2 + 1])                     # (U_f * g)_k
+        cnt = hi - lo + 1                            # (U_f * U_g)_k
+        out.append(hb[k] - c * (wf + wg) - c * c * cnt)
+    return out

@@ -1,0 +1,193 @@
+"""Pins the step model of the four variants to the paper's worked examples and to
+the schoolbook product; checks the invariants the paper states along the way.
+
+Fixtures: Sec. 1 (intro), Sec. 3.2 (reciprocal, base ten, N = 4), Sec. 3.3
+(negated, base ten), Sec. 3.4 (four points, base ten, N = 2).
+"""
+import random
+
+import pytest
+
+from oracle import ks_steps as S
+from oracle import pyref
+from tests._golden import load
+
+F = [274, 610, 887, 621]
+G = [553, 298, 424, 790]
+H = [151522, 418982, 788467, 1082839, 1043046, 964034, 490590]
+
+
+def test_decimal_N_matches_paper():
+    # b = 3 decimal digits, e = ceil(log10 4) = 1: N = 7, 4, 4, 2 (Sec. 1, 3.2-3.4)
+    e = S.ceil_log(4, 10)
+    assert e == 1
+    assert [S.variant_N(v, 3, e) for v in (1, 2, 3, 4)] == [7, 4, 4, 2]
+
+
+def test_ks1_intro_replay():
+    ex = load("intro_example.txt")
+    r = S.ks_mul_unsigned(F, G, 3, 1, base=10)
+    assert r.X == 10 ** 7
+    assert r.evals["F"] == ex["f(10^7)"] and r.evals["G"] == ex["g(10^7)"]
+    assert r.products["P"] == ex["h(10^7)"]
+    assert r.h == ex["h"] == H
+
+
+def test_ks3_example_replay():
+    ex = load("ks3_example.txt")
+    r = S.ks_mul_unsigned(F, G, 3, 3, base=10)
+    assert r.X == 10 ** ex["N"]
+    assert r.evals["F"] == ex["f(10^4)"]
+    assert r.evals["Fr"] == ex["10^12 f(10^-4)"]
+    assert r.evals["G"] == ex["g(10^4)"]
+    assert r.evals["Gr"] == ex["10^12 g(10^-4)"]
+    assert r.products["P"] == ex["h(10^4)"]
+    assert r.products["R"] == ex["10^24 h(10^-4)"]
+    rec = r.recoveries[0]
+    assert rec.u[0] == ex["u_0"] == rec.alpha[0]
+    assert rec.w[1] == ex["w_1"]
+    assert rec.eps[0] == ex["eps_0"]
+    assert rec.beta[0] == ex["beta_0"]
+    assert rec.h[0] == ex["h_0"]
+    assert r.products["P"] - rec.h[0] == ex["h(10^4) - h_0"]
+    assert r.products["R"] - 10 ** 24 * rec.h[0] == ex["10^24 h(10^-4) - 10^24 h_0"]
+    assert rec.h[1] == ex["h_1"]
+    assert r.h == H
+
+
+def test_ks2_example_replay():
+    ex = load("ks2_example.txt")
+    r = S.ks_mul_unsigned(F, G, 3, 2, base=10)
+    assert r.X == 10 ** ex["N"]
+    assert r.evals["F+"] == ex["f(10^4)"] and r.evals["F-"] == ex["f(-10^4)"]
+    assert r.evals["G+"] == ex["g(10^4)"] and r.evals["G-"] == ex["g(-10^4)"]
+    assert r.products["P+"] == ex["h(10^4)"] and r.products["P-"] == ex["h(-10^4)"]
+    assert r.halves["E"] == ex["h0(10^8)"]
+    assert r.halves["XO"] == ex["10^4 h1(10^8)"]
+    assert r.h == H
+
+
+def test_ks4_example_replay():
+    ex = load("ks4_example.txt")
+    r = S.ks_mul_unsigned(F, G, 3, 4, base=10)
+    assert r.X == 10 ** ex["N"]
+    sign = (-1) ** (len(F) - 1)  # rev f(-X) = (-1)^(L-1) X^(L-1) f(-1/X)
+    assert r.evals["F+"] == ex["f(10^2)"] and r.evals["F-"] == ex["f(-10^2)"]
+    assert r.evals["Fr+"] == ex["10^6 f(10^-2)"]
+    assert r.evals["Fr-"] == sign * ex["10^6 f(-10^-2)"]
+    assert r.evals["G+"] == ex["g(10^2)"] and r.evals["G-"] == ex["g(-10^2)"]
+    assert r.evals["Gr+"] == ex["10^6 g(10^-2)"]
+    assert r.evals["Gr-"] == sign * ex["10^6 g(-10^-2)"]
+    assert r.products["P+"] == ex["h(10^2)"] and r.products["P-"] == ex["h(-10^2)"]
+    assert r.products["R+"] == ex["10^12 h(10^-2)"]
+    assert r.products["R-"] == ex["10^12 h(-10^-2)"]
+    assert r.halves["E"] == ex["h0(10^4)"]
+    assert r.halves["ER"] == ex["10^12 h0(10^-4)"]
+    assert r.halves["XO"] == ex["10^2 h1(10^4)"]
+    assert r.halves["XOR"] == ex["10^10 h1(10^-4)"]
+    assert r.h == H
+
+
+def _check_recovery_invariants(rec, X):
+    assert all(d in (0, 1) for d in rec.delta)          # carries of eq. (carry-1)
+    assert all(e in (0, 1) for e in rec.eps)            # carries of eq. (carry-2)
+    assert all(0 <= a < X for a in rec.alpha)
+    assert all(0 <= bb < X - 1 for bb in rec.beta)      # eq. (beta-range)
+
+
+SHAPES = [(1, 1), (1, 2), (2, 1), (2, 2), (3, 2), (5, 5), (6, 3), (8, 8), (9, 16), (17, 4),
+          (16, 16), (31, 33)]
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("b", [1, 2, 5, 16, 47, 64, 65, 130])
+def test_variants_match_schoolbook(variant, b):
+    rng = random.Random(variant * 1000 + b)
+    for lf, lg in SHAPES:
+        f = [rng.randrange(1 << b) for _ in range(lf)]
+        g = [rng.randrange(1 << b) for _ in range(lg)]
+        r = S.ks_mul_unsigned(f, g, b, variant)
+        assert r.h == pyref.poly_mul(f, g), (lf, lg)
+        Xrec = r.X if variant == 3 else r.X * r.X
+        for rec in r.recoveries:
+            _check_recovery_invariants(rec, Xrec)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_variants_all_max(variant):
+    """Maximal coefficients meet the bound of Sec. 3 with equality; the
+    reconstruction must still see beta_i < 2^N - 1."""
+    for b in (1, 3, 8, 33):
+        for L in (1, 2, 3, 4, 7, 8, 9):
+            m = (1 << b) - 1
+            r = S.ks_mul_unsigned([m] * L, [m] * (L + 1), b, variant)
+            assert r.h == pyref.poly_mul([m] * L, [m] * (L + 1))
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("b", [1, 2, 8, 48, 64])
+def test_signed_bias_reading(variant, b):
+    rng = random.Random(b * 7 + variant)
+    lo, hi = -(1 << (b - 1)), 1 << (b - 1)
+    for lf, lg in SHAPES:
+        f = [rng.randrange(lo, hi) for _ in range(lf)]
+        g = [rng.randrange(lo, hi) for _ in range(lg)]
+        assert S.ks_mul_signed(f, g, b, variant) == pyref.poly_mul(f, g)
+    for lf, lg in [(4, 4), (5, 3)]:
+        assert S.ks_mul_signed([lo] * lf, [lo] * lg, b, variant) == pyref.poly_mul([lo] * lf, [lo] * lg)
+
+
+@pytest.mark.parametrize("b,L", [(8, 16), (48, 64), (64, 33), (5, 100)])
+def test_operand_lengths_match_propositions(b, L):
+    """Bit lengths of the evaluated operands against the Propositions of Sec. 3."""
+    m = (1 << b) - 1
+    f = [m] * L
+    e = S.ceil_log(L, 2)
+    N1, N2, N4 = S.variant_N(1, b, e), S.variant_N(2, b, e), S.variant_N(4, b, e)
+    assert S.evaluate(f, 2 ** N1).bit_length() == N1 * (L - 1) + b
+    Fp, Fm = S.eval_pm(f, 2 ** N2)
+    assert Fp.bit_length() == N2 * (L - 1) + b
+    assert abs(Fm).bit_length() <= N2 * (L - 1) + b
+    Fp4, _ = S.eval_pm(f, 2 ** N4)
+    # the overlapping sum may carry one bit beyond the Proposition's length
+    assert N4 * (L - 1) + b <= Fp4.bit_length() <= N4 * (L - 1) + b + 1
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch):
+    """A plausible slip in the reconstruction (dropping the epsilon carry) or in
+    the negated evaluation (odd part without its factor X) breaks a pin."""
+    good = S.recover
+
+    def no_eps(fwd, rev, n, X):
+        u = [S.digit(fwd, i, X) for i in range(n + 1)]
+        w = [S.digit(rev, n - j, X) for j in range(n + 1)]
+        alpha, beta, delta = [0] * n, [0] * n, [0] * n
+        alpha[0], a_prev = u[0], 0
+        for j in range(n - 1):
+            beta[j] = (w[j] - a_prev) % X
+            alpha[j + 1] = (u[j + 1] - beta[j] - delta[j]) % X
+            delta[j + 1] = (beta[j] + alpha[j + 1] + delta[j] - u[j + 1]) // X
+            a_prev = alpha[j]
+        beta[n - 1] = (w[n - 1] - a_prev) % X
+        return S.Recovery([alpha[i] + X * beta[i] for i in range(n)], alpha, beta, delta,
+                          [0] * n, u, w)
+
+    monkeypatch.setattr(S, "recover", no_eps)
+    rng = random.Random(3)
+    bad = 0
+    for _ in range(50):
+        f = [rng.randrange(1 << 16) for _ in range(9)]
+        g = [rng.randrange(1 << 16) for _ in range(9)]
+        bad += S.ks_mul_unsigned(f, g, 16, 3).h != pyref.poly_mul(f, g)
+    assert bad > 0
+    monkeypatch.setattr(S, "recover", good)
+
+    def wrong_pm(coeffs, X):  # odd part packed without its factor X
+        f0, f1 = S.even_odd(coeffs)
+        e = S.evaluate(f0, X * X)
+        o = S.evaluate(f1, X * X)
+        return e + o, e - o
+
+    monkeypatch.setattr(S, "eval_pm", wrong_pm)
+    with pytest.raises(AssertionError):
+        test_ks2_example_replay()
