@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark: Z[x] products/s and output Gbit/s, KS4 vs KS1, bit-exact, one GB300.
+
+Workload (the single-GPU configuration the metric is quoted on): one signed
+product, len_f = len_g = 16384, coefficients uniform in [-2^47, 2^47) from a
+fixed seed; all four variants (Sec. 3.1-3.4) run on the same inputs.  A step
+is one whole product (pack, sub-products, normalize/combine, unpack or
+reconstruction, signed correction) with inputs resident on the device; the
+headline `value` is KS4's products/s, the other variants are reported beside
+it under `variants`.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+library's stream; between steps a 256 MiB buffer is written to flush the
+129 MB L2 (outside the events).  Per-phase CUDA events inside the library give
+the dominant kernel's duration for the roofline.  `e2e` times the host-buffer
+entry point (ks_mul_host: H2D copy, product, D2H copy) with pinned buffers.
+
+`--impl reference` times the CPU oracle (plain schoolbook, all host cores) on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import ks_inputs  # noqa: E402
+
+WORKLOAD = {"workload": "zx_product_16384_s48", "len_f": 16384, "len_g": 16384,
+            "coeff_bits": 48, "is_signed": True, "seed_f": 20071229, "seed_g": 20071230}
+METRIC = "Z[x] products/s and output Gbit/s, KS4 vs KS1, bit-exact, 1 GB300"
+L2_FLUSH_BYTES = 256 << 20
+# 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC
+IMAD_PER_SM_CLK = 64
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return ap.parse_args()
+
+
+def output_bits(lf, lg, b):
+    e = (min(lf, lg) - 1).bit_length()
+    return (lf + lg - 1) * (2 * b + e)
+
+
+def inputs():
+    w = WORKLOAD
+    f = ks_inputs.random_poly(w["len_f"], w["coeff_bits"], w["is_signed"], w["seed_f"])
+    g = ks_inputs.random_poly(w["len_g"], w["coeff_bits"], w["is_signed"], w["seed_g"])
+    return f, g
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle arm
+def run_oracle(f, g, steps: int, warmup: int, budget_s: float):
+    import oracle
+    w = WORKLOAD
+    cores = os.cpu_count() or 1
+    for _ in range(max(0, min(warmup, 1))):
+        oracle.mul(f, g, w["coeff_bits"], w["is_signed"], threads=cores)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    for i in range(steps):
+        t0 = time.perf_counter()
+        oracle.mul(f, g, w["coeff_bits"], w["is_signed"], threads=cores)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end and i + 1 >= 1:
+            break
+    return times, cores
+
+
+def reference_main(args):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    f, g = inputs()
+    w = WORKLOAD
+    times, cores = run_oracle(f, g, args.steps, args.warmup, budget_s=240.0)
+    ms = 1000.0 * statistics.mean(times)
+    value = 1000.0 / ms
+    obits = output_bits(w["len_f"], w["len_g"], w["coeff_bits"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "products/s",
+        "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded splitmix64)",
+        "config": dict(WORKLOAD, variant="schoolbook oracle", l2="n/a (host)"),
+        "output_gbit_per_s": value * obits / 1e9,
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d full products of the workload" % len(times)},
+        "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main_ours(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_0712_4046_gb300 as ks
+
+    w = WORKLOAD
+    f, g = inputs()
+    lf, lg, b, sg = w["len_f"], w["len_g"], w["coeff_bits"], w["is_signed"]
+    tf = torch.from_numpy(f.view(np.int64)).to(dev)
+    tg = torch.from_numpy(g.view(np.int64)).to(dev)
+    ol = ks.out_limbs(lf, lg, b, sg)
+    lh = lf + lg - 1
+    h = torch.empty((lh, ol), dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    obits = output_bits(lf, lg, b)
+    hbm_gbs, sm_max_mhz, peak_kind = peaks()
+
+    results = {}
+    with Clocks(local) as clk:
+        for variant in (1, 2, 3, 4):
+            for _ in range(args.warmup):
+                ks.ks_mul(h, tf, tg, b, sg, variant, stream)
+            ks.status_sync(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            ks.profile_collect()
+            ks.profile_enable(True)
+            launches0 = ks.launch_count()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.zero_()
+                evs[i][0].record(stream)
+                ks.ks_mul(h, tf, tg, b, sg, variant, stream)
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            ks.profile_enable(False)
+            launches = ks.launch_count() - launches0
+            ks.status_sync(stream)
+            phases = ks.profile_collect()
+            step_ms = [a.elapsed_time(z) for a, z in evs]
+            total_ms = barrier_max(sum(step_ms), world, dev)
+            results[variant] = {"total_ms": total_ms, "ms_per_step": total_ms / args.steps,
+                                "launches": launches, "phases": phases}
+    clocks = clk.summary()
+
+    # ---- e2e through the host-buffer entry point (pinned buffers)
+    fh = torch.from_numpy(f.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    gh = torch.from_numpy(g.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    hh = torch.empty((lh, ol), dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    for _ in range(args.warmup):
+        ks.ks_mul_host(hh, fh, gh, b, sg, 4, 0, stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ks.ks_mul_host(hh, fh, gh, b, sg, 4, 0, stream)
+    e2e_s = barrier_max(time.perf_counter() - t0, world, dev)
+
+    # ---- roofline of the dominant phase of KS4
+    r4 = results[4]
+    info = ks.plan_info(lf, lg, b, sg, 4, ks.ENGINE_AUTO)
+    ph = {k: v for k, v in r4["phases"].items() if v[1] > 0}
+    dom = max(ph, key=lambda k: ph[k][0])
+    dom_ms = ph[dom][0] / ph[dom][1]
+    roof = roofline_for(dom, dom_ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        times, cores = run_oracle(f, g, 30, 1, budget_s=15.0)
+        v = len(times) / sum(times)
+        cpu = {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle",
+               "sample": "%d full products of the workload, all host threads" % len(times)}
+
+    if rank != 0:
+        return 0
+    ms4 = r4["ms_per_step"]
+    value = world * 1000.0 / ms4
+    variants = {}
+    for v, r in results.items():
+        pps = world * 1000.0 / r["ms_per_step"]
+        variants["KS%d" % v] = {"products_per_s": pps, "ms_per_step": r["ms_per_step"],
+                                "output_gbit_per_s": pps * obits / 1e9,
+                                "phases_ms": {k: round(x[0] / max(1, x[1]), 5)
+                                              for k, x in r["phases"].items() if x[1] > 0}}
+    line = {
+        "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms4,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded splitmix64)",
+        "config": dict(WORKLOAD, variant="KS4", engine=info["engine"],
+                       l2="flushed between steps (256 MiB write)",
+                       parallelism="replicas" if world > 1 else "single"),
+        "output_gbit_per_s": value * obits / 1e9,
+        "ks4_over_ks1": results[1]["ms_per_step"] / ms4,
+        "variants": variants,
+        "gpu_launches": int(r4["launches"]),
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "products/s",
+                "h2d_bytes_per_step": int(f.nbytes + g.nbytes),
+                "d2h_bytes_per_step": int(lh * ol * 8)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def roofline_for(phase, ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind):
+    """Algorithmic work of one launch of the dominant phase over its event time."""
+    nprod, nA, nB, ncols = info["nprod"], info["nA"], info["nB"], info["ncols"]
+    nw, nnorm, ol, il = info["nwords"], info["nnorm"], info["out_limbs"], info["in_limbs"]
+    sec = ms / 1000.0
+    if phase == "product" and info["engine"] == 1:
+        ops = 2.0 * nprod * nA * nB  # one multiply-add per digit pair
+        peak = SMS * IMAD_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12
+        ach = ops / sec / 1e12
+        return {"bound": "alu", "phase": phase, "achieved": ach, "peak": peak,
+                "unit": "TOP/s", "frac": ach / peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 64 IMAD/clk x 2 ops x max SM clock"}
+    if phase == "pack":
+        byts = (lf + lg) * il * 8 + nprod * (nA + nB) * 4
+    elif phase == "normalize":
+        byts = nprod * ncols * 8 + nnorm * nw * 4
+    elif phase in ("unpack", "recover"):
+        byts = nnorm * nw * 4 + (lf + lg - 1) * ol * 8
+    elif phase == "signed_fix":
+        byts = (lf + lg) * ol * 8 * 2 + (lf + lg - 1) * ol * 8 * 2
+    else:
+        byts = nprod * ncols * 8
+    ach = byts / sec / 1e9
+    return {"bound": "hbm", "phase": phase, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": ach / hbm_gbs, "traffic": None, "peak_kind": peak_kind}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    return main_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * ks.h -- C ABI of the GB300 multipoint Kronecker-substitution library.
+ *
+ * Computes h = f * g in Z[x] for dense polynomials with multi-word integer
+ * coefficients, by the Kronecker substitution of Harvey, "Faster polynomial
+ * multiplication via multipoint Kronecker substitution" (arXiv:0712.4046):
+ *
+ *   KS_1  evaluate at 2^N, N = 2b + e                      (Sec. 3.1)
+ *   KS_2  evaluate at +2^N and -2^N, N = b + ceil(e/2)     (Sec. 3.3)
+ *   KS_3  evaluate at 2^N and 2^-N,  N = b + ceil(e/2)     (Sec. 3.2)
+ *   KS_4  all four points, N = ceil((2b + e) / 4)          (Sec. 3.4)
+ *
+ * with b the coefficient bit bound and e = ceil(log2 min(len_f, len_g))
+ * (Sec. 3 states the method for equal lengths L; unequal lengths use the
+ * shorter one, which bounds the number of terms of each h_k).  Every variant
+ * returns the same, exact product.
+ *
+ * Coefficient layout (inputs and outputs):
+ *   - coefficient i occupies `limbs` consecutive little-endian uint64 words;
+ *     inputs use in_limbs = ceil(coeff_bits / 64), outputs use
+ *     ks_out_limbs(...) limbs;
+ *   - unsigned coefficients lie in [0, 2^b); signed ones in
+ *     [-2^(b-1), 2^(b-1)), two's complement, sign-extended over the limbs
+ *     (Sec. 3 treats non-negative coefficients; signed ones are handled by a
+ *     bias of 2^(b-1) and an exact correction, see ks_mul);
+ *   - h holds len_f + len_g - 1 coefficients in the same encoding.
+ *
+ * Pointers: "device" means memory the current CUDA device can address
+ * (cudaMalloc or torch CUDA tensors); "host" means ordinary or pinned host
+ * memory.  All device work is issued on `stream` (a cudaStream_t passed as
+ * void*, NULL = the legacy default stream) and is asynchronous unless stated.
+ *
+ * Errors: every call returns a ks_status; nothing is thrown across the ABI.
+ * Asynchronous device-side failures (a bounded wait that gave up) are
+ * reported by ks_status_sync().  On any error the output is unspecified.
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *ks_stream_t; /* a cudaStream_t */
+
+/* Variant selector (Sec. 3.1-3.4).  KS_AUTO lets the library choose. */
+enum { KS_AUTO = 0, KS_1 = 1, KS_2 = 2, KS_3 = 3, KS_4 = 4 };
+
+/* Engine for the independent big-integer sub-products. */
+enum {
+  KS_ENGINE_AUTO = 0,
+  KS_ENGINE_SCHOOLBOOK = 1, /* exact digit contraction on the INT32 pipe */
+  KS_ENGINE_NTT = 2,        /* multi-prime number-theoretic transform + CRT */
+  KS_ENGINE_TC = 3          /* exact digit contraction on the tensor cores */
+};
+
+typedef enum {
+  KS_OK = 0,
+  KS_EINVAL = -1,   /* bad length, bit size, variant, engine, pointer or aliasing */
+  KS_ERANGE = -2,   /* size beyond a documented maximum */
+  KS_ENOMEM = -3,   /* a device or host allocation failed */
+  KS_ECUDA = -4,    /* a CUDA runtime call failed (see ks_last_cuda_error) */
+  KS_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+  KS_ENOTSUP = -6   /* engine or mode not available for these sizes */
+} ks_status;
+
+/* Largest supported coefficient bound b (bits). */
+#define KS_MAX_COEFF_BITS 2048
+
+/*
+ * Limbs per output coefficient: ceil((2b + e + is_signed) / 64), where
+ * e = ceil(log2 min(len_f, len_g)).  Sec. 3, eq. (h-inequality):
+ * 0 <= h_i <= L (2^b - 1)^2 < 2^(2b+e) for unsigned inputs; a signed result
+ * needs one more bit for its sign.  Returns a negative ks_status on bad input.
+ */
+int ks_out_limbs(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed);
+
+/* Evaluation exponent N the given variant uses (Sec. 3.1-3.4); < 0 on error. */
+int ks_eval_bits(int64_t len_f, int64_t len_g, int coeff_bits, int variant);
+
+/*
+ * Bytes of device workspace ks_mul_ex needs for this problem, variant and
+ * engine (KS_AUTO / KS_ENGINE_AUTO resolve as ks_mul would).  < 0 on error.
+ */
+int64_t ks_workspace_bytes(int64_t len_f, int64_t len_g, int coeff_bits,
+                           int is_signed, int variant, int engine);
+
+/*
+ * h = f * g (device pointers), exactly.  f has len_f coefficients, g has
+ * len_g, both with coeff_bits-bit coefficients (signed if is_signed); h
+ * receives len_f + len_g - 1 coefficients of ks_out_limbs() limbs.
+ * h must not overlap f or g; f may equal g.  Workspace comes from a cache
+ * the library keeps per (device, stream) and grows on demand (so the first
+ * call for a size allocates; later ones do not).  Asynchronous on `stream`.
+ */
+int ks_mul(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
+           int64_t len_g, int coeff_bits, int is_signed, int variant,
+           ks_stream_t stream);
+
+/*
+ * As ks_mul, with an explicit engine and caller-owned device workspace of at
+ * least ks_workspace_bytes() bytes (256-byte aligned).  Allocates nothing.
+ */
+int ks_mul_ex(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
+              int64_t len_g, int coeff_bits, int is_signed, int variant,
+              int engine, void *workspace, int64_t workspace_bytes,
+              ks_stream_t stream);
+
+/*
+ * As ks_mul but with HOST buffers: copies f and g to the device, multiplies,
+ * copies h back, and returns when h is complete (synchronous).  Device
+ * buffers are cached per (device, stream).
+ */
+int ks_mul_host(uint64_t *h, const uint64_t *f, int64_t len_f,
+                const uint64_t *g, int64_t len_g, int coeff_bits,
+                int is_signed, int variant, int engine, ks_stream_t stream);
+
+/*
+ * (Z/pZ)[x] product (Sec. 4): residues in [0, p) as one uint64 limb each,
+ * 2 <= p < 2^63; h receives (h_k mod p), one limb each.  The polynomials are
+ * lifted to Z[x] with b = bitlength(p - 1), multiplied exactly by the chosen
+ * variant, and reduced.  Device pointers, asynchronous.
+ */
+int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
+               int64_t len_g, uint64_t p, int variant, ks_stream_t stream);
+
+/* One product of a batch (device pointers, layout as for ks_mul). */
+typedef struct {
+  uint64_t *h;
+  const uint64_t *f;
+  const uint64_t *g;
+  int64_t len_f, len_g;
+  int32_t coeff_bits, is_signed, variant, engine;
+} ks_problem;
+
+/*
+ * Runs n independent products on `stream`.  probs is a HOST array.  Each
+ * product's variant/engine may be KS_AUTO.  Asynchronous.
+ */
+int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream);
+
+/* Waits for `stream`, then reports a pending device-side error (or KS_OK). */
+int ks_status_sync(ks_stream_t stream);
+
+/* The variant and engine KS_AUTO / KS_ENGINE_AUTO resolve to for a problem. */
+int ks_choose(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+              int *variant, int *engine);
+
+/* Message for a ks_status; the last CUDA error string for KS_ECUDA. */
+const char *ks_strerror(int status);
+const char *ks_last_cuda_error(void);
+
+/*
+ * Instrumentation.  ks_launch_count: kernels the library has launched so far
+ * (a host-side counter).  ks_profile_enable(1) makes every later call record
+ * a pair of CUDA events around each phase on its stream; ks_profile_collect
+ * waits for those events and returns, per phase id (0 .. n-1, names from
+ * ks_phase_name), the summed milliseconds and the number of records, then
+ * clears them.  Phases: 0 pack, 1 product, 2 normalize, 3 unpack, 4 seeds,
+ * 5 recover, 6 signed_fix, 7 reduce_mod.
+ */
+long long ks_launch_count(void);
+
+/*
+ * The plan ks_mul_ex would run, as int64 fields (n of them are written):
+ * 0 variant, 1 engine, 2 N, 3 digit bits d, 4 sub-products, 5 digits of each
+ * f-side operand, 6 digits of each g-side operand, 7 column sums per
+ * sub-product, 8 words per normalized value, 9 normalized values,
+ * 10 reconstruction digit bits M (0 for KS_1 / KS_2), 11 chain length,
+ * 12 seed coefficients, 13 output limbs, 14 input limbs, 15 workspace bytes,
+ * 16 log2 of the transform length (NTT engine, else 0), 17-20 workspace byte
+ * offsets of the digits, column sums, normalized words and seeds, 21 words
+ * per seed, 22-23 reconstruction chains of the two runs.
+ */
+int ks_plan_info(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+                 int variant, int engine, int64_t *info, int n);
+void ks_profile_enable(int on);
+int ks_profile_collect(double *ms, long long *count, int n);
+const char *ks_phase_name(int phase);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int ks_version(void);
+
+/* Releases the cached workspaces of the calling device. */
+void ks_release_cache(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KS_H */

@@ -1,0 +1,210 @@
+"""Python binding of the GB300 multipoint Kronecker-substitution library.
+
+Thin ctypes marshalling over the C ABI declared in ``include/ks.h``: every
+step of the product runs in the library's CUDA kernels.  Polynomials are
+torch tensors of shape ``(L, limbs)`` holding the uint64 limbs (dtype int64 or
+uint64; the bits are what count).  There is no CPU fallback: if ``libks.so``
+is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libks.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("paper_0712_4046_gb300: %s is not built; run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first" % _LIB_PATH)
+
+lib = ctypes.CDLL(_LIB_PATH)
+
+KS_AUTO, KS_1, KS_2, KS_3, KS_4 = 0, 1, 2, 3, 4
+ENGINE_AUTO, ENGINE_SCHOOLBOOK, ENGINE_NTT, ENGINE_TC = 0, 1, 2, 3
+KS_OK, KS_EINVAL, KS_ERANGE, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+
+_i64, _ci, _vp, _u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64
+
+
+class KSProblem(ctypes.Structure):
+    _fields_ = [("h", _vp), ("f", _vp), ("g", _vp), ("len_f", _i64), ("len_g", _i64),
+                ("coeff_bits", ctypes.c_int32), ("is_signed", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("engine", ctypes.c_int32)]
+
+
+def _sig(name, res, *args):
+    fn = getattr(lib, name)
+    fn.restype = res
+    fn.argtypes = list(args)
+    return fn
+
+
+_sig("ks_out_limbs", _ci, _i64, _i64, _ci, _ci)
+_sig("ks_eval_bits", _ci, _i64, _i64, _ci, _ci)
+_sig("ks_workspace_bytes", _i64, _i64, _i64, _ci, _ci, _ci, _ci)
+_sig("ks_mul", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
+_sig("ks_mul_ex", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp, _i64, _vp)
+_sig("ks_mul_host", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp)
+_sig("ks_mul_mod", _ci, _vp, _vp, _i64, _vp, _i64, _u64, _ci, _vp)
+_sig("ks_mul_batch", _ci, ctypes.POINTER(KSProblem), _i64, _vp)
+_sig("ks_status_sync", _ci, _vp)
+_sig("ks_choose", _ci, _i64, _i64, _ci, _ci, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
+_sig("ks_strerror", ctypes.c_char_p, _ci)
+_sig("ks_last_cuda_error", ctypes.c_char_p)
+_sig("ks_version", _ci)
+_sig("ks_release_cache", None)
+_sig("ks_launch_count", ctypes.c_longlong)
+_sig("ks_profile_enable", None, _ci)
+_sig("ks_profile_collect", _ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+     _ci)
+_sig("ks_phase_name", ctypes.c_char_p, _ci)
+_sig("ks_plan_info", _ci, _i64, _i64, _ci, _ci, _ci, _ci, ctypes.POINTER(_i64), _ci)
+
+PLAN_FIELDS = ("variant", "engine", "N", "d", "nprod", "nA", "nB", "ncols", "nwords", "nnorm",
+               "M", "chain", "nseeds", "out_limbs", "in_limbs", "workspace_bytes", "ntt_log",
+               "off_digits", "off_cols", "off_words", "off_seeds", "seed_words", "nchains0",
+               "nchains1")
+
+N_PHASES = 8
+
+
+class KSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = "%s failed: %s (%d)" % (what, lib.ks_strerror(status).decode(), status)
+        if status == KS_ECUDA or status == KS_ENOMEM:
+            msg += ": " + lib.ks_last_cuda_error().decode()
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(status: int, what: str) -> None:
+    if status != KS_OK:
+        raise KSError(status, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def out_limbs(len_f: int, len_g: int, coeff_bits: int, is_signed: bool) -> int:
+    r = lib.ks_out_limbs(len_f, len_g, coeff_bits, int(is_signed))
+    if r < 0:
+        raise KSError(r, "ks_out_limbs")
+    return r
+
+
+def eval_bits(len_f: int, len_g: int, coeff_bits: int, variant: int) -> int:
+    r = lib.ks_eval_bits(len_f, len_g, coeff_bits, variant)
+    if r < 0:
+        raise KSError(r, "ks_eval_bits")
+    return r
+
+
+def workspace_bytes(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO):
+    r = lib.ks_workspace_bytes(len_f, len_g, coeff_bits, int(is_signed), variant, engine)
+    if r < 0:
+        raise KSError(int(r), "ks_workspace_bytes")
+    return r
+
+
+def choose(len_f, len_g, coeff_bits, is_signed):
+    v, e = _ci(0), _ci(0)
+    _check(lib.ks_choose(len_f, len_g, coeff_bits, int(is_signed), ctypes.byref(v),
+                         ctypes.byref(e)), "ks_choose")
+    return v.value, e.value
+
+
+def ks_mul(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
+    """h = f * g with device tensors (L, limbs); h preallocated (Lh, out_limbs)."""
+    _check(lib.ks_mul(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
+                      int(is_signed), variant, _stream_ptr(stream)), "ks_mul")
+
+
+def ks_mul_ex(h, f, g, coeff_bits, is_signed, variant, engine, workspace, stream=None):
+    _check(lib.ks_mul_ex(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
+                         int(is_signed), variant, engine, _dptr(workspace),
+                         workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+           "ks_mul_ex")
+
+
+def ks_mul_host(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO,
+                stream=None):
+    """Host numpy uint64 arrays in and out (synchronous)."""
+    import numpy as np
+    for a in (h, f, g):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.uint64 and a.flags.c_contiguous):
+            raise ValueError("expected C-contiguous uint64 numpy arrays")
+    _check(lib.ks_mul_host(h.ctypes.data, f.ctypes.data, f.shape[0], g.ctypes.data, g.shape[0],
+                           coeff_bits, int(is_signed), variant, engine, _stream_ptr(stream)),
+           "ks_mul_host")
+
+
+def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
+    _check(lib.ks_mul_mod(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], p, variant,
+                          _stream_ptr(stream)), "ks_mul_mod")
+
+
+def ks_mul_batch(problems, stream=None):
+    """problems: list of dicts with h, f, g (tensors), coeff_bits, is_signed, variant, engine."""
+    arr = (KSProblem * len(problems))()
+    for i, q in enumerate(problems):
+        arr[i] = KSProblem(_dptr(q["h"]).value, _dptr(q["f"]).value, _dptr(q["g"]).value,
+                           q["f"].shape[0], q["g"].shape[0], q["coeff_bits"],
+                           int(q["is_signed"]), q.get("variant", KS_AUTO),
+                           q.get("engine", ENGINE_AUTO))
+    _check(lib.ks_mul_batch(arr, len(problems), _stream_ptr(stream)), "ks_mul_batch")
+
+
+def status_sync(stream=None) -> None:
+    _check(lib.ks_status_sync(_stream_ptr(stream)), "ks_status_sync")
+
+
+def mul(f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO, stream=None):
+    """Allocating convenience wrapper: returns h = f * g as a new device tensor."""
+    import torch
+    ol = out_limbs(f.shape[0], g.shape[0], coeff_bits, is_signed)
+    h = torch.empty((f.shape[0] + g.shape[0] - 1, ol), dtype=torch.int64, device=f.device)
+    if engine == ENGINE_AUTO:
+        ks_mul(h, f, g, coeff_bits, is_signed, variant, stream)
+    else:
+        ws = torch.empty(max(workspace_bytes(f.shape[0], g.shape[0], coeff_bits, is_signed,
+                                             variant, engine), 8) // 8 + 32,
+                         dtype=torch.int64, device=f.device)
+        ks_mul_ex(h, f, g, coeff_bits, is_signed, variant, engine, ws, stream)
+    return h
+
+
+def launch_count() -> int:
+    return int(lib.ks_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    lib.ks_profile_enable(int(on))
+
+
+def profile_collect() -> dict:
+    """{phase name: (total ms, records)} for the calls made since the last collect."""
+    ms = (ctypes.c_double * N_PHASES)()
+    cnt = (ctypes.c_longlong * N_PHASES)()
+    _check(lib.ks_profile_collect(ms, cnt, N_PHASES), "ks_profile_collect")
+    return {lib.ks_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES)}
+
+
+def plan_info(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO) -> dict:
+    """The plan the library would run for this problem (sizes of every stage)."""
+    arr = (_i64 * len(PLAN_FIELDS))()
+    _check(lib.ks_plan_info(len_f, len_g, coeff_bits, int(is_signed), variant, engine, arr,
+                            len(PLAN_FIELDS)), "ks_plan_info")
+    return dict(zip(PLAN_FIELDS, [int(x) for x in arr]))

@@ -1,0 +1,612 @@
+// C ABI: planning (Sec. 3.1-3.4 sizes), workspace, and the launch sequence
+//   pack -> sub-products -> normalize/combine -> unpack | seeds + recover
+//        -> signed correction -> (mod p)
+// all on the caller's stream.
+#include <atomic>
+#include <mutex>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+
+#include "ks_internal.cuh"
+
+namespace ks {
+
+int64_t norm_tiles_for(int64_t nwords);
+size_t signed_prefix_bytes(int64_t lf, int64_t lg, int ol);
+
+static thread_local char g_cuda_err[256] = "";
+
+static int cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? KS_ENOMEM : KS_ECUDA;
+}
+#define KS_CUDA(call)                        \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// ------------------------------------------------------------- accounting
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct PhaseRecord {
+  int phase;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<PhaseRecord> g_prof;
+
+PhaseTimer::PhaseTimer(cudaStream_t s_, int phase_) : s(s_), phase(phase_), ev0(nullptr) {
+  if (!g_prof_on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  ev0 = e;
+}
+PhaseTimer::~PhaseTimer() {
+  if (ev0 == nullptr) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(PhaseRecord{phase, static_cast<cudaEvent_t>(ev0), e});
+}
+
+// device-side status word (0 = fine), one per device context
+__device__ int g_status_word;
+
+static int *status_ptr() {
+  static std::mutex mu;
+  static int *ptrs[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (ptrs[dev] == nullptr) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int *>(p);
+  }
+  return ptrs[dev];
+}
+
+int ceil_log2(int64_t n) {
+  int e = 0;
+  while (((int64_t)1 << e) < n) e++;
+  return e;
+}
+
+int variant_N(int variant, int b, int e) {
+  switch (variant) {
+    case KS_1: return 2 * b + e;             // Sec. 3.1
+    case KS_2:                               // Sec. 3.3
+    case KS_3: return b + (e + 1) / 2;       // Sec. 3.2
+    case KS_4: return (2 * b + e + 3) / 4;   // Sec. 3.4
+    default: return -1;
+  }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine) {
+  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
+  if (engine != KS_ENGINE_SCHOOLBOOK) return KS_ENOTSUP;
+  if (lf > ((int64_t)1 << 40) || lg > ((int64_t)1 << 40)) return KS_ERANGE;
+  p = Plan();
+  p.variant = variant;
+  p.engine = engine;
+  p.lf = lf;
+  p.lg = lg;
+  p.lh = lf + lg - 1;
+  p.b = b;
+  p.is_signed = is_signed ? 1 : 0;
+  p.e = ceil_log2(lf < lg ? lf : lg);
+  p.N = variant_N(variant, b, p.e);
+  p.in_limbs = (b + 63) / 64;
+  p.out_limbs = (2 * b + p.e + p.is_signed + 63) / 64;
+  p.d = 16;
+  p.nprod = variant == KS_1 ? 1 : (variant == KS_4 ? 4 : 2);
+  p.nnorm = p.nprod;
+  const int64_t bitsF = (int64_t)p.N * (lf - 1) + b;
+  const int64_t bitsG = (int64_t)p.N * (lg - 1) + b;
+  p.nA = (bitsF + p.d - 1) / p.d;
+  p.nB = (bitsG + p.d - 1) / p.d;
+  p.ncols = p.nA + p.nB - 1;
+  p.nwords = (p.d * p.ncols + 95) / 32 + 1;
+  p.ntiles = norm_tiles_for(p.nwords);
+  // digit magnitude: at most `pieces` fields meet a d-bit window
+  const int64_t pieces = (b + p.d - 2) / p.N + 1;
+  const double dmax = (double)pieces * (double)((1 << p.d) - 1);
+  const double colmax = dmax * dmax * (double)(p.nA < p.nB ? p.nA : p.nB);
+  if (colmax * 2.0 >= 9.2e18) return KS_ERANGE;
+  if (engine == KS_ENGINE_SCHOOLBOOK && (double)p.nA * (double)p.nB > 1.5e11) return KS_ENOTSUP;
+  if (engine == KS_ENGINE_NTT) {
+    int lg2 = 0;
+    while (((int64_t)1 << lg2) < p.ncols) lg2++;
+    if (lg2 > 30) return KS_ERANGE;
+    if (colmax * 2.0 >= 4.0e18) return KS_ERANGE;  // CRT range of the two primes
+    p.ntt_log = lg2;
+  }
+  if (variant == KS_3 || variant == KS_4) {
+    p.M = variant == KS_3 ? p.N : 2 * p.N;
+    if ((p.M + 31) / 32 > kMaxDigitWordsM) return KS_ERANGE;
+    if (variant == KS_3) {
+      p.nruns = 1;
+      p.run_n[0] = p.lh;
+    } else {
+      p.nruns = p.lh > 1 ? 2 : 1;
+      p.run_n[0] = (p.lh + 1) / 2;
+      p.run_n[1] = p.lh / 2;
+    }
+    const int64_t nmax = p.run_n[0];
+    p.chain = p.M <= 127 ? (nmax + 8191) / 8192 : (nmax + 511) / 512;
+    const int64_t minchain = p.M <= 127 ? 32 : 64;
+    if (p.chain < minchain) p.chain = minchain;
+    p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
+    p.nseeds = 0;
+    for (int r = 0; r < p.nruns; r++) {
+      p.nchains[r] = (p.run_n[r] + p.chain - 1) / p.chain;
+      p.nseeds += 2 * (p.nchains[r] - 1);
+    }
+  }
+  // workspace layout
+  size_t off = 0;
+  p.off_digits = off;
+  off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
+  p.off_cols = off;
+  off = align256(off + (size_t)p.nprod * p.ncols * 8);
+  p.off_words = off;
+  off = align256(off + (size_t)p.nnorm * p.nwords * 4);
+  p.off_agg = off;
+  off = align256(off + (size_t)p.nnorm * p.ntiles);
+  p.off_cin = off;
+  off = align256(off + (size_t)p.nnorm * p.ntiles);
+  p.off_seeds = off;
+  off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
+  p.off_prefix = off;
+  if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.out_limbs));
+  p.off_hp = off;  // exact product for ks_mul_mod (sized by the caller)
+  p.off_ntt = off;
+  if (engine == KS_ENGINE_NTT) off = align256(off + ntt_workspace_bytes(p.ntt_log, p.nprod));
+  p.total = off;
+  return KS_OK;
+}
+
+// KS_AUTO / KS_ENGINE_AUTO
+int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine) {
+  (void)is_signed;
+  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  const int e = ceil_log2(lf < lg ? lf : lg);
+  const int64_t lh = lf + lg - 1;
+  int v = *variant;
+  if (v == KS_AUTO) v = (lh >= 64) ? KS_4 : KS_1;
+  int eng = *engine;
+  if (eng == KS_ENGINE_AUTO) {
+    const double bits1 = (double)(2 * b + e) * (double)(lf < lg ? lf : lg);
+    (void)bits1;
+    eng = KS_ENGINE_SCHOOLBOOK;
+  }
+  *variant = v;
+  *engine = eng;
+  return KS_OK;
+}
+
+// --------------------------------------------------------------- execution
+// h: exact product destination (Lh x out_limbs).  ws: workspace of >= p.total.
+static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_t *g, char *ws,
+                    cudaStream_t s) {
+  int *status = status_ptr();
+  if (status == nullptr) return KS_ECUDA;
+  int32_t *dig = reinterpret_cast<int32_t *>(ws + p.off_digits);
+  int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
+  uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
+  uint8_t *agg = reinterpret_cast<uint8_t *>(ws + p.off_agg);
+  int8_t *cin = reinterpret_cast<int8_t *>(ws + p.off_cin);
+  uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
+
+  // sub-product p: (reversed, sigma)
+  static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
+  static const int kSig[5][4] = {{1}, {1}, {1, -1}, {1, 1}, {1, -1, 1, -1}};
+  PackArgs pa{};
+  pa.nops = 2 * p.nprod;
+  pa.N = p.N;
+  pa.b = p.b;
+  pa.d = p.d;
+  pa.in_limbs = p.in_limbs;
+  pa.flip = p.is_signed;
+  Product prods[4];
+  for (int q = 0; q < p.nprod; q++) {
+    int32_t *A = dig + (int64_t)q * (p.nA + p.nB);
+    int32_t *B = A + p.nA;
+    pa.op[2 * q] = PackOp{f, p.lf, kRev[p.variant][q], kSig[p.variant][q], A, p.nA};
+    pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
+    prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
+  }
+  {
+    PhaseTimer t(s, PH_PACK);
+    KS_CUDA(launch_pack(pa, s));
+  }
+  {
+    PhaseTimer t(s, PH_PRODUCT);
+    if (p.engine == KS_ENGINE_SCHOOLBOOK) {
+      KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)p.nprod * p.ncols * 8, s));
+      KS_CUDA(launch_schoolbook(prods, p.nprod, s));
+    } else {
+      KS_CUDA(launch_ntt_products(prods, p.nprod, p.ntt_log, p.d, ws + p.off_ntt, s));
+    }
+  }
+
+  // normalized combinations
+  NormJob jobs[4];
+  auto job = [&](int i, int c1, int c2, int sigma) {
+    jobs[i].c1 = cols + (int64_t)c1 * p.ncols;
+    jobs[i].n1 = p.ncols;
+    jobs[i].c2 = c2 >= 0 ? cols + (int64_t)c2 * p.ncols : nullptr;
+    jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
+    jobs[i].sigma = sigma;
+    jobs[i].out = words + (int64_t)i * p.nwords;
+    jobs[i].agg = agg + (int64_t)i * p.ntiles;
+    jobs[i].cin = cin + (int64_t)i * p.ntiles;
+  };
+  switch (p.variant) {
+    case KS_1: job(0, 0, -1, 1); break;
+    case KS_2: job(0, 0, 1, 1); job(1, 0, 1, -1); break;        // P+ + P-, P+ - P-
+    case KS_3: job(0, 0, -1, 1); job(1, 1, -1, 1); break;       // P, R
+    case KS_4: job(0, 0, 1, 1); job(1, 0, 1, -1);               // 2E, 2X O
+               job(2, 2, 3, 1); job(3, 2, 3, -1); break;        // 2ER, 2X OR
+  }
+  {
+    PhaseTimer t(s, PH_NORMALIZE);
+    KS_CUDA(launch_normalize(jobs, p.nnorm, p.d, p.nwords, p.ntiles, s));
+  }
+  const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
+                 *V3 = words + 3 * p.nwords;
+
+  const int ol = p.out_limbs;
+  if (p.variant == KS_1) {
+    PhaseTimer t(s, PH_UNPACK);
+    KS_CUDA(launch_unpack(h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N, s));
+  } else if (p.variant == KS_2) {
+    PhaseTimer t(s, PH_UNPACK);
+    KS_CUDA(launch_unpack(h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N, s));
+  } else {
+    RecoverRun runs[2];
+    const int64_t N = p.N;
+    if (p.variant == KS_3) {
+      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
+    } else {
+      const bool odd = (p.lh & 1) == 1;
+      // even coefficients: 2E with (2ER or 2X OR); odd: 2X O with (2X OR or 2ER)
+      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
+                           p.nchains[0], seeds, 0};
+      if (p.nruns > 1)
+        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
+                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
+    }
+    {
+      PhaseTimer t(s, PH_SEEDS);
+      KS_CUDA(launch_seeds(seeds, p.seed_words, runs, p.nruns, p.chain, f, p.lf, g, p.lg, p.b,
+                           p.in_limbs, p.is_signed, s));
+    }
+    {
+      PhaseTimer t(s, PH_RECOVER);
+      KS_CUDA(launch_recover(h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words,
+                             status, s));
+    }
+  }
+  if (p.is_signed) {
+    PhaseTimer t(s, PH_SIGNED);
+    KS_CUDA(launch_signed_fix(h, ol, f, p.lf, g, p.lg, p.b, p.in_limbs,
+                              reinterpret_cast<uint64_t *>(ws + p.off_prefix), s));
+  }
+  return KS_OK;
+}
+
+// --------------------------------------------------------------- caches
+struct CacheEntry {
+  int dev;
+  cudaStream_t stream;
+  int kind;  // 0 workspace, 1 host-call buffers
+  void *ptr;
+  size_t bytes;
+};
+static std::mutex g_cache_mu;
+static std::vector<CacheEntry> g_cache;
+
+static int cached_buffer(int kind, cudaStream_t s, size_t bytes, void **out) {
+  int dev = 0;
+  KS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto &c : g_cache) {
+    if (c.dev == dev && c.stream == s && c.kind == kind) {
+      if (c.bytes >= bytes) {
+        *out = c.ptr;
+        return KS_OK;
+      }
+      KS_CUDA(cudaStreamSynchronize(s));
+      cudaFree(c.ptr);
+      c.ptr = nullptr;
+      c.bytes = 0;
+      void *p = nullptr;
+      KS_CUDA(cudaMalloc(&p, bytes));
+      c.ptr = p;
+      c.bytes = bytes;
+      *out = p;
+      return KS_OK;
+    }
+  }
+  void *p = nullptr;
+  KS_CUDA(cudaMalloc(&p, bytes < 256 ? 256 : bytes));
+  g_cache.push_back(CacheEntry{dev, s, kind, p, bytes < 256 ? 256 : bytes});
+  *out = p;
+  return KS_OK;
+}
+
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+  const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+  return x < y + nb && y < x + na;
+}
+
+static int check_args(uint64_t *h, const uint64_t *f, int64_t lf, const uint64_t *g, int64_t lg,
+                      int b, int ol) {
+  if (!h || !f || !g) return KS_EINVAL;
+  const int il = (b + 63) / 64;
+  const size_t hb = (size_t)(lf + lg - 1) * ol * 8;
+  if (overlaps(h, hb, f, (size_t)lf * il * 8) || overlaps(h, hb, g, (size_t)lg * il * 8))
+    return KS_EINVAL;
+  return KS_OK;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+int ks_version(void) { return 100; }
+
+int ks_out_limbs(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed) {
+  if (len_f < 1 || len_g < 1 || coeff_bits < 1 || coeff_bits > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  const int e = ceil_log2(len_f < len_g ? len_f : len_g);
+  return (2 * coeff_bits + e + (is_signed ? 1 : 0) + 63) / 64;
+}
+
+int ks_eval_bits(int64_t len_f, int64_t len_g, int coeff_bits, int variant) {
+  if (len_f < 1 || len_g < 1 || coeff_bits < 1 || coeff_bits > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  const int v = variant_N(variant, coeff_bits, ceil_log2(len_f < len_g ? len_f : len_g));
+  return v < 0 ? KS_EINVAL : v;
+}
+
+int ks_choose(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed, int *variant,
+              int *engine) {
+  if (!variant || !engine) return KS_EINVAL;
+  return choose(len_f, len_g, coeff_bits, is_signed, variant, engine);
+}
+
+int64_t ks_workspace_bytes(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+                           int variant, int engine) {
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  return (int64_t)p.total;
+}
+
+int ks_mul_ex(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g, int64_t len_g,
+              int coeff_bits, int is_signed, int variant, int engine, void *workspace,
+              int64_t workspace_bytes, ks_stream_t stream) {
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  rc = check_args(h, f, len_f, g, len_g, coeff_bits, p.out_limbs);
+  if (rc != KS_OK) return rc;
+  if (workspace == nullptr || workspace_bytes < (int64_t)p.total ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return KS_EINVAL;
+  return run_plan(p, h, f, g, static_cast<char *>(workspace), static_cast<cudaStream_t>(stream));
+}
+
+int ks_mul(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g, int64_t len_g,
+           int coeff_bits, int is_signed, int variant, ks_stream_t stream) {
+  int engine = KS_ENGINE_AUTO;
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  rc = check_args(h, f, len_f, g, len_g, coeff_bits, p.out_limbs);
+  if (rc != KS_OK) return rc;
+  void *ws = nullptr;
+  rc = cached_buffer(0, static_cast<cudaStream_t>(stream), p.total, &ws);
+  if (rc != KS_OK) return rc;
+  return run_plan(p, h, f, g, static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
+}
+
+int ks_mul_host(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g, int64_t len_g,
+                int coeff_bits, int is_signed, int variant, int engine, ks_stream_t stream) {
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  if (!h || !f || !g) return KS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fb = align256((size_t)len_f * p.in_limbs * 8);
+  const size_t gb = align256((size_t)len_g * p.in_limbs * 8);
+  const size_t hb = align256((size_t)p.lh * p.out_limbs * 8);
+  void *buf = nullptr;
+  rc = cached_buffer(1, s, fb + gb + hb, &buf);
+  if (rc != KS_OK) return rc;
+  void *ws = nullptr;
+  rc = cached_buffer(0, s, p.total, &ws);
+  if (rc != KS_OK) return rc;
+  char *base = static_cast<char *>(buf);
+  uint64_t *df = reinterpret_cast<uint64_t *>(base);
+  uint64_t *dg = reinterpret_cast<uint64_t *>(base + fb);
+  uint64_t *dh = reinterpret_cast<uint64_t *>(base + fb + gb);
+  KS_CUDA(cudaMemcpyAsync(df, f, (size_t)len_f * p.in_limbs * 8, cudaMemcpyHostToDevice, s));
+  KS_CUDA(cudaMemcpyAsync(dg, g, (size_t)len_g * p.in_limbs * 8, cudaMemcpyHostToDevice, s));
+  rc = run_plan(p, dh, df, dg, static_cast<char *>(ws), s);
+  if (rc != KS_OK) return rc;
+  KS_CUDA(cudaMemcpyAsync(h, dh, (size_t)p.lh * p.out_limbs * 8, cudaMemcpyDeviceToHost, s));
+  KS_CUDA(cudaStreamSynchronize(s));
+  return ks_status_sync(stream);
+}
+
+int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g, int64_t len_g,
+               uint64_t p_mod, int variant, ks_stream_t stream) {
+  if (p_mod < 2 || p_mod >= (1ull << 63)) return KS_EINVAL;
+  int b = 0;
+  while (b < 64 && ((p_mod - 1) >> b) != 0) b++;
+  if (b < 1) b = 1;
+  int engine = KS_ENGINE_AUTO;
+  int rc = choose(len_f, len_g, b, 0, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, b, 0, variant, engine);
+  if (rc != KS_OK) return rc;
+  if (!h || !f || !g) return KS_EINVAL;
+  const size_t hpb = align256((size_t)p.lh * p.out_limbs * 8);
+  void *ws = nullptr;
+  rc = cached_buffer(0, static_cast<cudaStream_t>(stream), p.total + hpb, &ws);
+  if (rc != KS_OK) return rc;
+  char *base = static_cast<char *>(ws);
+  uint64_t *hp = reinterpret_cast<uint64_t *>(base + p.total);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = run_plan(p, hp, f, g, base, s);
+  if (rc != KS_OK) return rc;
+  {
+    PhaseTimer t(s, PH_MOD);
+    KS_CUDA(launch_reduce_mod(h, hp, p.out_limbs, p.lh, p_mod, s));
+  }
+  return KS_OK;
+}
+
+int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream) {
+  if (n < 0 || (n > 0 && probs == nullptr)) return KS_EINVAL;
+  for (int64_t i = 0; i < n; i++) {
+    const ks_problem &q = probs[i];
+    int v = q.variant, eng = q.engine;
+    int rc = choose(q.len_f, q.len_g, q.coeff_bits, q.is_signed, &v, &eng);
+    if (rc != KS_OK) return rc;
+    Plan p;
+    rc = make_plan(p, q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, eng);
+    if (rc != KS_OK) return rc;
+    rc = check_args(q.h, q.f, q.len_f, q.g, q.len_g, q.coeff_bits, p.out_limbs);
+    if (rc != KS_OK) return rc;
+    void *ws = nullptr;
+    rc = cached_buffer(0, static_cast<cudaStream_t>(stream), p.total, &ws);
+    if (rc != KS_OK) return rc;
+    rc = run_plan(p, q.h, q.f, q.g, static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
+    if (rc != KS_OK) return rc;
+  }
+  return KS_OK;
+}
+
+int ks_status_sync(ks_stream_t stream) {
+  KS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int *st = status_ptr();
+  if (st == nullptr) return KS_ECUDA;
+  int v = 0;
+  KS_CUDA(cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v != 0) {
+    const int zero = 0;
+    KS_CUDA(cudaMemcpy(st, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return v == 1 ? KS_ETIMEOUT : KS_ERANGE;
+  }
+  return KS_OK;
+}
+
+const char *ks_strerror(int status) {
+  switch (status) {
+    case KS_OK: return "ok";
+    case KS_EINVAL: return "invalid argument";
+    case KS_ERANGE: return "size beyond a supported maximum, or an internal range check failed";
+    case KS_ENOMEM: return "out of memory";
+    case KS_ECUDA: return "CUDA error";
+    case KS_ETIMEOUT: return "bounded device wait timed out";
+    case KS_ENOTSUP: return "engine not supported for these sizes";
+    default: return "unknown status";
+  }
+}
+
+const char *ks_last_cuda_error(void) { return g_cuda_err; }
+
+long long ks_launch_count(void) { return g_launches.load(); }
+
+int ks_plan_info(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed, int variant,
+                 int engine, int64_t *info, int n) {
+  if (info == nullptr || n < 1) return KS_EINVAL;
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  const int64_t v[] = {p.variant, p.engine, p.N, p.d, p.nprod, p.nA, p.nB, p.ncols, p.nwords,
+                       p.nnorm, p.M, p.chain, p.nseeds, p.out_limbs, p.in_limbs,
+                       (int64_t)p.total, p.ntt_log, (int64_t)p.off_digits,
+                       (int64_t)p.off_cols, (int64_t)p.off_words, (int64_t)p.off_seeds,
+                       p.seed_words, p.nchains[0], p.nchains[1]};
+  const int m = (int)(sizeof(v) / sizeof(v[0]));
+  for (int i = 0; i < n; i++) info[i] = i < m ? v[i] : 0;
+  return KS_OK;
+}
+
+void ks_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+int ks_profile_collect(double *ms, long long *count, int n) {
+  std::vector<PhaseRecord> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  for (int i = 0; i < n; i++) {
+    if (ms) ms[i] = 0.0;
+    if (count) count[i] = 0;
+  }
+  int rc = KS_OK;
+  for (auto &r : recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) rc = KS_ECUDA;
+    float t = 0.f;
+    if (rc == KS_OK && cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) rc = KS_ECUDA;
+    if (r.phase >= 0 && r.phase < n) {
+      if (ms) ms[r.phase] += t;
+      if (count) count[r.phase] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  return rc;
+}
+
+const char *ks_phase_name(int phase) {
+  static const char *names[] = {"pack", "product", "normalize", "unpack", "seeds", "recover",
+                                "signed_fix", "reduce_mod"};
+  return (phase >= 0 && phase < PH_COUNT) ? names[phase] : nullptr;
+}
+
+void ks_release_cache(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto it = g_cache.begin(); it != g_cache.end();) {
+    if (it->dev == dev) {
+      cudaStreamSynchronize(it->stream);
+      cudaFree(it->ptr);
+      it = g_cache.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/ks.h"
+
+namespace ks {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxOperands = 8;      // 4 sub-products x 2 sides
+constexpr int kMaxSeedWords = 136;   // exact seeds: (2b + e) bits, b <= 2048
+constexpr int kMaxDigitWordsM = 72;  // reconstruction digit: M <= 2304 bits
+
+// ---------------------------------------------------------------- planning
+struct Plan {
+  int variant = 0, engine = 0;
+  int64_t lf = 0, lg = 0, lh = 0;
+  int b = 0, e = 0, N = 0, is_signed = 0, in_limbs = 0, out_limbs = 0;
+  int d = 16;           // digit bits of the sub-product operands
+  int nprod = 0;        // independent sub-products (1, 2, 2, 4)
+  int64_t nA = 0, nB = 0;  // digits of each f-side / g-side operand
+  int64_t ncols = 0;    // column sums per sub-product
+  int64_t nwords = 0;   // 32-bit words per normalized combination
+  int nnorm = 0;        // normalized combinations (1, 2, 2, 4)
+  // reconstruction (Sec. 3.2; run twice for Sec. 3.4)
+  int M = 0;            // digit bits: N (KS3) or 2N (KS4)
+  int nruns = 0;
+  int64_t run_n[2] = {0, 0};
+  int64_t chain = 0;
+  int64_t nchains[2] = {0, 0};
+  int seed_words = 0;
+  int64_t nseeds = 0;
+  // number-theoretic-transform engine
+  int ntt_log = 0;      // transform length 2^ntt_log
+  // workspace layout (byte offsets from the base)
+  size_t off_digits = 0, off_cols = 0, off_words = 0, off_agg = 0, off_cin = 0;
+  size_t off_seeds = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
+  size_t total = 0;
+  int64_t ntiles = 0;   // scan tiles per normalized combination
+};
+
+int ceil_log2(int64_t n);
+int variant_N(int variant, int b, int e);
+// Fills `p` (layout included) for an explicit variant and engine; KS_OK or error.
+int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant,
+              int engine);
+int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine);
+
+// ---------------------------------------------------------------- kernels
+struct PackOp {
+  const uint64_t *poly;
+  int64_t L;
+  int reversed;  // coefficient t of the evaluated polynomial is poly[L-1-t]
+  int sigma;     // +1: f(X); -1: f(-X) (odd coefficients negated)
+  int32_t *out;
+  int64_t ndig;
+};
+
+struct PackArgs {
+  PackOp op[kMaxOperands];
+  int nops;
+  int N, b, d, in_limbs, flip;
+};
+
+// Signed digits of each evaluation (Sec. 3.1-3.4 evaluations at +-2^N and
+// the reversed polynomial), `d` bits per digit position.
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
+
+struct Product {
+  const int32_t *A;
+  int64_t nA;
+  const int32_t *B;
+  int64_t nB;
+  int64_t *C;  // nA + nB - 1 column sums, accumulated atomically (zero first)
+};
+
+cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s);
+
+// NTT engine: column sums of each product by a two-prime transform + CRT.
+size_t ntt_workspace_bytes(int log_n, int nprod);
+cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d,
+                                void *scratch, cudaStream_t s);
+
+struct NormJob {
+  const int64_t *c1;
+  int64_t n1;
+  const int64_t *c2;  // may be null
+  int64_t n2;
+  int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k)
+  uint32_t *out;
+  uint8_t *agg;       // per scan tile
+  int8_t *cin;        // per scan tile
+};
+
+// Normalizes up to 4 column-sum combinations into two's complement words.
+cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
+                             int64_t ntiles, cudaStream_t s);
+
+// KS1 / KS2 unpack: h'_k = bits [off + kN, off + kN + width) of V (k even) or
+// V_odd (k odd).
+cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
+                          const uint32_t *V_odd, int64_t nwords, int64_t off,
+                          int64_t N, int width, cudaStream_t s);
+
+struct RecoverRun {
+  const uint32_t *Vf;
+  int64_t off_f;
+  const uint32_t *Vr;
+  int64_t off_r;
+  int64_t n;           // coefficients in this run
+  int64_t kbase, kstride;  // h index of run coefficient i: kbase + kstride * i
+  int64_t nchains;
+  const uint32_t *seeds;   // 2 values per chain c >= 1 (seed_words words each)
+  int64_t seed_base;       // index of this run's first seed value
+};
+
+// Exact coefficients h'_k (biased, unsigned) for the chain starts.
+cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs,
+                         int nruns, int64_t chain, const uint64_t *f, int64_t lf,
+                         const uint64_t *g, int64_t lg, int b, int in_limbs,
+                         int flip, cudaStream_t s);
+
+cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
+                           int64_t nwords, int M, int64_t chain, int seed_words,
+                           int *status, cudaStream_t s);
+
+// Signed inputs: h_k = h'_k - 2^(b-1) (W_f,k + W_g,k) - 2^(2b-2) cnt_k mod 2^(64 ol).
+cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                              const uint64_t *g, int64_t lg, int b, int in_limbs,
+                              uint64_t *prefix, cudaStream_t s);
+
+// (Z/pZ)[x]: out_k = h'_k mod p.
+cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh,
+                              uint64_t p, cudaStream_t s);
+
+// ---------------------------------------------------------------- accounting
+// Kernel launches issued by the library (host counter), and optional per-phase
+// CUDA-event timing on the caller's stream.
+void note_launches(int n);
+enum Phase { PH_PACK = 0, PH_PRODUCT, PH_NORMALIZE, PH_UNPACK, PH_SEEDS, PH_RECOVER, PH_SIGNED,
+             PH_MOD, PH_COUNT };
+struct PhaseTimer {
+  cudaStream_t s;
+  int phase;
+  void *ev0;
+  PhaseTimer(cudaStream_t s_, int phase_);
+  ~PhaseTimer();
+};
+
+// ---------------------------------------------------------------- device helpers
+// bits [pos, pos + 64) of a little-endian word array; words >= n read as 0.
+__device__ __forceinline__ uint64_t get_bits64(const uint32_t *w, int64_t n, int64_t pos) {
+  int64_t i = pos >> 5;
+  int sh = (int)(pos & 31);
+  uint64_t w0 = (i >= 0 && i < n) ? w[i] : 0u;
+  uint64_t w1 = (i + 1 >= 0 && i + 1 < n) ? w[i + 1] : 0u;
+  uint64_t w2 = (i + 2 >= 0 && i + 2 < n) ? w[i + 2] : 0u;
+  uint64_t lo = w0 | (w1 << 32);
+  if (sh == 0) return lo;
+  return (lo >> sh) | (w2 << (64 - sh));
+}
+
+// Bits [x, x + len) (len <= 32, x >= 0) of a coefficient reduced to its low
+// b bits, with bit b-1 flipped when `flip` (the signed bias of 2^(b-1)).
+__device__ __forceinline__ uint32_t coeff_slice(const uint64_t *c, int in_limbs, int b,
+                                                int flip, int x, int len) {
+  if (x >= b) return 0u;
+  int li = x >> 6, sh = x & 63;
+  uint64_t lo = c[li];
+  uint64_t hi = (li + 1 < in_limbs) ? c[li + 1] : 0ull;
+  uint64_t v = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+  int keep = b - x;
+  if (keep < 64) v &= (1ull << keep) - 1ull;
+  if (flip) {
+    int fb = b - 1 - x;
+    if (fb < 64) v ^= 1ull << fb;
+  }
+  return (uint32_t)(v & ((1ull << len) - 1ull));
+}
+
+}  // namespace ks

@@ -1,0 +1,696 @@
+// Unpack (Sec. 3.1, 3.3), reciprocal reconstruction (Sec. 3.2, used twice by
+// Sec. 3.4), the signed-bias correction and the reduction mod p (Sec. 4).
+#include "ks_internal.cuh"
+
+namespace ks {
+
+// ------------------------------------------------------------------ unpack
+// h'_k = bits [off + kN, off + kN + width) of V (or of V_odd for odd k).
+// KS1: V = h(2^N), off = 0, width N.  KS2: V = P+ + P- = 2 h0(X^2) and
+// V_odd = P+ - P- = 2X h1(X^2); then both even and odd coefficients sit at
+// bit 1 + kN, width 2N (Sec. 3.3).
+__global__ void __launch_bounds__(256) unpack_kernel(uint64_t *h, int ol, int64_t lh,
+                                                     const uint32_t *V, const uint32_t *V_odd,
+                                                     int64_t nwords, int64_t off, int64_t N,
+                                                     int width) {
+  const int64_t total = lh * ol;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx / ol;
+    const int l = (int)(idx - k * ol);
+    const uint32_t *src = (V_odd != nullptr && (k & 1)) ? V_odd : V;
+    const int rem = width - 64 * l;
+    uint64_t v = 0;
+    if (rem > 0) {
+      v = get_bits64(src, nwords, off + k * N + 64 * (int64_t)l);
+      if (rem < 64) v &= (1ull << rem) - 1ull;
+    }
+    h[idx] = v;
+  }
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)b;
+}
+
+cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
+                          const uint32_t *V_odd, int64_t nwords, int64_t off, int64_t N,
+                          int width, cudaStream_t s) {
+  unpack_kernel<<<grid_for(lh * ol, 256), 256, 0, s>>>(h, ol, lh, V, V_odd, nwords, off, N,
+                                                       width);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ seeds
+// Exact h'_k = sum_t f'_t g'_(k-t) (biased, non-negative b-bit inputs) for the
+// chain starts of the reconstruction: one CTA per coefficient.  Each thread
+// multiplies its terms word by word and keeps 64-bit per-word sums; the CTA
+// adds those into shared 64-bit word sums and one thread propagates carries.
+namespace {
+constexpr int kSeedThreads = 128;
+constexpr int kMaxInWords = 64;  // b <= 2048
+struct SeedArgs {
+  RecoverRun run[2];
+  int nruns;
+  int64_t chain;
+};
+}  // namespace
+
+__device__ __forceinline__ int coeff_words(const uint64_t *c, int in_limbs, int b, int flip,
+                                           uint32_t *w) {
+  const int nw = (b + 31) / 32;
+  for (int i = 0; i < nw; i++) {
+    const int len = (b - 32 * i) < 32 ? (b - 32 * i) : 32;
+    w[i] = coeff_slice(c, in_limbs, b, flip, 32 * i, len);
+  }
+  return nw;
+}
+
+__global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int seed_words,
+                                                            SeedArgs a, const uint64_t *f,
+                                                            int64_t lf, const uint64_t *g,
+                                                            int64_t lg, int b, int in_limbs,
+                                                            int flip) {
+  __shared__ unsigned long long colsum[kMaxSeedWords];
+  // which seed: runs in order, chains c >= 1, values (c*chain - 1, c*chain)
+  int64_t sid = blockIdx.x;
+  int r = 0;
+  int64_t per_run = 2 * (a.run[0].nchains - 1);
+  while (r + 1 < a.nruns && sid >= per_run) {
+    sid -= per_run;
+    r++;
+    per_run = 2 * (a.run[r].nchains - 1);
+  }
+  const RecoverRun &R = a.run[r];
+  const int64_t c = sid / 2 + 1;
+  const int64_t i = c * a.chain - 1 + (sid & 1);
+  const int64_t k = R.kbase + R.kstride * i;
+  for (int w = threadIdx.x; w < seed_words; w += blockDim.x) colsum[w] = 0ull;
+  __syncthreads();
+
+  unsigned long long loc[2 * kMaxInWords + 2];
+  const int nw = (b + 31) / 32;
+  for (int w = 0; w < 2 * nw + 1; w++) loc[w] = 0ull;
+  int64_t t_lo = k - (lg - 1);
+  if (t_lo < 0) t_lo = 0;
+  const int64_t t_hi = k < lf - 1 ? k : lf - 1;
+  uint32_t fw[kMaxInWords], gw[kMaxInWords], pr[2 * kMaxInWords];
+  for (int64_t t = t_lo + threadIdx.x; t <= t_hi; t += blockDim.x) {
+    coeff_words(f + t * in_limbs, in_limbs, b, flip, fw);
+    coeff_words(g + (k - t) * in_limbs, in_limbs, b, flip, gw);
+    for (int w = 0; w < 2 * nw; w++) pr[w] = 0u;
+    for (int x = 0; x < nw; x++) {
+      uint64_t carry = 0;
+      for (int y = 0; y < nw; y++) {
+        const uint64_t tt = (uint64_t)fw[x] * gw[y] + pr[x + y] + carry;
+        pr[x + y] = (uint32_t)tt;
+        carry = tt >> 32;
+      }
+      pr[x + nw] = (uint32_t)carry;
+    }
+    for (int w = 0; w < 2 * nw; w++) loc[w] += pr[w];
+  }
+  for (int w = 0; w < 2 * nw && w < seed_words; w++)
+    if (loc[w]) atomicAdd(&colsum[w], loc[w]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t *out = seeds + (R.seed_base + sid) * seed_words;
+    unsigned long long carry = 0;
+    for (int w = 0; w < seed_words; w++) {
+      const unsigned long long v = colsum[w] + carry;
+      out[w] = (uint32_t)v;
+      carry = v >> 32;
+    }
+  }
+}
+
+cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs, int nruns,
+                         int64_t chain, const uint64_t *f, int64_t lf, const uint64_t *g,
+                         int64_t lg, int b, int in_limbs, int flip, cudaStream_t s) {
+  SeedArgs a{};
+  int64_t n = 0;
+  for (int r = 0; r < nruns; r++) {
+    a.run[r] = runs[r];
+    n += 2 * (runs[r].nchains - 1);
+  }
+  a.nruns = nruns;
+  a.chain = chain;
+  if (n == 0) return cudaSuccess;
+  if (seed_words > kMaxSeedWords || (b + 31) / 32 > kMaxInWords) return cudaErrorInvalidValue;
+  seed_kernel<<<(unsigned)n, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b,
+                                                   in_limbs, flip);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ recover
+// Sec. 3.2: from the base-X digits u_i of fwd = sum c_i X^i and w_i of
+// rev = sum c_(n-1-i) X^i (fwd = sum_{i<=n} u_i X^i, rev = sum_{i<=n}
+// w_(n-i) X^i), with c_i = alpha_i + X beta_i, 0 <= alpha_i < X,
+// 0 <= beta_i < X - 1, run for j = 0 .. n-2:
+//
+//   eps_j       = [alpha_j > w_(j+1)]
+//   beta_j      = w_j - alpha_(j-1) - eps_j            (mod X)
+//   alpha_(j+1) = u_(j+1) - beta_j - delta_j           (mod X)
+//   delta_(j+1) = (beta_j + alpha_(j+1) + delta_j - u_(j+1)) / X  in {0, 1}
+//
+// and finally beta_(n-1) = w_(n-1) - alpha_(n-2) (mod X).  The recurrence is
+// sequential; chains of `chain` steps run in parallel, chain c starting at
+// s = c * chain from the exact seeds h'_(s-1), h'_s: alpha_(s-1), alpha_s,
+// beta_(s-1) follow directly, and delta_(s-1) = u_s - beta_(s-1) - alpha_s
+// (mod X, necessarily 0 or 1) gives delta_s = (beta_(s-1) + alpha_s +
+// delta_(s-1) - u_s) / X.
+namespace {
+struct RecoverArgs {
+  RecoverRun run[2];
+  int nruns;
+  int64_t nwords;
+  int M;
+  int64_t chain;
+  int seed_words;
+};
+
+// digit arithmetic on W 32-bit words, values in [0, 2^M)
+struct Dig {
+  uint32_t w[kMaxDigitWordsM];
+};
+
+__device__ __forceinline__ void dig_load(Dig &x, const uint32_t *V, int64_t nwords, int64_t pos,
+                                         int M) {
+  const int W = (M + 31) / 32;
+  for (int i = 0; i < W; i += 2) {
+    const uint64_t v = get_bits64(V, nwords, pos + 32 * (int64_t)i);
+    x.w[i] = (uint32_t)v;
+    if (i + 1 < W) x.w[i + 1] = (uint32_t)(v >> 32);
+  }
+  const int top = M - 32 * (W - 1);
+  if (top < 32) x.w[W - 1] &= (1u << top) - 1u;
+}
+__device__ __forceinline__ void dig_load_local(Dig &x, const uint32_t *src, int nsrc, int pos,
+                                               int M) {
+  const int W = (M + 31) / 32;
+  for (int i = 0; i < W; i += 2) {
+    const uint64_t v = get_bits64(src, nsrc, pos + 32 * (int64_t)i);
+    x.w[i] = (uint32_t)v;
+    if (i + 1 < W) x.w[i + 1] = (uint32_t)(v >> 32);
+  }
+  const int top = M - 32 * (W - 1);
+  if (top < 32) x.w[W - 1] &= (1u << top) - 1u;
+}
+__device__ __forceinline__ bool dig_gt(const Dig &a, const Dig &b, int W) {
+  for (int i = W - 1; i >= 0; i--)
+    if (a.w[i] != b.w[i]) return a.w[i] > b.w[i];
+  return false;
+}
+// r = (a - b - c) mod 2^M
+__device__ __forceinline__ void dig_sub(Dig &r, const Dig &a, const Dig &b, uint32_t c, int M) {
+  const int W = (M + 31) / 32;
+  int64_t borrow = c;
+  for (int i = 0; i < W; i++) {
+    const int64_t t = (int64_t)a.w[i] - b.w[i] - borrow;
+    r.w[i] = (uint32_t)t;
+    borrow = t < 0 ? 1 : 0;
+  }
+  const int top = M - 32 * (W - 1);
+  if (top < 32) r.w[W - 1] &= (1u << top) - 1u;
+}
+// floor((a + b + c) / 2^M) for a, b < 2^M, c in {0, 1}
+__device__ __forceinline__ uint32_t dig_add_carry(const Dig &a, const Dig &b, uint32_t c, int M) {
+  const int W = (M + 31) / 32;
+  uint64_t carry = c;
+  uint32_t topw = 0;
+  for (int i = 0; i < W; i++) {
+    const uint64_t t = (uint64_t)a.w[i] + b.w[i] + carry;
+    topw = (uint32_t)t;
+    carry = t >> 32;
+  }
+  const int top = M - 32 * (W - 1);
+  if (top == 32) return (uint32_t)carry;
+  return (topw >> top) & 1u;
+}
+// out limbs of alpha + 2^M beta
+__device__ void write_coeff(uint64_t *out, int ol, const Dig &al, const Dig &be, int M) {
+  const int W = (M + 31) / 32;
+  for (int l = 0; l < ol; l++) {
+    uint64_t v = 0;
+    for (int half = 0; half < 2; half++) {
+      const int64_t p0 = 64 * (int64_t)l + 32 * half;  // bit position of this 32-bit chunk
+      uint64_t chunk = 0;
+      // from alpha: bits [p0, p0+32) below M
+      if (p0 < M) {
+        const int wi = (int)(p0 >> 5);
+        uint32_t x = al.w[wi];
+        chunk |= x;  // alpha's bits above M are zero
+      }
+      // from beta: bits [p0 - M, p0 - M + 32)
+      const int64_t q = p0 - M;
+      if (q + 32 > 0 && q < (int64_t)32 * W) {
+        const int64_t wi = q >= 0 ? (q >> 5) : -1;
+        const int sh = (int)(q & 31);
+        const uint64_t lo = (wi >= 0 && wi < W) ? be.w[wi] : 0u;
+        const uint64_t hi = (wi + 1 >= 0 && wi + 1 < W) ? be.w[wi + 1] : 0u;
+        const uint64_t pair = lo | (hi << 32);
+        uint32_t part;
+        if (q >= 0)
+          part = (uint32_t)(pair >> sh);
+        else
+          part = (uint32_t)(((uint64_t)be.w[0]) << (int)(-q));  // -q < 32
+        chunk |= part;
+      }
+      v |= (chunk & 0xffffffffull) << (32 * half);
+    }
+    out[l] = v;
+  }
+}
+}  // namespace
+
+// Digits of at most 63 bits live in one 64-bit register; digits of 64..127
+// bits in a pair of 64-bit limbs (D2) with explicit carries.
+__device__ __forceinline__ uint64_t load_d1(const uint32_t *V, int64_t nwords, int64_t pos, int M) {
+  return get_bits64(V, nwords, pos) & ((1ull << M) - 1ull);
+}
+struct D2 {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ uint64_t hi_mask(int M) {  // 64 <= M <= 127
+  return (M - 64 == 64) ? ~0ull : ((1ull << (M - 64)) - 1ull);
+}
+__device__ __forceinline__ D2 load_d2(const uint32_t *V, int64_t nwords, int64_t pos, int M) {
+  D2 r;
+  r.lo = get_bits64(V, nwords, pos);
+  r.hi = get_bits64(V, nwords, pos + 64) & hi_mask(M);
+  return r;
+}
+// (a - b - c) mod 2^M, c in {0, 1}
+__device__ __forceinline__ D2 sub_d2(D2 a, D2 b, uint64_t c, int M) {
+  D2 r;
+  const uint64_t t = a.lo - b.lo;
+  const uint64_t bw1 = a.lo < b.lo;
+  r.lo = t - c;
+  const uint64_t bw2 = t < c;
+  r.hi = (a.hi - b.hi - bw1 - bw2) & hi_mask(M);
+  return r;
+}
+// floor((a + b + c) / 2^M) for a, b < 2^M, c in {0, 1}
+__device__ __forceinline__ uint64_t carry_d2(D2 a, D2 b, uint64_t c, int M) {
+  const uint64_t s1 = a.lo + b.lo;
+  const uint64_t c1 = s1 < a.lo;
+  const uint64_t s2 = s1 + c;
+  const uint64_t c2 = s2 < s1;
+  const uint64_t hs = a.hi + b.hi + c1 + c2;  // < 2^(M-63) <= 2^64
+  return (hs >> (M - 64)) & 1ull;
+}
+__device__ __forceinline__ bool gt_d2(D2 a, D2 b) {
+  return a.hi != b.hi ? a.hi > b.hi : a.lo > b.lo;
+}
+// out limbs of alpha + 2^M beta, alpha, beta < 2^M
+__device__ __forceinline__ void write_h1(uint64_t *out, int ol, uint64_t a, uint64_t be, int M) {
+  out[0] = a | (be << M);
+  if (ol > 1) out[1] = be >> (64 - M);
+  for (int l = 2; l < ol; l++) out[l] = 0;
+}
+__device__ __forceinline__ void write_h2(uint64_t *out, int ol, D2 a, D2 be, int M) {
+  uint64_t s[5] = {a.lo, a.hi, 0, 0, 0};
+  const int r = M & 63;  // beta starts in limb 1 (64 <= M < 128)
+  s[1] |= be.lo << r;
+  s[2] |= (r ? (be.lo >> (64 - r)) : 0ull) | (be.hi << r);
+  s[3] |= r ? (be.hi >> (64 - r)) : 0ull;
+  for (int l = 0; l < ol; l++) out[l] = l < 5 ? s[l] : 0ull;
+}
+
+__device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, int &r) {
+  r = 0;
+  while (r < a.nruns && gid >= a.run[r].nchains) {
+    gid -= a.run[r].nchains;
+    r++;
+  }
+  return r < a.nruns;
+}
+
+// M <= 63
+__global__ void __launch_bounds__(128) recover_kernel1(uint64_t *h, int ol, RecoverArgs a,
+                                                       int *status) {
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int r;
+  if (!chain_index(a, gid, r)) return;
+  const RecoverRun &R = a.run[r];
+  const int M = a.M;
+  const uint64_t mask = (1ull << M) - 1ull;
+  const int64_t n = R.n;
+  const int64_t s = gid * a.chain;
+  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
+  uint64_t a_prev, a_cur, delta;
+  if (s == 0) {
+    a_prev = 0;
+    a_cur = load_d1(R.Vf, a.nwords, R.off_f, M);
+    delta = 0;
+  } else {
+    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
+    a_prev = load_d1(sd, a.seed_words, 0, M);
+    const uint64_t b_prev = load_d1(sd, a.seed_words, M, M);
+    a_cur = load_d1(sd + a.seed_words, a.seed_words, 0, M);
+    const uint64_t us = load_d1(R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
+    const uint64_t dprev = (us - b_prev - a_cur) & mask;
+    if (dprev > 1) atomicExch(status, 2);
+    delta = (b_prev + a_cur + dprev - us) >> M;
+  }
+  uint64_t w_cur = load_d1(R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
+  for (int64_t j = s; j < e; j++) {
+    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
+    if (j <= n - 2) {
+      const uint64_t w_next = load_d1(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+      const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
+      const uint64_t beta = (w_cur - a_prev - eps) & mask;
+      const uint64_t u_next = load_d1(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      const uint64_t a_next = (u_next - beta - delta) & mask;
+      const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
+      if (dnext > 1) atomicExch(status, 2);
+      write_h1(out, ol, a_cur, beta, M);
+      a_prev = a_cur;
+      a_cur = a_next;
+      delta = dnext;
+      w_cur = w_next;
+    } else {
+      write_h1(out, ol, a_cur, (w_cur - a_prev) & mask, M);
+    }
+  }
+}
+
+// 64 <= M <= 127
+__global__ void __launch_bounds__(128) recover_kernel2(uint64_t *h, int ol, RecoverArgs a,
+                                                       int *status) {
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int r;
+  if (!chain_index(a, gid, r)) return;
+  const RecoverRun &R = a.run[r];
+  const int M = a.M;
+  const int64_t n = R.n;
+  const int64_t s = gid * a.chain;
+  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
+  const D2 zero = {0ull, 0ull};
+  D2 a_prev, a_cur;
+  uint64_t delta;
+  if (s == 0) {
+    a_prev = zero;
+    a_cur = load_d2(R.Vf, a.nwords, R.off_f, M);
+    delta = 0;
+  } else {
+    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
+    a_prev = load_d2(sd, a.seed_words, 0, M);
+    const D2 b_prev = load_d2(sd, a.seed_words, M, M);
+    a_cur = load_d2(sd + a.seed_words, a.seed_words, 0, M);
+    const D2 us = load_d2(R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
+    const D2 dprev = sub_d2(sub_d2(us, b_prev, 0, M), a_cur, 0, M);
+    if (dprev.hi != 0 || dprev.lo > 1) atomicExch(status, 2);
+    delta = carry_d2(b_prev, a_cur, dprev.lo & 1ull, M);
+  }
+  D2 w_cur = load_d2(R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
+  for (int64_t j = s; j < e; j++) {
+    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
+    if (j <= n - 2) {
+      const D2 w_next = load_d2(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+      const uint64_t eps = gt_d2(a_cur, w_next) ? 1ull : 0ull;
+      const D2 beta = sub_d2(sub_d2(w_cur, a_prev, 0, M), zero, eps, M);
+      const D2 u_next = load_d2(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      const D2 a_next = sub_d2(sub_d2(u_next, beta, 0, M), zero, delta, M);
+      const uint64_t dnext = carry_d2(beta, a_next, delta, M);
+      write_h2(out, ol, a_cur, beta, M);
+      a_prev = a_cur;
+      a_cur = a_next;
+      delta = dnext;
+      w_cur = w_next;
+    } else {
+      write_h2(out, ol, a_cur, sub_d2(w_cur, a_prev, 0, M), M);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(64) recover_wide(uint64_t *h, int ol, RecoverArgs a,
+                                                   int *status) {
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = 0;
+  while (r < a.nruns && gid >= a.run[r].nchains) {
+    gid -= a.run[r].nchains;
+    r++;
+  }
+  if (r >= a.nruns) return;
+  const RecoverRun &R = a.run[r];
+  const int M = a.M;
+  const int W = (M + 31) / 32;
+  const int64_t n = R.n;
+  const int64_t s = gid * a.chain;
+  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
+  Dig a_prev, a_cur, delta_d, w_cur, w_next, u_next, beta, a_next, zero;
+  for (int i = 0; i < W; i++) zero.w[i] = 0;
+  uint32_t delta;
+  if (s == 0) {
+    a_prev = zero;
+    dig_load(a_cur, R.Vf, a.nwords, R.off_f, M);
+    delta = 0;
+  } else {
+    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
+    Dig b_prev, us, dp;
+    dig_load_local(a_prev, sd, a.seed_words, 0, M);
+    dig_load_local(b_prev, sd, a.seed_words, M, M);
+    dig_load_local(a_cur, sd + a.seed_words, a.seed_words, 0, M);
+    dig_load(us, R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
+    Dig t1;
+    dig_sub(t1, us, b_prev, 0, M);
+    dig_sub(dp, t1, a_cur, 0, M);
+    bool ok = dp.w[0] <= 1;
+    for (int i = 1; i < W; i++) ok = ok && dp.w[i] == 0;
+    if (!ok) atomicExch(status, 2);
+    delta = dig_add_carry(b_prev, a_cur, dp.w[0] & 1u, M);
+  }
+  (void)delta_d;
+  dig_load(w_cur, R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
+  for (int64_t j = s; j < e; j++) {
+    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
+    if (j <= n - 2) {
+      dig_load(w_next, R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+      const uint32_t eps = dig_gt(a_cur, w_next, W) ? 1u : 0u;
+      dig_sub(beta, w_cur, a_prev, eps, M);
+      dig_load(u_next, R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      dig_sub(a_next, u_next, beta, delta, M);
+      const uint32_t dnext = dig_add_carry(beta, a_next, delta, M);
+      write_coeff(out, ol, a_cur, beta, M);
+      a_prev = a_cur;
+      a_cur = a_next;
+      delta = dnext;
+      w_cur = w_next;
+    } else {
+      dig_sub(beta, w_cur, a_prev, 0, M);
+      write_coeff(out, ol, a_cur, beta, M);
+    }
+  }
+}
+
+cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
+                           int64_t nwords, int M, int64_t chain, int seed_words, int *status,
+                           cudaStream_t s) {
+  RecoverArgs a{};
+  int64_t total = 0;
+  for (int r = 0; r < nruns; r++) {
+    a.run[r] = runs[r];
+    total += runs[r].nchains;
+  }
+  a.nruns = nruns;
+  a.nwords = nwords;
+  a.M = M;
+  a.chain = chain;
+  a.seed_words = seed_words;
+  if (total == 0) return cudaSuccess;
+  note_launches(1);
+  if (M <= 63) {
+    recover_kernel1<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(h, ol, a, status);
+  } else if (M <= 127) {
+    recover_kernel2<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(h, ol, a, status);
+  } else {
+    if ((M + 31) / 32 > kMaxDigitWordsM) return cudaErrorInvalidValue;
+    recover_wide<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(h, ol, a, status);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ signed
+// The signed bias: f'_t = f_t + c, c = 2^(b-1), and likewise g', so
+//   f g = f' g' - c (f * U_g + U_f * g) - c^2 U_f * U_g,
+// U the all-ones polynomials.  (f * U_g)_k is the window sum of f_t over
+// t in [max(0, k - Lg + 1), min(k, Lf - 1)], a difference of prefix sums.
+// Everything is computed mod 2^(64 ol), which is exact because the final
+// coefficient fits ol limbs of two's complement.
+namespace {
+constexpr int kPrefThreads = 256;
+constexpr int kMaxOl = 72;
+}
+
+__device__ __forceinline__ void add_sext(uint64_t *acc, const uint64_t *x, int in_limbs, int ol) {
+  const uint64_t ext = (x[in_limbs - 1] >> 63) ? ~0ull : 0ull;
+  uint64_t carry = 0;
+  for (int l = 0; l < ol; l++) {
+    const uint64_t v = l < in_limbs ? x[l] : ext;
+    const uint64_t s1 = acc[l] + v;
+    const uint64_t c1 = s1 < v;
+    const uint64_t s2 = s1 + carry;
+    const uint64_t c2 = s2 < carry;
+    acc[l] = s2;
+    carry = c1 | c2;
+  }
+}
+
+// blockIdx.x = 0: prefix sums of f; 1: of g.  prefix rows are ol limbs.
+__global__ void __launch_bounds__(kPrefThreads) prefix_kernel(const uint64_t *f, int64_t lf,
+                                                              const uint64_t *g, int64_t lg,
+                                                              int in_limbs, int ol,
+                                                              uint64_t *pf, uint64_t *pg,
+                                                              uint64_t *offs) {
+  const uint64_t *x = blockIdx.x == 0 ? f : g;
+  const int64_t L = blockIdx.x == 0 ? lf : lg;
+  uint64_t *P = blockIdx.x == 0 ? pf : pg;
+  uint64_t *O = offs + (int64_t)blockIdx.x * kPrefThreads * ol;
+  const int64_t per = (L + kPrefThreads - 1) / kPrefThreads;
+  const int64_t t0 = threadIdx.x * per;
+  const int64_t t1 = (t0 + per < L) ? t0 + per : L;
+  uint64_t acc[kMaxOl];
+  for (int l = 0; l < ol; l++) acc[l] = 0;
+  for (int64_t t = t0; t < t1; t++) {
+    add_sext(acc, x + t * in_limbs, in_limbs, ol);
+    for (int l = 0; l < ol; l++) P[t * ol + l] = acc[l];
+  }
+  for (int l = 0; l < ol; l++) O[threadIdx.x * ol + l] = acc[l];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run[kMaxOl];
+    for (int l = 0; l < ol; l++) run[l] = 0;
+    for (int t = 0; t < kPrefThreads; t++) {
+      uint64_t tot[kMaxOl];
+      for (int l = 0; l < ol; l++) tot[l] = O[t * ol + l];
+      for (int l = 0; l < ol; l++) O[t * ol + l] = run[l];
+      uint64_t carry = 0;
+      for (int l = 0; l < ol; l++) {
+        const uint64_t s1 = run[l] + tot[l];
+        const uint64_t c1 = s1 < tot[l];
+        const uint64_t s2 = s1 + carry;
+        carry = c1 | (s2 < carry);
+        run[l] = s2;
+      }
+    }
+  }
+  __syncthreads();
+  for (int l = 0; l < ol; l++) acc[l] = O[threadIdx.x * ol + l];
+  for (int64_t t = t0; t < t1; t++) {
+    uint64_t carry = 0;
+    for (int l = 0; l < ol; l++) {
+      const uint64_t v = P[t * ol + l];
+      const uint64_t s1 = v + acc[l];
+      const uint64_t c1 = s1 < acc[l];
+      const uint64_t s2 = s1 + carry;
+      carry = c1 | (s2 < carry);
+      P[t * ol + l] = s2;
+    }
+  }
+}
+
+// r = r - (x << sh)  mod 2^(64 ol)
+__device__ __forceinline__ void sub_shifted(uint64_t *r, const uint64_t *x, int ol, int sh) {
+  const int q = sh >> 6, rr = sh & 63;
+  uint64_t borrow = 0;
+  for (int l = 0; l < ol; l++) {
+    const int a = l - q;
+    uint64_t v = 0;
+    if (a >= 0 && a < ol) v = x[a] << rr;
+    if (rr && a - 1 >= 0 && a - 1 < ol) v |= x[a - 1] >> (64 - rr);
+    const uint64_t d1 = r[l] - v;
+    const uint64_t b1 = r[l] < v;
+    const uint64_t d2 = d1 - borrow;
+    const uint64_t b2 = d1 < borrow;
+    r[l] = d2;
+    borrow = b1 | b2;
+  }
+}
+
+__global__ void __launch_bounds__(128) signed_fix_kernel(uint64_t *h, int ol, int64_t lf,
+                                                         int64_t lg, int b, const uint64_t *pf,
+                                                         const uint64_t *pg) {
+  const int64_t lh = lf + lg - 1;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lh;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t w[kMaxOl], tmp[kMaxOl];
+    // W_f + W_g, each a difference of prefix sums
+    const int64_t fhi = k < lf - 1 ? k : lf - 1;
+    const int64_t ghi = k < lg - 1 ? k : lg - 1;
+    for (int l = 0; l < ol; l++) w[l] = pf[fhi * ol + l];
+    if (k - lg >= 0) sub_shifted(w, pf + (k - lg) * ol, ol, 0);
+    for (int l = 0; l < ol; l++) tmp[l] = 0;
+    sub_shifted(tmp, pg + ghi * ol, ol, 0);          // tmp = -S_g(ghi)
+    if (k - lf >= 0) {
+      uint64_t neg[kMaxOl];
+      for (int l = 0; l < ol; l++) neg[l] = 0;
+      sub_shifted(neg, pg + (k - lf) * ol, ol, 0);   // -S_g(k - lf)
+      sub_shifted(tmp, neg, ol, 0);                  // tmp = -(W_g)
+    }
+    sub_shifted(w, tmp, ol, 0);                      // w = W_f + W_g
+    uint64_t *hk = h + k * ol;
+    uint64_t r[kMaxOl];
+    for (int l = 0; l < ol; l++) r[l] = hk[l];
+    sub_shifted(r, w, ol, b - 1);
+    const int64_t lo = (k - lg + 1) > 0 ? k - lg + 1 : 0;
+    uint64_t cnt[kMaxOl];
+    for (int l = 0; l < ol; l++) cnt[l] = 0;
+    cnt[0] = (uint64_t)(fhi - lo + 1);
+    sub_shifted(r, cnt, ol, 2 * b - 2);
+    for (int l = 0; l < ol; l++) hk[l] = r[l];
+  }
+}
+
+cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                              const uint64_t *g, int64_t lg, int b, int in_limbs,
+                              uint64_t *prefix, cudaStream_t s) {
+  if (ol > kMaxOl) return cudaErrorInvalidValue;
+  uint64_t *pf = prefix;
+  uint64_t *pg = pf + lf * ol;
+  uint64_t *offs = pg + lg * ol;
+  prefix_kernel<<<2, kPrefThreads, 0, s>>>(f, lf, g, lg, in_limbs, ol, pf, pg, offs);
+  const int64_t lh = lf + lg - 1;
+  signed_fix_kernel<<<grid_for(lh, 128), 128, 0, s>>>(h, ol, lf, lg, b, pf, pg);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+size_t signed_prefix_bytes(int64_t lf, int64_t lg, int ol) {
+  return (size_t)(lf + lg + 2 * kPrefThreads) * ol * 8;
+}
+
+// ------------------------------------------------------------------ mod p
+// r = (hi * 2^64 + lo) mod p for hi < p < 2^63, by shift-and-subtract.
+__device__ __forceinline__ uint64_t mod_128(uint64_t hi, uint64_t lo, uint64_t p) {
+  for (int i = 0; i < 64; i++) {
+    hi = (hi << 1) | (lo >> 63);
+    lo <<= 1;
+    if (hi >= p) hi -= p;
+  }
+  return hi;
+}
+
+__global__ void __launch_bounds__(256) reduce_mod_kernel(uint64_t *out, const uint64_t *h, int ol,
+                                                         int64_t lh, uint64_t p) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lh;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t r = 0;
+    for (int l = ol - 1; l >= 0; l--) r = mod_128(r, h[k * ol + l], p);
+    out[k] = r;
+  }
+}
+
+cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh, uint64_t p,
+                              cudaStream_t s) {
+  reduce_mod_kernel<<<grid_for(lh, 256), 256, 0, s>>>(out, h, ol, lh, p);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ks

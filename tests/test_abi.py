@@ -1,0 +1,82 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+``include/*.h`` declares, and its host-only planning calls give the sizes of
+Sec. 3 (N per variant, output limbs)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ks():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_0712_4046_gb300 as ks
+    return ks
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("ks_") and not name.endswith("_t"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ks_mul", "ks_mul_ex", "ks_mul_host", "ks_mul_mod", "ks_mul_batch",
+                 "ks_out_limbs", "ks_workspace_bytes", "ks_status_sync", "ks_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(ks):
+    lib = ctypes.CDLL(ks._LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_eval_bits_follow_the_paper(ks):
+    # N = 2b + e, b + ceil(e/2), b + ceil(e/2), ceil((2b + e)/4)  (Sec. 3.1-3.4)
+    for L, b in [(1, 1), (4, 3), (1024, 64), (16384, 48), (1 << 20, 256), (1000, 7)]:
+        e = (L - 1).bit_length()
+        assert ks.eval_bits(L, L, b, 1) == 2 * b + e
+        assert ks.eval_bits(L, L, b, 2) == b + (e + 1) // 2
+        assert ks.eval_bits(L, L, b, 3) == b + (e + 1) // 2
+        assert ks.eval_bits(L, L, b, 4) == (2 * b + e + 3) // 4
+    # config sizes quoted from the Propositions: L=16384, b=48 -> KS1 N=110
+    assert ks.eval_bits(16384, 16384, 48, 1) == 110
+    assert ks.eval_bits(16384, 16384, 48, 4) == 28
+    assert ks.eval_bits(1024, 1024, 64, 4) == 35
+    # unequal lengths take e from the shorter polynomial
+    assert ks.eval_bits(5, 1000, 10, 1) == 2 * 10 + 3
+
+
+def test_out_limbs_and_errors(ks):
+    assert ks.out_limbs(1024, 1024, 64, False) == 3     # 138 bits
+    assert ks.out_limbs(16384, 16384, 48, True) == 2    # 111 bits
+    assert ks.out_limbs(1, 1, 32, False) == 1
+    with pytest.raises(ks.KSError):
+        ks.out_limbs(0, 5, 8, False)
+    with pytest.raises(ks.KSError):
+        ks.out_limbs(5, 5, 0, False)
+    with pytest.raises(ks.KSError):
+        ks.eval_bits(5, 5, 8, 7)
+    assert ks.lib.ks_strerror(ks.KS_EINVAL) == b"invalid argument"
+    assert ks.lib.ks_version() >= 100
+
+
+def test_workspace_is_host_computable(ks):
+    for v in (1, 2, 3, 4):
+        n = ks.workspace_bytes(16384, 16384, 48, True, v, ks.ENGINE_SCHOOLBOOK)
+        assert n > 0 and n % 256 == 0
+    v, e = ks.choose(16384, 16384, 48, True)
+    assert v in (1, 2, 3, 4) and e in (1, 2, 3)
