@@ -127,6 +127,37 @@ int ks_mul_host(uint64_t *h, const uint64_t *f, int64_t len_f,
 int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
                int64_t len_g, uint64_t p, int variant, ks_stream_t stream);
 
+/*
+ * ks_mul_static -- ks_mul without any allocation.  (The paper has no
+ * counterpart; this entry point is a deployment convenience.)
+ *
+ * For callers that cannot allocate device memory when they multiply: code
+ * whose device memory is owned and budgeted by another allocator (a
+ * framework's caching pool, a fixed-size serving arena), code that must not
+ * trigger cudaMalloc / cudaFree because those calls can synchronize the whole
+ * device and stall unrelated work, and plugin hosts that forbid allocation
+ * after start-up.  ks_mul grows a cached workspace on demand and ks_mul_ex
+ * needs the caller to provide one; this call needs neither.
+ *
+ * Scratch lives in one file-scope device array of KS_STATIC_SCRATCH_BYTES
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits.  Problems whose workspace (ks_workspace_bytes with
+ * KS_ENGINE_AUTO) is larger are refused with KS_ERANGE before anything runs.
+ * The caller still passes f, g and h as device memory, exactly as for
+ * ks_mul; the call makes no cudaMalloc, cudaFree or other allocating call.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture begins.  All calls, from any thread or stream,
+ * share the one array and it keeps the last call's contents; the parts that
+ * must start at zero are cleared on `stream` by every call.  Calls that
+ * overlap on the GPU race on the array: order them (one stream, or events).
+ */
+#define KS_STATIC_SCRATCH_BYTES (16 << 20)
+int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f,
+                  const uint64_t *g, int64_t len_g, int coeff_bits,
+                  int is_signed, int variant, ks_stream_t stream);
+
 /* One product of a batch (device pointers, layout as for ks_mul). */
 typedef struct {
   uint64_t *h;

@@ -48,6 +48,9 @@ _sig("ks_mul_ex", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp, _i64,
 _sig("ks_mul_host", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp)
 _sig("ks_mul_mod", _ci, _vp, _vp, _i64, _vp, _i64, _u64, _ci, _vp)
 _sig("ks_mul_batch", _ci, ctypes.POINTER(KSProblem), _i64, _vp)
+_sig("ks_mul_static", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
+
+STATIC_SCRATCH_BYTES = 16 << 20
 _sig("ks_status_sync", _ci, _vp)
 _sig("ks_choose", _ci, _i64, _i64, _ci, _ci, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
 _sig("ks_strerror", ctypes.c_char_p, _ci)
@@ -149,6 +152,15 @@ def ks_mul_host(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_A
     _check(lib.ks_mul_host(h.ctypes.data, f.ctypes.data, f.shape[0], g.ctypes.data, g.shape[0],
                            coeff_bits, int(is_signed), variant, engine, _stream_ptr(stream)),
            "ks_mul_host")
+
+
+def ks_mul_static(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
+    """As ks_mul, but the library allocates nothing: its scratch is a fixed
+    device array inside the library (STATIC_SCRATCH_BYTES), for callers that
+    may not allocate device memory at call time.  Calls sharing the array must
+    not overlap on the GPU; larger problems raise KSError (KS_ERANGE)."""
+    _check(lib.ks_mul_static(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
+                             int(is_signed), variant, _stream_ptr(stream)), "ks_mul_static")
 
 
 def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):

@@ -360,6 +360,30 @@ static int check_args(uint64_t *h, const uint64_t *f, int64_t lf, const uint64_t
   return KS_OK;
 }
 
+// ------------------------------------------------------- no-allocation scratch
+// Scratch for ks_mul_static: one file-scope device array.  Every GPU that
+// loads this library holds it (KS_STATIC_SCRATCH_BYTES) until the process
+// exits.  Host code must not use the array's name as a device address; its
+// address on the current device is looked up once per device below.
+static __device__ __align__(256) unsigned char g_static_scratch[KS_STATIC_SCRATCH_BYTES];
+
+static int static_scratch_ptr(char **out) {
+  static std::mutex mu;
+  static char *ptrs[64] = {nullptr};
+  int dev = 0;
+  KS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return KS_ERANGE;
+  std::lock_guard<std::mutex> lk(mu);
+  if (ptrs[dev] == nullptr) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ptrs[dev] = static_cast<char *>(p);
+  }
+  *out = ptrs[dev];
+  return KS_OK;
+}
+
 }  // namespace ks
 
 using namespace ks;
@@ -507,6 +531,26 @@ int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream) {
     if (rc != KS_OK) return rc;
   }
   return KS_OK;
+}
+
+int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
+                  int64_t len_g, int coeff_bits, int is_signed, int variant,
+                  ks_stream_t stream) {
+  int engine = KS_ENGINE_AUTO;
+  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  Plan p;
+  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  if (rc != KS_OK) return rc;
+  if (p.total > (size_t)KS_STATIC_SCRATCH_BYTES) return KS_ERANGE;
+  rc = check_args(h, f, len_f, g, len_g, coeff_bits, p.out_limbs);
+  if (rc != KS_OK) return rc;
+  char *ws = nullptr;
+  rc = static_scratch_ptr(&ws);
+  if (rc != KS_OK) return rc;
+  // run_plan clears the column sums (the only scratch that must start at
+  // zero) on `stream` before the products accumulate into them.
+  return run_plan(p, h, f, g, ws, static_cast<cudaStream_t>(stream));
 }
 
 int ks_status_sync(ks_stream_t stream) {
