@@ -13,7 +13,7 @@
 namespace ks {
 
 int64_t norm_tiles_for(int64_t nwords);
-size_t signed_prefix_bytes(int64_t lf, int64_t lg, int ol);
+size_t signed_prefix_bytes(int64_t lf, int64_t lg, int il);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -142,8 +142,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
       p.run_n[1] = p.lh / 2;
     }
     const int64_t nmax = p.run_n[0];
-    p.chain = p.M <= 127 ? (nmax + 8191) / 8192 : (nmax + 511) / 512;
-    const int64_t minchain = p.M <= 127 ? 32 : 64;
+    p.chain = p.M <= 127 ? (nmax + 2047) / 2048 : (nmax + 511) / 512;
+    const int64_t minchain = 64;
     if (p.chain < minchain) p.chain = minchain;
     p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
     p.nseeds = 0;
@@ -167,7 +167,7 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.off_seeds = off;
   off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
   p.off_prefix = off;
-  if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.out_limbs));
+  if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.in_limbs));
   p.off_hp = off;  // exact product for ks_mul_mod (sized by the caller)
   p.off_ntt = off;
   if (engine == KS_ENGINE_NTT) off = align256(off + ntt_workspace_bytes(p.ntt_log, p.nprod));

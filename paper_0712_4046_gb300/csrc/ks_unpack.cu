@@ -47,12 +47,13 @@ cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
 
 // ------------------------------------------------------------------ seeds
 // Exact h'_k = sum_t f'_t g'_(k-t) (biased, non-negative b-bit inputs) for the
-// chain starts of the reconstruction: one CTA per coefficient.  Each thread
-// multiplies its terms word by word and keeps 64-bit per-word sums; the CTA
-// adds those into shared 64-bit word sums and one thread propagates carries.
+// chain starts of the reconstruction: one CTA per coefficient.  A thread
+// multiplies its terms word by word (NW 32-bit words per coefficient, a
+// compile-time size so the words stay in registers) and keeps 64-bit per-word
+// sums; the CTA adds those into shared 64-bit word sums and one thread
+// propagates the carries.
 namespace {
 constexpr int kSeedThreads = 128;
-constexpr int kMaxInWords = 64;  // b <= 2048
 struct SeedArgs {
   RecoverRun run[2];
   int nruns;
@@ -60,23 +61,23 @@ struct SeedArgs {
 };
 }  // namespace
 
-__device__ __forceinline__ int coeff_words(const uint64_t *c, int in_limbs, int b, int flip,
-                                           uint32_t *w) {
-  const int nw = (b + 31) / 32;
-  for (int i = 0; i < nw; i++) {
-    const int len = (b - 32 * i) < 32 ? (b - 32 * i) : 32;
-    w[i] = coeff_slice(c, in_limbs, b, flip, 32 * i, len);
+template <int NW>
+__device__ __forceinline__ void coeff_words(const uint64_t *c, int in_limbs, int b, int flip,
+                                            uint32_t *w) {
+#pragma unroll
+  for (int i = 0; i < NW; i++) {
+    const int rem = b - 32 * i;
+    w[i] = rem > 0 ? coeff_slice(c, in_limbs, b, flip, 32 * i, rem < 32 ? rem : 32) : 0u;
   }
-  return nw;
 }
 
+template <int NW>
 __global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int seed_words,
                                                             SeedArgs a, const uint64_t *f,
                                                             int64_t lf, const uint64_t *g,
                                                             int64_t lg, int b, int in_limbs,
                                                             int flip) {
   __shared__ unsigned long long colsum[kMaxSeedWords];
-  // which seed: runs in order, chains c >= 1, values (c*chain - 1, c*chain)
   int64_t sid = blockIdx.x;
   int r = 0;
   int64_t per_run = 2 * (a.run[0].nchains - 1);
@@ -92,30 +93,35 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int
   for (int w = threadIdx.x; w < seed_words; w += blockDim.x) colsum[w] = 0ull;
   __syncthreads();
 
-  unsigned long long loc[2 * kMaxInWords + 2];
-  const int nw = (b + 31) / 32;
-  for (int w = 0; w < 2 * nw + 1; w++) loc[w] = 0ull;
+  unsigned long long loc[2 * NW];
+#pragma unroll
+  for (int w = 0; w < 2 * NW; w++) loc[w] = 0ull;
   int64_t t_lo = k - (lg - 1);
   if (t_lo < 0) t_lo = 0;
   const int64_t t_hi = k < lf - 1 ? k : lf - 1;
-  uint32_t fw[kMaxInWords], gw[kMaxInWords], pr[2 * kMaxInWords];
   for (int64_t t = t_lo + threadIdx.x; t <= t_hi; t += blockDim.x) {
-    coeff_words(f + t * in_limbs, in_limbs, b, flip, fw);
-    coeff_words(g + (k - t) * in_limbs, in_limbs, b, flip, gw);
-    for (int w = 0; w < 2 * nw; w++) pr[w] = 0u;
-    for (int x = 0; x < nw; x++) {
+    uint32_t fw[NW], gw[NW], pr[2 * NW];
+    coeff_words<NW>(f + t * in_limbs, in_limbs, b, flip, fw);
+    coeff_words<NW>(g + (k - t) * in_limbs, in_limbs, b, flip, gw);
+#pragma unroll
+    for (int w = 0; w < 2 * NW; w++) pr[w] = 0u;
+#pragma unroll
+    for (int x = 0; x < NW; x++) {
       uint64_t carry = 0;
-      for (int y = 0; y < nw; y++) {
+#pragma unroll
+      for (int y = 0; y < NW; y++) {
         const uint64_t tt = (uint64_t)fw[x] * gw[y] + pr[x + y] + carry;
         pr[x + y] = (uint32_t)tt;
         carry = tt >> 32;
       }
-      pr[x + nw] = (uint32_t)carry;
+      pr[x + NW] = (uint32_t)carry;
     }
-    for (int w = 0; w < 2 * nw; w++) loc[w] += pr[w];
+#pragma unroll
+    for (int w = 0; w < 2 * NW; w++) loc[w] += pr[w];
   }
-  for (int w = 0; w < 2 * nw && w < seed_words; w++)
-    if (loc[w]) atomicAdd(&colsum[w], loc[w]);
+#pragma unroll
+  for (int w = 0; w < 2 * NW; w++)
+    if (w < seed_words && loc[w]) atomicAdd(&colsum[w], loc[w]);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t *out = seeds + (R.seed_base + sid) * seed_words;
@@ -140,9 +146,27 @@ cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs
   a.nruns = nruns;
   a.chain = chain;
   if (n == 0) return cudaSuccess;
-  if (seed_words > kMaxSeedWords || (b + 31) / 32 > kMaxInWords) return cudaErrorInvalidValue;
-  seed_kernel<<<(unsigned)n, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b,
-                                                   in_limbs, flip);
+  if (seed_words > kMaxSeedWords) return cudaErrorInvalidValue;
+  const int nw = (b + 31) / 32;
+  const unsigned grid = (unsigned)n;
+#define KS_SEEDS(NW)                                                                        \
+  seed_kernel<NW><<<grid, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b, \
+                                                in_limbs, flip)
+  if (nw <= 2)
+    KS_SEEDS(2);
+  else if (nw <= 4)
+    KS_SEEDS(4);
+  else if (nw <= 8)
+    KS_SEEDS(8);
+  else if (nw <= 16)
+    KS_SEEDS(16);
+  else if (nw <= 32)
+    KS_SEEDS(32);
+  else if (nw <= 64)
+    KS_SEEDS(64);
+  else
+    return cudaErrorInvalidValue;
+#undef KS_SEEDS
   note_launches(1);
   return cudaGetLastError();
 }
@@ -359,23 +383,36 @@ __global__ void __launch_bounds__(128) recover_kernel1(uint64_t *h, int ol, Reco
     delta = (b_prev + a_cur + dprev - us) >> M;
   }
   uint64_t w_cur = load_d1(R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
-  for (int64_t j = s; j < e; j++) {
-    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
-    if (j <= n - 2) {
-      const uint64_t w_next = load_d1(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
-      const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
-      const uint64_t beta = (w_cur - a_prev - eps) & mask;
-      const uint64_t u_next = load_d1(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
-      const uint64_t a_next = (u_next - beta - delta) & mask;
-      const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
-      if (dnext > 1) atomicExch(status, 2);
-      write_h1(out, ol, a_cur, beta, M);
-      a_prev = a_cur;
-      a_cur = a_next;
-      delta = dnext;
-      w_cur = w_next;
-    } else {
-      write_h1(out, ol, a_cur, (w_cur - a_prev) & mask, M);
+  constexpr int kAhead = 8;  // digits are loaded kAhead steps ahead of their use
+  for (int64_t j0 = s; j0 < e; j0 += kAhead) {
+    uint64_t ub[kAhead], wb[kAhead];
+#pragma unroll
+    for (int q = 0; q < kAhead; q++) {
+      const int64_t j = j0 + q;
+      ub[q] = load_d1(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      wb[q] = load_d1(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+    }
+#pragma unroll
+    for (int q = 0; q < kAhead; q++) {
+      const int64_t j = j0 + q;
+      if (j >= e) break;
+      uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
+      if (j <= n - 2) {
+        const uint64_t w_next = wb[q];
+        const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
+        const uint64_t beta = (w_cur - a_prev - eps) & mask;
+        const uint64_t u_next = ub[q];
+        const uint64_t a_next = (u_next - beta - delta) & mask;
+        const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
+        if (dnext > 1) atomicExch(status, 2);
+        write_h1(out, ol, a_cur, beta, M);
+        a_prev = a_cur;
+        a_cur = a_next;
+        delta = dnext;
+        w_cur = w_next;
+      } else {
+        write_h1(out, ol, a_cur, (w_cur - a_prev) & mask, M);
+      }
     }
   }
 }
@@ -514,155 +551,6 @@ cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nrun
     recover_wide<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(h, ol, a, status);
   }
   return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ signed
-// The signed bias: f'_t = f_t + c, c = 2^(b-1), and likewise g', so
-//   f g = f' g' - c (f * U_g + U_f * g) - c^2 U_f * U_g,
-// U the all-ones polynomials.  (f * U_g)_k is the window sum of f_t over
-// t in [max(0, k - Lg + 1), min(k, Lf - 1)], a difference of prefix sums.
-// Everything is computed mod 2^(64 ol), which is exact because the final
-// coefficient fits ol limbs of two's complement.
-namespace {
-constexpr int kPrefThreads = 256;
-constexpr int kMaxOl = 72;
-}
-
-__device__ __forceinline__ void add_sext(uint64_t *acc, const uint64_t *x, int in_limbs, int ol) {
-  const uint64_t ext = (x[in_limbs - 1] >> 63) ? ~0ull : 0ull;
-  uint64_t carry = 0;
-  for (int l = 0; l < ol; l++) {
-    const uint64_t v = l < in_limbs ? x[l] : ext;
-    const uint64_t s1 = acc[l] + v;
-    const uint64_t c1 = s1 < v;
-    const uint64_t s2 = s1 + carry;
-    const uint64_t c2 = s2 < carry;
-    acc[l] = s2;
-    carry = c1 | c2;
-  }
-}
-
-// blockIdx.x = 0: prefix sums of f; 1: of g.  prefix rows are ol limbs.
-__global__ void __launch_bounds__(kPrefThreads) prefix_kernel(const uint64_t *f, int64_t lf,
-                                                              const uint64_t *g, int64_t lg,
-                                                              int in_limbs, int ol,
-                                                              uint64_t *pf, uint64_t *pg,
-                                                              uint64_t *offs) {
-  const uint64_t *x = blockIdx.x == 0 ? f : g;
-  const int64_t L = blockIdx.x == 0 ? lf : lg;
-  uint64_t *P = blockIdx.x == 0 ? pf : pg;
-  uint64_t *O = offs + (int64_t)blockIdx.x * kPrefThreads * ol;
-  const int64_t per = (L + kPrefThreads - 1) / kPrefThreads;
-  const int64_t t0 = threadIdx.x * per;
-  const int64_t t1 = (t0 + per < L) ? t0 + per : L;
-  uint64_t acc[kMaxOl];
-  for (int l = 0; l < ol; l++) acc[l] = 0;
-  for (int64_t t = t0; t < t1; t++) {
-    add_sext(acc, x + t * in_limbs, in_limbs, ol);
-    for (int l = 0; l < ol; l++) P[t * ol + l] = acc[l];
-  }
-  for (int l = 0; l < ol; l++) O[threadIdx.x * ol + l] = acc[l];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t run[kMaxOl];
-    for (int l = 0; l < ol; l++) run[l] = 0;
-    for (int t = 0; t < kPrefThreads; t++) {
-      uint64_t tot[kMaxOl];
-      for (int l = 0; l < ol; l++) tot[l] = O[t * ol + l];
-      for (int l = 0; l < ol; l++) O[t * ol + l] = run[l];
-      uint64_t carry = 0;
-      for (int l = 0; l < ol; l++) {
-        const uint64_t s1 = run[l] + tot[l];
-        const uint64_t c1 = s1 < tot[l];
-        const uint64_t s2 = s1 + carry;
-        carry = c1 | (s2 < carry);
-        run[l] = s2;
-      }
-    }
-  }
-  __syncthreads();
-  for (int l = 0; l < ol; l++) acc[l] = O[threadIdx.x * ol + l];
-  for (int64_t t = t0; t < t1; t++) {
-    uint64_t carry = 0;
-    for (int l = 0; l < ol; l++) {
-      const uint64_t v = P[t * ol + l];
-      const uint64_t s1 = v + acc[l];
-      const uint64_t c1 = s1 < acc[l];
-      const uint64_t s2 = s1 + carry;
-      carry = c1 | (s2 < carry);
-      P[t * ol + l] = s2;
-    }
-  }
-}
-
-// r = r - (x << sh)  mod 2^(64 ol)
-__device__ __forceinline__ void sub_shifted(uint64_t *r, const uint64_t *x, int ol, int sh) {
-  const int q = sh >> 6, rr = sh & 63;
-  uint64_t borrow = 0;
-  for (int l = 0; l < ol; l++) {
-    const int a = l - q;
-    uint64_t v = 0;
-    if (a >= 0 && a < ol) v = x[a] << rr;
-    if (rr && a - 1 >= 0 && a - 1 < ol) v |= x[a - 1] >> (64 - rr);
-    const uint64_t d1 = r[l] - v;
-    const uint64_t b1 = r[l] < v;
-    const uint64_t d2 = d1 - borrow;
-    const uint64_t b2 = d1 < borrow;
-    r[l] = d2;
-    borrow = b1 | b2;
-  }
-}
-
-__global__ void __launch_bounds__(128) signed_fix_kernel(uint64_t *h, int ol, int64_t lf,
-                                                         int64_t lg, int b, const uint64_t *pf,
-                                                         const uint64_t *pg) {
-  const int64_t lh = lf + lg - 1;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lh;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t w[kMaxOl], tmp[kMaxOl];
-    // W_f + W_g, each a difference of prefix sums
-    const int64_t fhi = k < lf - 1 ? k : lf - 1;
-    const int64_t ghi = k < lg - 1 ? k : lg - 1;
-    for (int l = 0; l < ol; l++) w[l] = pf[fhi * ol + l];
-    if (k - lg >= 0) sub_shifted(w, pf + (k - lg) * ol, ol, 0);
-    for (int l = 0; l < ol; l++) tmp[l] = 0;
-    sub_shifted(tmp, pg + ghi * ol, ol, 0);          // tmp = -S_g(ghi)
-    if (k - lf >= 0) {
-      uint64_t neg[kMaxOl];
-      for (int l = 0; l < ol; l++) neg[l] = 0;
-      sub_shifted(neg, pg + (k - lf) * ol, ol, 0);   // -S_g(k - lf)
-      sub_shifted(tmp, neg, ol, 0);                  // tmp = -(W_g)
-    }
-    sub_shifted(w, tmp, ol, 0);                      // w = W_f + W_g
-    uint64_t *hk = h + k * ol;
-    uint64_t r[kMaxOl];
-    for (int l = 0; l < ol; l++) r[l] = hk[l];
-    sub_shifted(r, w, ol, b - 1);
-    const int64_t lo = (k - lg + 1) > 0 ? k - lg + 1 : 0;
-    uint64_t cnt[kMaxOl];
-    for (int l = 0; l < ol; l++) cnt[l] = 0;
-    cnt[0] = (uint64_t)(fhi - lo + 1);
-    sub_shifted(r, cnt, ol, 2 * b - 2);
-    for (int l = 0; l < ol; l++) hk[l] = r[l];
-  }
-}
-
-cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
-                              const uint64_t *g, int64_t lg, int b, int in_limbs,
-                              uint64_t *prefix, cudaStream_t s) {
-  if (ol > kMaxOl) return cudaErrorInvalidValue;
-  uint64_t *pf = prefix;
-  uint64_t *pg = pf + lf * ol;
-  uint64_t *offs = pg + lg * ol;
-  prefix_kernel<<<2, kPrefThreads, 0, s>>>(f, lf, g, lg, in_limbs, ol, pf, pg, offs);
-  const int64_t lh = lf + lg - 1;
-  signed_fix_kernel<<<grid_for(lh, 128), 128, 0, s>>>(h, ol, lf, lg, b, pf, pg);
-  note_launches(2);
-  return cudaGetLastError();
-}
-
-size_t signed_prefix_bytes(int64_t lf, int64_t lg, int ol) {
-  return (size_t)(lf + lg + 2 * kPrefThreads) * ol * 8;
 }
 
 // ------------------------------------------------------------------ mod p
