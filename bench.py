@@ -66,12 +66,21 @@ def inputs():
     return f, g
 
 
+BF16_TFLOPS = 1900.0
+PEAK_KIND = "fallback"
+
+
 def peaks():
+    """HBM GB/s, max SM MHz, and the kind of figure (measured or fallback)."""
+    global BF16_TFLOPS, PEAK_KIND
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             p = json.load(fh)
+        BF16_TFLOPS = float(p["bf16_tflops"])
+        PEAK_KIND = "measured"
         return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
+        BF16_TFLOPS, PEAK_KIND = 1900.0, "fallback"
         return 6800.0, 2070.0, "fallback"
 
 
@@ -219,10 +228,24 @@ def main_ours(args):
     hbm_gbs, sm_max_mhz, peak_kind = peaks()
 
     results = {}
+    # (label, variant, engine): the library's choice for every variant, plus the
+    # INT32-pipe schoolbook engine for KS1 and KS4 (the plain GPU baseline)
+    runs = [("KS1", 1, 0), ("KS2", 2, 0), ("KS3", 3, 0), ("KS4", 4, 0),
+            ("KS1_int32", 1, ks.ENGINE_SCHOOLBOOK), ("KS4_int32", 4, ks.ENGINE_SCHOOLBOOK)]
+    ws = {}
     with Clocks(local) as clk:
-        for variant in (1, 2, 3, 4):
+        for label, variant, engine in runs:
+            if engine:
+                n = ks.workspace_bytes(lf, lg, b, sg, variant, engine)
+                ws[label] = torch.empty(n // 8 + 32, dtype=torch.int64, device=dev)
+
+            def step():
+                if engine:
+                    ks.ks_mul_ex(h, tf, tg, b, sg, variant, engine, ws[label], stream)
+                else:
+                    ks.ks_mul(h, tf, tg, b, sg, variant, stream)
             for _ in range(args.warmup):
-                ks.ks_mul(h, tf, tg, b, sg, variant, stream)
+                step()
             ks.status_sync(stream)
             torch.cuda.synchronize()
             if world > 1:
@@ -235,7 +258,7 @@ def main_ours(args):
             for i in range(args.steps):
                 flush.zero_()
                 evs[i][0].record(stream)
-                ks.ks_mul(h, tf, tg, b, sg, variant, stream)
+                step()
                 evs[i][1].record(stream)
             torch.cuda.synchronize()
             ks.profile_enable(False)
@@ -244,8 +267,9 @@ def main_ours(args):
             phases = ks.profile_collect()
             step_ms = [a.elapsed_time(z) for a, z in evs]
             total_ms = barrier_max(sum(step_ms), world, dev)
-            results[variant] = {"total_ms": total_ms, "ms_per_step": total_ms / args.steps,
-                                "launches": launches, "phases": phases}
+            results[label] = {"total_ms": total_ms, "ms_per_step": total_ms / args.steps,
+                              "launches": launches, "phases": phases,
+                              "variant": variant, "engine": engine}
     clocks = clk.summary()
 
     # ---- e2e through the host-buffer entry point (pinned buffers)
@@ -262,7 +286,7 @@ def main_ours(args):
     e2e_s = barrier_max(time.perf_counter() - t0, world, dev)
 
     # ---- roofline of the dominant phase of KS4
-    r4 = results[4]
+    r4 = results["KS4"]
     info = ks.plan_info(lf, lg, b, sg, 4, ks.ENGINE_AUTO)
     ph = {k: v for k, v in r4["phases"].items() if v[1] > 0}
     dom = max(ph, key=lambda k: ph[k][0])
@@ -283,7 +307,9 @@ def main_ours(args):
     variants = {}
     for v, r in results.items():
         pps = world * 1000.0 / r["ms_per_step"]
-        variants["KS%d" % v] = {"products_per_s": pps, "ms_per_step": r["ms_per_step"],
+        variants[v] = {"products_per_s": pps, "ms_per_step": r["ms_per_step"],
+                                "engine": ks.plan_info(lf, lg, b, sg, r["variant"],
+                                                       r["engine"])["engine"],
                                 "output_gbit_per_s": pps * obits / 1e9,
                                 "phases_ms": {k: round(x[0] / max(1, x[1]), 5)
                                               for k, x in r["phases"].items() if x[1] > 0}}
@@ -296,7 +322,8 @@ def main_ours(args):
                        l2="flushed between steps (256 MiB write)",
                        parallelism="replicas" if world > 1 else "single"),
         "output_gbit_per_s": value * obits / 1e9,
-        "ks4_over_ks1": results[1]["ms_per_step"] / ms4,
+        "ks4_over_ks1": results["KS1"]["ms_per_step"] / ms4,
+        "ks4_over_int32_ks1": results["KS1_int32"]["ms_per_step"] / ms4,
         "variants": variants,
         "gpu_launches": int(r4["launches"]),
         "roofline": roof,
@@ -315,6 +342,13 @@ def roofline_for(phase, ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind)
     nprod, nA, nB, ncols = info["nprod"], info["nA"], info["nB"], info["ncols"]
     nw, nnorm, ol, il = info["nwords"], info["nnorm"], info["out_limbs"], info["in_limbs"]
     sec = ms / 1000.0
+    if phase == "product" and info["engine"] == 3:
+        flops = 2.0 * nprod * nA * nB  # one multiply-add per pair of 7-bit digits
+        peak = BF16_TFLOPS
+        ach = flops / sec / 1e12
+        return {"bound": "tensor", "phase": phase, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_kind": PEAK_KIND + " dense bf16 (fp16 runs at the bf16 rate)"}
     if phase == "product" and info["engine"] == 1:
         ops = 2.0 * nprod * nA * nB  # one multiply-add per digit pair
         peak = SMS * IMAD_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12

@@ -93,7 +93,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine) {
   if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
   if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
-  if (engine != KS_ENGINE_SCHOOLBOOK) return KS_ENOTSUP;
+  if (engine != KS_ENGINE_SCHOOLBOOK && engine != KS_ENGINE_TC) return KS_ENOTSUP;
   if (lf > ((int64_t)1 << 40) || lg > ((int64_t)1 << 40)) return KS_ERANGE;
   p = Plan();
   p.variant = variant;
@@ -107,7 +107,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.N = variant_N(variant, b, p.e);
   p.in_limbs = (b + 63) / 64;
   p.out_limbs = (2 * b + p.e + p.is_signed + 63) / 64;
-  p.d = 16;
+  p.d = engine == KS_ENGINE_TC ? 7 : 16;
+  p.dn = engine == KS_ENGINE_TC ? 28 : p.d;
   p.nprod = variant == KS_1 ? 1 : (variant == KS_4 ? 4 : 2);
   p.nnorm = p.nprod;
   const int64_t bitsF = (int64_t)p.N * (lf - 1) + b;
@@ -115,7 +116,17 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.nA = (bitsF + p.d - 1) / p.d;
   p.nB = (bitsG + p.d - 1) / p.d;
   p.ncols = p.nA + p.nB - 1;
-  p.nwords = (p.d * p.ncols + 95) / 32 + 1;
+  if (engine == KS_ENGINE_TC) {
+    // one more digit: the carry out of the local recoding of overlapping fields
+    p.nA += 1;
+    p.nB += 1;
+    p.ncols = p.nA + p.nB - 1;
+    tc_geometry(p.nA, p.nB, p.tg);
+    p.ncols = p.tg.ncols;
+    for (int q = 0; q < 4; q++) p.ks[q] = 8;
+    if (p.tg.T > ((int64_t)1 << 20)) return KS_ERANGE;
+  }
+  p.nwords = (p.dn * p.ncols + 95) / 32 + 1;
   p.ntiles = norm_tiles_for(p.nwords);
   // digit magnitude: at most `pieces` fields meet a d-bit window
   const int64_t pieces = (b + p.d - 2) / p.N + 1;
@@ -142,8 +153,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
       p.run_n[1] = p.lh / 2;
     }
     const int64_t nmax = p.run_n[0];
-    p.chain = p.M <= 127 ? (nmax + 2047) / 2048 : (nmax + 511) / 512;
-    const int64_t minchain = 64;
+    p.chain = p.M <= 127 ? (nmax + 4095) / 4096 : (nmax + 511) / 512;
+    const int64_t minchain = p.M <= 127 ? 32 : 64;
     if (p.chain < minchain) p.chain = minchain;
     p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
     p.nseeds = 0;
@@ -155,7 +166,10 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   // workspace layout
   size_t off = 0;
   p.off_digits = off;
-  off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
+  if (engine == KS_ENGINE_TC)
+    off = align256(off + (size_t)p.nprod * tc_operand_bytes(p.tg));
+  else
+    off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
   p.off_words = off;
@@ -166,6 +180,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   off = align256(off + (size_t)p.nnorm * p.ntiles);
   p.off_seeds = off;
   off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
+  p.off_seedacc = off;
+  off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_prefix = off;
   if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.in_limbs));
   p.off_hp = off;  // exact product for ks_mul_mod (sized by the caller)
@@ -179,16 +195,11 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
 int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine) {
   (void)is_signed;
   if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
-  const int e = ceil_log2(lf < lg ? lf : lg);
   const int64_t lh = lf + lg - 1;
   int v = *variant;
   if (v == KS_AUTO) v = (lh >= 64) ? KS_4 : KS_1;
   int eng = *engine;
-  if (eng == KS_ENGINE_AUTO) {
-    const double bits1 = (double)(2 * b + e) * (double)(lf < lg ? lf : lg);
-    (void)bits1;
-    eng = KS_ENGINE_SCHOOLBOOK;
-  }
+  if (eng == KS_ENGINE_AUTO) eng = KS_ENGINE_TC;
   *variant = v;
   *engine = eng;
   return KS_OK;
@@ -225,11 +236,21 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
     prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
   }
-  {
-    PhaseTimer t(s, PH_PACK);
-    KS_CUDA(launch_pack(pa, s));
-  }
-  {
+  if (p.engine == KS_ENGINE_TC) {
+    {
+      PhaseTimer t(s, PH_PACK);
+      KS_CUDA(launch_tc_pack(pa, p.tg, p.nprod, ws + p.off_digits, s));
+    }
+    PhaseTimer t(s, PH_PRODUCT);
+    int64_t *C[4];
+    for (int q = 0; q < p.nprod; q++) C[q] = cols + (int64_t)q * p.ncols;
+    KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)p.nprod * p.ncols * 8, s));
+    KS_CUDA(launch_tc_products(p.tg, p.nprod, p.ks, ws + p.off_digits, C, status, s));
+  } else {
+    {
+      PhaseTimer t(s, PH_PACK);
+      KS_CUDA(launch_pack(pa, s));
+    }
     PhaseTimer t(s, PH_PRODUCT);
     if (p.engine == KS_ENGINE_SCHOOLBOOK) {
       KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)p.nprod * p.ncols * 8, s));
@@ -260,7 +281,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   }
   {
     PhaseTimer t(s, PH_NORMALIZE);
-    KS_CUDA(launch_normalize(jobs, p.nnorm, p.d, p.nwords, p.ntiles, s));
+    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, s));
   }
   const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
                  *V3 = words + 3 * p.nwords;
@@ -288,8 +309,9 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     }
     {
       PhaseTimer t(s, PH_SEEDS);
-      KS_CUDA(launch_seeds(seeds, p.seed_words, runs, p.nruns, p.chain, f, p.lf, g, p.lg, p.b,
-                           p.in_limbs, p.is_signed, s));
+      KS_CUDA(launch_seeds(seeds, p.seed_words,
+                           reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
+                           p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, s));
     }
     {
       PhaseTimer t(s, PH_RECOVER);

@@ -15,11 +15,26 @@ constexpr int kMaxSeedWords = 136;   // exact seeds: (2b + e) bits, b <= 2048
 constexpr int kMaxDigitWordsM = 72;  // reconstruction digit: M <= 2304 bits
 
 // ---------------------------------------------------------------- planning
+// Geometry of the tensor-core engine for one sub-product of nA x nB 7-bit digits.
+struct TcGeom {
+  int64_t nA = 0, nB = 0;
+  int64_t dmax = 0;   // largest block offset delta (blocks of 128 digits)
+  int64_t R = 0;      // rows (blocks of 128 digits) of the B operand
+  int64_t Pcols = 0;  // output block columns
+  int64_t T = 0;      // output tiles of 128 block columns
+  int64_t nG = 0;     // raw A digits stored (fp16, offset by 127, zero padded)
+  int64_t rows = 0;   // rows per B plane, zero padding included
+  int64_t ncols = 0;  // output column sums of four 7-bit digits (28-bit digits)
+};
+
 struct Plan {
   int variant = 0, engine = 0;
   int64_t lf = 0, lg = 0, lh = 0;
   int b = 0, e = 0, N = 0, is_signed = 0, in_limbs = 0, out_limbs = 0;
   int d = 16;           // digit bits of the sub-product operands
+  int dn = 16;          // digit bits of the column sums fed to the normalization
+  int ks[4] = {8, 8, 8, 8};  // tensor-core delta steps per exact accumulation chunk
+  TcGeom tg;
   int nprod = 0;        // independent sub-products (1, 2, 2, 4)
   int64_t nA = 0, nB = 0;  // digits of each f-side / g-side operand
   int64_t ncols = 0;    // column sums per sub-product
@@ -37,7 +52,7 @@ struct Plan {
   int ntt_log = 0;      // transform length 2^ntt_log
   // workspace layout (byte offsets from the base)
   size_t off_digits = 0, off_cols = 0, off_words = 0, off_agg = 0, off_cin = 0;
-  size_t off_seeds = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
+  size_t off_seeds = 0, off_seedacc = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
 };
@@ -79,6 +94,14 @@ struct Product {
 
 cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s);
 
+// Tensor-core engine (tcgen05, kind::f16): fp16 operand layouts, then the MMA kernel.
+void tc_geometry(int64_t nA, int64_t nB, TcGeom &g);
+size_t tc_operand_bytes(const TcGeom &g);
+cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
+                           cudaStream_t s);
+cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
+                               int64_t *const *C, int *status, cudaStream_t s);
+
 // NTT engine: column sums of each product by a two-prime transform + CRT.
 size_t ntt_workspace_bytes(int log_n, int nprod);
 cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d,
@@ -118,9 +141,10 @@ struct RecoverRun {
 };
 
 // Exact coefficients h'_k (biased, unsigned) for the chain starts.
-cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs,
-                         int nruns, int64_t chain, const uint64_t *f, int64_t lf,
-                         const uint64_t *g, int64_t lg, int b, int in_limbs,
+// seed_acc: scratch of 6 64-bit words per seed (the b <= 64 blocked path).
+cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
+                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
+                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs,
                          int flip, cudaStream_t s);
 
 cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
@@ -179,6 +203,35 @@ __device__ __forceinline__ uint32_t coeff_slice(const uint64_t *c, int in_limbs,
     if (fb < 64) v ^= 1ull << fb;
   }
   return (uint32_t)(v & ((1ull << len) - 1ull));
+}
+
+// Signed digit j (bits [jd, jd + d)) of one evaluation: the sum over the
+// coefficients t whose field [tN, tN + b) meets the window of +- (their bits
+// inside it), with the sign -1 for odd t at the point -2^N (Sec. 3.3, 3.4).
+__device__ __forceinline__ int32_t digit_at(const PackOp &op, int64_t j, int64_t N, int b, int d,
+                                            int in_limbs, int flip) {
+  const int64_t lo = j * d;
+  int64_t t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
+  int64_t t_hi = (lo + d - 1) / N;
+  if (t_hi > op.L - 1) t_hi = op.L - 1;
+  int32_t val = 0;
+  for (int64_t t = t_lo; t <= t_hi; t++) {
+    const int64_t pos = t * N;
+    const int64_t src = op.reversed ? (op.L - 1 - t) : t;
+    const uint64_t *c = op.poly + src * in_limbs;
+    uint32_t piece;
+    if (pos >= lo) {
+      const int sh = (int)(pos - lo);
+      piece = coeff_slice(c, in_limbs, b, flip, 0, d - sh) << sh;
+    } else {
+      piece = coeff_slice(c, in_limbs, b, flip, (int)(lo - pos), d);
+    }
+    if (op.sigma < 0 && (t & 1))
+      val -= (int32_t)piece;
+    else
+      val += (int32_t)piece;
+  }
+  return val;
 }
 
 }  // namespace ks

@@ -17,14 +17,14 @@
 //     incoming carry c to floor((s_j + c) / 2^32), a function on the three
 //     carry values.  Functions compose associatively, so the carries are a
 //     parallel prefix: warp shuffles, then the block, then the tiles (one
-//     tile = 2048 words per CTA), then a second pass applies them.
+//     tile = 512 words per CTA), then a second pass applies them.
 #include "ks_internal.cuh"
 
 namespace ks {
 
 namespace {
-constexpr int kThreads = 256;
-constexpr int kWPT = 8;                     // words per thread
+constexpr int kThreads = 128;
+constexpr int kWPT = 4;                     // words per thread
 constexpr int kTileWords = kThreads * kWPT; // words per tile
 constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
 
@@ -134,26 +134,41 @@ __global__ void __launch_bounds__(kThreads) norm_aggregate(NormArgs a) {
   if (threadIdx.x == 0) J.agg[tile] = (uint8_t)total;
 }
 
-// One CTA per job: carries into every tile (the first tile gets 0).
+// One CTA per job: carries into every tile (the first tile gets 0), by a
+// parallel prefix of the tile functions (each thread composes a run of tiles,
+// then warp shuffles and one more level across the warps).
 __global__ void __launch_bounds__(1024) norm_tiles(NormArgs a) {
   const NormJob &J = a.job[blockIdx.x];
-  __shared__ uint32_t part[1024];
+  __shared__ uint32_t wtot[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t per = (a.ntiles + 1023) / 1024;
   const int64_t t0 = (int64_t)threadIdx.x * per;
   uint32_t f = kIdentity;
   for (int64_t t = t0; t < t0 + per && t < a.ntiles; t++) f = compose(J.agg[t], f);
-  part[threadIdx.x] = f;
+  uint32_t incl = f;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl = compose(incl, o);
+  }
+  uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = kIdentity;
+  if (lane == 31) wtot[wid] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = kIdentity;
-    for (int i = 0; i < 1024; i++) {
-      uint32_t v = part[i];
-      part[i] = run;  // exclusive
-      run = compose(v, run);
+  if (wid == 0) {
+    uint32_t v = wtot[lane];
+    uint32_t wi = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, wi, off);
+      if (lane >= off) wi = compose(wi, o);
     }
+    uint32_t we = __shfl_up_sync(0xffffffffu, wi, 1);
+    if (lane == 0) we = kIdentity;
+    wtot[lane] = we;
   }
   __syncthreads();
-  int c = apply_fn(part[threadIdx.x], 0);
+  int c = apply_fn(compose(excl, wtot[wid]), 0);
   for (int64_t t = t0; t < t0 + per && t < a.ntiles; t++) {
     J.cin[t] = (int8_t)c;
     c = apply_fn(J.agg[t], c);

@@ -34,29 +34,7 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
       o++;
     }
     const PackOp &op = a.op[o];
-    const int64_t lo = j * d;
-    // coefficients t with tN < lo + d and tN + b > lo
-    int64_t t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
-    int64_t t_hi = (lo + d - 1) / N;
-    if (t_hi > op.L - 1) t_hi = op.L - 1;
-    int32_t val = 0;
-    for (int64_t t = t_lo; t <= t_hi; t++) {
-      const int64_t pos = t * N;
-      const int64_t src = op.reversed ? (op.L - 1 - t) : t;
-      const uint64_t *c = op.poly + src * a.in_limbs;
-      uint32_t piece;
-      if (pos >= lo) {
-        int sh = (int)(pos - lo);
-        piece = coeff_slice(c, a.in_limbs, b, a.flip, 0, d - sh) << sh;
-      } else {
-        int64_t x = lo - pos;  // < b
-        piece = coeff_slice(c, a.in_limbs, b, a.flip, (int)x, d);
-      }
-      if (op.sigma < 0 && (t & 1))
-        val -= (int32_t)piece;
-      else
-        val += (int32_t)piece;
-    }
+    const int32_t val = digit_at(op, j, N, b, d, a.in_limbs, a.flip);
     op.out[j] = val;
   }
 }

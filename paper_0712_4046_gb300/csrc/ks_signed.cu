@@ -13,8 +13,9 @@
 // cross coefficients.  The correction itself is computed mod 2^(64 ol),
 // which is exact because the final coefficient fits ol limbs.
 //
-// Prefix sums: a three-phase scan (block totals, scan of the totals, apply)
-// over both polynomials at once, ELEMS consecutive coefficients per thread.
+// Prefix sums: for polynomials of up to 2^16 coefficients a single launch in
+// which each CTA also sums the blocks before its own; longer ones use a
+// three-phase scan (block totals, scan of the totals, apply).
 #include "ks_internal.cuh"
 
 namespace ks {
@@ -172,6 +173,51 @@ __global__ void __launch_bounds__(kThreads) pref_apply(PrefArgs a) {
   }
 }
 
+// Polynomials of up to kSmallL coefficients: a single launch.  Each CTA
+// first sums every coefficient before its block (redundant across CTAs, at
+// most kSmallL / 2 extra reads per CTA), then scans its own block.
+constexpr int64_t kSmallL = 1 << 16;
+
+__global__ void __launch_bounds__(kThreads) pref_single(PrefArgs a) {
+  int64_t blk = blockIdx.x;
+  const int q = which(a, blk);
+  const int64_t b0 = blk * kBlock;
+  const int64_t t0 = b0 + (int64_t)threadIdx.x * kElems;
+  const int il = a.il, rec = 2 * il + 1;
+  for (int l = 0; l <= il; l++) {
+    // sum of the preceding blocks
+    U2 before = {0, 0};
+    for (int64_t t = threadIdx.x; t < b0; t += kThreads) {
+      const uint64_t *c = a.x[q] + t * il;
+      before = add2(before, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    }
+    U2 tot_before;
+    block_excl(before, &tot_before);
+    U2 mine = {0, 0};
+    for (int e = 0; e < kElems; e++) {
+      const int64_t t = t0 + e;
+      if (t >= a.L[q]) break;
+      const uint64_t *c = a.x[q] + t * il;
+      mine = add2(mine, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    }
+    U2 tot;
+    U2 run = add2(block_excl(mine, &tot), tot_before);
+    for (int e = 0; e < kElems; e++) {
+      const int64_t t = t0 + e;
+      if (t >= a.L[q]) break;
+      const uint64_t *c = a.x[q] + t * il;
+      run = add2(run, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+      uint64_t *P = a.P[q] + t * rec;
+      if (l < il) {
+        P[2 * l] = run.lo;
+        P[2 * l + 1] = run.hi;
+      } else {
+        P[2 * il] = run.lo;
+      }
+    }
+  }
+}
+
 // acc (ol limbs, mod 2^(64 ol)) += sign * (window sum of x over [lo, hi]),
 // from the per-limb prefix records.
 __device__ __forceinline__ void add_window(uint64_t *acc, int ol, const uint64_t *P, int il,
@@ -283,15 +329,21 @@ cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf
   a.P[0] = prefix;
   a.P[1] = prefix + lf * rec;
   a.bt = prefix + (lf + lg) * rec;
-  const unsigned nb = (unsigned)(a.nblocks[0] + a.nblocks[1]);
-  pref_block_totals<<<nb, kThreads, 0, s>>>(a);
-  pref_scan_totals<<<2, 64, 0, s>>>(a);
-  pref_apply<<<nb, kThreads, 0, s>>>(a);
+  int launches = 2;
+  if (lf <= kSmallL && lg <= kSmallL) {
+    pref_single<<<(unsigned)(a.nblocks[0] + a.nblocks[1]), kThreads, 0, s>>>(a);
+  } else {
+    const unsigned nb = (unsigned)(a.nblocks[0] + a.nblocks[1]);
+    pref_block_totals<<<nb, kThreads, 0, s>>>(a);
+    pref_scan_totals<<<2, 64, 0, s>>>(a);
+    pref_apply<<<nb, kThreads, 0, s>>>(a);
+    launches = 4;
+  }
   const int64_t lh = lf + lg - 1;
   int64_t grid = (lh + 127) / 128;
   if (grid > 152 * 32) grid = 152 * 32;
   signed_fix_kernel<<<(unsigned)grid, 128, 0, s>>>(h, ol, lf, lg, b, in_limbs, a.P[0], a.P[1]);
-  note_launches(4);
+  note_launches(launches);
   return cudaGetLastError();
 }
 

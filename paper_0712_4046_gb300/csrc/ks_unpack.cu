@@ -134,9 +134,170 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int
   }
 }
 
-cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs, int nruns,
-                         int64_t chain, const uint64_t *f, int64_t lf, const uint64_t *g,
-                         int64_t lg, int b, int in_limbs, int flip, cudaStream_t s) {
+// b <= 64: each coefficient is one 64-bit word; products are 128-bit and a
+// thread keeps a 192-bit running sum in three registers.
+__global__ void __launch_bounds__(kSeedThreads) seed_kernel64(uint32_t *seeds, int seed_words,
+                                                              SeedArgs a, const uint64_t *f,
+                                                              int64_t lf, const uint64_t *g,
+                                                              int64_t lg, int b, int in_limbs,
+                                                              int flip) {
+  __shared__ unsigned long long colsum[kMaxSeedWords];
+  int64_t sid = blockIdx.x;
+  int r = 0;
+  int64_t per_run = 2 * (a.run[0].nchains - 1);
+  while (r + 1 < a.nruns && sid >= per_run) {
+    sid -= per_run;
+    r++;
+    per_run = 2 * (a.run[r].nchains - 1);
+  }
+  const RecoverRun &R = a.run[r];
+  const int64_t c = sid / 2 + 1;
+  const int64_t i = c * a.chain - 1 + (sid & 1);
+  const int64_t k = R.kbase + R.kstride * i;
+  for (int w = threadIdx.x; w < seed_words; w += blockDim.x) colsum[w] = 0ull;
+  __syncthreads();
+  const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+  const uint64_t fl = flip ? (1ull << (b - 1)) : 0ull;
+  uint64_t a0 = 0, a1 = 0, a2 = 0;
+  int64_t t_lo = k - (lg - 1);
+  if (t_lo < 0) t_lo = 0;
+  const int64_t t_hi = k < lf - 1 ? k : lf - 1;
+  for (int64_t t = t_lo + threadIdx.x; t <= t_hi; t += blockDim.x) {
+    const uint64_t x = (f[t * in_limbs] & mask) ^ fl;
+    const uint64_t y = (g[(k - t) * in_limbs] & mask) ^ fl;
+    const uint64_t lo = x * y, hi = __umul64hi(x, y);
+    a0 += lo;
+    const uint64_t c1 = a0 < lo;
+    const uint64_t h1 = hi + c1;  // hi <= 2^64 - 2
+    a1 += h1;
+    a2 += a1 < h1;
+  }
+  const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
+                          (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
+#pragma unroll
+  for (int w = 0; w < 6; w++)
+    if (w < seed_words && w6[w]) atomicAdd(&colsum[w], (unsigned long long)w6[w]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t *out = seeds + (R.seed_base + sid) * seed_words;
+    unsigned long long carry = 0;
+    for (int w = 0; w < seed_words; w++) {
+      const unsigned long long v = colsum[w] + carry;
+      out[w] = (uint32_t)v;
+      carry = v >> 32;
+    }
+  }
+}
+
+// Blocked seeds, b <= 64: a CTA computes kSG consecutive seeds of one run.
+// For each chunk of kST indices t it stages f'_t and the window of g' those
+// seeds need in shared memory (the seeds' k differ by at most kSW - kST), so
+// every input word is read from L2 once per CTA rather than once per seed.
+// 16 threads per seed accumulate 192-bit sums over a strided part of the chunk.
+namespace {
+constexpr int kSG = 16;
+constexpr int kST = 512;
+constexpr int kSW = 2048;
+constexpr int64_t kSlice = 2048;  // indices t per CTA
+struct SeedBArgs {
+  RecoverRun run[2];
+  int nruns;
+  int64_t chain;
+  int64_t groups[2];
+};
+__device__ __forceinline__ int64_t seed_k(const RecoverRun &R, int64_t chain, int64_t sid) {
+  const int64_t c = sid / 2 + 1;
+  return R.kbase + R.kstride * (c * chain - 1 + (sid & 1));
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) seed_blocked64(unsigned long long *acc, SeedBArgs a,
+                                                      const uint64_t *f, int64_t lf,
+                                                      const uint64_t *g, int64_t lg, int b,
+                                                      int in_limbs, int flip) {
+  __shared__ uint64_t sf[kST];
+  __shared__ uint64_t sg[kSW];
+  __shared__ unsigned long long colsum[kSG][6];
+  int64_t gid = blockIdx.x;
+  int r = 0;
+  while (r + 1 < a.nruns && gid >= a.groups[r]) {
+    gid -= a.groups[r];
+    r++;
+  }
+  const RecoverRun &R = a.run[r];
+  const int64_t nseeds = 2 * (R.nchains - 1);
+  const int64_t sid0 = gid * kSG;
+  const int nS = (int)(nseeds - sid0 < kSG ? nseeds - sid0 : kSG);
+  const int tid = threadIdx.x;
+  const int sl = tid >> 4, sub = tid & 15;
+  for (int i = tid; i < kSG * 6; i += 256) (&colsum[0][0])[i] = 0ull;
+  const int64_t kmin = seed_k(R, a.chain, sid0);
+  const int64_t kmax = seed_k(R, a.chain, sid0 + nS - 1);
+  const int64_t kk = sl < nS ? seed_k(R, a.chain, sid0 + sl) : -1;
+  const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+  const uint64_t fl = flip ? (1ull << (b - 1)) : 0ull;
+  uint64_t a0 = 0, a1 = 0, a2 = 0;
+  // this CTA's slice of the t range
+  int64_t tlo = kmin - lg + 1 > 0 ? kmin - lg + 1 : 0;
+  int64_t thi = kmax < lf - 1 ? kmax : lf - 1;
+  const int64_t s_lo = tlo + (int64_t)blockIdx.y * kSlice;
+  const int64_t s_hi = s_lo + kSlice - 1 < thi ? s_lo + kSlice - 1 : thi;
+  for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
+    const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
+    const int64_t jlo = kmin - t0 - T + 1;
+    const int W = (int)(kmax - kmin + T);
+    __syncthreads();
+    for (int i = tid; i < T; i += 256) sf[i] = (f[(t0 + i) * in_limbs] & mask) ^ fl;
+    for (int i = tid; i < W; i += 256) {
+      const int64_t j = jlo + i;
+      sg[i] = (j >= 0 && j < lg) ? ((g[j * in_limbs] & mask) ^ fl) : 0ull;
+    }
+    __syncthreads();
+    if (kk >= 0) {
+      for (int i = sub; i < T; i += 16) {
+        const int64_t j = kk - (t0 + i);  // in [jlo, jlo + W) by construction
+        const uint64_t x = sf[i];
+        const uint64_t y = sg[j - jlo];
+        const uint64_t lo = x * y, hi = __umul64hi(x, y);
+        a0 += lo;
+        const uint64_t h1 = hi + (a0 < lo);
+        a1 += h1;
+        a2 += a1 < h1;
+      }
+    }
+  }
+  if (kk >= 0) {
+    const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
+                            (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
+#pragma unroll
+    for (int w = 0; w < 6; w++)
+      if (w6[w]) atomicAdd(&colsum[sl][w], (unsigned long long)w6[w]);
+  }
+  __syncthreads();
+  if (tid < nS * 6) {
+    const int sidx = tid / 6, w = tid % 6;
+    const unsigned long long v = colsum[sidx][w];
+    if (v) atomicAdd(acc + (R.seed_base + sid0 + sidx) * 6 + w, v);
+  }
+}
+
+// word sums (6 x 64-bit per seed) -> carried 32-bit seed words
+__global__ void __launch_bounds__(128) seed_finish(uint32_t *seeds, int seed_words,
+                                                   const unsigned long long *acc, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long carry = 0;
+  for (int w = 0; w < seed_words; w++) {
+    const unsigned long long v = (w < 6 ? acc[i * 6 + w] : 0ull) + carry;
+    seeds[i * seed_words + w] = (uint32_t)v;
+    carry = v >> 32;
+  }
+}
+
+cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
+                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
+                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs, int flip,
+                         cudaStream_t s) {
   SeedArgs a{};
   int64_t n = 0;
   for (int r = 0; r < nruns; r++) {
@@ -152,7 +313,33 @@ cudaError_t launch_seeds(uint32_t *seeds, int seed_words, const RecoverRun *runs
 #define KS_SEEDS(NW)                                                                        \
   seed_kernel<NW><<<grid, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b, \
                                                 in_limbs, flip)
-  if (nw <= 2)
+  // blocked path when the seeds of a group lie close enough together
+  bool blocked = b <= 64;
+  for (int r = 0; r < nruns && blocked; r++)
+    if (runs[r].kstride * (chain * (kSG / 2) + 1) + kST > kSW) blocked = false;
+  if (blocked) {
+    SeedBArgs sb{};
+    int64_t groups = 0;
+    for (int r = 0; r < nruns; r++) {
+      sb.run[r] = runs[r];
+      sb.groups[r] = (2 * (runs[r].nchains - 1) + kSG - 1) / kSG;
+      groups += sb.groups[r];
+    }
+    sb.nruns = nruns;
+    sb.chain = chain;
+    const int64_t lmin = lf < lg ? lf : lg;
+    // a group's t range is at most min(Lf, Lg) plus the spread of its k (< kSW)
+    const int64_t slices = (lmin + kSW + kSlice - 1) / kSlice;
+    cudaError_t e = cudaMemsetAsync(seed_acc, 0, (size_t)n * 6 * 8, s);
+    if (e != cudaSuccess) return e;
+    seed_blocked64<<<dim3((unsigned)groups, (unsigned)slices), 256, 0, s>>>(
+        seed_acc, sb, f, lf, g, lg, b, in_limbs, flip);
+    seed_finish<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(seeds, seed_words, seed_acc, n);
+    note_launches(1);
+  } else if (b <= 64)
+    seed_kernel64<<<grid, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b, in_limbs,
+                                                flip);
+  else if (nw <= 2)
     KS_SEEDS(2);
   else if (nw <= 4)
     KS_SEEDS(4);

@@ -15,6 +15,7 @@ from tests._gpu import assert_same, gpu_mul, random_case, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 VARIANTS = [1, 2, 3, 4]
+ENGINES = [1, 3]  # INT32 schoolbook, tensor cores
 
 
 @pytest.fixture(scope="module")
@@ -29,53 +30,62 @@ SHAPES = [(1, 1), (1, 5), (5, 1), (2, 2), (3, 4), (7, 7), (16, 15), (33, 64), (1
           (257, 300), (1000, 999), (2048, 1500)]
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("signed", [False, True])
 @pytest.mark.parametrize("b", [1, 2, 7, 31, 48, 63, 64, 65, 100, 128])
-def test_random_shapes(ks, variant, signed, b):
+def test_random_shapes(ks, engine, variant, signed, b):
     for i, (lf, lg) in enumerate(SHAPES):
         if b >= 100 and lf * lg > 300000:
             continue
         f, g = random_case(lf, lg, b, signed, 1000 * b + 10 * i + variant)
         want = oracle.mul(f, g, b, signed)
-        got = gpu_mul(ks, f, g, b, signed, variant, ks.ENGINE_SCHOOLBOOK)
-        assert_same(got, want, "variant %d b=%d signed=%d shape=%s" % (variant, b, signed,
-                                                                       (lf, lg)))
+        got = gpu_mul(ks, f, g, b, signed, variant, engine)
+        assert_same(got, want, "engine %d variant %d b=%d signed=%d shape=%s"
+                    % (engine, variant, b, signed, (lf, lg)))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("b", [200, 256, 511, 1024])
-def test_wide_coefficients(ks, variant, b):
+def test_wide_coefficients(ks, engine, variant, b):
     for signed in (False, True):
         for lf, lg in [(1, 1), (9, 4), (40, 41)]:
             f, g = random_case(lf, lg, b, signed, b + lf + 3 * variant + signed)
             want = oracle.mul(f, g, b, signed)
-            got = gpu_mul(ks, f, g, b, signed, variant, ks.ENGINE_SCHOOLBOOK)
-            assert_same(got, want, "variant %d b=%d signed=%d" % (variant, b, signed))
+            got = gpu_mul(ks, f, g, b, signed, variant, engine)
+            assert_same(got, want, "engine %d variant %d b=%d signed=%d"
+                        % (engine, variant, b, signed))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_extremes(ks, variant):
+def test_extremes(ks, engine, variant):
+    """All-maximal digits drive every exact accumulation to its bound (for the
+    tensor cores: fp32 partial sums of 16,516,096 < 2^24 per chunk)."""
     for b in (1, 8, 48, 64, 65):
-        for lf, lg in [(1, 1), (4, 4), (8, 9), (64, 64), (513, 200)]:
+        for lf, lg in [(1, 1), (4, 4), (8, 9), (64, 64), (513, 200), (1500, 1500)]:
             m = (1 << b) - 1
             f, g = gen.const_poly(lf, b, m), gen.const_poly(lg, b, m)
-            assert_same(gpu_mul(ks, f, g, b, False, variant), oracle.mul(f, g, b, False),
-                        "all-max b=%d" % b)
+            assert_same(gpu_mul(ks, f, g, b, False, variant, engine), oracle.mul(f, g, b, False),
+                        "all-max b=%d engine %d" % (b, engine))
             lo, hi = -(1 << (b - 1)), (1 << (b - 1)) - 1
             for a, c in [(lo, lo), (lo, hi), (hi, hi)]:
                 f, g = gen.const_poly(lf, b, a), gen.const_poly(lg, b, c)
-                assert_same(gpu_mul(ks, f, g, b, True, variant), oracle.mul(f, g, b, True),
-                            "signed extremes b=%d" % b)
+                assert_same(gpu_mul(ks, f, g, b, True, variant, engine),
+                            oracle.mul(f, g, b, True), "signed extremes b=%d engine %d"
+                            % (b, engine))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_zero_and_aliasing(ks, variant):
+def test_zero_and_aliasing(ks, engine, variant):
     b = 40
     z = np.zeros((50, 1), dtype=np.uint64)
     f, _ = random_case(50, 1, b, True, 5)
     for signed in (False, True):
-        assert_same(gpu_mul(ks, z, f, b, signed, variant), oracle.mul(z, f, b, signed), "zero")
+        assert_same(gpu_mul(ks, z, f, b, signed, variant, engine), oracle.mul(z, f, b, signed),
+                    "zero")
     # f aliasing g: the same device buffer on both sides
     tf = to_dev(f)
     h = ks.mul(tf, tf, b, True, variant)
