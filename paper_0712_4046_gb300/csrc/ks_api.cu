@@ -93,7 +93,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine) {
   if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
   if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
-  if (engine != KS_ENGINE_SCHOOLBOOK && engine != KS_ENGINE_TC) return KS_ENOTSUP;
+  if (engine != KS_ENGINE_SCHOOLBOOK && engine != KS_ENGINE_TC && engine != KS_ENGINE_NTT)
+    return KS_ENOTSUP;
   if (lf > ((int64_t)1 << 40) || lg > ((int64_t)1 << 40)) return KS_ERANGE;
   p = Plan();
   p.variant = variant;
@@ -137,8 +138,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   if (engine == KS_ENGINE_NTT) {
     int lg2 = 0;
     while (((int64_t)1 << lg2) < p.ncols) lg2++;
-    if (lg2 > 30) return KS_ERANGE;
-    if (colmax * 2.0 >= 4.0e18) return KS_ERANGE;  // CRT range of the two primes
+    if (lg2 > 27) return KS_ERANGE;                 // transform length <= 2^27
+    if (colmax * 2.0 >= 4.5e18) return KS_ERANGE;  // |C_k| < p1 p2 / 2 for the CRT
     p.ntt_log = lg2;
   }
   if (variant == KS_3 || variant == KS_4) {
@@ -199,7 +200,15 @@ int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engi
   int v = *variant;
   if (v == KS_AUTO) v = (lh >= 64) ? KS_4 : KS_1;
   int eng = *engine;
-  if (eng == KS_ENGINE_AUTO) eng = KS_ENGINE_TC;
+  if (eng == KS_ENGINE_AUTO) {
+    // 7-bit digit products below the cutoff run on the tensor cores, larger
+    // ones through the transform (quasi-linear)
+    const int e = ceil_log2(lf < lg ? lf : lg);
+    const int N = variant_N(v, b, e);
+    const double dA = ((double)N * (double)(lf - 1) + b) / 7.0;
+    const double dB = ((double)N * (double)(lg - 1) + b) / 7.0;
+    eng = (dA * dB <= 2.0e10) ? KS_ENGINE_TC : KS_ENGINE_NTT;
+  }
   *variant = v;
   *engine = eng;
   return KS_OK;

@@ -185,12 +185,21 @@ __global__ void __launch_bounds__(kThreads) pref_single(PrefArgs a) {
   const int64_t t0 = b0 + (int64_t)threadIdx.x * kElems;
   const int il = a.il, rec = 2 * il + 1;
   for (int l = 0; l <= il; l++) {
-    // sum of the preceding blocks
-    U2 before = {0, 0};
-    for (int64_t t = threadIdx.x; t < b0; t += kThreads) {
-      const uint64_t *c = a.x[q] + t * il;
-      before = add2(before, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    // sum of the preceding blocks (four independent partial sums per thread)
+    U2 bp[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int64_t t = threadIdx.x;
+    for (; t + 3 * kThreads < b0; t += 4 * kThreads) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const uint64_t *c = a.x[q] + (t + u * kThreads) * il;
+        bp[u] = add2(bp[u], U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+      }
     }
+    for (; t < b0; t += kThreads) {
+      const uint64_t *c = a.x[q] + t * il;
+      bp[0] = add2(bp[0], U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    }
+    const U2 before = add2(add2(bp[0], bp[1]), add2(bp[2], bp[3]));
     U2 tot_before;
     block_excl(before, &tot_before);
     U2 mine = {0, 0};

@@ -254,15 +254,39 @@ __global__ void __launch_bounds__(256) seed_blocked64(unsigned long long *acc, S
     }
     __syncthreads();
     if (kk >= 0) {
-      for (int i = sub; i < T; i += 16) {
-        const int64_t j = kk - (t0 + i);  // in [jlo, jlo + W) by construction
+      // four independent 192-bit partial sums keep several products in flight
+      uint64_t b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
+      const int base = (int)(kk - t0 - jlo);  // sg index of t = t0
+      int i = sub;
+      for (; i + 48 < T; i += 64) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const uint64_t x = sf[i + 16 * u];
+          const uint64_t y = sg[base - i - 16 * u];
+          const uint64_t lo = x * y, hi = __umul64hi(x, y);
+          b0[u] += lo;
+          const uint64_t h1 = hi + (b0[u] < lo);
+          b1[u] += h1;
+          b2[u] += b1[u] < h1;
+        }
+      }
+      for (; i < T; i += 16) {
         const uint64_t x = sf[i];
-        const uint64_t y = sg[j - jlo];
+        const uint64_t y = sg[base - i];
         const uint64_t lo = x * y, hi = __umul64hi(x, y);
-        a0 += lo;
-        const uint64_t h1 = hi + (a0 < lo);
-        a1 += h1;
-        a2 += a1 < h1;
+        b0[0] += lo;
+        const uint64_t h1 = hi + (b0[0] < lo);
+        b1[0] += h1;
+        b2[0] += b1[0] < h1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        a0 += b0[u];
+        const uint64_t c0 = a0 < b0[u];
+        const uint64_t m = b1[u] + c0;
+        const uint64_t c1 = m < c0;
+        a1 += m;
+        a2 += b2[u] + c1 + (a1 < m);
       }
     }
   }

@@ -15,7 +15,7 @@ from tests._gpu import assert_same, gpu_mul, random_case, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 VARIANTS = [1, 2, 3, 4]
-ENGINES = [1, 3]  # INT32 schoolbook, tensor cores
+ENGINES = [1, 2, 3]  # INT32 schoolbook, NTT, tensor cores
 
 
 @pytest.fixture(scope="module")
