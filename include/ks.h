@@ -168,10 +168,44 @@ typedef struct {
 } ks_problem;
 
 /*
- * Runs n independent products on `stream`.  probs is a HOST array.  Each
- * product's variant/engine may be KS_AUTO.  Asynchronous.
+ * Runs n independent products on `stream` as one batched launch sequence and
+ * returns when they are done (synchronous; it plans, allocates and frees a
+ * plan -- use the plan API below to reuse one).  probs is a HOST array of
+ * descriptors with DEVICE pointers.  Each product's variant and engine may
+ * be KS_AUTO.
  */
 int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream);
+
+/*
+ * Batched plans (no counterpart in the paper; its Sec. 1 remark that the
+ * sub-products are independent is what they exploit).  ks_plan_create plans
+ * n products (problem array on the HOST, device pointers inside), allocates
+ * one device workspace for all of them and uploads the per-kernel work
+ * descriptors.  ks_plan_execute issues one launch per phase for the whole
+ * batch on `stream` (asynchronous); the four sub-products of every four-point
+ * product are independent work items of one persistent tensor-core kernel.
+ * ks_plan_capture runs the plan once, then records its launches into a CUDA
+ * graph on `stream` (a non-default stream); later ks_plan_execute calls on
+ * that stream replay the graph.  The plan keeps the pointers it was created
+ * with: the inputs may change between executes, the buffers may not move.
+ * Dispatch modes choose variant and engine where a problem says KS_AUTO:
+ *   KS_DISPATCH_AUTO  the library's choice (cost table, then learned model)
+ *   KS_DISPATCH_KS1   always KS_1 (the standard substitution), engine auto
+ *   KS_DISPATCH_TABLE the autotuned table only
+ *   KS_DISPATCH_MLP   the learned cost model only
+ */
+typedef struct ks_plan ks_plan;
+enum { KS_DISPATCH_AUTO = 0, KS_DISPATCH_KS1 = 1, KS_DISPATCH_TABLE = 2, KS_DISPATCH_MLP = 3 };
+int ks_plan_create(ks_plan **plan, const ks_problem *probs, int64_t n, int dispatch_mode);
+int ks_plan_execute(ks_plan *plan, ks_stream_t stream);
+int ks_plan_capture(ks_plan *plan, ks_stream_t stream);
+/* Kernel launches of the last non-graph execute; device bytes the plan holds. */
+long long ks_plan_launches(const ks_plan *plan);
+int64_t ks_plan_workspace_bytes(const ks_plan *plan);
+/* The variant and engine the plan chose for product i. */
+int ks_plan_choice(const ks_plan *plan, int64_t i, int *variant, int *engine);
+/* Waits for the device, then frees the plan (NULL is ignored). */
+void ks_plan_destroy(ks_plan *plan);
 
 /* Waits for `stream`, then reports a pending device-side error (or KS_OK). */
 int ks_status_sync(ks_stream_t stream);

@@ -48,6 +48,15 @@ _sig("ks_mul_ex", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp, _i64,
 _sig("ks_mul_host", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp)
 _sig("ks_mul_mod", _ci, _vp, _vp, _i64, _vp, _i64, _u64, _ci, _vp)
 _sig("ks_mul_batch", _ci, ctypes.POINTER(KSProblem), _i64, _vp)
+_sig("ks_plan_create", _ci, ctypes.POINTER(_vp), ctypes.POINTER(KSProblem), _i64, _ci)
+_sig("ks_plan_execute", _ci, _vp, _vp)
+_sig("ks_plan_capture", _ci, _vp, _vp)
+_sig("ks_plan_launches", ctypes.c_longlong, _vp)
+_sig("ks_plan_workspace_bytes", _i64, _vp)
+_sig("ks_plan_choice", _ci, _vp, _i64, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
+_sig("ks_plan_destroy", None, _vp)
+
+DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
 _sig("ks_mul_static", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
 
 STATIC_SCRATCH_BYTES = 16 << 20
@@ -168,15 +177,59 @@ def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
                           _stream_ptr(stream)), "ks_mul_mod")
 
 
-def ks_mul_batch(problems, stream=None):
-    """problems: list of dicts with h, f, g (tensors), coeff_bits, is_signed, variant, engine."""
+def _problems(problems):
     arr = (KSProblem * len(problems))()
     for i, q in enumerate(problems):
         arr[i] = KSProblem(_dptr(q["h"]).value, _dptr(q["f"]).value, _dptr(q["g"]).value,
                            q["f"].shape[0], q["g"].shape[0], q["coeff_bits"],
                            int(q["is_signed"]), q.get("variant", KS_AUTO),
                            q.get("engine", ENGINE_AUTO))
-    _check(lib.ks_mul_batch(arr, len(problems), _stream_ptr(stream)), "ks_mul_batch")
+    return arr
+
+
+def ks_mul_batch(problems, stream=None):
+    """problems: list of dicts with h, f, g (tensors), coeff_bits, is_signed, variant, engine."""
+    _check(lib.ks_mul_batch(_problems(problems), len(problems), _stream_ptr(stream)),
+           "ks_mul_batch")
+
+
+class Plan:
+    """A batched plan (ks_plan_*): create once, execute many times."""
+
+    def __init__(self, problems, dispatch=DISPATCH_AUTO):
+        self._keep = problems  # the tensors must outlive the plan
+        self.n = len(problems)
+        self.ptr = ctypes.c_void_p()
+        _check(lib.ks_plan_create(ctypes.byref(self.ptr), _problems(problems), self.n, dispatch),
+               "ks_plan_create")
+
+    def execute(self, stream=None):
+        _check(lib.ks_plan_execute(self.ptr, _stream_ptr(stream)), "ks_plan_execute")
+
+    def capture(self, stream):
+        _check(lib.ks_plan_capture(self.ptr, _stream_ptr(stream)), "ks_plan_capture")
+
+    def launches(self) -> int:
+        return int(lib.ks_plan_launches(self.ptr))
+
+    def workspace_bytes(self) -> int:
+        return int(lib.ks_plan_workspace_bytes(self.ptr))
+
+    def choice(self, i):
+        v, e = _ci(0), _ci(0)
+        _check(lib.ks_plan_choice(self.ptr, i, ctypes.byref(v), ctypes.byref(e)), "ks_plan_choice")
+        return v.value, e.value
+
+    def close(self):
+        if self.ptr:
+            lib.ks_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def status_sync(stream=None) -> None:

@@ -58,7 +58,7 @@ PhaseTimer::~PhaseTimer() {
 // device-side status word (0 = fine), one per device context
 __device__ int g_status_word;
 
-static int *status_ptr() {
+int *status_ptr() {
   static std::mutex mu;
   static int *ptrs[64] = {nullptr};
   int dev = 0;
@@ -214,6 +214,14 @@ int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engi
   return KS_OK;
 }
 
+// dispatch modes of the batched plans: 0 the library's choice, 1 KS1 wherever
+// the variant is left to the library
+int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *variant,
+                int *engine) {
+  if (mode == KS_DISPATCH_KS1 && *variant == KS_AUTO) *variant = KS_1;
+  return choose(lf, lg, b, is_signed, variant, engine);
+}
+
 // --------------------------------------------------------------- execution
 // h: exact product destination (Lh x out_limbs).  ws: workspace of >= p.total.
 static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_t *g, char *ws,
@@ -298,10 +306,10 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   const int ol = p.out_limbs;
   if (p.variant == KS_1) {
     PhaseTimer t(s, PH_UNPACK);
-    KS_CUDA(launch_unpack(h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N, s));
+    KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N}, s));
   } else if (p.variant == KS_2) {
     PhaseTimer t(s, PH_UNPACK);
-    KS_CUDA(launch_unpack(h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N, s));
+    KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N}, s));
   } else {
     RecoverRun runs[2];
     const int64_t N = p.N;
@@ -545,23 +553,15 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
 
 int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream) {
   if (n < 0 || (n > 0 && probs == nullptr)) return KS_EINVAL;
-  for (int64_t i = 0; i < n; i++) {
-    const ks_problem &q = probs[i];
-    int v = q.variant, eng = q.engine;
-    int rc = choose(q.len_f, q.len_g, q.coeff_bits, q.is_signed, &v, &eng);
-    if (rc != KS_OK) return rc;
-    Plan p;
-    rc = make_plan(p, q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, eng);
-    if (rc != KS_OK) return rc;
-    rc = check_args(q.h, q.f, q.len_f, q.g, q.len_g, q.coeff_bits, p.out_limbs);
-    if (rc != KS_OK) return rc;
-    void *ws = nullptr;
-    rc = cached_buffer(0, static_cast<cudaStream_t>(stream), p.total, &ws);
-    if (rc != KS_OK) return rc;
-    rc = run_plan(p, q.h, q.f, q.g, static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
-    if (rc != KS_OK) return rc;
-  }
-  return KS_OK;
+  if (n == 0) return KS_OK;
+  ks_plan *plan = nullptr;
+  int rc = ks_plan_create(&plan, probs, n, KS_DISPATCH_AUTO);
+  if (rc != KS_OK) return rc;
+  rc = ks_plan_execute(plan, stream);
+  if (rc == KS_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    rc = KS_ECUDA;
+  ks_plan_destroy(plan);
+  return rc;
 }
 
 int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,

@@ -1,0 +1,494 @@
+// Batched executor: many independent products (uneven lengths, bit sizes,
+// variants and engines) in one launch sequence.
+//
+// ks_plan_create plans every product (variant and engine per the dispatch
+// mode), carves one workspace for all of them, and scatters each product's
+// kernel descriptors into per-kernel arrays in device memory together with
+// the prefix sums of their block counts.  ks_plan_execute then issues one
+// launch per phase for the whole batch -- pack, tensor-core operand layout,
+// the INT32 and tensor-core products (the tensor-core kernel is persistent
+// over the work items of every sub-product of every product, so the four
+// sub-products of a four-point product are independent items), carry
+// normalization, unpack, seeds and reconstruction per word-size class, and the
+// signed correction -- about fifteen launches whatever the batch size.
+// Products routed to the transform engine (large ones) run their transform
+// launches individually inside the same sequence.  The first execute on a
+// stream captures the sequence into a CUDA graph; later executes replay it.
+#include <mutex>
+#include <stdlib.h>
+#include <string.h>
+#include <vector>
+
+#include "ks_internal.cuh"
+#include "ks_src.cuh"
+
+namespace ks {
+
+int *status_ptr();
+int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *variant,
+                int *engine);
+
+struct ZeroArgs {
+  uint64_t *p;
+  int64_t n;  // 64-bit words
+};
+
+template <class Src>
+__global__ void __launch_bounds__(256) zero_kernel(Src src) {
+  int64_t local;
+  const ZeroArgs &a = src.locate(blockIdx.x, local);
+  const int64_t i = local * 256 + threadIdx.x;
+  if (i < a.n) a.p[i] = 0ull;
+}
+
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// one per-kernel descriptor list: host vector + block counts, then uploaded
+template <class T>
+struct List {
+  std::vector<T> v;
+  std::vector<int64_t> prefix{0};
+  T *d = nullptr;
+  int64_t *dprefix = nullptr;
+  void add(const T &x, int64_t blocks) {
+    v.push_back(x);
+    prefix.push_back(prefix.back() + blocks);
+  }
+  int n() const { return (int)v.size(); }
+  int64_t blocks() const { return prefix.back(); }
+  size_t bytes() const { return align256(v.size() * sizeof(T)) + align256(prefix.size() * 8); }
+  void place(char *&hbase, char *&dbase) {
+    d = reinterpret_cast<T *>(dbase);
+    memcpy(hbase, v.data(), v.size() * sizeof(T));
+    hbase += align256(v.size() * sizeof(T));
+    dbase += align256(v.size() * sizeof(T));
+    dprefix = reinterpret_cast<int64_t *>(dbase);
+    memcpy(hbase, prefix.data(), prefix.size() * 8);
+    hbase += align256(prefix.size() * 8);
+    dbase += align256(prefix.size() * 8);
+  }
+};
+
+struct NttJob {
+  Product prods[4];
+  int nprod, log_n, d;
+  char *scratch;
+};
+struct SingleJob {  // products whose signed correction needs the long-prefix path
+  uint64_t *h;
+  int ol;
+  const uint64_t *f, *g;
+  int64_t lf, lg;
+  int b, il;
+  uint64_t *prefix;
+};
+}  // namespace
+
+}  // namespace ks
+
+struct ks_plan {
+  int64_t n = 0;
+  std::vector<ks::Plan> plans;
+  std::vector<ks_problem> probs;
+  char *ws = nullptr;       // device workspace of all products
+  size_t ws_bytes = 0;
+  char *desc = nullptr;     // device descriptor arrays
+  char *hdesc = nullptr;    // pinned host copy
+  size_t desc_bytes = 0;
+  ks::List<ks::ZeroArgs> zero;
+  ks::List<ks::PackArgs> pack;
+  ks::List<ks::TcPackArgs> tcpack;
+  ks::List<ks::SchoolArgs> school;
+  ks::List<ks::TcArgs> tc;
+  ks::List<ks::NormArgs> norm_tiles, norm_jobs;
+  ks::List<ks::UnpackArgs> unpack;
+  ks::List<ks::SeedBArgs> seedb, seedb_finish;
+  ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
+  ks::List<ks::RecoverArgs> recover[3];
+  ks::List<ks::PrefArgs> pref;
+  ks::List<ks::FixArgs> fix;
+  std::vector<ks::NttJob> ntt;
+  std::vector<ks::SingleJob> singles;
+  int64_t tc_items = 0;
+  long long launches = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int device = 0;
+};
+
+namespace ks {
+namespace {
+int seed_kind_index(int kind) {
+  switch (kind) {
+    case 2: return 0;
+    case 102: return 1;
+    case 104: return 2;
+    case 108: return 3;
+    case 116: return 4;
+    case 132: return 5;
+    case 164: return 6;
+  }
+  return -1;
+}
+const int kSeedKinds[7] = {2, 102, 104, 108, 116, 132, 164};
+
+#define KS_TRY(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return e_;                 \
+  } while (0)
+
+cudaError_t issue(ks_plan *P, cudaStream_t s) {
+  if (P->zero.n()) {
+    zero_kernel<Many<ZeroArgs>><<<(unsigned)P->zero.blocks(), 256, 0, s>>>(
+        Many<ZeroArgs>{P->zero.d, P->zero.dprefix, P->zero.n()});
+    note_launches(1);
+    KS_TRY(cudaGetLastError());
+  }
+  if (P->pack.n())
+    KS_TRY(launch_pack_batch(P->pack.d, P->pack.dprefix, P->pack.n(), P->pack.blocks(), s));
+  if (P->tcpack.n())
+    KS_TRY(launch_tc_pack_batch(P->tcpack.d, P->tcpack.dprefix, P->tcpack.n(),
+                                P->tcpack.blocks(), s));
+  if (P->school.n())
+    KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
+                                   P->school.blocks(), s));
+  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_items, s));
+  for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
+  if (P->norm_tiles.n())
+    KS_TRY(launch_normalize_batch(P->norm_tiles.d, P->norm_tiles.dprefix, P->norm_jobs.dprefix,
+                                  P->norm_tiles.n(), P->norm_tiles.blocks(),
+                                  P->norm_jobs.blocks(), s));
+  if (P->unpack.n())
+    KS_TRY(launch_unpack_batch(P->unpack.d, P->unpack.dprefix, P->unpack.n(),
+                               P->unpack.blocks(), s));
+  if (P->seedb.n())
+    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb_finish.dprefix,
+                                      P->seedb.n(), P->seedb.blocks(),
+                                      P->seedb_finish.blocks(), s));
+  for (int i = 0; i < 7; i++)
+    if (P->seedk[i].n())
+      KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
+                                     P->seedk[i].n(), P->seedk[i].blocks(), s));
+  for (int c = 0; c < 3; c++)
+    if (P->recover[c].n())
+      KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
+                                  P->recover[c].n(), P->recover[c].blocks(), s));
+  if (P->pref.n())
+    KS_TRY(launch_signed_batch(P->pref.d, P->pref.dprefix, P->fix.d, P->fix.dprefix, P->pref.n(),
+                               P->pref.blocks(), P->fix.blocks(), s));
+  for (auto &j : P->singles)
+    KS_TRY(launch_signed_fix(j.h, j.ol, j.f, j.lf, j.g, j.lg, j.b, j.il, j.prefix, s));
+  return cudaSuccess;
+}
+}  // namespace
+
+// Fills the descriptor lists of one product (same launches as the single path).
+static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws, int *status) {
+  int32_t *dig = reinterpret_cast<int32_t *>(ws + p.off_digits);
+  int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
+  uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
+  uint8_t *agg = reinterpret_cast<uint8_t *>(ws + p.off_agg);
+  int8_t *cin = reinterpret_cast<int8_t *>(ws + p.off_cin);
+  uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
+  static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
+  static const int kSig[5][4] = {{1}, {1}, {1, -1}, {1, 1}, {1, -1, 1, -1}};
+  PackArgs pa{};
+  pa.nops = 2 * p.nprod;
+  pa.N = p.N;
+  pa.b = p.b;
+  pa.d = p.d;
+  pa.in_limbs = p.in_limbs;
+  pa.flip = p.is_signed;
+  Product prods[4];
+  for (int k = 0; k < p.nprod; k++) {
+    int32_t *A = dig + (int64_t)k * (p.nA + p.nB);
+    int32_t *B = A + p.nA;
+    pa.op[2 * k] = PackOp{q.f, p.lf, kRev[p.variant][k], kSig[p.variant][k], A, p.nA};
+    pa.op[2 * k + 1] = PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB};
+    prods[k] = Product{A, p.nA, B, p.nB, cols + (int64_t)k * p.ncols};
+  }
+  if (p.engine == KS_ENGINE_TC) {
+    TcPackArgs ta;
+    int64_t blocks;
+    make_tc_pack_args(pa, p.tg, p.nprod, ws + p.off_digits, ta, blocks);
+    P->tcpack.add(ta, blocks);
+    const int64_t nz = (int64_t)p.nprod * p.ncols;
+    P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nz}, (nz + 255) / 256);
+  } else {
+    P->pack.add(pa, pack_blocks(pa));
+    if (p.engine == KS_ENGINE_SCHOOLBOOK) {
+      SchoolArgs sa;
+      if (make_school_args(prods, p.nprod, sa) != 0) return KS_EINVAL;
+      P->school.add(sa, sa.block_prefix[p.nprod]);
+      const int64_t nz = (int64_t)p.nprod * p.ncols;
+      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nz}, (nz + 255) / 256);
+    } else {
+      NttJob j{};
+      for (int k = 0; k < p.nprod; k++) j.prods[k] = prods[k];
+      j.nprod = p.nprod;
+      j.log_n = p.ntt_log;
+      j.d = p.d;
+      j.scratch = ws + p.off_ntt;
+      P->ntt.push_back(j);
+    }
+  }
+  NormJob jobs[4];
+  auto job = [&](int i, int c1, int c2, int sigma) {
+    jobs[i].c1 = cols + (int64_t)c1 * p.ncols;
+    jobs[i].n1 = p.ncols;
+    jobs[i].c2 = c2 >= 0 ? cols + (int64_t)c2 * p.ncols : nullptr;
+    jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
+    jobs[i].sigma = sigma;
+    jobs[i].out = words + (int64_t)i * p.nwords;
+    jobs[i].agg = agg + (int64_t)i * p.ntiles;
+    jobs[i].cin = cin + (int64_t)i * p.ntiles;
+  };
+  switch (p.variant) {
+    case KS_1: job(0, 0, -1, 1); break;
+    case KS_2: job(0, 0, 1, 1); job(1, 0, 1, -1); break;
+    case KS_3: job(0, 0, -1, 1); job(1, 1, -1, 1); break;
+    case KS_4: job(0, 0, 1, 1); job(1, 0, 1, -1); job(2, 2, 3, 1); job(3, 2, 3, -1); break;
+  }
+  NormArgs na;
+  if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
+  P->norm_tiles.add(na, (int64_t)p.nnorm * p.ntiles);
+  P->norm_jobs.add(na, p.nnorm);
+  const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
+                 *V3 = words + 3 * p.nwords;
+  const int ol = p.out_limbs;
+  if (p.variant == KS_1 || p.variant == KS_2) {
+    UnpackArgs ua = p.variant == KS_1
+                        ? UnpackArgs{q.h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N}
+                        : UnpackArgs{q.h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N};
+    P->unpack.add(ua, unpack_blocks(ua));
+  } else {
+    RecoverRun runs[2];
+    const int64_t N = p.N;
+    if (p.variant == KS_3) {
+      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
+    } else {
+      const bool odd = (p.lh & 1) == 1;
+      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
+                           p.nchains[0], seeds, 0};
+      if (p.nruns > 1)
+        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
+                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
+    }
+    SeedPlan sp;
+    if (make_seed_plan(seeds, p.seed_words,
+                       reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs, p.nruns,
+                       p.chain, q.f, p.lf, q.g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
+      return KS_ERANGE;
+    if (sp.kind == 1) {
+      P->seedb.add(sp.bl, sp.blocks);
+      P->seedb_finish.add(sp.bl, sp.finish_blocks);
+      const int64_t nz = sp.nseeds * 6;
+      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(sp.bl.acc), nz}, (nz + 255) / 256);
+    } else if (sp.kind != 0) {
+      const int i = seed_kind_index(sp.kind);
+      if (i < 0) return KS_ERANGE;
+      P->seedk[i].add(sp.a, sp.blocks);
+    }
+    RecoverArgs ra;
+    int64_t blocks;
+    if (make_recover_args(q.h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words, status,
+                          ra, blocks) != 0)
+      return KS_ERANGE;
+    P->recover[recover_class(p.M) - 1].add(ra, blocks);
+  }
+  if (p.is_signed) {
+    PrefArgs pr;
+    FixArgs fx;
+    int64_t pb, fb;
+    uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
+    if (make_signed_args(q.h, ol, q.f, p.lf, q.g, p.lg, p.b, p.in_limbs, prefix, pr, fx, pb, fb)) {
+      P->pref.add(pr, pb);
+      P->fix.add(fx, fb);
+    } else {
+      P->singles.push_back(SingleJob{q.h, ol, q.f, q.g, p.lf, p.lg, p.b, p.in_limbs, prefix});
+    }
+  }
+  return KS_OK;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispatch_mode) {
+  if (out == nullptr || n < 0 || (n > 0 && probs == nullptr)) return KS_EINVAL;
+  *out = nullptr;
+  ks_plan *P = new (std::nothrow) ks_plan();
+  if (P == nullptr) return KS_ENOMEM;
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return KS_ECUDA;
+  }
+  P->n = n;
+  P->plans.resize(n);
+  P->probs.assign(probs, probs + n);
+  std::vector<size_t> offs(n);
+  size_t total = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const ks_problem &q = probs[i];
+    if (!q.h || !q.f || !q.g) {
+      delete P;
+      return KS_EINVAL;
+    }
+    int v = q.variant, e = q.engine;
+    int rc = choose_mode(q.len_f, q.len_g, q.coeff_bits, q.is_signed, dispatch_mode, &v, &e);
+    if (rc == KS_OK) rc = make_plan(P->plans[i], q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e);
+    if (rc != KS_OK) {
+      delete P;
+      return rc;
+    }
+    offs[i] = total;
+    total += align256(P->plans[i].total);
+  }
+  P->ws_bytes = total < 256 ? 256 : total;
+  if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+    delete P;
+    return KS_ENOMEM;
+  }
+  int *status = status_ptr();
+  // tensor-core work items: one chunk granularity for the whole batch
+  int64_t tc_chunks_total = 0;
+  for (int64_t i = 0; i < n; i++)
+    if (P->plans[i].engine == KS_ENGINE_TC)
+      tc_chunks_total += tc_chunks(P->plans[i].tg, P->plans[i].nprod, P->plans[i].ks);
+  const int cpi = tc_batch_chunks_per_item(tc_chunks_total);
+  for (int64_t i = 0; i < n; i++) {
+    const Plan &p = P->plans[i];
+    char *ws = P->ws + offs[i];
+    int rc = add_product(P, p, probs[i], ws, status);
+    if (rc == KS_OK && p.engine == KS_ENGINE_TC) {
+      TcArgs ta;
+      int64_t *C[4];
+      for (int k = 0; k < p.nprod; k++)
+        C[k] = reinterpret_cast<int64_t *>(ws + p.off_cols) + (int64_t)k * p.ncols;
+      make_tc_args(p.tg, p.nprod, p.ks, ws + p.off_digits, C, status, cpi, ta);
+      P->tc.add(ta, ta.item_prefix[p.nprod]);
+    }
+    if (rc != KS_OK) {
+      cudaFree(P->ws);
+      delete P;
+      return rc;
+    }
+  }
+  P->tc_items = P->tc.blocks();
+  // descriptor arrays: one device allocation, filled from a pinned host copy
+  size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
+              P->tc.bytes() + P->norm_tiles.bytes() + P->norm_jobs.bytes() + P->unpack.bytes() +
+              P->seedb.bytes() + P->seedb_finish.bytes() + P->pref.bytes() + P->fix.bytes();
+  for (int i = 0; i < 7; i++) db += P->seedk[i].bytes();
+  for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
+  P->desc_bytes = db;
+  if (cudaMalloc(&P->desc, db) != cudaSuccess || cudaMallocHost(&P->hdesc, db) != cudaSuccess) {
+    ks_plan_destroy(P);
+    return KS_ENOMEM;
+  }
+  char *h = P->hdesc, *d = P->desc;
+  P->zero.place(h, d);
+  P->pack.place(h, d);
+  P->tcpack.place(h, d);
+  P->school.place(h, d);
+  P->tc.place(h, d);
+  P->norm_tiles.place(h, d);
+  P->norm_jobs.place(h, d);
+  // both normalization lists describe the same jobs; use the first array
+  P->norm_jobs.d = P->norm_tiles.d;
+  P->unpack.place(h, d);
+  P->seedb.place(h, d);
+  P->seedb_finish.place(h, d);
+  P->seedb_finish.d = P->seedb.d;
+  for (int i = 0; i < 7; i++) P->seedk[i].place(h, d);
+  for (int c = 0; c < 3; c++) P->recover[c].place(h, d);
+  P->pref.place(h, d);
+  P->fix.place(h, d);
+  if (cudaMemcpy(P->desc, P->hdesc, db, cudaMemcpyHostToDevice) != cudaSuccess) {
+    ks_plan_destroy(P);
+    return KS_ECUDA;
+  }
+  *out = P;
+  return KS_OK;
+}
+
+int ks_plan_execute(ks_plan *P, ks_stream_t stream) {
+  if (P == nullptr) return KS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return KS_EINVAL;
+  const long long before = ks_launch_count();
+  if (P->graph != nullptr && P->graph_stream == s) {
+    if (cudaGraphLaunch(P->graph, s) != cudaSuccess) return KS_ECUDA;
+    return KS_OK;
+  }
+  cudaError_t e = issue(P, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KS_ENOMEM : KS_ECUDA;
+  P->launches = ks_launch_count() - before;
+  return KS_OK;
+}
+
+int ks_plan_capture(ks_plan *P, ks_stream_t stream) {
+  if (P == nullptr) return KS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (s == nullptr) return KS_EINVAL;  // the legacy stream cannot be captured
+  if (P->graph != nullptr) {
+    cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
+  }
+  // kernels with large shared memory and the transform tables are set up
+  // by one plain execution first
+  int rc = ks_plan_execute(P, stream);
+  if (rc != KS_OK) return rc;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return KS_ECUDA;
+  cudaError_t e = issue(P, s);
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    return KS_ECUDA;
+  }
+  e = cudaGraphInstantiate(&P->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    P->graph = nullptr;
+    return KS_ECUDA;
+  }
+  P->graph_stream = s;
+  return KS_OK;
+}
+
+long long ks_plan_launches(const ks_plan *P) { return P ? P->launches : -1; }
+
+int64_t ks_plan_workspace_bytes(const ks_plan *P) {
+  return P ? (int64_t)(P->ws_bytes + P->desc_bytes) : -1;
+}
+
+int ks_plan_choice(const ks_plan *P, int64_t i, int *variant, int *engine) {
+  if (P == nullptr || i < 0 || i >= P->n || !variant || !engine) return KS_EINVAL;
+  *variant = P->plans[i].variant;
+  *engine = P->plans[i].engine;
+  return KS_OK;
+}
+
+void ks_plan_destroy(ks_plan *P) {
+  if (P == nullptr) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  cudaDeviceSynchronize();
+  if (P->graph) cudaGraphExecDestroy(P->graph);
+  if (P->ws) cudaFree(P->ws);
+  if (P->desc) cudaFree(P->desc);
+  if (P->hdesc) cudaFreeHost(P->hdesc);
+  cudaSetDevice(cur);
+  delete P;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <cuda_fp16.h>
 
 #include "../../include/ks.h"
 
@@ -83,6 +84,9 @@ struct PackArgs {
 // Signed digits of each evaluation (Sec. 3.1-3.4 evaluations at +-2^N and
 // the reversed polynomial), `d` bits per digit position.
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
+int64_t pack_blocks(const PackArgs &a);
+cudaError_t launch_pack_batch(const PackArgs *d, const int64_t *prefix, int n, int64_t blocks,
+                              cudaStream_t s);
 
 struct Product {
   const int32_t *A;
@@ -94,6 +98,16 @@ struct Product {
 
 cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s);
 
+struct SchoolArgs {
+  Product p[4];
+  int nprod;
+  int64_t block_prefix[5];
+  int64_t ichunks[4];
+};
+int make_school_args(const Product *prods, int nprod, SchoolArgs &a);  // 0 on success
+cudaError_t launch_schoolbook_batch(const SchoolArgs *d, const int64_t *prefix, int n,
+                                    int64_t blocks, cudaStream_t s);
+
 // Tensor-core engine (tcgen05, kind::f16): fp16 operand layouts, then the MMA kernel.
 void tc_geometry(int64_t nA, int64_t nB, TcGeom &g);
 size_t tc_operand_bytes(const TcGeom &g);
@@ -101,6 +115,45 @@ cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char 
                            cudaStream_t s);
 cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
                                int64_t *const *C, int *status, cudaStream_t s);
+struct TcProduct {
+  const __half *Araw;  // raw A digits, offset by 127 (index x holds digit x - 127)
+  int64_t nAraw;
+  const __half *BRT;
+  int64_t rows;
+  int64_t dmax, R, T;  // largest delta, rows of B, tiles
+  int64_t items_per_tile;
+  int ks;
+  int64_t *C;
+  int64_t ncols;
+};
+
+struct TcArgs {
+  TcProduct p[4];
+  int nprod;
+  int64_t item_prefix[5];
+  int chunks_per_item;
+  int *status;
+};
+
+struct TcPackArgs {
+  PackOp op[kMaxOperands];
+  int nprod;
+  int N, b, in_limbs, flip;
+  __half *Araw[4];
+  __half *BRT[4];
+  int64_t nAraw, rows, R, nA, nB;
+};
+
+void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
+                       TcPackArgs &a, int64_t &blocks);
+cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int n,
+                                 int64_t blocks, cudaStream_t s);
+int64_t tc_chunks(const TcGeom &g, int nprod, const int *ks);
+int tc_batch_chunks_per_item(int64_t total_chunks);
+void make_tc_args(const TcGeom &g, int nprod, const int *ks, char *base, int64_t *const *C,
+                  int *status, int cpi, TcArgs &a);
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t items,
+                            cudaStream_t s);
 
 // NTT engine: column sums of each product by a two-prime transform + CRT.
 size_t ntt_workspace_bytes(int log_n, int nprod);
@@ -122,11 +175,34 @@ struct NormJob {
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
                              int64_t ntiles, cudaStream_t s);
 
+struct NormArgs {
+  NormJob job[4];
+  int njobs;
+  int d;
+  int64_t nwords;
+  int64_t ntiles;
+};
+int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
+                   NormArgs &a);
+cudaError_t launch_normalize_batch(const NormArgs *d, const int64_t *prefix_tiles,
+                                   const int64_t *prefix_jobs, int n, int64_t tiles,
+                                   int64_t jobs, cudaStream_t s);
+
 // KS1 / KS2 unpack: h'_k = bits [off + kN, off + kN + width) of V (k even) or
 // V_odd (k odd).
-cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
-                          const uint32_t *V_odd, int64_t nwords, int64_t off,
-                          int64_t N, int width, cudaStream_t s);
+struct UnpackArgs {
+  uint64_t *h;
+  int ol;
+  int64_t lh;
+  const uint32_t *V;
+  const uint32_t *V_odd;
+  int64_t nwords, off, N;
+  int width;
+};
+cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s);
+int64_t unpack_blocks(const UnpackArgs &a);
+cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int n,
+                                int64_t blocks, cudaStream_t s);
 
 struct RecoverRun {
   const uint32_t *Vf;
@@ -141,17 +217,94 @@ struct RecoverRun {
 };
 
 // Exact coefficients h'_k (biased, unsigned) for the chain starts.
+struct SeedArgs {
+  RecoverRun run[2];
+  int nruns;
+  int64_t chain;
+  uint32_t *seeds;
+  int seed_words;
+  const uint64_t *f, *g;
+  int64_t lf, lg;
+  int b, in_limbs, flip;
+};
+struct SeedBArgs {  // blocked path (b <= 64): groups x t-slices, 64-bit word sums
+  RecoverRun run[2];
+  int nruns;
+  int64_t chain;
+  int64_t groups[2];
+  int64_t slices, nseeds;
+  unsigned long long *acc;
+  uint32_t *seeds;
+  int seed_words;
+  const uint64_t *f, *g;
+  int64_t lf, lg;
+  int b, in_limbs, flip;
+};
+struct SeedPlan {
+  int kind = 0;  // 0 none, 1 blocked, 2 one 64-bit word, 100 + words: templated
+  SeedArgs a;
+  SeedBArgs bl;
+  int64_t blocks = 0, finish_blocks = 0, nseeds = 0;
+};
 // seed_acc: scratch of 6 64-bit words per seed (the b <= 64 blocked path).
+int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
+                   const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
+                   const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp);
+cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s);
 cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
                          const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
                          int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs,
                          int flip, cudaStream_t s);
+cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks,
+                                       const int64_t *prefix_finish, int n, int64_t blocks,
+                                       int64_t finish_blocks, cudaStream_t s);
+cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
+                                    int64_t blocks, cudaStream_t s);
 
+struct RecoverArgs {
+  RecoverRun run[2];
+  int nruns;
+  int64_t nwords;
+  int M;
+  int64_t chain;
+  int seed_words;
+  uint64_t *h;
+  int ol;
+  int *status;
+};
+int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
+                      int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,
+                      int64_t &blocks);
+int recover_class(int M);
 cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
                            int64_t nwords, int M, int64_t chain, int seed_words,
                            int *status, cudaStream_t s);
+cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
+                                 int64_t blocks, cudaStream_t s);
 
 // Signed inputs: h_k = h'_k - 2^(b-1) (W_f,k + W_g,k) - 2^(2b-2) cnt_k mod 2^(64 ol).
+struct PrefArgs {
+  const uint64_t *x[2];
+  int64_t L[2];
+  int64_t nblocks[2];
+  int il;
+  uint64_t *P[2];    // per element: il x (lo, hi), then the negative count
+  uint64_t *bt;      // per block: the same record, block totals -> exclusive offsets
+};
+struct FixArgs {
+  uint64_t *h;
+  int ol;
+  int64_t lf, lg;
+  int b, il;
+  const uint64_t *pf, *pg;
+};
+// true when the single-launch prefix applies (both lengths <= 2^16)
+bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
+                      int64_t lg, int b, int in_limbs, uint64_t *prefix, PrefArgs &a,
+                      FixArgs &fx, int64_t &pref_blocks, int64_t &fix_blocks);
+cudaError_t launch_signed_batch(const PrefArgs *pa, const int64_t *pref_prefix,
+                                const FixArgs *fa, const int64_t *fix_prefix, int n,
+                                int64_t pref_blocks, int64_t fix_blocks, cudaStream_t s);
 cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
                               const uint64_t *g, int64_t lg, int b, int in_limbs,
                               uint64_t *prefix, cudaStream_t s);

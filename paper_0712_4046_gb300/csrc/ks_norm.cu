@@ -19,6 +19,7 @@
 //     parallel prefix: warp shuffles, then the block, then the tiles (one
 //     tile = 512 words per CTA), then a second pass applies them.
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
@@ -27,14 +28,6 @@ constexpr int kThreads = 128;
 constexpr int kWPT = 4;                     // words per thread
 constexpr int kTileWords = kThreads * kWPT; // words per tile
 constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
-
-struct NormArgs {
-  NormJob job[4];
-  int njobs;
-  int d;
-  int64_t nwords;
-  int64_t ntiles;
-};
 
 // carry-transfer function: 2 bits per input carry c in {-1,0,1}, value c'+1
 __device__ __forceinline__ int apply_fn(uint32_t f, int c) {
@@ -123,9 +116,12 @@ __device__ uint32_t block_exclusive(uint32_t v, uint32_t *total) {
   return compose(excl, wpre);
 }
 
-__global__ void __launch_bounds__(kThreads) norm_aggregate(NormArgs a) {
-  const NormJob &J = a.job[blockIdx.y];
-  const int64_t tile = blockIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(kThreads) norm_aggregate(Src src) {
+  int64_t bid;
+  const NormArgs &a = src.locate(blockIdx.x, bid);
+  const NormJob &J = a.job[bid / a.ntiles];
+  const int64_t tile = bid % a.ntiles;
   const int64_t j0 = tile * kTileWords + (int64_t)threadIdx.x * kWPT;
   int64_t s[kWPT];
   const uint32_t agg = thread_words(J, a.d, j0, s);
@@ -137,8 +133,11 @@ __global__ void __launch_bounds__(kThreads) norm_aggregate(NormArgs a) {
 // One CTA per job: carries into every tile (the first tile gets 0), by a
 // parallel prefix of the tile functions (each thread composes a run of tiles,
 // then warp shuffles and one more level across the warps).
-__global__ void __launch_bounds__(1024) norm_tiles(NormArgs a) {
-  const NormJob &J = a.job[blockIdx.x];
+template <class Src>
+__global__ void __launch_bounds__(1024) norm_tiles(Src src) {
+  int64_t jid;
+  const NormArgs &a = src.locate(blockIdx.x, jid);
+  const NormJob &J = a.job[jid];
   __shared__ uint32_t wtot[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t per = (a.ntiles + 1023) / 1024;
@@ -175,9 +174,12 @@ __global__ void __launch_bounds__(1024) norm_tiles(NormArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) norm_apply(NormArgs a) {
-  const NormJob &J = a.job[blockIdx.y];
-  const int64_t tile = blockIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(kThreads) norm_apply(Src src) {
+  int64_t bid;
+  const NormArgs &a = src.locate(blockIdx.x, bid);
+  const NormJob &J = a.job[bid / a.ntiles];
+  const int64_t tile = bid % a.ntiles;
   const int64_t j0 = tile * kTileWords + (int64_t)threadIdx.x * kWPT;
   int64_t s[kWPT];
   const uint32_t agg = thread_words(J, a.d, j0, s);
@@ -193,20 +195,41 @@ __global__ void __launch_bounds__(kThreads) norm_apply(NormArgs a) {
 
 }  // namespace
 
-cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, cudaStream_t s) {
-  if (njobs < 1 || njobs > 4) return cudaErrorInvalidValue;
-  if (ntiles * kTileWords < nwords) return cudaErrorInvalidValue;
-  NormArgs a{};
+int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
+                   NormArgs &a) {
+  if (njobs < 1 || njobs > 4) return -1;
+  if (ntiles * kTileWords < nwords) return -1;
+  a = NormArgs{};
   for (int i = 0; i < njobs; i++) a.job[i] = jobs[i];
   a.njobs = njobs;
   a.d = d;
   a.nwords = nwords;
   a.ntiles = ntiles;
-  dim3 grid((unsigned)ntiles, (unsigned)njobs);
-  norm_aggregate<<<grid, kThreads, 0, s>>>(a);
-  norm_tiles<<<njobs, 1024, 0, s>>>(a);
-  norm_apply<<<grid, kThreads, 0, s>>>(a);
+  return 0;
+}
+
+cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
+                             int64_t ntiles, cudaStream_t s) {
+  NormArgs a;
+  if (make_norm_args(jobs, njobs, d, nwords, ntiles, a) != 0) return cudaErrorInvalidValue;
+  const One<NormArgs> one{a};
+  norm_aggregate<One<NormArgs>><<<(unsigned)(ntiles * njobs), kThreads, 0, s>>>(one);
+  norm_tiles<One<NormArgs>><<<njobs, 1024, 0, s>>>(one);
+  norm_apply<One<NormArgs>><<<(unsigned)(ntiles * njobs), kThreads, 0, s>>>(one);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+// prefix_tiles: block prefix over njobs * ntiles; prefix_jobs: over njobs
+cudaError_t launch_normalize_batch(const NormArgs *d, const int64_t *prefix_tiles,
+                                   const int64_t *prefix_jobs, int n, int64_t tiles,
+                                   int64_t jobs, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  norm_aggregate<Many<NormArgs>><<<(unsigned)tiles, kThreads, 0, s>>>(
+      Many<NormArgs>{d, prefix_tiles, n});
+  norm_tiles<Many<NormArgs>><<<(unsigned)jobs, 1024, 0, s>>>(Many<NormArgs>{d, prefix_jobs, n});
+  norm_apply<Many<NormArgs>><<<(unsigned)tiles, kThreads, 0, s>>>(
+      Many<NormArgs>{d, prefix_tiles, n});
   note_launches(3);
   return cudaGetLastError();
 }

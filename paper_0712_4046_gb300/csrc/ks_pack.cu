@@ -17,35 +17,42 @@
 // Signed inputs are biased to unsigned b-bit values by flipping bit b-1
 // (c + 2^(b-1)); the exact correction is applied after unpacking.
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
-__global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
+template <class Src>
+__global__ void __launch_bounds__(256) pack_kernel(Src src) {
+  int64_t local;
+  const PackArgs &a = src.locate(blockIdx.x, local);
+  int64_t j = local * 256 + threadIdx.x;
+  int o = 0;
+  while (o < a.nops && j >= a.op[o].ndig) {
+    j -= a.op[o].ndig;
+    o++;
+  }
+  if (o >= a.nops) return;
+  a.op[o].out[j] = digit_at(a.op[o], j, a.N, a.b, a.d, a.in_limbs, a.flip);
+}
+
+int64_t pack_blocks(const PackArgs &a) {
   int64_t total = 0;
   for (int o = 0; o < a.nops; o++) total += a.op[o].ndig;
-  const int64_t N = a.N;
-  const int b = a.b, d = a.d;
-  for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
-       gid += (int64_t)gridDim.x * blockDim.x) {
-    int o = 0;
-    int64_t j = gid;
-    while (j >= a.op[o].ndig) {
-      j -= a.op[o].ndig;
-      o++;
-    }
-    const PackOp &op = a.op[o];
-    const int32_t val = digit_at(op, j, N, b, d, a.in_limbs, a.flip);
-    op.out[j] = val;
-  }
+  return (total + 255) / 256;
 }
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
-  int64_t total = 0;
-  for (int o = 0; o < a.nops; o++) total += a.op[o].ndig;
-  if (total == 0) return cudaSuccess;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  const int64_t blocks = pack_blocks(a);
+  if (blocks == 0) return cudaSuccess;
+  pack_kernel<One<PackArgs>><<<(unsigned)blocks, 256, 0, s>>>(One<PackArgs>{a});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batch(const PackArgs *d, const int64_t *prefix, int n, int64_t blocks,
+                              cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  pack_kernel<Many<PackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<PackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }

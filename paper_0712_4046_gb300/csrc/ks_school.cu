@@ -18,6 +18,7 @@
 // Split over i (split-K) supplies the parallelism; the atomics make the
 // partial sums of different CTAs meet without a separate reduction pass.
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
@@ -26,21 +27,16 @@ constexpr int kThreads = 256;
 constexpr int kR = 8;
 constexpr int kTK = kThreads * kR;  // output columns per CTA
 constexpr int kTI = 1024;           // i-chunk per CTA
-
-struct SchoolArgs {
-  Product p[4];
-  int nprod;
-  int64_t block_prefix[5];
-  int64_t ichunks[4];
-};
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) schoolbook_kernel(SchoolArgs a) {
+template <class Src>
+__global__ void __launch_bounds__(kThreads) schoolbook_kernel(Src src) {
   __shared__ __align__(16) int32_t sA[kTI];
   __shared__ __align__(16) int32_t sB[kTK + kTI];
   __shared__ long long sHi[kThreads][7];
 
-  int64_t bid = blockIdx.x;
+  int64_t bid;
+  const SchoolArgs &a = src.locate(blockIdx.x, bid);
   int p = 0;
   while (p + 1 < a.nprod && bid >= a.block_prefix[p + 1]) p++;
   const Product P = a.p[p];
@@ -108,9 +104,9 @@ __global__ void __launch_bounds__(kThreads) schoolbook_kernel(SchoolArgs a) {
   }
 }
 
-cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s) {
-  if (nprod < 1 || nprod > 4) return cudaErrorInvalidValue;
-  SchoolArgs a{};
+int make_school_args(const Product *prods, int nprod, SchoolArgs &a) {
+  if (nprod < 1 || nprod > 4) return -1;
+  a = SchoolArgs{};
   a.nprod = nprod;
   a.block_prefix[0] = 0;
   for (int p = 0; p < nprod; p++) {
@@ -120,10 +116,26 @@ cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s) {
     a.ichunks[p] = (prods[p].nA + kTI - 1) / kTI;
     a.block_prefix[p + 1] = a.block_prefix[p] + ctiles * a.ichunks[p];
   }
+  return 0;
+}
+
+cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s) {
+  SchoolArgs a;
+  if (make_school_args(prods, nprod, a) != 0) return cudaErrorInvalidValue;
   const int64_t blocks = a.block_prefix[nprod];
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  schoolbook_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(a);
+  schoolbook_kernel<One<SchoolArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(One<SchoolArgs>{a});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schoolbook_batch(const SchoolArgs *d, const int64_t *prefix, int n,
+                                    int64_t blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  schoolbook_kernel<Many<SchoolArgs>>
+      <<<(unsigned)blocks, kThreads, 0, s>>>(Many<SchoolArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 // which each CTA also sums the blocks before its own; longer ones use a
 // three-phase scan (block totals, scan of the totals, apply).
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
@@ -43,14 +44,6 @@ __device__ __forceinline__ U2 sub2(U2 a, U2 b) {
   return r;
 }
 
-struct PrefArgs {
-  const uint64_t *x[2];
-  int64_t L[2];
-  int64_t nblocks[2];
-  int il;
-  uint64_t *P[2];    // per element: il x (lo, hi), then the negative count
-  uint64_t *bt;      // per block: the same record, block totals -> exclusive offsets
-};
 
 // (block, polynomial) of this CTA
 __device__ __forceinline__ int which(const PrefArgs &a, int64_t &blk) {
@@ -178,8 +171,10 @@ __global__ void __launch_bounds__(kThreads) pref_apply(PrefArgs a) {
 // most kSmallL / 2 extra reads per CTA), then scans its own block.
 constexpr int64_t kSmallL = 1 << 16;
 
-__global__ void __launch_bounds__(kThreads) pref_single(PrefArgs a) {
-  int64_t blk = blockIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(kThreads) pref_single(Src src) {
+  int64_t blk;
+  const PrefArgs &a = src.locate(blockIdx.x, blk);
   const int q = which(a, blk);
   const int64_t b0 = blk * kBlock;
   const int64_t t0 = b0 + (int64_t)threadIdx.x * kElems;
@@ -289,12 +284,18 @@ __device__ __forceinline__ void sub_shifted(uint64_t *r, const uint64_t *x, int 
   }
 }
 
-__global__ void __launch_bounds__(128) signed_fix_kernel(uint64_t *h, int ol, int64_t lf,
-                                                         int64_t lg, int b, int il,
-                                                         const uint64_t *pf, const uint64_t *pg) {
+template <class Src>
+__global__ void __launch_bounds__(128) signed_fix_kernel(Src src) {
+  int64_t local;
+  const FixArgs &fa = src.locate(blockIdx.x, local);
+  uint64_t *h = fa.h;
+  const int ol = fa.ol, b = fa.b, il = fa.il;
+  const int64_t lf = fa.lf, lg = fa.lg;
+  const uint64_t *pf = fa.pf, *pg = fa.pg;
   const int64_t lh = lf + lg - 1;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lh;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  {
+    const int64_t k = local * 128 + threadIdx.x;
+    if (k >= lh) return;
     uint64_t w[kMaxOl];
     for (int l = 0; l < ol; l++) w[l] = 0;
     const int64_t fhi = k < lf - 1 ? k : lf - 1;
@@ -317,17 +318,11 @@ __global__ void __launch_bounds__(128) signed_fix_kernel(uint64_t *h, int ol, in
 
 static int64_t nblocks_for(int64_t L) { return (L + kBlock - 1) / kBlock; }
 
-size_t signed_prefix_bytes(int64_t lf, int64_t lg, int il) {
-  const int rec = 2 * il + 1;
-  return (size_t)(lf + lg + nblocks_for(lf) + nblocks_for(lg)) * rec * 8;
-}
-
-cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
-                              const uint64_t *g, int64_t lg, int b, int in_limbs,
-                              uint64_t *prefix, cudaStream_t s) {
-  if (ol > kMaxOl || in_limbs > kMaxIn) return cudaErrorInvalidValue;
+bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
+                      int64_t lg, int b, int in_limbs, uint64_t *prefix, PrefArgs &a,
+                      FixArgs &fx, int64_t &pref_blocks, int64_t &fix_blocks) {
   const int rec = 2 * in_limbs + 1;
-  PrefArgs a{};
+  a = PrefArgs{};
   a.x[0] = f;
   a.x[1] = g;
   a.L[0] = lf;
@@ -338,22 +333,49 @@ cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf
   a.P[0] = prefix;
   a.P[1] = prefix + lf * rec;
   a.bt = prefix + (lf + lg) * rec;
+  fx = FixArgs{h, ol, lf, lg, b, in_limbs, a.P[0], a.P[1]};
+  pref_blocks = a.nblocks[0] + a.nblocks[1];
+  fix_blocks = (lf + lg - 1 + 127) / 128;
+  return lf <= kSmallL && lg <= kSmallL;  // single-launch prefix possible
+}
+
+cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                              const uint64_t *g, int64_t lg, int b, int in_limbs,
+                              uint64_t *prefix, cudaStream_t s) {
+  if (ol > kMaxOl || in_limbs > kMaxIn) return cudaErrorInvalidValue;
+  PrefArgs a;
+  FixArgs fx;
+  int64_t pb, fb;
+  const bool single = make_signed_args(h, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb);
   int launches = 2;
-  if (lf <= kSmallL && lg <= kSmallL) {
-    pref_single<<<(unsigned)(a.nblocks[0] + a.nblocks[1]), kThreads, 0, s>>>(a);
+  if (single) {
+    pref_single<One<PrefArgs>><<<(unsigned)pb, kThreads, 0, s>>>(One<PrefArgs>{a});
   } else {
-    const unsigned nb = (unsigned)(a.nblocks[0] + a.nblocks[1]);
-    pref_block_totals<<<nb, kThreads, 0, s>>>(a);
+    pref_block_totals<<<(unsigned)pb, kThreads, 0, s>>>(a);
     pref_scan_totals<<<2, 64, 0, s>>>(a);
-    pref_apply<<<nb, kThreads, 0, s>>>(a);
+    pref_apply<<<(unsigned)pb, kThreads, 0, s>>>(a);
     launches = 4;
   }
-  const int64_t lh = lf + lg - 1;
-  int64_t grid = (lh + 127) / 128;
-  if (grid > 152 * 32) grid = 152 * 32;
-  signed_fix_kernel<<<(unsigned)grid, 128, 0, s>>>(h, ol, lf, lg, b, in_limbs, a.P[0], a.P[1]);
+  signed_fix_kernel<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
   note_launches(launches);
   return cudaGetLastError();
+}
+
+cudaError_t launch_signed_batch(const PrefArgs *pa, const int64_t *pref_prefix,
+                                const FixArgs *fa, const int64_t *fix_prefix, int n,
+                                int64_t pref_blocks, int64_t fix_blocks, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  pref_single<Many<PrefArgs>><<<(unsigned)pref_blocks, kThreads, 0, s>>>(
+      Many<PrefArgs>{pa, pref_prefix, n});
+  signed_fix_kernel<Many<FixArgs>><<<(unsigned)fix_blocks, 128, 0, s>>>(
+      Many<FixArgs>{fa, fix_prefix, n});
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+size_t signed_prefix_bytes(int64_t lf, int64_t lg, int il) {
+  const int rec = 2 * il + 1;
+  return (size_t)(lf + lg + nblocks_for(lf) + nblocks_for(lg)) * rec * 8;
 }
 
 }  // namespace ks

@@ -40,6 +40,7 @@
 #include <cuda_fp16.h>
 
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
@@ -61,35 +62,6 @@ constexpr int kMaxItemChunks = 64;
 // (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kNT >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 constexpr uint64_t kWaitNs = 1000000000ull;
-
-struct TcProduct {
-  const __half *Araw;  // raw A digits, offset by 127 (index x holds digit x - 127)
-  int64_t nAraw;
-  const __half *BRT;
-  int64_t rows;
-  int64_t dmax, R, T;  // largest delta, rows of B, tiles
-  int64_t items_per_tile;
-  int ks;
-  int64_t *C;
-  int64_t ncols;
-};
-
-struct TcArgs {
-  TcProduct p[4];
-  int nprod;
-  int64_t item_prefix[5];
-  int chunks_per_item;
-  int *status;
-};
-
-struct TcPackArgs {
-  PackOp op[kMaxOperands];
-  int nprod;
-  int N, b, in_limbs, flip;
-  __half *Araw[4];
-  __half *BRT[4];
-  int64_t nAraw, rows, R, nA, nB;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -207,11 +179,15 @@ __device__ __forceinline__ int32_t tc_digit(const PackOp &op, int64_t j, int64_t
   return v;
 }
 
-__global__ void __launch_bounds__(256) tc_pack_kernel(TcPackArgs a) {
+template <class Src>
+__global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
+  int64_t local;
+  const TcPackArgs &a = src.locate(blockIdx.x, local);
   const int64_t perA = a.nAraw, perB = 16 * a.rows * 8, per = perA + perB;
   const int64_t total = per * a.nprod;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  {
+    const int64_t e = local * 256 + threadIdx.x;
+    if (e >= total) return;
     const int q = (int)(e / per);
     const int64_t r = e - q * per;
     if (r < perA) {
@@ -233,7 +209,8 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(TcPackArgs a) {
 }
 
 // ------------------------------------------------------------------ MMA
-__global__ void __launch_bounds__(kThreads, 2) tc_kernel(TcArgs a) {
+template <class Src>
+__global__ void __launch_bounds__(kThreads, 2) tc_kernel(Src src, int64_t total) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_full;
   __shared__ __align__(8) uint64_t bar_mma;
@@ -261,11 +238,14 @@ __global__ void __launch_bounds__(kThreads, 2) tc_kernel(TcArgs a) {
   uint32_t ph_full = 0, ph_mma = 0;
   bool aborted = false, load_pending = false, mma_pending = false;
 
-  const int64_t total = a.item_prefix[a.nprod];
   const int quad = warp & 3, half = warp >> 2;
+  int *status = nullptr;
   const int qd = quad * 32 + lane;  // this thread's digit row (TMEM lane)
 
-  for (int64_t item = blockIdx.x; item < total && !aborted; item += gridDim.x) {
+  for (int64_t gitem = blockIdx.x; gitem < total && !aborted; gitem += gridDim.x) {
+    int64_t item;
+    const TcArgs &a = src.locate(gitem, item);
+    status = a.status;
     int qp = 0;
     while (qp + 1 < a.nprod && item >= a.item_prefix[qp + 1]) qp++;
     const TcProduct &P = a.p[qp];
@@ -395,12 +375,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_kernel(TcArgs a) {
 
   if (aborted) {
     if (tid == 0) {
-      atomicExch(a.status, 1);
+      if (status) atomicExch(status, 1);
       if (load_pending) mbar_wait(&bar_full, ph_full ^ 1);
       if (mma_pending) mbar_wait(&bar_mma, ph_mma ^ 1);
     }
   }
-  if (tid == 0 && bad_range) atomicExch(a.status, 3);
+  if (tid == 0 && bad_range && status) atomicExch(status, 3);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -425,9 +405,9 @@ size_t tc_operand_bytes(const TcGeom &g) {
 }
 static size_t raw_bytes(const TcGeom &g) { return ((size_t)g.nG * 2 + 255) & ~(size_t)255; }
 
-cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
-                           cudaStream_t s) {
-  TcPackArgs a{};
+void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
+                       TcPackArgs &a, int64_t &blocks) {
+  a = TcPackArgs{};
   for (int i = 0; i < 2 * nprod; i++) a.op[i] = pa.op[i];
   a.nprod = nprod;
   a.N = pa.N;
@@ -444,44 +424,73 @@ cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char 
   a.R = g.R;
   a.nA = g.nA;
   a.nB = g.nB;
-  const int64_t total = (g.nG + 16 * g.rows * 8) * nprod;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  tc_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  blocks = ((g.nG + 16 * g.rows * 8) * nprod + 255) / 256;
+}
+
+cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
+                           cudaStream_t s) {
+  TcPackArgs a;
+  int64_t blocks;
+  make_tc_pack_args(pa, g, nprod, base, a, blocks);
+  tc_pack_kernel<One<TcPackArgs>><<<(unsigned)blocks, 256, 0, s>>>(One<TcPackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
-                               int64_t *const *C, int *status, cudaStream_t s) {
+cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int n,
+                                 int64_t blocks, cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  tc_pack_kernel<Many<TcPackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<TcPackArgs>{d, prefix, n});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+static cudaError_t tc_attr() {
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return e0;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmem);
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<One<TcArgs>>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_kernel<Many<TcArgs>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmem);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  TcArgs a{};
-  a.nprod = nprod;
-  a.status = status;
-  const size_t per = tc_operand_bytes(g);
-  int64_t total_chunks = 0;
-  int64_t cmax[4];
-  for (int q = 0; q < nprod; q++) {
-    const int64_t span = g.dmax + 1 < g.R + kNT - 1 ? g.dmax + 1 : g.R + kNT - 1;
-    cmax[q] = (span + ks[q] - 1) / ks[q];
-    total_chunks += cmax[q] * g.T;
-  }
+  return cudaSuccess;
+}
+
+// chunks per item for a total chunk count: enough items for ~8 per CTA slot
+static int chunks_per_item(int64_t total_chunks) {
   int64_t cpi = (total_chunks + 1215) / 1216;
   if (cpi < 1) cpi = 1;
   if (cpi > kMaxItemChunks) cpi = kMaxItemChunks;
-  a.chunks_per_item = (int)cpi;
+  return (int)cpi;
+}
+
+int64_t tc_chunks(const TcGeom &g, int nprod, const int *ks) {
+  int64_t total = 0;
+  for (int q = 0; q < nprod; q++) {
+    const int64_t span = g.dmax + 1 < g.R + kNT - 1 ? g.dmax + 1 : g.R + kNT - 1;
+    total += (span + ks[q] - 1) / ks[q] * g.T;
+  }
+  return total;
+}
+
+void make_tc_args(const TcGeom &g, int nprod, const int *ks, char *base, int64_t *const *C,
+                  int *status, int cpi, TcArgs &a) {
+  a = TcArgs{};
+  a.nprod = nprod;
+  a.status = status;
+  a.chunks_per_item = cpi;
+  const size_t per = tc_operand_bytes(g);
   a.item_prefix[0] = 0;
   for (int q = 0; q < nprod; q++) {
+    const int64_t span = g.dmax + 1 < g.R + kNT - 1 ? g.dmax + 1 : g.R + kNT - 1;
+    const int64_t cmax = (span + ks[q] - 1) / ks[q];
     TcProduct &P = a.p[q];
     P.Araw = reinterpret_cast<const __half *>(base + q * per);
     P.nAraw = g.nG;
@@ -490,18 +499,39 @@ cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *
     P.dmax = g.dmax;
     P.R = g.R;
     P.T = g.T;
-    P.items_per_tile = (cmax[q] + cpi - 1) / cpi;
+    P.items_per_tile = (cmax + cpi - 1) / cpi;
     P.ks = ks[q];
     P.C = C[q];
     P.ncols = g.ncols;
     a.item_prefix[q + 1] = a.item_prefix[q] + g.T * P.items_per_tile;
   }
+}
+
+cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
+                               int64_t *const *C, int *status, cudaStream_t s) {
+  cudaError_t e = tc_attr();
+  if (e != cudaSuccess) return e;
+  TcArgs a;
+  make_tc_args(g, nprod, ks, base, C, status, chunks_per_item(tc_chunks(g, nprod, ks)), a);
   const int64_t items = a.item_prefix[nprod];
   if (items <= 0) return cudaSuccess;
-  int64_t grid = items < 2 * 152 ? items : 2 * 152;
-  tc_kernel<<<(unsigned)grid, kThreads, kSmem, s>>>(a);
+  const int64_t grid = items < 2 * 152 ? items : 2 * 152;
+  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, items);
   note_launches(1);
   return cudaGetLastError();
 }
+
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t items,
+                            cudaStream_t s) {
+  if (n == 0 || items == 0) return cudaSuccess;
+  cudaError_t e = tc_attr();
+  if (e != cudaSuccess) return e;
+  const int64_t grid = items < 2 * 152 ? items : 2 * 152;
+  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, items);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+int tc_batch_chunks_per_item(int64_t total_chunks) { return chunks_per_item(total_chunks); }
 
 }  // namespace ks

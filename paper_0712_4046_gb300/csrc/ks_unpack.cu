@@ -1,6 +1,7 @@
 // Unpack (Sec. 3.1, 3.3), reciprocal reconstruction (Sec. 3.2, used twice by
 // Sec. 3.4), the signed-bias correction and the reduction mod p (Sec. 4).
 #include "ks_internal.cuh"
+#include "ks_src.cuh"
 
 namespace ks {
 
@@ -9,24 +10,22 @@ namespace ks {
 // KS1: V = h(2^N), off = 0, width N.  KS2: V = P+ + P- = 2 h0(X^2) and
 // V_odd = P+ - P- = 2X h1(X^2); then both even and odd coefficients sit at
 // bit 1 + kN, width 2N (Sec. 3.3).
-__global__ void __launch_bounds__(256) unpack_kernel(uint64_t *h, int ol, int64_t lh,
-                                                     const uint32_t *V, const uint32_t *V_odd,
-                                                     int64_t nwords, int64_t off, int64_t N,
-                                                     int width) {
-  const int64_t total = lh * ol;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = idx / ol;
-    const int l = (int)(idx - k * ol);
-    const uint32_t *src = (V_odd != nullptr && (k & 1)) ? V_odd : V;
-    const int rem = width - 64 * l;
-    uint64_t v = 0;
-    if (rem > 0) {
-      v = get_bits64(src, nwords, off + k * N + 64 * (int64_t)l);
-      if (rem < 64) v &= (1ull << rem) - 1ull;
-    }
-    h[idx] = v;
+template <class Src>
+__global__ void __launch_bounds__(256) unpack_kernel(Src src) {
+  int64_t local;
+  const UnpackArgs &a = src.locate(blockIdx.x, local);
+  const int64_t idx = local * 256 + threadIdx.x;
+  if (idx >= a.lh * a.ol) return;
+  const int64_t k = idx / a.ol;
+  const int l = (int)(idx - k * a.ol);
+  const uint32_t *src_w = (a.V_odd != nullptr && (k & 1)) ? a.V_odd : a.V;
+  const int rem = a.width - 64 * l;
+  uint64_t v = 0;
+  if (rem > 0) {
+    v = get_bits64(src_w, a.nwords, a.off + k * a.N + 64 * (int64_t)l);
+    if (rem < 64) v &= (1ull << rem) - 1ull;
   }
+  a.h[idx] = v;
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -36,11 +35,18 @@ static unsigned grid_for(int64_t n, int threads) {
   return (unsigned)b;
 }
 
-cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
-                          const uint32_t *V_odd, int64_t nwords, int64_t off, int64_t N,
-                          int width, cudaStream_t s) {
-  unpack_kernel<<<grid_for(lh * ol, 256), 256, 0, s>>>(h, ol, lh, V, V_odd, nwords, off, N,
-                                                       width);
+int64_t unpack_blocks(const UnpackArgs &a) { return (a.lh * a.ol + 255) / 256; }
+
+cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s) {
+  unpack_kernel<One<UnpackArgs>><<<(unsigned)unpack_blocks(a), 256, 0, s>>>(One<UnpackArgs>{a});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int n,
+                                int64_t blocks, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  unpack_kernel<Many<UnpackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<UnpackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -54,11 +60,6 @@ cudaError_t launch_unpack(uint64_t *h, int ol, int64_t lh, const uint32_t *V,
 // propagates the carries.
 namespace {
 constexpr int kSeedThreads = 128;
-struct SeedArgs {
-  RecoverRun run[2];
-  int nruns;
-  int64_t chain;
-};
 }  // namespace
 
 template <int NW>
@@ -71,14 +72,16 @@ __device__ __forceinline__ void coeff_words(const uint64_t *c, int in_limbs, int
   }
 }
 
-template <int NW>
-__global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int seed_words,
-                                                            SeedArgs a, const uint64_t *f,
-                                                            int64_t lf, const uint64_t *g,
-                                                            int64_t lg, int b, int in_limbs,
-                                                            int flip) {
+template <int NW, class Src>
+__global__ void __launch_bounds__(kSeedThreads) seed_kernel(Src src) {
   __shared__ unsigned long long colsum[kMaxSeedWords];
-  int64_t sid = blockIdx.x;
+  int64_t sid;
+  const SeedArgs &a = src.locate(blockIdx.x, sid);
+  uint32_t *seeds = a.seeds;
+  const int seed_words = a.seed_words;
+  const uint64_t *f = a.f, *g = a.g;
+  const int64_t lf = a.lf, lg = a.lg;
+  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
   int r = 0;
   int64_t per_run = 2 * (a.run[0].nchains - 1);
   while (r + 1 < a.nruns && sid >= per_run) {
@@ -136,13 +139,16 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(uint32_t *seeds, int
 
 // b <= 64: each coefficient is one 64-bit word; products are 128-bit and a
 // thread keeps a 192-bit running sum in three registers.
-__global__ void __launch_bounds__(kSeedThreads) seed_kernel64(uint32_t *seeds, int seed_words,
-                                                              SeedArgs a, const uint64_t *f,
-                                                              int64_t lf, const uint64_t *g,
-                                                              int64_t lg, int b, int in_limbs,
-                                                              int flip) {
+template <class Src>
+__global__ void __launch_bounds__(kSeedThreads) seed_kernel64(Src src) {
   __shared__ unsigned long long colsum[kMaxSeedWords];
-  int64_t sid = blockIdx.x;
+  int64_t sid;
+  const SeedArgs &a = src.locate(blockIdx.x, sid);
+  uint32_t *seeds = a.seeds;
+  const int seed_words = a.seed_words;
+  const uint64_t *f = a.f, *g = a.g;
+  const int64_t lf = a.lf, lg = a.lg;
+  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
   int r = 0;
   int64_t per_run = 2 * (a.run[0].nchains - 1);
   while (r + 1 < a.nruns && sid >= per_run) {
@@ -199,26 +205,25 @@ constexpr int kSG = 16;
 constexpr int kST = 512;
 constexpr int kSW = 2048;
 constexpr int64_t kSlice = 2048;  // indices t per CTA
-struct SeedBArgs {
-  RecoverRun run[2];
-  int nruns;
-  int64_t chain;
-  int64_t groups[2];
-};
 __device__ __forceinline__ int64_t seed_k(const RecoverRun &R, int64_t chain, int64_t sid) {
   const int64_t c = sid / 2 + 1;
   return R.kbase + R.kstride * (c * chain - 1 + (sid & 1));
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) seed_blocked64(unsigned long long *acc, SeedBArgs a,
-                                                      const uint64_t *f, int64_t lf,
-                                                      const uint64_t *g, int64_t lg, int b,
-                                                      int in_limbs, int flip) {
+template <class Src>
+__global__ void __launch_bounds__(256) seed_blocked64(Src src) {
   __shared__ uint64_t sf[kST];
   __shared__ uint64_t sg[kSW];
   __shared__ unsigned long long colsum[kSG][6];
-  int64_t gid = blockIdx.x;
+  int64_t bid;
+  const SeedBArgs &a = src.locate(blockIdx.x, bid);
+  unsigned long long *acc = a.acc;
+  const uint64_t *f = a.f, *g = a.g;
+  const int64_t lf = a.lf, lg = a.lg;
+  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
+  const int64_t slice = bid % a.slices;
+  int64_t gid = bid / a.slices;
   int r = 0;
   while (r + 1 < a.nruns && gid >= a.groups[r]) {
     gid -= a.groups[r];
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(256) seed_blocked64(unsigned long long *acc, S
   // this CTA's slice of the t range
   int64_t tlo = kmin - lg + 1 > 0 ? kmin - lg + 1 : 0;
   int64_t thi = kmax < lf - 1 ? kmax : lf - 1;
-  const int64_t s_lo = tlo + (int64_t)blockIdx.y * kSlice;
+  const int64_t s_lo = tlo + slice * kSlice;
   const int64_t s_hi = s_lo + kSlice - 1 < thi ? s_lo + kSlice - 1 : thi;
   for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
     const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
@@ -306,10 +311,15 @@ __global__ void __launch_bounds__(256) seed_blocked64(unsigned long long *acc, S
 }
 
 // word sums (6 x 64-bit per seed) -> carried 32-bit seed words
-__global__ void __launch_bounds__(128) seed_finish(uint32_t *seeds, int seed_words,
-                                                   const unsigned long long *acc, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+template <class Src>
+__global__ void __launch_bounds__(128) seed_finish(Src src) {
+  int64_t local;
+  const SeedBArgs &a = src.locate(blockIdx.x, local);
+  const int64_t i = local * 128 + threadIdx.x;
+  if (i >= a.nseeds) return;
+  uint32_t *seeds = a.seeds;
+  const int seed_words = a.seed_words;
+  const unsigned long long *acc = a.acc;
   unsigned long long carry = 0;
   for (int w = 0; w < seed_words; w++) {
     const unsigned long long v = (w < 6 ? acc[i * 6 + w] : 0ull) + carry;
@@ -318,31 +328,35 @@ __global__ void __launch_bounds__(128) seed_finish(uint32_t *seeds, int seed_wor
   }
 }
 
-cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
-                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
-                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs, int flip,
-                         cudaStream_t s) {
-  SeedArgs a{};
+int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
+                   const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
+                   const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp) {
+  sp = SeedPlan{};
   int64_t n = 0;
-  for (int r = 0; r < nruns; r++) {
-    a.run[r] = runs[r];
-    n += 2 * (runs[r].nchains - 1);
-  }
+  for (int r = 0; r < nruns; r++) n += 2 * (runs[r].nchains - 1);
+  sp.nseeds = n;
+  if (n == 0) return 0;
+  if (seed_words > kMaxSeedWords) return -1;
+  SeedArgs &a = sp.a;
+  for (int r = 0; r < nruns; r++) a.run[r] = runs[r];
   a.nruns = nruns;
   a.chain = chain;
-  if (n == 0) return cudaSuccess;
-  if (seed_words > kMaxSeedWords) return cudaErrorInvalidValue;
-  const int nw = (b + 31) / 32;
-  const unsigned grid = (unsigned)n;
-#define KS_SEEDS(NW)                                                                        \
-  seed_kernel<NW><<<grid, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b, \
-                                                in_limbs, flip)
+  a.seeds = seeds;
+  a.seed_words = seed_words;
+  a.f = f;
+  a.g = g;
+  a.lf = lf;
+  a.lg = lg;
+  a.b = b;
+  a.in_limbs = in_limbs;
+  a.flip = flip;
+  sp.blocks = n;
   // blocked path when the seeds of a group lie close enough together
   bool blocked = b <= 64;
   for (int r = 0; r < nruns && blocked; r++)
     if (runs[r].kstride * (chain * (kSG / 2) + 1) + kST > kSW) blocked = false;
   if (blocked) {
-    SeedBArgs sb{};
+    SeedBArgs &sb = sp.bl;
     int64_t groups = 0;
     for (int r = 0; r < nruns; r++) {
       sb.run[r] = runs[r];
@@ -353,33 +367,95 @@ cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *se
     sb.chain = chain;
     const int64_t lmin = lf < lg ? lf : lg;
     // a group's t range is at most min(Lf, Lg) plus the spread of its k (< kSW)
-    const int64_t slices = (lmin + kSW + kSlice - 1) / kSlice;
-    cudaError_t e = cudaMemsetAsync(seed_acc, 0, (size_t)n * 6 * 8, s);
+    sb.slices = (lmin + kSW + kSlice - 1) / kSlice;
+    sb.nseeds = n;
+    sb.acc = seed_acc;
+    sb.seeds = seeds;
+    sb.seed_words = seed_words;
+    sb.f = f;
+    sb.g = g;
+    sb.lf = lf;
+    sb.lg = lg;
+    sb.b = b;
+    sb.in_limbs = in_limbs;
+    sb.flip = flip;
+    sp.kind = 1;
+    sp.blocks = groups * sb.slices;
+    sp.finish_blocks = (n + 127) / 128;
+    return 0;
+  }
+  const int nw = (b + 31) / 32;
+  if (b <= 64) {
+    sp.kind = 2;
+  } else {
+    int cls = 2;
+    while (cls < nw) cls *= 2;
+    if (cls > 64) return -1;
+    sp.kind = 100 + cls;  // word-count class of the templated kernel
+  }
+  return 0;
+}
+
+template <class Src>
+static void launch_seed_kind(int kind, int64_t blocks, const Src &src, cudaStream_t s) {
+  const unsigned grid = (unsigned)blocks;
+  switch (kind) {
+    case 2: seed_kernel64<Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 102: seed_kernel<2, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 104: seed_kernel<4, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 108: seed_kernel<8, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 116: seed_kernel<16, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 132: seed_kernel<32, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+    case 164: seed_kernel<64, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
+  }
+}
+
+cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
+  if (sp.nseeds == 0) return cudaSuccess;
+  if (sp.kind == 1) {
+    cudaError_t e = cudaMemsetAsync(sp.bl.acc, 0, (size_t)sp.nseeds * 6 * 8, s);
     if (e != cudaSuccess) return e;
-    seed_blocked64<<<dim3((unsigned)groups, (unsigned)slices), 256, 0, s>>>(
-        seed_acc, sb, f, lf, g, lg, b, in_limbs, flip);
-    seed_finish<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(seeds, seed_words, seed_acc, n);
+    const One<SeedBArgs> one{sp.bl};
+    seed_blocked64<One<SeedBArgs>><<<(unsigned)sp.blocks, 256, 0, s>>>(one);
+    seed_finish<One<SeedBArgs>><<<(unsigned)sp.finish_blocks, 128, 0, s>>>(one);
+    note_launches(2);
+  } else {
+    launch_seed_kind(sp.kind, sp.blocks, One<SeedArgs>{sp.a}, s);
     note_launches(1);
-  } else if (b <= 64)
-    seed_kernel64<<<grid, kSeedThreads, 0, s>>>(seeds, seed_words, a, f, lf, g, lg, b, in_limbs,
-                                                flip);
-  else if (nw <= 2)
-    KS_SEEDS(2);
-  else if (nw <= 4)
-    KS_SEEDS(4);
-  else if (nw <= 8)
-    KS_SEEDS(8);
-  else if (nw <= 16)
-    KS_SEEDS(16);
-  else if (nw <= 32)
-    KS_SEEDS(32);
-  else if (nw <= 64)
-    KS_SEEDS(64);
-  else
-    return cudaErrorInvalidValue;
-#undef KS_SEEDS
+  }
+  return cudaGetLastError();
+}
+
+// batches: blocked (kind 1) products, then per kind the others
+cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks,
+                                       const int64_t *prefix_finish, int n, int64_t blocks,
+                                       int64_t finish_blocks, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  seed_blocked64<Many<SeedBArgs>><<<(unsigned)blocks, 256, 0, s>>>(
+      Many<SeedBArgs>{d, prefix_blocks, n});
+  seed_finish<Many<SeedBArgs>><<<(unsigned)finish_blocks, 128, 0, s>>>(
+      Many<SeedBArgs>{d, prefix_finish, n});
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
+                                    int64_t blocks, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  launch_seed_kind(kind, blocks, Many<SeedArgs>{d, prefix, n}, s);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
+                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
+                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs, int flip,
+                         cudaStream_t s) {
+  SeedPlan sp;
+  if (make_seed_plan(seeds, seed_words, seed_acc, runs, nruns, chain, f, lf, g, lg, b, in_limbs,
+                     flip, sp) != 0)
+    return cudaErrorInvalidValue;
+  return launch_seed_plan(sp, s);
 }
 
 // ------------------------------------------------------------------ recover
@@ -400,14 +476,6 @@ cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *se
 // (mod X, necessarily 0 or 1) gives delta_s = (beta_(s-1) + alpha_s +
 // delta_(s-1) - u_s) / X.
 namespace {
-struct RecoverArgs {
-  RecoverRun run[2];
-  int nruns;
-  int64_t nwords;
-  int M;
-  int64_t chain;
-  int seed_words;
-};
 
 // digit arithmetic on W 32-bit words, values in [0, 2^M)
 struct Dig {
@@ -567,9 +635,14 @@ __device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, 
 }
 
 // M <= 63
-__global__ void __launch_bounds__(128) recover_kernel1(uint64_t *h, int ol, RecoverArgs a,
-                                                       int *status) {
-  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(128) recover_kernel1(Src src) {
+  int64_t local;
+  const RecoverArgs &a = src.locate(blockIdx.x, local);
+  uint64_t *h = a.h;
+  const int ol = a.ol;
+  int *status = a.status;
+  int64_t gid = local * 128 + threadIdx.x;
   int r;
   if (!chain_index(a, gid, r)) return;
   const RecoverRun &R = a.run[r];
@@ -629,9 +702,14 @@ __global__ void __launch_bounds__(128) recover_kernel1(uint64_t *h, int ol, Reco
 }
 
 // 64 <= M <= 127
-__global__ void __launch_bounds__(128) recover_kernel2(uint64_t *h, int ol, RecoverArgs a,
-                                                       int *status) {
-  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(128) recover_kernel2(Src src) {
+  int64_t local;
+  const RecoverArgs &a = src.locate(blockIdx.x, local);
+  uint64_t *h = a.h;
+  const int ol = a.ol;
+  int *status = a.status;
+  int64_t gid = local * 128 + threadIdx.x;
   int r;
   if (!chain_index(a, gid, r)) return;
   const RecoverRun &R = a.run[r];
@@ -677,9 +755,14 @@ __global__ void __launch_bounds__(128) recover_kernel2(uint64_t *h, int ol, Reco
   }
 }
 
-__global__ void __launch_bounds__(64) recover_wide(uint64_t *h, int ol, RecoverArgs a,
-                                                   int *status) {
-  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <class Src>
+__global__ void __launch_bounds__(64) recover_wide(Src src) {
+  int64_t local;
+  const RecoverArgs &a = src.locate(blockIdx.x, local);
+  uint64_t *h = a.h;
+  const int ol = a.ol;
+  int *status = a.status;
+  int64_t gid = local * 64 + threadIdx.x;
   int r = 0;
   while (r < a.nruns && gid >= a.run[r].nchains) {
     gid -= a.run[r].nchains;
@@ -737,10 +820,10 @@ __global__ void __launch_bounds__(64) recover_wide(uint64_t *h, int ol, RecoverA
   }
 }
 
-cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
-                           int64_t nwords, int M, int64_t chain, int seed_words, int *status,
-                           cudaStream_t s) {
-  RecoverArgs a{};
+int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
+                      int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,
+                      int64_t &blocks) {
+  a = RecoverArgs{};
   int64_t total = 0;
   for (int r = 0; r < nruns; r++) {
     a.run[r] = runs[r];
@@ -751,16 +834,45 @@ cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nrun
   a.M = M;
   a.chain = chain;
   a.seed_words = seed_words;
-  if (total == 0) return cudaSuccess;
+  a.h = h;
+  a.ol = ol;
+  a.status = status;
+  if ((M + 31) / 32 > kMaxDigitWordsM) return -1;
+  const int per = M <= 127 ? 128 : 64;
+  blocks = (total + per - 1) / per;
+  return 0;
+}
+
+int recover_class(int M) { return M <= 63 ? 1 : (M <= 127 ? 2 : 3); }
+
+template <class Src>
+static void launch_recover_class(int cls, int64_t blocks, const Src &src, cudaStream_t s) {
+  if (cls == 1)
+    recover_kernel1<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
+  else if (cls == 2)
+    recover_kernel2<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
+  else
+    recover_wide<Src><<<(unsigned)blocks, 64, 0, s>>>(src);
+}
+
+cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
+                           int64_t nwords, int M, int64_t chain, int seed_words, int *status,
+                           cudaStream_t s) {
+  RecoverArgs a;
+  int64_t blocks;
+  if (make_recover_args(h, ol, runs, nruns, nwords, M, chain, seed_words, status, a, blocks) != 0)
+    return cudaErrorInvalidValue;
+  if (blocks == 0) return cudaSuccess;
+  launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, s);
   note_launches(1);
-  if (M <= 63) {
-    recover_kernel1<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(h, ol, a, status);
-  } else if (M <= 127) {
-    recover_kernel2<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(h, ol, a, status);
-  } else {
-    if ((M + 31) / 32 > kMaxDigitWordsM) return cudaErrorInvalidValue;
-    recover_wide<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(h, ol, a, status);
-  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
+                                 int64_t blocks, cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  launch_recover_class(cls, blocks, Many<RecoverArgs>{d, prefix, n}, s);
+  note_launches(1);
   return cudaGetLastError();
 }
 
