@@ -285,6 +285,9 @@ def main_ours(args):
         ks.ks_mul_host(hh, fh, gh, b, sg, 4, 0, stream)
     e2e_s = barrier_max(time.perf_counter() - t0, world, dev)
 
+    # ---- batched workload: 4096 uneven products, one plan per dispatch mode, CUDA graph
+    batched = run_batched(ks, dev, stream, flush, args.steps, args.warmup, world)
+
     # ---- roofline of the dominant phase of KS4
     r4 = results["KS4"]
     info = ks.plan_info(lf, lg, b, sg, 4, ks.ENGINE_AUTO)
@@ -332,9 +335,70 @@ def main_ours(args):
                 "h2d_bytes_per_step": int(f.nbytes + g.nbytes),
                 "d2h_bytes_per_step": int(lh * ol * 8)},
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     print(json.dumps(line))
     return 0
+
+
+BATCH = {"workload": "uneven_batch_4096", "n": 4096, "seed": 20071231, "len": [8, 8192],
+         "coeff_bits": [4, 512], "signed_fraction": 0.5}
+
+
+def run_batched(ks, dev, stream, flush, steps, warmup, world):
+    """4096 independent products (lengths log-uniform in [8, 8192] drawn
+    independently, bits log-uniform in [4, 512], half signed) in one batched
+    plan, replayed as a CUDA graph; fixed KS1 vs the autotuned table vs the
+    learned model."""
+    import torch
+    lf, lg, cb, sg = ks_inputs.uneven_batch(BATCH["n"], BATCH["seed"])
+    probs = []
+    out_bits = 0
+    for i in range(BATCH["n"]):
+        f = ks_inputs.random_poly(int(lf[i]), int(cb[i]), bool(sg[i]), 7 * i + 1)
+        g = ks_inputs.random_poly(int(lg[i]), int(cb[i]), bool(sg[i]), 7 * i + 2)
+        ol = ks.out_limbs(int(lf[i]), int(lg[i]), int(cb[i]), bool(sg[i]))
+        h = torch.empty((int(lf[i] + lg[i] - 1), ol), dtype=torch.int64, device=dev)
+        probs.append(dict(h=h, f=torch.from_numpy(f.view(np.int64)).to(dev),
+                          g=torch.from_numpy(g.view(np.int64)).to(dev),
+                          coeff_bits=int(cb[i]), is_signed=bool(sg[i])))
+        out_bits += output_bits(int(lf[i]), int(lg[i]), int(cb[i]))
+    side = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, mode in (("fixed_ks1", ks.DISPATCH_KS1), ("table", ks.DISPATCH_TABLE),
+                       ("mlp", ks.DISPATCH_MLP)):
+        plan = ks.Plan(probs, mode)
+        plan.capture(side)
+        for _ in range(warmup):
+            plan.execute(side)
+        side.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            with torch.cuda.stream(side):
+                flush.zero_()
+            evs[i][0].record(side)
+            plan.execute(side)
+            evs[i][1].record(side)
+        side.synchronize()
+        ks.status_sync(side)
+        ms = barrier_max(sum(a.elapsed_time(z) for a, z in evs), world, dev) / steps
+        choices = {}
+        for i in range(len(probs)):
+            v, e = plan.choice(i)
+            key = "KS%d/%s" % (v, {1: "int32", 2: "ntt", 3: "tc"}[e])
+            choices[key] = choices.get(key, 0) + 1
+        res[name] = {"products_per_s": world * BATCH["n"] * 1000.0 / ms, "ms_per_batch": ms,
+                     "output_gbit_per_s": world * out_bits / ms / 1e6,
+                     "launches_per_batch": plan.launches(), "choices": choices}
+        plan.close()
+    res["config"] = dict(BATCH, graph=True, dispatch_state_installed=ks.DISPATCH_STATE_INSTALLED)
+    res["mlp_over_fixed_ks1"] = res["mlp"]["products_per_s"] / res["fixed_ks1"]["products_per_s"]
+    res["table_over_fixed_ks1"] = (res["table"]["products_per_s"]
+                                   / res["fixed_ks1"]["products_per_s"])
+    return res
 
 
 def roofline_for(phase, ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind):

@@ -207,6 +207,50 @@ int ks_plan_choice(const ks_plan *plan, int64_t i, int *variant, int *engine);
 /* Waits for the device, then frees the plan (NULL is ignored). */
 void ks_plan_destroy(ks_plan *plan);
 
+/*
+ * Dispatch: the autotuned table and the learned cost model (no counterpart
+ * in the paper, which picks the variant by hand per experiment; Sec. 4 notes
+ * that small degrees favour the standard substitution).  Neither affects the
+ * result -- every choice is an exact path -- only which path runs where a
+ * problem says KS_AUTO.
+ *
+ * ks_tune_time: mean device time per product (ms) of one (variant, engine)
+ * on `batch` equal-shaped products with synthetic coefficients, over `reps`
+ * executions of a batched plan, after two warm-up executions (synchronous).
+ *
+ * ks_dispatch_set_table: installs the autotuned table, n rows of 6 int32:
+ * (len_f, len_g, coeff_bits, is_signed, best variant, best engine).  KS_AUTO
+ * then takes the nearest row in log2 space (n = 0 clears it).
+ *
+ * The cost model is an MLP 5 -> 32 -> 32 -> 12 (ReLU) whose output
+ * 3 (variant - 1) + e (e = 0 schoolbook, 1 NTT, 2 tensor cores) predicts
+ * log2 of the time per product in microseconds from the features
+ * (log2 len_f / 20, log2 len_g / 20, log2 bits / 11, signed, log2 batch / 12).
+ * Parameters: KS_MLP_PARAMS floats, W1 [32x5], b1, W2 [32x32], b2, W3 [12x32],
+ * b3.  ks_mlp_train: full-batch Adam on the GPU (the library's forward,
+ * backward and update kernels), masked mean squared error; params updated in
+ * place.  ks_mlp_grad: one forward and backward pass on the GPU, the gradient
+ * and loss returned to the host.  ks_mlp_predict: inference kernel for n
+ * feature rows (requires installed parameters).  ks_mlp_set_params installs
+ * parameters for dispatch (NULL uninstalls).  All arrays here are HOST arrays;
+ * x is n x 5, t and mask are n x 12.
+ */
+#define KS_MLP_IN 5
+#define KS_MLP_HIDDEN 32
+#define KS_MLP_OUT 12
+int ks_tune_time(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+                 int variant, int engine, int batch, int reps,
+                 double *ms_per_product);
+int ks_dispatch_set_table(int64_t n, const int32_t *rows);
+int64_t ks_mlp_param_count(void);
+int ks_mlp_set_params(const float *params);
+int ks_mlp_train(float *params, const float *x, const float *t,
+                 const float *mask, int64_t n, int steps, float lr,
+                 float *loss);
+int ks_mlp_grad(const float *params, const float *x, const float *t,
+                const float *mask, int64_t n, float *grad, float *loss);
+int ks_mlp_predict(const float *x, int64_t n, float *y);
+
 /* Waits for `stream`, then reports a pending device-side error (or KS_OK). */
 int ks_status_sync(ks_stream_t stream);
 

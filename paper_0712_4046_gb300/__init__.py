@@ -57,6 +57,16 @@ _sig("ks_plan_choice", _ci, _vp, _i64, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
 _sig("ks_plan_destroy", None, _vp)
 
 DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
+
+_fp = ctypes.POINTER(ctypes.c_float)
+_sig("ks_tune_time", _ci, _i64, _i64, _ci, _ci, _ci, _ci, _ci, _ci, ctypes.POINTER(ctypes.c_double))
+_sig("ks_dispatch_set_table", _ci, _i64, ctypes.POINTER(ctypes.c_int32))
+_sig("ks_mlp_param_count", _i64)
+_sig("ks_mlp_set_params", _ci, _fp)
+_sig("ks_mlp_train", _ci, _fp, _fp, _fp, _fp, _i64, _ci, ctypes.c_float, _fp)
+_sig("ks_mlp_grad", _ci, _fp, _fp, _fp, _fp, _i64, _fp, _fp)
+_sig("ks_mlp_predict", _ci, _fp, _i64, _fp)
+MLP_IN, MLP_HIDDEN, MLP_OUT = 5, 32, 12
 _sig("ks_mul_static", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
 
 STATIC_SCRATCH_BYTES = 16 << 20
@@ -273,3 +283,94 @@ def plan_info(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGIN
     _check(lib.ks_plan_info(len_f, len_g, coeff_bits, int(is_signed), variant, engine, arr,
                             len(PLAN_FIELDS)), "ks_plan_info")
     return dict(zip(PLAN_FIELDS, [int(x) for x in arr]))
+
+
+# ------------------------------------------------------------------ dispatch
+def _f32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def tune_time(len_f, len_g, coeff_bits, is_signed, variant, engine, batch=1, reps=5) -> float:
+    """Device milliseconds per product of one (variant, engine) configuration."""
+    ms = ctypes.c_double(0.0)
+    _check(lib.ks_tune_time(len_f, len_g, coeff_bits, int(is_signed), variant, engine, batch,
+                            reps, ctypes.byref(ms)), "ks_tune_time")
+    return ms.value
+
+
+def dispatch_set_table(rows) -> None:
+    """rows: iterable of (len_f, len_g, coeff_bits, is_signed, variant, engine)."""
+    import numpy as np
+    arr = np.ascontiguousarray(np.array(list(rows), dtype=np.int32).reshape(-1, 6))
+    _check(lib.ks_dispatch_set_table(arr.shape[0],
+                                     arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "ks_dispatch_set_table")
+
+
+def mlp_param_count() -> int:
+    return int(lib.ks_mlp_param_count())
+
+
+def mlp_set_params(params) -> None:
+    if params is None:
+        _check(lib.ks_mlp_set_params(None), "ks_mlp_set_params")
+        return
+    p, pp = _f32(params)
+    _check(lib.ks_mlp_set_params(pp), "ks_mlp_set_params")
+
+
+def mlp_train(params, x, t, mask, steps, lr):
+    """Returns (trained params, final loss); every step runs on the GPU."""
+    import numpy as np
+    p = np.array(params, dtype=np.float32, copy=True)
+    pp = p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    xa, xp = _f32(x)
+    ta, tp = _f32(t)
+    ma, mp = _f32(mask)
+    loss = ctypes.c_float(0.0)
+    _check(lib.ks_mlp_train(pp, xp, tp, mp, xa.shape[0], steps, lr, ctypes.byref(loss)),
+           "ks_mlp_train")
+    return p, float(loss.value)
+
+
+def mlp_grad(params, x, t, mask):
+    """One forward + backward on the GPU: (gradient, loss)."""
+    import numpy as np
+    pa, pp = _f32(params)
+    xa, xp = _f32(x)
+    ta, tp = _f32(t)
+    ma, mp = _f32(mask)
+    g = np.zeros(mlp_param_count(), dtype=np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(lib.ks_mlp_grad(pp, xp, tp, mp, xa.shape[0],
+                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)),
+           "ks_mlp_grad")
+    return g, float(loss.value)
+
+
+def mlp_predict(x):
+    """Inference kernel over feature rows (installed parameters)."""
+    import numpy as np
+    xa, xp = _f32(x)
+    y = np.zeros((xa.shape[0], MLP_OUT), dtype=np.float32)
+    _check(lib.ks_mlp_predict(xp, xa.shape[0], y.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "ks_mlp_predict")
+    return y
+
+
+def _install_dispatch_state():
+    """Installs the committed autotuned table and cost model when they were
+    measured on this kind of device (name and SM count); silent otherwise."""
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return False
+        from . import dispatch
+        return dispatch.install()
+    except Exception:
+        return False
+
+
+DISPATCH_STATE_INSTALLED = _install_dispatch_state()

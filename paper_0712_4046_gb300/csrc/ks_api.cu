@@ -135,6 +135,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   const double colmax = dmax * dmax * (double)(p.nA < p.nB ? p.nA : p.nB);
   if (colmax * 2.0 >= 9.2e18) return KS_ERANGE;
   if (engine == KS_ENGINE_SCHOOLBOOK && (double)p.nA * (double)p.nB > 1.5e11) return KS_ENOTSUP;
+  // the contraction engines are quadratic: beyond ~0.1 s of work the transform is the engine
+  if (engine == KS_ENGINE_TC && (double)p.nA * (double)p.nB > 5.0e13) return KS_ENOTSUP;
   if (engine == KS_ENGINE_NTT) {
     int lg2 = 0;
     while (((int64_t)1 << lg2) < p.ncols) lg2++;
@@ -192,10 +194,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   return KS_OK;
 }
 
-// KS_AUTO / KS_ENGINE_AUTO
-int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine) {
-  (void)is_signed;
-  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+// KS_AUTO / KS_ENGINE_AUTO without a table or model: the heuristic
+static int choose_heuristic(int64_t lf, int64_t lg, int b, int *variant, int *engine) {
   const int64_t lh = lf + lg - 1;
   int v = *variant;
   if (v == KS_AUTO) v = (lh >= 64) ? KS_4 : KS_1;
@@ -214,12 +214,91 @@ int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engi
   return KS_OK;
 }
 
+bool table_lookup(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine);
+
+// a choice is usable when it plans (engine limits)
+static bool feasible(int64_t lf, int64_t lg, int b, int is_signed, int v, int e) {
+  Plan p;
+  return make_plan(p, lf, lg, b, is_signed, v, e) == KS_OK;
+}
+
+int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine) {
+  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  if (*variant == KS_AUTO && *engine == KS_ENGINE_AUTO) {
+    int tv = 0, te = 0;
+    if (table_lookup(lf, lg, b, is_signed, &tv, &te) && feasible(lf, lg, b, is_signed, tv, te)) {
+      *variant = tv;
+      *engine = te;
+      return KS_OK;
+    }
+  }
+  int v = *variant, e = *engine;
+  choose_heuristic(lf, lg, b, &v, &e);
+  if (*engine == KS_ENGINE_AUTO && !feasible(lf, lg, b, is_signed, v, e))
+    e = (e == KS_ENGINE_TC) ? KS_ENGINE_NTT : KS_ENGINE_TC;
+  *variant = v;
+  *engine = e;
+  return KS_OK;
+}
+
 // dispatch modes of the batched plans: 0 the library's choice, 1 KS1 wherever
 // the variant is left to the library
 int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *variant,
                 int *engine) {
   if (mode == KS_DISPATCH_KS1 && *variant == KS_AUTO) *variant = KS_1;
+  if (mode == KS_DISPATCH_KS1 || mode == KS_DISPATCH_MLP) {
+    // no table for these modes (the model's choice is made by the plan)
+    if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+    int v = *variant, e = *engine;
+    choose_heuristic(lf, lg, b, &v, &e);
+    if (*engine == KS_ENGINE_AUTO && !feasible(lf, lg, b, is_signed, v, e))
+      e = (e == KS_ENGINE_TC) ? KS_ENGINE_NTT : KS_ENGINE_TC;
+    *variant = v;
+    *engine = e;
+    return KS_OK;
+  }
   return choose(lf, lg, b, is_signed, variant, engine);
+}
+
+bool mlp_installed();
+int mlp_predict_host(const float *x, int64_t n, float *y);
+void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, int64_t batch, float *x);
+
+// Learned dispatch for a batch: one GPU inference over every product whose
+// variant and engine are both left to the library; the cheapest feasible
+// prediction wins.  Returns false when no model is installed.
+bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *engines) {
+  if (!mlp_installed()) return false;
+  std::vector<float> x(n * KS_MLP_IN), y(n * KS_MLP_OUT);
+  for (int64_t i = 0; i < n; i++)
+    mlp_features(probs[i].len_f, probs[i].len_g, probs[i].coeff_bits, probs[i].is_signed, n,
+                 &x[i * KS_MLP_IN]);
+  if (mlp_predict_host(x.data(), n, y.data()) != KS_OK) return false;
+  static const int kEng[3] = {KS_ENGINE_SCHOOLBOOK, KS_ENGINE_NTT, KS_ENGINE_TC};
+  for (int64_t i = 0; i < n; i++) {
+    const ks_problem &q = probs[i];
+    variants[i] = q.variant;
+    engines[i] = q.engine;
+    if (q.variant != KS_AUTO || q.engine != KS_ENGINE_AUTO) continue;
+    int order[KS_MLP_OUT];
+    for (int j = 0; j < KS_MLP_OUT; j++) order[j] = j;
+    for (int a = 1; a < KS_MLP_OUT; a++)  // insertion sort by predicted time
+      for (int c = a; c > 0 && y[i * KS_MLP_OUT + order[c]] < y[i * KS_MLP_OUT + order[c - 1]];
+           c--) {
+        const int t = order[c];
+        order[c] = order[c - 1];
+        order[c - 1] = t;
+      }
+    for (int a = 0; a < KS_MLP_OUT; a++) {
+      const int v = order[a] / 3 + 1, e = kEng[order[a] % 3];
+      if (feasible(q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e)) {
+        variants[i] = v;
+        engines[i] = e;
+        break;
+      }
+    }
+  }
+  return true;
 }
 
 // --------------------------------------------------------------- execution

@@ -27,6 +27,7 @@ namespace ks {
 int *status_ptr();
 int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *variant,
                 int *engine);
+bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *engines);
 
 struct ZeroArgs {
   uint64_t *p;
@@ -333,13 +334,17 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->probs.assign(probs, probs + n);
   std::vector<size_t> offs(n);
   size_t total = 0;
+  // the learned model, where installed and allowed, chooses for the whole batch at once
+  std::vector<int> mv(n, 0), me(n, 0);
+  const bool learned = (dispatch_mode == KS_DISPATCH_MLP || dispatch_mode == KS_DISPATCH_AUTO) &&
+                       n > 0 && mlp_choose_batch(probs, n, mv.data(), me.data());
   for (int64_t i = 0; i < n; i++) {
     const ks_problem &q = probs[i];
     if (!q.h || !q.f || !q.g) {
       delete P;
       return KS_EINVAL;
     }
-    int v = q.variant, e = q.engine;
+    int v = learned ? mv[i] : q.variant, e = learned ? me[i] : q.engine;
     int rc = choose_mode(q.len_f, q.len_g, q.coeff_bits, q.is_signed, dispatch_mode, &v, &e);
     if (rc == KS_OK) rc = make_plan(P->plans[i], q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e);
     if (rc != KS_OK) {
