@@ -118,14 +118,15 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.nB = (bitsG + p.d - 1) / p.d;
   p.ncols = p.nA + p.nB - 1;
   if (engine == KS_ENGINE_TC) {
-    // one more digit: the carry out of the local recoding of overlapping fields
+    // one more digit: the carry out of the balanced recoding
     p.nA += 1;
     p.nB += 1;
     p.ncols = p.nA + p.nB - 1;
     tc_geometry(p.nA, p.nB, p.tg);
     p.ncols = p.tg.ncols;
-    for (int q = 0; q < 4; q++) p.ks[q] = 8;
     if (p.tg.T > ((int64_t)1 << 20)) return KS_ERANGE;
+    // exact fp32 chunks need |recoded digit| <= 72: at most eight fields per 7-bit window
+    if ((b + p.d - 2) / p.N + 1 > 8) return KS_ENOTSUP;
   }
   p.nwords = (p.dn * p.ncols + 95) / 32 + 1;
   p.ntiles = norm_tiles_for(p.nwords);
@@ -335,13 +336,13 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   if (p.engine == KS_ENGINE_TC) {
     {
       PhaseTimer t(s, PH_PACK);
-      KS_CUDA(launch_tc_pack(pa, p.tg, p.nprod, ws + p.off_digits, s));
+      KS_CUDA(launch_tc_pack(pa, p.tg, p.nprod, ws + p.off_digits, cols,
+                             (int64_t)p.nprod * p.ncols, s));
     }
     PhaseTimer t(s, PH_PRODUCT);
     int64_t *C[4];
     for (int q = 0; q < p.nprod; q++) C[q] = cols + (int64_t)q * p.ncols;
-    KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)p.nprod * p.ncols * 8, s));
-    KS_CUDA(launch_tc_products(p.tg, p.nprod, p.ks, ws + p.off_digits, C, status, s));
+    KS_CUDA(launch_tc_products(p.tg, p.nprod, ws + p.off_digits, C, status, s));
   } else {
     {
       PhaseTimer t(s, PH_PACK);

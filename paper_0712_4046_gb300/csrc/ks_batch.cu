@@ -111,7 +111,7 @@ struct ks_plan {
   ks::List<ks::FixArgs> fix;
   std::vector<ks::NttJob> ntt;
   std::vector<ks::SingleJob> singles;
-  int64_t tc_items = 0;
+  int64_t tc_chunks = 0;
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -155,7 +155,7 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
   if (P->school.n())
     KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
                                    P->school.blocks(), s));
-  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_items, s));
+  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_chunks, s));
   for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
   if (P->norm_tiles.n())
     KS_TRY(launch_normalize_batch(P->norm_tiles.d, P->norm_tiles.dprefix, P->norm_jobs.dprefix,
@@ -360,12 +360,6 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     return KS_ENOMEM;
   }
   int *status = status_ptr();
-  // tensor-core work items: one chunk granularity for the whole batch
-  int64_t tc_chunks_total = 0;
-  for (int64_t i = 0; i < n; i++)
-    if (P->plans[i].engine == KS_ENGINE_TC)
-      tc_chunks_total += tc_chunks(P->plans[i].tg, P->plans[i].nprod, P->plans[i].ks);
-  const int cpi = tc_batch_chunks_per_item(tc_chunks_total);
   for (int64_t i = 0; i < n; i++) {
     const Plan &p = P->plans[i];
     char *ws = P->ws + offs[i];
@@ -375,8 +369,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       int64_t *C[4];
       for (int k = 0; k < p.nprod; k++)
         C[k] = reinterpret_cast<int64_t *>(ws + p.off_cols) + (int64_t)k * p.ncols;
-      make_tc_args(p.tg, p.nprod, p.ks, ws + p.off_digits, C, status, cpi, ta);
-      P->tc.add(ta, ta.item_prefix[p.nprod]);
+      make_tc_args(p.tg, p.nprod, ws + p.off_digits, C, status, ta);
+      P->tc.add(ta, ta.chunk_prefix[p.nprod]);
     }
     if (rc != KS_OK) {
       cudaFree(P->ws);
@@ -384,7 +378,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       return rc;
     }
   }
-  P->tc_items = P->tc.blocks();
+  P->tc_chunks = P->tc.blocks();
   // descriptor arrays: one device allocation, filled from a pinned host copy
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
               P->tc.bytes() + P->norm_tiles.bytes() + P->norm_jobs.bytes() + P->unpack.bytes() +

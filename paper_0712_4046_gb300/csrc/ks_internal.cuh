@@ -23,7 +23,7 @@ struct TcGeom {
   int64_t R = 0;      // rows (blocks of 128 digits) of the B operand
   int64_t Pcols = 0;  // output block columns
   int64_t T = 0;      // output tiles of 128 block columns
-  int64_t nG = 0;     // raw A digits stored (fp16, offset by 127, zero padded)
+  int64_t nE = 0;     // rows of the A window array (8 fp16 digits each, zero padded)
   int64_t rows = 0;   // rows per B plane, zero padding included
   int64_t ncols = 0;  // output column sums of four 7-bit digits (28-bit digits)
 };
@@ -34,7 +34,6 @@ struct Plan {
   int b = 0, e = 0, N = 0, is_signed = 0, in_limbs = 0, out_limbs = 0;
   int d = 16;           // digit bits of the sub-product operands
   int dn = 16;          // digit bits of the column sums fed to the normalization
-  int ks[4] = {8, 8, 8, 8};  // tensor-core delta steps per exact accumulation chunk
   TcGeom tg;
   int nprod = 0;        // independent sub-products (1, 2, 2, 4)
   int64_t nA = 0, nB = 0;  // digits of each f-side / g-side operand
@@ -111,18 +110,18 @@ cudaError_t launch_schoolbook_batch(const SchoolArgs *d, const int64_t *prefix, 
 // Tensor-core engine (tcgen05, kind::f16): fp16 operand layouts, then the MMA kernel.
 void tc_geometry(int64_t nA, int64_t nB, TcGeom &g);
 size_t tc_operand_bytes(const TcGeom &g);
+// also clears `nzero` column-sum words at `zero`
 cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
-                           cudaStream_t s);
-cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
+                           int64_t *zero, int64_t nzero, cudaStream_t s);
+cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base,
                                int64_t *const *C, int *status, cudaStream_t s);
 struct TcProduct {
-  const __half *Araw;  // raw A digits, offset by 127 (index x holds digit x - 127)
-  int64_t nAraw;
+  const __half *E;     // A windows: row h holds digits h - 127 .. h - 120
+  int64_t nE;
   const __half *BRT;
   int64_t rows;
   int64_t dmax, R, T;  // largest delta, rows of B, tiles
-  int64_t items_per_tile;
-  int ks;
+  int64_t chunks;  // accumulation chunks over all output tiles
   int64_t *C;
   int64_t ncols;
 };
@@ -130,8 +129,7 @@ struct TcProduct {
 struct TcArgs {
   TcProduct p[4];
   int nprod;
-  int64_t item_prefix[5];
-  int chunks_per_item;
+  int64_t chunk_prefix[5];  // chunks of the sub-products before each one
   int *status;
 };
 
@@ -139,20 +137,24 @@ struct TcPackArgs {
   PackOp op[kMaxOperands];
   int nprod;
   int N, b, in_limbs, flip;
-  __half *Araw[4];
+  __half *E[4];
   __half *BRT[4];
-  int64_t nAraw, rows, R, nA, nB;
+  int64_t nE, rows, R, nA, nB;
+  int64_t segA, segB;  // pack CTAs per A operand and per B operand
+  int64_t *zero;       // column sums cleared by the same launch (nzero words), or null
+  int64_t nzero;
 };
 
 void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
-                       TcPackArgs &a, int64_t &blocks);
+                       TcPackArgs &a, int64_t &blocks, int64_t *zero = nullptr,
+                       int64_t nzero = 0);
 cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int n,
                                  int64_t blocks, cudaStream_t s);
-int64_t tc_chunks(const TcGeom &g, int nprod, const int *ks);
-int tc_batch_chunks_per_item(int64_t total_chunks);
-void make_tc_args(const TcGeom &g, int nprod, const int *ks, char *base, int64_t *const *C,
-                  int *status, int cpi, TcArgs &a);
-cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t items,
+int64_t tc_chunks(const TcGeom &g);  // accumulation chunks of one sub-product
+void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
+                  TcArgs &a);
+// the prefix (in chunks) over the descriptors splits evenly over one CTA per SM
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t chunks,
                             cudaStream_t s);
 
 // NTT engine: column sums of each product by a two-prime transform + CRT.

@@ -21,6 +21,12 @@ struct One {
     local = bid;
     return d;
   }
+  // also the index of the descriptor (always 0)
+  __device__ __forceinline__ const T &locate(int64_t bid, int64_t &local, int &idx) const {
+    local = bid;
+    idx = 0;
+    return d;
+  }
 };
 
 template <class T>
@@ -39,6 +45,11 @@ struct Many {
     }
     local = bid - prefix[lo];
     return d[lo];
+  }
+  __device__ __forceinline__ const T &locate(int64_t bid, int64_t &local, int &idx) const {
+    const T &r = locate(bid, local);
+    idx = (int)(&r - d);
+    return r;
   }
 };
 

@@ -2,41 +2,52 @@
 // 7-bit digit strings on the 5th-generation tensor cores (tcgen05.mma,
 // kind::f16, fp16 operands, fp32 accumulation in tensor memory).
 //
-// Exactness.  Digits are integers with |D| <= 127, exactly representable in
-// fp16.  (A + evaluation whose fields overlap, N < b in the four-point
-// variant, first has digits in [0, 254]; those are recoded locally as
-// D'_j = D_j - 128 [D_j >= 64] + [D_(j-1) >= 64], which lies in [-64, 127],
-// keeps the value, and needs no carry chain.)  One accumulation chunk adds at
-// most 128 * 8 products per output digit, so every partial sum stays below
-// 128 * 8 * 127^2 = 16,516,096 < 2^24, where fp32 holds every integer
-// exactly.  After each chunk the accumulator
-// is read out of tensor memory, converted to int32 (exact) and added to
-// per-thread integer sums; after a work item the sums of four neighbouring
-// digits are merged into one 28-bit-digit column sum and added to global
-// memory with a 64-bit atomic.
+// Digits and exactness.  Each evaluation digit D_j (a signed sum of at most
+// eight 7-bit bit slices, Sec. 3) is recoded into the balanced form
+//   D'_j = D_j - 128 c_j + c_(j-1),   c_j = floor((D_j + 64) / 128),
+// which keeps the value of the digit string (one more top digit holds the
+// last carry), needs no carry chain, and gives |D'_j| <= 72.  An accumulation
+// chunk of ks <= 16 block offsets adds at most 16 * 128 products per output
+// digit, so every partial sum stays below 2048 * 72^2 = 10,616,832 < 2^24 and
+// fp32 holds it exactly.  After each chunk the accumulator is read out of
+// tensor memory, converted to int32 (exact) and added to per-thread integer
+// sums; after a work item the sums of four neighbouring digits are merged
+// into one 28-bit-digit column sum and added to global memory with a 64-bit
+// atomic.
 //
 // Blocking (a product of digit strings is a Toeplitz matrix-vector product):
 // write output digit k = 128 p + q.  For a block offset delta,
 //   C[q, p] += sum_t' A[128 delta + q - 127 + t'] * B[128 (p - delta) + 127 - t'],
 // t' = 0..127.  The A factor depends on q + t' only (a Hankel matrix), so its
-// 8x8 core matrices depend on q/8 + t'/8 only: the A operand is a strip of
-// 8x8 core matrices G_s (G_s[q0][t0] = A[8 s + q0 + t0 - 127]) and one shared
-// memory descriptor with both core-matrix strides equal to 128 bytes walks
-// it -- no 128 x 128 Toeplitz tile is ever stored.  The strip of one chunk is
-// expanded in shared memory from 128 * 8 + 144 consecutive raw digits (one
-// bulk copy), so global memory holds 2 bytes per digit.  For B, the reversed digit
-// string is cut into rows of 128 digits and stored as 16 K-planes (8 digits =
-// 16 bytes per row per plane); the N dimension of the MMA runs over rows, so
+// 8x8 core matrices depend on q/8 + t'/8 only: the A operand of a chunk is a
+// strip of 16 ks + 15 core matrices G_s (G_s[q0][t0] = A[8 s + q0 + t0 - 127])
+// and one shared memory descriptor with both core-matrix strides equal to 128
+// bytes walks it -- no 128 x 128 Toeplitz tile is ever stored.  Row h of a
+// core-matrix strip is the window of eight digits A[h - 127 .. h - 120]; the
+// packing kernel writes every such window once (16 bytes per digit position),
+// so the strip of a chunk is one contiguous bulk copy.  For B, the reversed
+// digit string is cut into rows of 128 digits and stored as 16 K-planes (8
+// digits = 16 bytes per row per plane); the N dimension of the MMA runs over
+// rows (column n of the accumulator is block column p = P0 + 127 - n), so
 // moving from delta to delta + 1 is a 16-byte shift of the B descriptor.
-// Both operands are copied to shared memory with cp.async.bulk (one copy for
-// the raw A digits, one per B plane) completing on an mbarrier.
 //
-// Work: a CTA (8 warps, two per SM) owns an output tile of 128 digits x 128
-// block columns and a run of accumulation chunks; the tensor core of one CTA
-// overlaps the copies and the tensor-memory read-out of the other.  Every
-// mbarrier wait is bounded (about one second of %globaltimer); on expiry the
-// kernel records KS status 1, waits (bounded) for its own copies and MMAs,
-// releases its tensor memory and returns.
+// Trimming.  For a block offset delta only block columns with
+// 0 <= p - delta < R meet B; the MMA of that offset covers just those columns,
+// rounded out to multiples of 16 (its N and its accumulator column offset),
+// so the triangles at both ends of a tile cost almost nothing.  A chunk opens
+// with one MMA of an all-zero A strip that clears the whole accumulator.  The
+// B planes carry 16 zero rows on each side, enough for the rounding.
+//
+// Pipeline (one CTA per SM, persistent over work items of (sub-product,
+// output tile, run of chunks)): warp 0 copies the operands of each chunk into
+// a ring of three shared memory stages (cp.async.bulk completing on an
+// mbarrier), warp 1 issues the MMAs of a chunk into one of two tensor memory
+// accumulators and commits them to the stage's "empty" and the accumulator's
+// "full" barrier, and eight epilogue warps read each accumulator out while
+// the tensor core fills the other one.  Every mbarrier wait is bounded (about
+// one second of %globaltimer); on expiry the CTA records KS status 1, waits
+// (bounded) for its own copies and MMAs, releases its tensor memory and
+// returns.
 #include <cuda_fp16.h>
 
 #include "ks_internal.cuh"
@@ -46,22 +57,30 @@ namespace ks {
 
 namespace {
 constexpr int kTM = 128;                   // MMA M: digits per output block column
-constexpr int kNT = 128;                   // MMA N: block columns per tile
-constexpr int kKS = 8;                     // largest number of delta steps per chunk
-constexpr int kThreads = 256;
+constexpr int kNT = 128;                   // MMA N (largest): block columns per tile
+constexpr int kKS = 16;                    // largest number of delta steps per chunk
+constexpr int kStages = 2;
 constexpr int kCoreA = 16 * kKS + 15;      // A strip core matrices per chunk
 constexpr int kBRows = kNT + kKS - 1;      // B rows per plane per chunk
 constexpr int kStageA = kCoreA * 128;
 constexpr int kPlaneB = kBRows * 16;
 constexpr int kStageB = 16 * kPlaneB;
-constexpr int kRawA = 2 * (128 * kKS + 144);  // raw A digits of one chunk (bytes)
-constexpr int kSmem = kStageA + kStageB + kRawA;
-constexpr int kPad = kNT + 3 * kKS;        // zero rows on each side of the B planes
-constexpr int kMaxItemChunks = 64;
+constexpr int kStage = kStageA + kStageB;
+constexpr int kZeroA = 17 * 128;           // all-zero strip of the clearing MMA
+constexpr int kStaging = 128 * 32 * 8;     // column sums of one output tile (int64)
+constexpr int kSmem = kStages * kStage + kZeroA + kStaging;
+constexpr int kPadB = 16;                  // zero rows on each side of the B planes
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kNumAcc = 4;
+constexpr int kTmemCols = kNT * kNumAcc;
+constexpr int kMaxItemChunks = 128;        // int32 sums: 128 * 10,616,832 < 2^31
+constexpr int kPackSeg = 2048;             // A window rows / reversed B digits per pack CTA
 // instruction descriptor, kind::f16: D = f32 (bits 4-5 = 1), A = B = f16
 // (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kNT >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kIdescM = (1u << 4) | ((uint32_t)(kTM >> 4) << 24);
 constexpr uint64_t kWaitNs = 1000000000ull;
+static_assert(kSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -101,6 +120,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   while (!mbar_try_wait(bar, parity))
     if (globaltimer() - t0 > kWaitNs) return false;
   return true;
+}
+// all eight epilogue warps meet (bounded); false on timeout
+__device__ __forceinline__ bool epi_sync(uint64_t *bar, uint32_t &ph, int lane) {
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+  const bool ok = mbar_wait(bar, ph);
+  ph ^= 1;
+  return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile(
@@ -158,6 +185,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// bulk reduction (add, u64) of `bytes` from shared to global memory, bulk async-group
+__device__ __forceinline__ void bulk_reduce_add_u64(void *dst, const void *src, uint32_t bytes) {
+  asm volatile(
+      "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(dst),
+      "r"(smem_u32(src)), "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 // shared memory matrix descriptor, no swizzle: start, leading (K) and stride
 // (M/N) byte offsets between 8x16-byte core matrices, version bits 46-48 = 1
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -167,224 +210,483 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }  // namespace
 
 // ------------------------------------------------------------------ pack
-// digit j of an evaluation, recoded into [-127, 127] when its fields overlap
-__device__ __forceinline__ int32_t tc_digit(const PackOp &op, int64_t j, int64_t n, int N, int b,
-                                            int in_limbs, int flip) {
-  if (j < 0 || j >= n) return 0;
-  int32_t v = digit_at(op, j, N, b, 7, in_limbs, flip);
-  if (op.sigma > 0 && N < b) {
-    const int32_t prev = j > 0 ? digit_at(op, j - 1, N, b, 7, in_limbs, flip) : 0;
-    v = v - (v >= 64 ? 128 : 0) + (prev >= 64 ? 1 : 0);
-  }
-  return v;
+__device__ __forceinline__ int32_t carry7(int32_t d) { return (d + 64) >> 7; }
+// balanced recoding of digit d whose lower neighbour is prev
+__device__ __forceinline__ int32_t recode7(int32_t d, int32_t prev) {
+  return d - (carry7(d) << 7) + carry7(prev);
 }
 
+// One CTA writes kPackSeg rows of an A window array or 16 storage rows of the
+// 16 B planes of one sub-product: first the plain 7-bit digits of the segment
+// (one more for the recoding carry) into shared memory, then the recoded
+// fp16 digits in the operand layout, 16 bytes per thread, coalesced.
 template <class Src>
 __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
+  __shared__ int32_t raw[kPackSeg + 8];
+  __shared__ __align__(16) __half dig[kPackSeg + 8];
   int64_t local;
   const TcPackArgs &a = src.locate(blockIdx.x, local);
-  const int64_t perA = a.nAraw, perB = 16 * a.rows * 8, per = perA + perB;
-  const int64_t total = per * a.nprod;
-  {
-    const int64_t e = local * 256 + threadIdx.x;
-    if (e >= total) return;
-    const int q = (int)(e / per);
-    const int64_t r = e - q * per;
-    if (r < perA) {
-      const int32_t v = tc_digit(a.op[2 * q], r - 127, a.nA, a.N, a.b, a.in_limbs, a.flip);
-      a.Araw[q][r] = __int2half_rn(v);
-    } else {
-      const int64_t r2 = r - perA;
-      const int64_t t1 = r2 / (a.rows * 8);
-      const int64_t rem = r2 - t1 * a.rows * 8;
-      const int64_t rho = rem / 8 - kPad;
-      const int t0 = (int)(rem & 7);
-      int32_t v = 0;
-      if (rho >= 0 && rho < a.R)
-        v = tc_digit(a.op[2 * q + 1], 128 * a.R - 1 - (128 * rho + 8 * t1 + t0), a.nB, a.N, a.b,
-                     a.in_limbs, a.flip);
-      a.BRT[q][r2] = __int2half_rn(v);
+  const int64_t per = a.segA + a.segB;
+  const int tid = threadIdx.x;
+  if (local >= per * a.nprod) {  // the column sums the product kernel accumulates into
+    const int64_t i0 = (local - per * a.nprod) * 2048;
+    for (int i = tid; i < 2048; i += 256)
+      if (i0 + i < a.nzero) a.zero[i0 + i] = 0;
+    return;
+  }
+  const int q = (int)(local / per);
+  const int64_t r = local - q * per;
+  if (r < a.segA) {
+    // window rows h in [h0, h0 + kPackSeg); row h = digits h - 127 .. h - 120
+    const PackOp &op = a.op[2 * q];
+    const int64_t h0 = r * kPackSeg;
+    const int64_t x0 = h0 - 127;
+    for (int i = tid; i < kPackSeg + 8; i += 256) {
+      const int64_t j = x0 - 1 + i;
+      raw[i] = j < 0 ? 0 : digit_at(op, j, a.N, a.b, 7, a.in_limbs, a.flip);
+    }
+    __syncthreads();
+    for (int i = tid; i < kPackSeg + 7; i += 256) dig[i] = __int2half_rn(recode7(raw[i + 1], raw[i]));
+    __syncthreads();
+    __half *E = a.E[q];
+    for (int i = tid; i < kPackSeg; i += 256) {
+      const int64_t h = h0 + i;
+      if (h >= a.nE) break;
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        w[u] = (uint32_t)__half_as_ushort(dig[i + 2 * u]) |
+               ((uint32_t)__half_as_ushort(dig[i + 2 * u + 1]) << 16);
+      *reinterpret_cast<uint4 *>(E + h * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    // storage rows s in [s0, s0 + 16) of every plane; storage row s is the
+    // reversed row rho = s - kPadB, which holds reversed digits 128 rho .. + 127
+    const PackOp &op = a.op[2 * q + 1];
+    const int64_t s0 = (r - a.segA) * 16;
+    const int64_t rho0 = s0 - kPadB;
+    const int64_t top = 128 * a.R - 1;  // digit index of reversed position 0
+    for (int m = tid; m < kPackSeg + 1; m += 256) {
+      const int64_t j = top - (128 * rho0 + m);
+      raw[m] = (j < 0 || j > top) ? 0 : digit_at(op, j, a.N, a.b, 7, a.in_limbs, a.flip);
+    }
+    __syncthreads();
+    for (int m = tid; m < kPackSeg; m += 256) dig[m] = __int2half_rn(recode7(raw[m], raw[m + 1]));
+    __syncthreads();
+    const int t1 = tid >> 4, u = tid & 15;
+    const int64_t s = s0 + u;
+    if (s < a.rows) {
+      const int64_t rho = rho0 + u;
+      uint4 o = make_uint4(0u, 0u, 0u, 0u);
+      if (rho >= 0 && rho < a.R) o = *reinterpret_cast<const uint4 *>(dig + 128 * u + 8 * t1);
+      *reinterpret_cast<uint4 *>(a.BRT[q] + (t1 * a.rows + s) * 8) = o;
     }
   }
 }
 
 // ------------------------------------------------------------------ MMA
-template <class Src>
-__global__ void __launch_bounds__(kThreads, 2) tc_kernel(Src src, int64_t total) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar_full;
-  __shared__ __align__(8) uint64_t bar_mma;
-  __shared__ uint32_t tmem_sh;
-  __shared__ int bad_range;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t *sA = smem;                       // expanded Hankel strip
-  uint8_t *sB = smem + kStageA;             // 16 B planes
-  uint8_t *sR = smem + kStageA + kStageB;   // raw A digits of the chunk
+namespace {
+// Output tile t (block columns 128 t .. 128 t + 127) meets the block offsets
+// delta in [dlo, dhi]; they form nch chunks of kKS offsets.  Every tile
+// t < T meets at least one offset.
+__host__ __device__ __forceinline__ void tc_tile(int64_t dmax, int64_t R, int64_t t,
+                                                 int64_t &dlo, int64_t &dhi, int64_t &nch) {
+  dlo = 128 * t - R + 1 > 0 ? 128 * t - R + 1 : 0;
+  dhi = 128 * t + 127 < dmax ? 128 * t + 127 : dmax;
+  nch = (dhi - dlo) / kKS + 1;
+}
 
+// Chunks of the tiles before tile t, in closed form: with kKS = 16 dividing
+// 128 the chunk count of a tile is 8 t + 8 while dlo = 0 and dhi = 128 t + 127,
+// constant while exactly one of them is clipped, and K - 8 t once both are.
+static_assert(kKS == 16, "the closed form assumes 16 offsets per chunk");
+__host__ __device__ __forceinline__ int64_t tc_chunk_prefix(int64_t dmax, int64_t R, int64_t t) {
+  const int64_t tA = (R - 1) / 128;                    // dlo = 0 up to tile tA
+  const int64_t tB = dmax >= 127 ? (dmax - 127) / 128 : -1;  // dhi unclipped up to tB
+  const int64_t lo = tA < tB ? tA : tB, hi = tA < tB ? tB : tA;
+  int64_t P = 0;
+  const int64_t m = t < lo + 1 ? t : lo + 1;
+  if (m > 0) P += 4 * m * (m + 1);
+  int64_t a = lo + 1, b = t < hi + 1 ? t : hi + 1;
+  if (b > a) P += (b - a) * (tA < tB ? (R + 126) / 16 + 1 : dmax / 16 + 1);
+  a = hi + 1;
+  b = t;
+  if (b > a) P += (b - a) * ((dmax + R - 1) / 16 + 1) - 4 * (a + b - 1) * (b - a);
+  return P;
+}
+
+// one work item, as the producer hands it to the MMA issuer and the epilogue
+struct __align__(16) TcSlot {
+  const __half *E, *BRT;
+  int64_t *C;
+  int *status;
+  int64_t nE, rows, R, ncols, P0, dlo, dhi;
+  int c0, c1, pad, done;
+};
+constexpr int kItemSlots = 4;
+
+// The item that holds global chunk `s`: its descriptor, sub-product and tile
+// (a binary search over the closed-form tile prefix), and the chunks of that
+// tile from s up to at most s_end.
+template <class Src>
+__device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it) {
+  int64_t local;
+  const TcArgs &a = src.locate(s, local);
+  int q = 0;
+  while (q + 1 < a.nprod && local >= a.chunk_prefix[q + 1]) q++;
+  const TcProduct &P = a.p[q];
+  const int64_t L = local - a.chunk_prefix[q];
+  int64_t tlo = 0, thi = P.T - 1;  // last tile whose prefix is <= L
+  while (tlo < thi) {
+    const int64_t mid = (tlo + thi + 1) >> 1;
+    if (tc_chunk_prefix(P.dmax, P.R, mid) <= L)
+      tlo = mid;
+    else
+      thi = mid - 1;
+  }
+  int64_t dlo, dhi, nch;
+  tc_tile(P.dmax, P.R, tlo, dlo, dhi, nch);
+  const int64_t c = L - tc_chunk_prefix(P.dmax, P.R, tlo);
+  int64_t c1 = nch;
+  if (c1 - c > s_end - s) c1 = c + (s_end - s);
+  if (c1 - c > kMaxItemChunks) c1 = c + kMaxItemChunks;
+  it.E = P.E;
+  it.BRT = P.BRT;
+  it.C = P.C;
+  it.status = a.status;
+  it.nE = P.nE;
+  it.rows = P.rows;
+  it.R = P.R;
+  it.ncols = P.ncols;
+  it.P0 = tlo * kNT;
+  it.dlo = dlo;
+  it.dhi = dhi;
+  it.c0 = (int)c;
+  it.c1 = (int)c1;
+  it.pad = 0;
+  it.done = 0;
+}
+
+__device__ __forceinline__ void slot_store(TcSlot *dst, const TcSlot &v) {
+  const uint4 *s = reinterpret_cast<const uint4 *>(&v);
+  uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(TcSlot) / 16); i++) d[i] = s[i];
+}
+__device__ __forceinline__ void slot_load(TcSlot &v, const TcSlot *src) {
+  const uint4 *s = reinterpret_cast<const uint4 *>(src);
+  uint4 *d = reinterpret_cast<uint4 *>(&v);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(TcSlot) / 16); i++) d[i] = s[i];
+}
+}  // namespace
+
+template <class Src>
+__global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_full[kStages];
+  __shared__ __align__(8) uint64_t bar_empty[kStages];
+  __shared__ __align__(8) uint64_t bar_tfull[kNumAcc];
+  __shared__ __align__(8) uint64_t bar_tempty[kNumAcc];
+  __shared__ __align__(8) uint64_t bar_ifull[kItemSlots];
+  __shared__ __align__(8) uint64_t bar_iempty[kItemSlots];
+  __shared__ __align__(8) uint64_t bar_drain;
+  __shared__ __align__(8) uint64_t bar_epi;
+  __shared__ TcSlot slots[kItemSlots];
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh, bad_range_sh;
+  __shared__ int *status_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int *abort_v = &abort_sh;
+
+  // the B planes and the zero strip start as zeros: B rows a chunk does not
+  // copy stay finite (the clearing MMA multiplies them by zero)
+  for (int st = 0; st < kStages; st++)
+    for (int i = tid; i < kStageB / 16; i += kThreads)
+      reinterpret_cast<uint4 *>(smem + st * kStage + kStageA)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < kZeroA / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(smem + kStages * kStage)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
-    tmem_alloc(&tmem_sh, kNT);
+    tmem_alloc(&tmem_sh, kTmemCols);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bar_full, 1);
-    mbar_init(&bar_mma, 1);
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    for (int b = 0; b < kNumAcc; b++) {
+      mbar_init(&bar_tfull[b], 1);
+      mbar_init(&bar_tempty[b], kEpiWarps);
+    }
+    for (int s = 0; s < kItemSlots; s++) {
+      mbar_init(&bar_ifull[s], 1);
+      mbar_init(&bar_iempty[s], 1 + kEpiWarps);
+    }
+    mbar_init(&bar_drain, 1);
+    mbar_init(&bar_epi, kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bad_range = 0;
+    abort_sh = 0;
+    bad_range_sh = 0;
+    status_sh = nullptr;
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
-  uint32_t ph_full = 0, ph_mma = 0;
-  bool aborted = false, load_pending = false, mma_pending = false;
 
-  const int quad = warp & 3, half = warp >> 2;
-  int *status = nullptr;
-  const int qd = quad * 32 + lane;  // this thread's digit row (TMEM lane)
-
-  for (int64_t gitem = blockIdx.x; gitem < total && !aborted; gitem += gridDim.x) {
-    int64_t item;
-    const TcArgs &a = src.locate(gitem, item);
-    status = a.status;
-    int qp = 0;
-    while (qp + 1 < a.nprod && item >= a.item_prefix[qp + 1]) qp++;
-    const TcProduct &P = a.p[qp];
-    const int64_t local = item - a.item_prefix[qp];
-    const int64_t t = local / P.items_per_tile;
-    const int64_t g = local - t * P.items_per_tile;
-    const int64_t P0 = t * kNT;
-    const int64_t dlo = P0 - P.R + 1 > 0 ? P0 - P.R + 1 : 0;
-    const int64_t dhi = P0 + kNT - 1 < P.dmax ? P0 + kNT - 1 : P.dmax;
-    if (dlo > dhi) continue;
-    const int ks = P.ks;
-    const int64_t nchunks = (dhi - dlo + ks) / ks;
-    const int64_t c0 = g * a.chunks_per_item;
-    const int64_t c1 = c0 + a.chunks_per_item < nchunks ? c0 + a.chunks_per_item : nchunks;
-    if (c0 >= c1) continue;
-
-    // one chunk's operands: raw A digits and 16 B planes
-    auto issue = [&](int64_t c) {
-      const int64_t d0 = dlo + c * ks;
-      const int64_t x0 = 128 * d0;
-      const uint32_t abytes = (uint32_t)(2 * (128 * ks + 144));
-      const int64_t rho0 = P.R - P0 - kNT + d0 + kPad;
-      const uint32_t rbytes = (uint32_t)(kNT + ks - 1) * 16u;
-      if (x0 < 0 || x0 + 128 * ks + 144 > P.nAraw || rho0 < 0 ||
-          rho0 + kNT + ks - 1 > P.rows) {
-        bad_range = 1;
-        mbar_arrive(&bar_full);  // complete the phase without copies
-        return;
-      }
-      mbar_expect_tx(&bar_full, abytes + 16u * rbytes);
-      bulk_g2s(sR, P.Araw + x0, abytes, &bar_full);
-      for (int t1 = 0; t1 < 16; t1++)
-        bulk_g2s(sB + t1 * kPlaneB, P.BRT + (t1 * P.rows + rho0) * 8, rbytes, &bar_full);
-    };
-
-    int32_t acc[64];
-#pragma unroll
-    for (int i = 0; i < 64; i++) acc[i] = 0;
-    if (tid == 0) issue(c0);
-    load_pending = true;
-    for (int64_t c = c0; c < c1; c++) {
-      bool ok = mbar_wait(&bar_full, ph_full);
-      ph_full ^= 1;
-      if (__syncthreads_or(!ok)) {
-        aborted = true;
-        break;
-      }
-      load_pending = false;
-      // expand the Hankel strip: core matrix s, row q0 = raw digits [8 s + q0, 8 s + q0 + 8)
-      {
-        const uint32_t *raw = reinterpret_cast<const uint32_t *>(sR);
-        const int nrows = (16 * ks + 15) * 8;
-        for (int rr = tid; rr < nrows; rr += kThreads) {
-          const int h0 = rr;  // 8 * s + q0 == row index
-          uint4 o;
-          if ((h0 & 1) == 0) {
-            const int w = h0 >> 1;
-            o = make_uint4(raw[w], raw[w + 1], raw[w + 2], raw[w + 3]);
-          } else {
-            const int w = h0 >> 1;
-            const uint32_t x0 = raw[w], x1 = raw[w + 1], x2 = raw[w + 2], x3 = raw[w + 3],
-                           x4 = raw[w + 4];
-            o = make_uint4(__funnelshift_r(x0, x1, 16), __funnelshift_r(x1, x2, 16),
-                           __funnelshift_r(x2, x3, 16), __funnelshift_r(x3, x4, 16));
-          }
-          *reinterpret_cast<uint4 *>(sA + (size_t)rr * 16) = o;
+  if (warp == 0) {
+    // ---------------- producer: item sequence, operand copies into the stage ring
+    if (lane == 0) {
+      int stage = 0, islot = 0;
+      uint32_t phase = 0, iphase = 0, armed = 0, armed_par = 0;
+      bool aborted = false;
+      // this CTA's even share of the chunk sequence
+      const int64_t s_beg = total * blockIdx.x / gridDim.x;
+      const int64_t s_end = total * (blockIdx.x + 1) / gridDim.x;
+      for (int64_t s = s_beg;;) {
+        TcSlot it;
+        const bool have = s < s_end;
+        if (have)
+          tc_decode(src, s, s_end, it);
+        else
+          it.done = 1;
+        if (!mbar_wait(&bar_iempty[islot], iphase ^ 1) || *abort_v) {
+          aborted = true;
+          break;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-      }
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        for (int j = 0; j < ks; j++)
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            const uint64_t ad = sdesc(a0 + (uint32_t)(16 * j + 2 * k) * 128u, 128u, 128u);
-            const uint64_t bd = sdesc(b0 + (uint32_t)(2 * k) * kPlaneB + (uint32_t)j * 16u,
-                                      (uint32_t)kPlaneB, 128u);
-            mma_f16(tmem, ad, bd, kIdesc, (j | k) != 0 ? 1u : 0u);
+        slot_store(&slots[islot], it);
+        mbar_arrive(&bar_ifull[islot]);  // release: the slot is visible to the consumers
+        if (++islot == kItemSlots) {
+          islot = 0;
+          iphase ^= 1;
+        }
+        if (!have) break;
+        s += it.c1 - it.c0;
+        if (status_sh == nullptr) status_sh = it.status;
+        for (int c = it.c0; c < it.c1; c++) {
+          if (!mbar_wait(&bar_empty[stage], phase ^ 1) || *abort_v) {
+            aborted = true;
+            break;
           }
-        mma_commit(&bar_mma);
+          uint8_t *sA = smem + stage * kStage;
+          uint8_t *sB = sA + kStageA;
+          const int64_t d0 = it.dlo + (int64_t)c * kKS;
+          const int64_t h0 = 128 * d0;
+          const int64_t nrowsA = 128 * kKS + 120;
+          const int64_t r0 = it.R - kNT - it.P0 + d0;  // reversed B row of stage row 0
+          const int64_t lo = r0 > -kPadB ? r0 : -kPadB;
+          const int64_t hi = r0 + kNT + kKS - 1 < it.R + kPadB ? r0 + kNT + kKS - 1 : it.R + kPadB;
+          if (h0 < 0 || h0 + nrowsA > it.nE || lo >= hi || hi + kPadB > it.rows) {
+            bad_range_sh = 1;
+            mbar_arrive(&bar_full[stage]);  // complete the phase without copies
+          } else {
+            const uint32_t bbytes = (uint32_t)(hi - lo) * 16u;
+            mbar_expect_tx(&bar_full[stage], (uint32_t)nrowsA * 16u + 16u * bbytes);
+            bulk_g2s(sA, it.E + h0 * 8, (uint32_t)nrowsA * 16u, &bar_full[stage]);
+            for (int t1 = 0; t1 < 16; t1++)
+              bulk_g2s(sB + t1 * kPlaneB + (lo - r0) * 16,
+                       it.BRT + (t1 * it.rows + lo + kPadB) * 8, bbytes, &bar_full[stage]);
+          }
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (aborted) break;
       }
-      mma_pending = true;
-      ok = mbar_wait(&bar_mma, ph_mma);
-      ph_mma ^= 1;
-      if (__syncthreads_or(!ok)) {
+      if (aborted) {
+        *abort_v = 1;
+        for (int s = 0; s < kStages; s++)  // copies still in flight land before exit
+          if (armed & (1u << s)) mbar_wait(&bar_full[s], (armed_par >> s) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: one chunk = clearing MMA + trimmed MMAs
+    if (lane == 0) {
+      int stage = 0, acc = 0, islot = 0;
+      uint32_t phase = 0, aphase = 0, iphase = 0;
+      bool aborted = false, issued = false;
+      const uint64_t zdesc = sdesc(smem_u32(smem + kStages * kStage), 128u, 128u);
+      for (;;) {
+        if (!mbar_wait(&bar_ifull[islot], iphase) || *abort_v) {
+          aborted = true;
+          break;
+        }
+        TcSlot it;
+        slot_load(it, &slots[islot]);
+        mbar_arrive(&bar_iempty[islot]);
+        if (++islot == kItemSlots) {
+          islot = 0;
+          iphase ^= 1;
+        }
+        if (it.done) break;
+        for (int c = it.c0; c < it.c1; c++) {
+          if (!mbar_wait(&bar_full[stage], phase) || !mbar_wait(&bar_tempty[acc], aphase ^ 1) ||
+              *abort_v) {
+            aborted = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + stage * kStage), b0 = a0 + kStageA;
+          const uint32_t dt = tmem + (uint32_t)(acc * kNT);
+          mma_f16(dt, zdesc, sdesc(b0, (uint32_t)kPlaneB, 128u),
+                  kIdescM | ((uint32_t)(kNT >> 3) << 17), 0u);
+          const int64_t d0 = it.dlo + (int64_t)c * kKS;
+          // block columns n' of offset delta: [P0 + 128 - delta - R, P0 + 128 - delta) clipped
+          const int64_t top = it.P0 + kNT - d0;
+          int jmax = kKS;
+          if (d0 + jmax - 1 > it.dhi) jmax = (int)(it.dhi - d0 + 1);
+          for (int j = 0; j < jmax; j++) {
+            int64_t lo = top - j - it.R;
+            int64_t hi = top - j;
+            if (lo < 0) lo = 0;
+            if (hi > kNT) hi = kNT;
+            const uint32_t lo16 = (uint32_t)lo & ~15u;
+            const uint32_t hi16 = ((uint32_t)hi + 15u) & ~15u;
+            const uint32_t idesc = kIdescM | (((hi16 - lo16) >> 3) << 17);
+            const uint32_t aj = a0 + (uint32_t)(16 * j) * 128u;
+            const uint32_t bj = b0 + ((uint32_t)j + lo16) * 16u;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+              mma_f16(dt + lo16, sdesc(aj + (uint32_t)(2 * k) * 128u, 128u, 128u),
+                      sdesc(bj + (uint32_t)(2 * k) * kPlaneB, (uint32_t)kPlaneB, 128u), idesc, 1u);
+          }
+          mma_commit(&bar_empty[stage]);
+          mma_commit(&bar_tfull[acc]);
+          issued = true;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (++acc == kNumAcc) {
+            acc = 0;
+            aphase ^= 1;
+          }
+        }
+        if (aborted) break;
+      }
+      if (aborted) {
+        *abort_v = 1;
+        if (issued) {  // every MMA issued so far completes before the memory is released
+          mma_commit(&bar_drain);
+          mbar_wait(&bar_drain, 0);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: tensor memory -> integer sums -> column atomics
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int u = lane & 3;
+    const bool epi_leader = warp == 2 && lane == 0;
+    long long *staging = reinterpret_cast<long long *>(smem + kStages * kStage + kZeroA);
+    int acc = 0, islot = 0;
+    uint32_t aphase = 0, iphase = 0, ephase = 0;
+    bool aborted = false;
+    for (;;) {
+      const bool iok = mbar_wait(&bar_ifull[islot], iphase);
+      if (__any_sync(0xffffffffu, !iok || *abort_v)) {
         aborted = true;
         break;
       }
-      mma_pending = false;
-      if (c + 1 < c1) {
-        if (tid == 0) issue(c + 1);  // the MMAs are done with the stage
-        load_pending = true;
+      TcSlot it;
+      slot_load(it, &slots[islot]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_iempty[islot]);
+      if (++islot == kItemSlots) {
+        islot = 0;
+        iphase ^= 1;
       }
-      tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
-      uint32_t r[32];
-      tmem_ld32(taddr, r);
-      tmem_wait_ld();
+      if (it.done) break;
+      int32_t sum[64];
 #pragma unroll
-      for (int i = 0; i < 32; i++) acc[i] += __float2int_rn(__uint_as_float(r[i]));
-      tmem_ld32(taddr + 32, r);
-      tmem_wait_ld();
+      for (int i = 0; i < 64; i++) sum[i] = 0;
+      for (int c = it.c0; c < it.c1; c++) {
+        const bool ok = mbar_wait(&bar_tfull[acc], aphase);
+        if (__any_sync(0xffffffffu, !ok || *abort_v)) {
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr =
+            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * kNT + half * 64);
+        uint32_t r[32];
+        tmem_ld32(taddr, r);
+        tmem_wait_ld();
 #pragma unroll
-      for (int i = 0; i < 32; i++) acc[32 + i] += __float2int_rn(__uint_as_float(r[i]));
-      tc_fence_before();
-      __syncthreads();
-    }
-    if (aborted) break;
-    // four neighbouring digits (lanes) -> one 28-bit-digit column sum
-#pragma unroll 4
-    for (int i = 0; i < 64; i++) {
-      const long long v0 = acc[i];
-      const long long v1 = __shfl_down_sync(0xffffffffu, v0, 1);
-      const long long v2 = __shfl_down_sync(0xffffffffu, v0, 2);
-      const long long v3 = __shfl_down_sync(0xffffffffu, v0, 3);
-      if ((lane & 3) == 0) {
-        const long long v = v0 + v1 * 128 + v2 * 16384 + v3 * 2097152;
-        const int64_t p = P0 + kNT - 1 - (half * 64 + i);
-        const int64_t kappa = 32 * p + (qd >> 2);
-        if (v != 0 && kappa < P.ncols)
-          atomicAdd(reinterpret_cast<unsigned long long *>(P.C + kappa), (unsigned long long)v);
+        for (int i = 0; i < 32; i++) sum[i] += __float2int_rn(__uint_as_float(r[i]));
+        tmem_ld32(taddr + 32, r);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_tempty[acc]);
+#pragma unroll
+        for (int i = 0; i < 32; i++) sum[32 + i] += __float2int_rn(__uint_as_float(r[i]));
+        if (++acc == kNumAcc) {
+          acc = 0;
+          aphase ^= 1;
+        }
+      }
+      if (aborted) break;
+      // Four neighbouring digits (lanes 4g .. 4g + 3, weights 128^w) form one
+      // 28-bit-digit column sum.  A two-round butterfly over each group of
+      // four block columns gives lane 4g + u the whole sum of column i + u:
+      // round 1 (lanes u, u ^ 1) pairs the columns i + (u & 1) and
+      // i + 2 + (u & 1), round 2 (lanes u, u ^ 2) completes column i + u.
+      // The tile's 4096 column sums (block column p = P0 + row, 32 per row)
+      // are contiguous in C: they are staged in shared memory and added with
+      // one bulk reduction.
+      if (epi_leader) bulk_wait_read_all();  // the previous tile's reduction has read the staging
+      if (!epi_sync(&bar_epi, ephase, lane)) {
+        aborted = true;
+        break;
+      }
+      {
+        const bool odd = (u & 1) != 0, up = (u & 2) != 0;
+        const long long w_me = 1ll << (7 * u), w_x1 = 1ll << (7 * (u ^ 1));
+        long long *srow = staging + 8 * quad + (lane >> 2);
+#pragma unroll
+        for (int i = 0; i < 64; i += 4) {
+          const int32_t m01 = odd ? sum[i + 1] : sum[i];
+          const int32_t m23 = odd ? sum[i + 3] : sum[i + 2];
+          const int32_t r01 = __shfl_xor_sync(0xffffffffu, odd ? sum[i] : sum[i + 1], 1);
+          const int32_t r23 = __shfl_xor_sync(0xffffffffu, odd ? sum[i + 2] : sum[i + 3], 1);
+          const long long p01 = (long long)m01 * w_me + (long long)r01 * w_x1;
+          const long long p23 = (long long)m23 * w_me + (long long)r23 * w_x1;
+          const long long v = (up ? p23 : p01) + __shfl_xor_sync(0xffffffffu, up ? p01 : p23, 2);
+          srow[(kNT - 1 - half * 64 - i - u) * 32] = v;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (!epi_sync(&bar_epi, ephase, lane)) {
+        aborted = true;
+        break;
+      }
+      if (epi_leader) {
+        const int64_t k0 = 32 * it.P0;
+        int64_t n = it.ncols - k0;
+        if (n > 4096) n = 4096;
+        if (n > 0) {
+          bulk_reduce_add_u64(it.C + k0, staging, (uint32_t)n * 8u);
+          bulk_commit();
+        }
       }
     }
+    if (aborted) *abort_v = 1;
+    if (epi_leader) bulk_wait_all();  // every reduction has landed before the CTA exits
   }
 
-  if (aborted) {
-    if (tid == 0) {
-      if (status) atomicExch(status, 1);
-      if (load_pending) mbar_wait(&bar_full, ph_full ^ 1);
-      if (mma_pending) mbar_wait(&bar_mma, ph_mma ^ 1);
-    }
-  }
-  if (tid == 0 && bad_range && status) atomicExch(status, 3);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kNT);
+  if (tid == 0 && status_sh) {
+    if (*abort_v) atomicExch(status_sh, 1);
+    if (bad_range_sh) atomicExch(status_sh, 3);
+  }
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ host
@@ -395,18 +697,16 @@ void tc_geometry(int64_t nA, int64_t nB, TcGeom &g) {
   g.R = (nB + 127) / 128;
   g.Pcols = g.dmax + g.R;
   g.T = (g.Pcols + kNT - 1) / kNT;
-  g.nG = 128 * (g.dmax + 1 + kKS) + 288;  // raw A digits, offset by 127
-  g.rows = g.R + 2 * kPad;
-  g.ncols = (nA + nB - 2) / 4 + 1;
+  g.nE = 128 * (g.dmax + kKS) + 128;  // window rows read by the last chunk, padded
+  g.rows = g.R + 2 * kPadB;
+  g.ncols = ((nA + nB - 2) / 4 + 2) & ~(int64_t)1;  // even: 16-byte aligned column arrays
 }
 
-size_t tc_operand_bytes(const TcGeom &g) {
-  return (((size_t)g.nG * 2 + 255) & ~(size_t)255) + (size_t)16 * g.rows * 16;
-}
-static size_t raw_bytes(const TcGeom &g) { return ((size_t)g.nG * 2 + 255) & ~(size_t)255; }
+static size_t window_bytes(const TcGeom &g) { return ((size_t)g.nE * 16 + 255) & ~(size_t)255; }
+size_t tc_operand_bytes(const TcGeom &g) { return window_bytes(g) + (size_t)16 * g.rows * 16; }
 
 void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
-                       TcPackArgs &a, int64_t &blocks) {
+                       TcPackArgs &a, int64_t &blocks, int64_t *zero, int64_t nzero) {
   a = TcPackArgs{};
   for (int i = 0; i < 2 * nprod; i++) a.op[i] = pa.op[i];
   a.nprod = nprod;
@@ -416,22 +716,26 @@ void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *bas
   a.flip = pa.flip;
   const size_t per = tc_operand_bytes(g);
   for (int q = 0; q < nprod; q++) {
-    a.Araw[q] = reinterpret_cast<__half *>(base + q * per);
-    a.BRT[q] = reinterpret_cast<__half *>(base + q * per + raw_bytes(g));
+    a.E[q] = reinterpret_cast<__half *>(base + q * per);
+    a.BRT[q] = reinterpret_cast<__half *>(base + q * per + window_bytes(g));
   }
-  a.nAraw = g.nG;
+  a.nE = g.nE;
   a.rows = g.rows;
   a.R = g.R;
   a.nA = g.nA;
   a.nB = g.nB;
-  blocks = ((g.nG + 16 * g.rows * 8) * nprod + 255) / 256;
+  a.segA = (g.nE + kPackSeg - 1) / kPackSeg;
+  a.segB = (g.rows + 15) / 16;
+  a.zero = zero;
+  a.nzero = zero ? nzero : 0;
+  blocks = (a.segA + a.segB) * nprod + (a.nzero + 2047) / 2048;
 }
 
 cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char *base,
-                           cudaStream_t s) {
+                           int64_t *zero, int64_t nzero, cudaStream_t s) {
   TcPackArgs a;
   int64_t blocks;
-  make_tc_pack_args(pa, g, nprod, base, a, blocks);
+  make_tc_pack_args(pa, g, nprod, base, a, blocks, zero, nzero);
   tc_pack_kernel<One<TcPackArgs>><<<(unsigned)blocks, 256, 0, s>>>(One<TcPackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
@@ -445,8 +749,10 @@ cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int
   return cudaGetLastError();
 }
 
-static cudaError_t tc_attr() {
+// per-device launch attributes and SM count (the grid: one CTA per SM)
+static cudaError_t tc_attr(int *sms) {
   static bool attr_done[64] = {false};
+  static int sm_count[64] = {0};
   int dev = 0;
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return e0;
@@ -458,80 +764,64 @@ static cudaError_t tc_attr() {
     e = cudaFuncSetAttribute(tc_kernel<Many<TcArgs>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmem);
     if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
+  if (sms) *sms = sm_count[dev] > 0 ? sm_count[dev] : 1;
   return cudaSuccess;
 }
 
-// chunks per item for a total chunk count: enough items for ~8 per CTA slot
-static int chunks_per_item(int64_t total_chunks) {
-  int64_t cpi = (total_chunks + 1215) / 1216;
-  if (cpi < 1) cpi = 1;
-  if (cpi > kMaxItemChunks) cpi = kMaxItemChunks;
-  return (int)cpi;
-}
+int64_t tc_chunks(const TcGeom &g) { return tc_chunk_prefix(g.dmax, g.R, g.T); }
 
-int64_t tc_chunks(const TcGeom &g, int nprod, const int *ks) {
-  int64_t total = 0;
-  for (int q = 0; q < nprod; q++) {
-    const int64_t span = g.dmax + 1 < g.R + kNT - 1 ? g.dmax + 1 : g.R + kNT - 1;
-    total += (span + ks[q] - 1) / ks[q] * g.T;
-  }
-  return total;
-}
-
-void make_tc_args(const TcGeom &g, int nprod, const int *ks, char *base, int64_t *const *C,
-                  int *status, int cpi, TcArgs &a) {
+void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
+                  TcArgs &a) {
   a = TcArgs{};
   a.nprod = nprod;
   a.status = status;
-  a.chunks_per_item = cpi;
   const size_t per = tc_operand_bytes(g);
-  a.item_prefix[0] = 0;
+  a.chunk_prefix[0] = 0;
   for (int q = 0; q < nprod; q++) {
-    const int64_t span = g.dmax + 1 < g.R + kNT - 1 ? g.dmax + 1 : g.R + kNT - 1;
-    const int64_t cmax = (span + ks[q] - 1) / ks[q];
     TcProduct &P = a.p[q];
-    P.Araw = reinterpret_cast<const __half *>(base + q * per);
-    P.nAraw = g.nG;
-    P.BRT = reinterpret_cast<const __half *>(base + q * per + raw_bytes(g));
+    P.E = reinterpret_cast<const __half *>(base + q * per);
+    P.nE = g.nE;
+    P.BRT = reinterpret_cast<const __half *>(base + q * per + window_bytes(g));
     P.rows = g.rows;
     P.dmax = g.dmax;
     P.R = g.R;
     P.T = g.T;
-    P.items_per_tile = (cmax + cpi - 1) / cpi;
-    P.ks = ks[q];
+    P.chunks = tc_chunks(g);
     P.C = C[q];
     P.ncols = g.ncols;
-    a.item_prefix[q + 1] = a.item_prefix[q] + g.T * P.items_per_tile;
+    a.chunk_prefix[q + 1] = a.chunk_prefix[q] + P.chunks;
   }
 }
 
-cudaError_t launch_tc_products(const TcGeom &g, int nprod, const int *ks, char *base,
-                               int64_t *const *C, int *status, cudaStream_t s) {
-  cudaError_t e = tc_attr();
+cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base, int64_t *const *C,
+                               int *status, cudaStream_t s) {
+  int sms = 0;
+  cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
   TcArgs a;
-  make_tc_args(g, nprod, ks, base, C, status, chunks_per_item(tc_chunks(g, nprod, ks)), a);
-  const int64_t items = a.item_prefix[nprod];
-  if (items <= 0) return cudaSuccess;
-  const int64_t grid = items < 2 * 152 ? items : 2 * 152;
-  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, items);
+  make_tc_args(g, nprod, base, C, status, a);
+  const int64_t chunks = a.chunk_prefix[nprod];
+  if (chunks <= 0) return cudaSuccess;
+  const int64_t grid = chunks < sms ? chunks : sms;
+  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, chunks);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t items,
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t chunks,
                             cudaStream_t s) {
-  if (n == 0 || items == 0) return cudaSuccess;
-  cudaError_t e = tc_attr();
+  if (n == 0 || chunks == 0) return cudaSuccess;
+  int sms = 0;
+  cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
-  const int64_t grid = items < 2 * 152 ? items : 2 * 152;
-  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, items);
+  const int64_t grid = chunks < sms ? chunks : sms;
+  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, chunks);
   note_launches(1);
   return cudaGetLastError();
 }
-
-int tc_batch_chunks_per_item(int64_t total_chunks) { return chunks_per_item(total_chunks); }
 
 }  // namespace ks
