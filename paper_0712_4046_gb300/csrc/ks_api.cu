@@ -128,7 +128,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     // exact fp32 chunks need |recoded digit| <= 72: at most eight fields per 7-bit window
     if ((b + p.d - 2) / p.N + 1 > 8) return KS_ENOTSUP;
   }
-  p.nwords = (p.dn * p.ncols + 95) / 32 + 1;
+  // a multiple of four: every normalized combination starts 16-byte aligned
+  p.nwords = ((p.dn * p.ncols + 95) / 32 + 1 + 3) & ~(int64_t)3;
   p.ntiles = norm_tiles_for(p.nwords);
   // digit magnitude: at most `pieces` fields meet a d-bit window
   const int64_t pieces = (b + p.d - 2) / p.N + 1;
@@ -158,8 +159,11 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     }
     const int64_t nmax = p.run_n[0];
     p.chain = p.M <= 127 ? (nmax + 4095) / 4096 : (nmax + 511) / 512;
-    const int64_t minchain = p.M <= 127 ? 32 : 64;
+    const int64_t minchain = 64;
     if (p.chain < minchain) p.chain = minchain;
+    int64_t c2 = 1;  // a power of two (the staged reconstruction indexes by shifts)
+    while (c2 < p.chain) c2 <<= 1;
+    p.chain = c2;
     p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
     p.nseeds = 0;
     for (int r = 0; r < p.nruns; r++) {

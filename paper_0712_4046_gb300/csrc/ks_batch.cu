@@ -107,6 +107,7 @@ struct ks_plan {
   ks::List<ks::SeedBArgs> seedb, seedb_finish;
   ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
   ks::List<ks::RecoverArgs> recover[3];
+  int recover_smem = 0;  // class 1: the largest staged-digit buffer of the batch
   ks::List<ks::PrefArgs> pref;
   ks::List<ks::FixArgs> fix;
   std::vector<ks::NttJob> ntt;
@@ -175,7 +176,7 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
   for (int c = 0; c < 3; c++)
     if (P->recover[c].n())
       KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
-                                  P->recover[c].n(), P->recover[c].blocks(), s));
+                                  P->recover[c].n(), P->recover[c].blocks(), P->recover_smem, s));
   if (P->pref.n())
     KS_TRY(launch_signed_batch(P->pref.d, P->pref.dprefix, P->fix.d, P->fix.dprefix, P->pref.n(),
                                P->pref.blocks(), P->fix.blocks(), s));
@@ -298,6 +299,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
                           ra, blocks) != 0)
       return KS_ERANGE;
     P->recover[recover_class(p.M) - 1].add(ra, blocks);
+    if (ra.smem > P->recover_smem) P->recover_smem = ra.smem;
   }
   if (p.is_signed) {
     PrefArgs pr;

@@ -273,6 +273,8 @@ struct RecoverArgs {
   uint64_t *h;
   int ol;
   int *status;
+  int64_t rblocks[2];  // M <= 63: CTAs of 32 chains per run
+  int smem;            // M <= 63: staged digit words of one CTA (bytes)
 };
 int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
                       int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,
@@ -281,8 +283,9 @@ int recover_class(int M);
 cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
                            int64_t nwords, int M, int64_t chain, int seed_words,
                            int *status, cudaStream_t s);
+// smem: the largest RecoverArgs::smem of the batch (class 1)
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
-                                 int64_t blocks, cudaStream_t s);
+                                 int64_t blocks, int smem, cudaStream_t s);
 
 // Signed inputs: h_k = h'_k - 2^(b-1) (W_f,k + W_g,k) - 2^(2b-2) cnt_k mod 2^(64 ol).
 struct PrefArgs {
@@ -298,9 +301,12 @@ struct FixArgs {
   int ol;
   int64_t lf, lg;
   int b, il;
-  const uint64_t *pf, *pg;
+  const uint64_t *pf, *pg;  // prefix records
+  const uint64_t *f, *g;    // the coefficients
+  const uint64_t *tf, *tg;  // unused (null)
 };
-// true when the single-launch prefix applies (both lengths <= 2^16)
+// true when the short path applies (lengths <= 16384, in_limbs <= 8, ol <= 17):
+// one scanning CTA per polynomial (pref_blocks = 2), then the correction
 bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
                       int64_t lg, int b, int in_limbs, uint64_t *prefix, PrefArgs &a,
                       FixArgs &fx, int64_t &pref_blocks, int64_t &fix_blocks);

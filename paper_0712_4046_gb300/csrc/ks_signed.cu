@@ -13,9 +13,10 @@
 // cross coefficients.  The correction itself is computed mod 2^(64 ol),
 // which is exact because the final coefficient fits ol limbs.
 //
-// Prefix sums: for polynomials of up to 2^16 coefficients a single launch in
-// which each CTA also sums the blocks before its own; longer ones use a
-// three-phase scan (block totals, scan of the totals, apply).
+// Prefix records: polynomials of up to 16384 coefficients are scanned in one
+// launch of one CTA per 512-coefficient tile; longer ones by a three-phase
+// scan (block totals, scan of the totals, apply).  The correction then reads
+// four records per output k.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -166,59 +167,195 @@ __global__ void __launch_bounds__(kThreads) pref_apply(PrefArgs a) {
   }
 }
 
-// Polynomials of up to kSmallL coefficients: a single launch.  Each CTA
-// first sums every coefficient before its block (redundant across CTAs, at
-// most kSmallL / 2 extra reads per CTA), then scans its own block.
-constexpr int64_t kSmallL = 1 << 16;
+// ---------------------------------------------------------------- short polynomials
+// Up to kScanL coefficients: one CTA per tile of 512 coefficients.  It sums
+// the coefficients of every earlier tile (512 threads, at most 32 independent
+// loads each), scans its own tile across the block, and writes the prefix
+// records of the tile (coalesced).  No CTA waits on another.
+constexpr int kPT = 512;
+constexpr int64_t kScanL = (int64_t)kPT * 32;
+
+// field l of coefficient t: limb l (l < il), or 1 when the coefficient is negative (l = il)
+__device__ __forceinline__ uint64_t field(const uint64_t *x, int il, int64_t t, int l) {
+  const uint64_t *c = x + t * il;
+  return l < il ? c[l] : (c[il - 1] >> 63);
+}
+
+// inclusive block scan of v and block total of p (kPT threads)
+__device__ __forceinline__ void tile_scan(U2 &v, U2 &p, U2 *wsum, U2 *wscan) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    U2 o, r;
+    o.lo = __shfl_up_sync(0xffffffffu, v.lo, off);
+    o.hi = __shfl_up_sync(0xffffffffu, v.hi, off);
+    if (lane >= off) v = add2(v, o);
+    r.lo = __shfl_xor_sync(0xffffffffu, p.lo, off);
+    r.hi = __shfl_xor_sync(0xffffffffu, p.hi, off);
+    p = add2(p, r);
+  }
+  __syncthreads();
+  if (lane == 31) wscan[wid] = v;
+  if (lane == 0) wsum[wid] = p;
+  __syncthreads();
+  U2 base = {0, 0};
+#pragma unroll
+  for (int w = 0; w < kPT / 32; w++) {
+    base = add2(base, wsum[w]);
+    if (w < wid) base = add2(base, wscan[w]);
+  }
+  v = add2(base, v);
+}
 
 template <class Src>
-__global__ void __launch_bounds__(kThreads) pref_single(Src src) {
+__global__ void __launch_bounds__(kPT) pref_tile(Src src) {
+  __shared__ U2 wsum[kPT / 32];
+  __shared__ U2 wscan[kPT / 32];
   int64_t blk;
   const PrefArgs &a = src.locate(blockIdx.x, blk);
-  const int q = which(a, blk);
-  const int64_t b0 = blk * kBlock;
-  const int64_t t0 = b0 + (int64_t)threadIdx.x * kElems;
+  const int q = blk < a.nblocks[0] ? 0 : 1;
+  if (q) blk -= a.nblocks[0];
+  const uint64_t *x = q ? a.x[1] : a.x[0];
+  const int64_t L = q ? a.L[1] : a.L[0];
+  uint64_t *P = q ? a.P[1] : a.P[0];
   const int il = a.il, rec = 2 * il + 1;
-  for (int l = 0; l <= il; l++) {
-    // sum of the preceding blocks (four independent partial sums per thread)
-    U2 bp[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    int64_t t = threadIdx.x;
-    for (; t + 3 * kThreads < b0; t += 4 * kThreads) {
+  const int tid = threadIdx.x;
+  const int64_t t = blk * kPT + tid;
+  for (int l = 0; l < il; l++) {
+    // element tid of every earlier tile (blk < 32): limb l, and for the top
+    // limb also the count of negative coefficients, from the same loads
+    U2 p = {0, 0}, pn = {0, 0};
+    const bool top = l == il - 1;
+    for (int64_t m0 = 0; m0 < blk; m0 += 16) {
+      uint64_t v[16];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint64_t *c = a.x[q] + (t + u * kThreads) * il;
-        bp[u] = add2(bp[u], U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+      for (int u = 0; u < 16; u++)
+        v[u] = m0 + u < blk ? x[((m0 + u) * kPT + tid) * il + l] : 0ull;
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        p = add2(p, U2{v[u], 0});
+        pn.lo += v[u] >> 63;
       }
     }
-    for (; t < b0; t += kThreads) {
-      const uint64_t *c = a.x[q] + t * il;
-      bp[0] = add2(bp[0], U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    const uint64_t e = t < L ? x[t * il + l] : 0ull;
+    U2 sv = U2{e, 0};
+    tile_scan(sv, p, wsum, wscan);
+    if (t < L) {
+      P[t * rec + 2 * l] = sv.lo;
+      P[t * rec + 2 * l + 1] = sv.hi;
     }
-    const U2 before = add2(add2(bp[0], bp[1]), add2(bp[2], bp[3]));
-    U2 tot_before;
-    block_excl(before, &tot_before);
-    U2 mine = {0, 0};
-    for (int e = 0; e < kElems; e++) {
-      const int64_t t = t0 + e;
-      if (t >= a.L[q]) break;
-      const uint64_t *c = a.x[q] + t * il;
-      mine = add2(mine, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
+    if (top) {
+      U2 sn = U2{e >> 63, 0};
+      tile_scan(sn, pn, wsum, wscan);
+      if (t < L) P[t * rec + 2 * il] = sn.lo;
     }
-    U2 tot;
-    U2 run = add2(block_excl(mine, &tot), tot_before);
-    for (int e = 0; e < kElems; e++) {
-      const int64_t t = t0 + e;
-      if (t >= a.L[q]) break;
-      const uint64_t *c = a.x[q] + t * il;
-      run = add2(run, U2{l < il ? c[l] : (c[il - 1] >> 63), 0});
-      uint64_t *P = a.P[q] + t * rec;
-      if (l < il) {
-        P[2 * l] = run.lo;
-        P[2 * l + 1] = run.hi;
-      } else {
-        P[2 * il] = run.lo;
+  }
+}
+
+// r -= x << sh (mod 2^(64 ol)), fixed-size arrays
+template <int OL>
+__device__ __forceinline__ void sub_shifted_fixed(uint64_t (&r)[OL], const uint64_t (&x)[OL],
+                                                  int ol, int sh) {
+  const int q = sh >> 6, rr = sh & 63;
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int l = 0; l < OL; l++) {
+    if (l < ol) {
+      uint64_t v = 0;
+#pragma unroll
+      for (int m = 0; m < OL; m++) {  // limb l of x << sh, with static register indices
+        if (m == l - q) v |= x[m] << rr;
+        if (rr && m == l - q - 1) v |= x[m] >> (64 - rr);
+      }
+      const uint64_t d1 = r[l] - v;
+      const uint64_t b1 = r[l] < v;
+      const uint64_t d2 = d1 - borrow;
+      const uint64_t b2 = d1 < borrow;
+      r[l] = d2;
+      borrow = b1 | b2;
+    }
+  }
+}
+
+// w += sign * (window sum from prefix records A - B, B null for an empty lower part)
+template <int IL, int OL>
+__device__ __forceinline__ void add_window_fixed(uint64_t (&w)[OL], const uint64_t *A,
+                                                 const uint64_t *B, int il) {
+#pragma unroll
+  for (int l = 0; l < IL; l++) {
+    if (l < il) {
+      U2 d = U2{A[2 * l], A[2 * l + 1]};
+      if (B) d = sub2(d, U2{B[2 * l], B[2 * l + 1]});
+      uint64_t carry = 0;
+#pragma unroll
+      for (int m = 0; m < OL; m++) {
+        if (m >= l) {
+          const uint64_t add = m == l ? d.lo : (m == l + 1 ? d.hi : 0ull);
+          const uint64_t s1 = w[m] + add;
+          const uint64_t c1 = s1 < add;
+          const uint64_t s2 = s1 + carry;
+          const uint64_t c2 = s2 < carry;
+          w[m] = s2;
+          carry = c1 + c2;
+        }
       }
     }
+  }
+  // minus 2^(64 il) times the count of negative coefficients in the window
+  const uint64_t neg = A[2 * il] - (B ? B[2 * il] : 0ull);
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int m = 0; m < OL; m++) {
+    if (m >= il) {
+      const uint64_t v = m == il ? neg : 0ull;
+      const uint64_t d1 = w[m] - v;
+      const uint64_t b1 = w[m] < v;
+      const uint64_t d2 = d1 - borrow;
+      const uint64_t b2 = d1 < borrow;
+      w[m] = d2;
+      borrow = b1 | b2;
+    }
+  }
+}
+
+template <int IL, int OL>
+__device__ __forceinline__ void signed_fix_body(const FixArgs &fa, int64_t k) {
+  const int ol = fa.ol, il = fa.il, rec = 2 * il + 1;
+  const int64_t lf = fa.lf, lg = fa.lg;
+  if (k >= lf + lg - 1) return;
+  uint64_t w[OL], r[OL], cnt[OL];
+#pragma unroll
+  for (int l = 0; l < OL; l++) w[l] = cnt[l] = 0;
+  const int64_t fhi = k < lf - 1 ? k : lf - 1;
+  const int64_t flo = k - lg + 1 > 0 ? k - lg + 1 : 0;
+  const int64_t ghi = k < lg - 1 ? k : lg - 1;
+  const int64_t glo = k - lf + 1 > 0 ? k - lf + 1 : 0;
+  add_window_fixed<IL, OL>(w, fa.pf + fhi * rec, flo > 0 ? fa.pf + (flo - 1) * rec : nullptr, il);
+  add_window_fixed<IL, OL>(w, fa.pg + ghi * rec, glo > 0 ? fa.pg + (glo - 1) * rec : nullptr, il);
+  uint64_t *hk = fa.h + k * ol;
+#pragma unroll
+  for (int l = 0; l < OL; l++) r[l] = l < ol ? hk[l] : 0ull;
+  cnt[0] = (uint64_t)(fhi - flo + 1);
+  sub_shifted_fixed<OL>(r, w, ol, fa.b - 1);
+  sub_shifted_fixed<OL>(r, cnt, ol, 2 * fa.b - 2);
+#pragma unroll
+  for (int l = 0; l < OL; l++)
+    if (l < ol) hk[l] = r[l];
+}
+
+// h_k -= 2^(b-1) (W_f + W_g)_k + 2^(2b-2) cnt_k, one output per thread;
+// the limb-count class is uniform per CTA (a batch may mix classes)
+template <class Src>
+__global__ void __launch_bounds__(128) signed_fix_fast(Src src) {
+  int64_t local;
+  const FixArgs &fa = src.locate(blockIdx.x, local);
+  const int64_t k = local * 128 + threadIdx.x;
+  switch (fa.il) {
+    case 1: signed_fix_body<1, 3>(fa, k); break;
+    case 2: signed_fix_body<2, 5>(fa, k); break;
+    case 3:
+    case 4: signed_fix_body<4, 9>(fa, k); break;
+    default: signed_fix_body<8, 17>(fa, k); break;
   }
 }
 
@@ -333,10 +470,15 @@ bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const 
   a.P[0] = prefix;
   a.P[1] = prefix + lf * rec;
   a.bt = prefix + (lf + lg) * rec;
-  fx = FixArgs{h, ol, lf, lg, b, in_limbs, a.P[0], a.P[1]};
-  pref_blocks = a.nblocks[0] + a.nblocks[1];
+  fx = FixArgs{h, ol, lf, lg, b, in_limbs, a.P[0], a.P[1], f, g, nullptr, nullptr};
   fix_blocks = (lf + lg - 1 + 127) / 128;
-  return lf <= kSmallL && lg <= kSmallL;  // single-launch prefix possible
+  const bool fast = lf <= kScanL && lg <= kScanL && in_limbs <= 8 && ol <= 17;
+  if (fast) {  // tiles of 512 coefficients
+    a.nblocks[0] = (lf + kPT - 1) / kPT;
+    a.nblocks[1] = (lg + kPT - 1) / kPT;
+  }
+  pref_blocks = a.nblocks[0] + a.nblocks[1];
+  return fast;
 }
 
 cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
@@ -346,18 +488,20 @@ cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf
   PrefArgs a;
   FixArgs fx;
   int64_t pb, fb;
-  const bool single = make_signed_args(h, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb);
-  int launches = 2;
-  if (single) {
-    pref_single<One<PrefArgs>><<<(unsigned)pb, kThreads, 0, s>>>(One<PrefArgs>{a});
-  } else {
-    pref_block_totals<<<(unsigned)pb, kThreads, 0, s>>>(a);
-    pref_scan_totals<<<2, 64, 0, s>>>(a);
-    pref_apply<<<(unsigned)pb, kThreads, 0, s>>>(a);
-    launches = 4;
+  if (make_signed_args(h, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb)) {
+    pref_tile<One<PrefArgs>><<<(unsigned)pb, kPT, 0, s>>>(One<PrefArgs>{a});
+    signed_fix_fast<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
+    note_launches(2);
+    return cudaGetLastError();
   }
-  signed_fix_kernel<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
-  note_launches(launches);
+  pref_block_totals<<<(unsigned)pb, kThreads, 0, s>>>(a);
+  pref_scan_totals<<<2, 64, 0, s>>>(a);
+  pref_apply<<<(unsigned)pb, kThreads, 0, s>>>(a);
+  if (in_limbs <= 8 && ol <= 17)
+    signed_fix_fast<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
+  else
+    signed_fix_kernel<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
+  note_launches(4);
   return cudaGetLastError();
 }
 
@@ -365,9 +509,9 @@ cudaError_t launch_signed_batch(const PrefArgs *pa, const int64_t *pref_prefix,
                                 const FixArgs *fa, const int64_t *fix_prefix, int n,
                                 int64_t pref_blocks, int64_t fix_blocks, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  pref_single<Many<PrefArgs>><<<(unsigned)pref_blocks, kThreads, 0, s>>>(
+  pref_tile<Many<PrefArgs>><<<(unsigned)pref_blocks, kPT, 0, s>>>(
       Many<PrefArgs>{pa, pref_prefix, n});
-  signed_fix_kernel<Many<FixArgs>><<<(unsigned)fix_blocks, 128, 0, s>>>(
+  signed_fix_fast<Many<FixArgs>><<<(unsigned)fix_blocks, 128, 0, s>>>(
       Many<FixArgs>{fa, fix_prefix, n});
   note_launches(2);
   return cudaGetLastError();

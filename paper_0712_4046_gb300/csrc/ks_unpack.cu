@@ -211,10 +211,24 @@ __device__ __forceinline__ int64_t seed_k(const RecoverRun &R, int64_t chain, in
 }
 }  // namespace
 
+// 32 x 32 -> 64-bit multiply-add (one instruction)
+__device__ __forceinline__ void mad_wide(unsigned long long &acc, uint32_t x, uint32_t y) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(y));
+}
+
+// b <= 48: values split into 24-bit halves, x = xl + 2^24 xh, with xs = xl + xh;
+// x y = xl yl + (xs ys - xl yl - xh yh) 2^24 + xh yh 2^48, three multiply-adds per
+// pair whose sums over one slice (2048 t, 32 per thread) stay below 2^56.
+// Thread (sub, sq): t = sub, sub + 64, ... of each chunk, seeds sq + 4 r (r < 4),
+// one load of x serving four seeds.
+__device__ __forceinline__ uint4 split24(uint64_t v) {
+  const uint32_t lo = (uint32_t)(v & 0xFFFFFFull), hi = (uint32_t)(v >> 24);
+  return make_uint4(lo, hi, lo + hi, 0u);
+}
+
 template <class Src>
 __global__ void __launch_bounds__(256) seed_blocked64(Src src) {
-  __shared__ uint64_t sf[kST];
-  __shared__ uint64_t sg[kSW];
+  __shared__ __align__(16) uint8_t sraw[kST * 16 + kSW * 16];
   __shared__ unsigned long long colsum[kSG][6];
   int64_t bid;
   const SeedBArgs &a = src.locate(blockIdx.x, bid);
@@ -234,73 +248,168 @@ __global__ void __launch_bounds__(256) seed_blocked64(Src src) {
   const int64_t sid0 = gid * kSG;
   const int nS = (int)(nseeds - sid0 < kSG ? nseeds - sid0 : kSG);
   const int tid = threadIdx.x;
-  const int sl = tid >> 4, sub = tid & 15;
   for (int i = tid; i < kSG * 6; i += 256) (&colsum[0][0])[i] = 0ull;
   const int64_t kmin = seed_k(R, a.chain, sid0);
   const int64_t kmax = seed_k(R, a.chain, sid0 + nS - 1);
-  const int64_t kk = sl < nS ? seed_k(R, a.chain, sid0 + sl) : -1;
   const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
   const uint64_t fl = flip ? (1ull << (b - 1)) : 0ull;
-  uint64_t a0 = 0, a1 = 0, a2 = 0;
+  const bool split = b <= 48;
   // this CTA's slice of the t range
   int64_t tlo = kmin - lg + 1 > 0 ? kmin - lg + 1 : 0;
   int64_t thi = kmax < lf - 1 ? kmax : lf - 1;
   const int64_t s_lo = tlo + slice * kSlice;
   const int64_t s_hi = s_lo + kSlice - 1 < thi ? s_lo + kSlice - 1 : thi;
-  for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
-    const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
-    const int64_t jlo = kmin - t0 - T + 1;
-    const int W = (int)(kmax - kmin + T);
-    __syncthreads();
-    for (int i = tid; i < T; i += 256) sf[i] = (f[(t0 + i) * in_limbs] & mask) ^ fl;
-    for (int i = tid; i < W; i += 256) {
-      const int64_t j = jlo + i;
-      sg[i] = (j >= 0 && j < lg) ? ((g[j * in_limbs] & mask) ^ fl) : 0ull;
-    }
-    __syncthreads();
-    if (kk >= 0) {
-      // four independent 192-bit partial sums keep several products in flight
-      uint64_t b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
-      const int base = (int)(kk - t0 - jlo);  // sg index of t = t0
-      int i = sub;
-      for (; i + 48 < T; i += 64) {
+  if (split) {
+    uint4 *sf = reinterpret_cast<uint4 *>(sraw);
+    uint4 *sg = sf + kST;
+    const int sub = tid & 63, sq = tid >> 6;
+    int64_t kk[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) kk[u] = sq + 4 * u < nS ? seed_k(R, a.chain, sid0 + sq + 4 * u) : -1;
+    unsigned long long ll[4] = {0, 0, 0, 0}, hh[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+    for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
+      const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
+      const int64_t jlo = kmin - t0 - T + 1;
+      const int W = (int)(kmax - kmin + T);
+      // every global load of the chunk is issued before any of them is used
+      uint64_t vf[kST / 256], vg[kSW / 256];
+#pragma unroll
+      for (int m = 0; m < kST / 256; m++) {
+        const int i = tid + 256 * m;
+        vf[m] = i < T ? f[(t0 + i) * in_limbs] : 0ull;
+      }
+#pragma unroll
+      for (int m = 0; m < kSW / 256; m++) {
+        const int i = tid + 256 * m;
+        const int64_t j = jlo + i;
+        vg[m] = (i < W && j >= 0 && j < lg) ? g[j * in_limbs] : 0ull;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < kST / 256; m++) {
+        const int i = tid + 256 * m;
+        if (i < T) sf[i] = split24((vf[m] & mask) ^ fl);
+      }
+#pragma unroll
+      for (int m = 0; m < kSW / 256; m++) {
+        const int i = tid + 256 * m;
+        const int64_t j = jlo + i;
+        if (i < W) sg[i] = split24((j >= 0 && j < lg) ? ((vg[m] & mask) ^ fl) : 0ull);
+      }
+      __syncthreads();
+      int base[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) base[u] = kk[u] >= 0 ? (int)(kk[u] - t0 - jlo) : 0;
+      for (int i = sub; i < T; i += 64) {
+        const uint4 x = sf[i];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          const uint64_t x = sf[i + 16 * u];
-          const uint64_t y = sg[base - i - 16 * u];
-          const uint64_t lo = x * y, hi = __umul64hi(x, y);
-          b0[u] += lo;
-          const uint64_t h1 = hi + (b0[u] < lo);
-          b1[u] += h1;
-          b2[u] += b1[u] < h1;
+          if (kk[u] >= 0) {
+            const uint4 y = sg[base[u] - i];
+            mad_wide(ll[u], x.x, y.x);
+            mad_wide(hh[u], x.y, y.y);
+            mad_wide(ss[u], x.z, y.z);
+          }
         }
       }
-      for (; i < T; i += 16) {
-        const uint64_t x = sf[i];
-        const uint64_t y = sg[base - i];
-        const uint64_t lo = x * y, hi = __umul64hi(x, y);
-        b0[0] += lo;
-        const uint64_t h1 = hi + (b0[0] < lo);
-        b1[0] += h1;
-        b2[0] += b1[0] < h1;
-      }
+    }
+    // reduce over the 64 threads of each seed through shared memory:
+    // red[seed][value][sub], then one thread per (seed, value) sums 64 entries
+    __syncthreads();
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(sraw);
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        a0 += b0[u];
-        const uint64_t c0 = a0 < b0[u];
-        const uint64_t m = b1[u] + c0;
-        const uint64_t c1 = m < c0;
-        a1 += m;
-        a2 += b2[u] + c1 + (a1 < m);
+    for (int u = 0; u < 4; u++) {
+      const int sd = sq + 4 * u;
+      red[(sd * 3 + 0) * 64 + sub] = ll[u];
+      red[(sd * 3 + 1) * 64 + sub] = hh[u];
+      red[(sd * 3 + 2) * 64 + sub] = ss[u];
+    }
+    __syncthreads();
+    unsigned long long tot = 0;
+    if (tid < kSG * 3) {
+      const unsigned long long *rr = red + tid * 64;
+#pragma unroll 16
+      for (int i = 0; i < 64; i++) tot += rr[(i + tid) & 63];
+    }
+    __syncthreads();
+    if (tid < kSG * 3) red[tid] = tot;
+    __syncthreads();
+    if (tid < nS) {
+      const unsigned long long l = red[tid * 3], hv = red[tid * 3 + 1], sv = red[tid * 3 + 2];
+      // ll + (ss - ll - hh) 2^24 + hh 2^48 as 128 bits (the middle term is non-negative)
+      const uint64_t mid = sv - l - hv;
+      const uint64_t ml = mid << 24, mh = mid >> 40;
+      const uint64_t hl = hv << 48, hhi = hv >> 16;
+      uint64_t lo = l + ml;
+      uint64_t hi = mh + hhi + (lo < ml);
+      lo += hl;
+      hi += lo < hl;
+      colsum[tid][0] = (uint32_t)lo;
+      colsum[tid][1] = (uint32_t)(lo >> 32);
+      colsum[tid][2] = (uint32_t)hi;
+      colsum[tid][3] = (uint32_t)(hi >> 32);
+    }
+  } else {
+    uint64_t *sf = reinterpret_cast<uint64_t *>(sraw);
+    uint64_t *sg = sf + kST;
+    const int sl = tid >> 4, sub = tid & 15;
+    const int64_t kk = sl < nS ? seed_k(R, a.chain, sid0 + sl) : -1;
+    uint64_t a0 = 0, a1 = 0, a2 = 0;
+    for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
+      const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
+      const int64_t jlo = kmin - t0 - T + 1;
+      const int W = (int)(kmax - kmin + T);
+      __syncthreads();
+      for (int i = tid; i < T; i += 256) sf[i] = (f[(t0 + i) * in_limbs] & mask) ^ fl;
+      for (int i = tid; i < W; i += 256) {
+        const int64_t j = jlo + i;
+        sg[i] = (j >= 0 && j < lg) ? ((g[j * in_limbs] & mask) ^ fl) : 0ull;
+      }
+      __syncthreads();
+      if (kk >= 0) {
+        // four independent 192-bit partial sums keep several products in flight
+        uint64_t b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
+        const int base = (int)(kk - t0 - jlo);  // sg index of t = t0
+        int i = sub;
+        for (; i + 48 < T; i += 64) {
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const uint64_t x = sf[i + 16 * u];
+            const uint64_t y = sg[base - i - 16 * u];
+            const uint64_t lo = x * y, hi = __umul64hi(x, y);
+            b0[u] += lo;
+            const uint64_t h1 = hi + (b0[u] < lo);
+            b1[u] += h1;
+            b2[u] += b1[u] < h1;
+          }
+        }
+        for (; i < T; i += 16) {
+          const uint64_t x = sf[i];
+          const uint64_t y = sg[base - i];
+          const uint64_t lo = x * y, hi = __umul64hi(x, y);
+          b0[0] += lo;
+          const uint64_t h1 = hi + (b0[0] < lo);
+          b1[0] += h1;
+          b2[0] += b1[0] < h1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          a0 += b0[u];
+          const uint64_t c0 = a0 < b0[u];
+          const uint64_t m = b1[u] + c0;
+          const uint64_t c1 = m < c0;
+          a1 += m;
+          a2 += b2[u] + c1 + (a1 < m);
+        }
       }
     }
-  }
-  if (kk >= 0) {
-    const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
-                            (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
+    if (kk >= 0) {
+      const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
+                              (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
 #pragma unroll
-    for (int w = 0; w < 6; w++)
-      if (w6[w]) atomicAdd(&colsum[sl][w], (unsigned long long)w6[w]);
+      for (int w = 0; w < 6; w++)
+        if (w6[w]) atomicAdd(&colsum[sl][w], (unsigned long long)w6[w]);
+    }
   }
   __syncthreads();
   if (tid < nS * 6) {
@@ -701,6 +810,231 @@ __global__ void __launch_bounds__(128) recover_kernel1(Src src) {
   }
 }
 
+// ---- bulk copies into shared memory (one thread issues, all wait, bounded)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void stage_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes,
+                                           uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// wait for phase 0 of the barrier, about one second at most; false on timeout
+__device__ __forceinline__ bool stage_wait(uint64_t *bar) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar))
+        : "memory");
+    if (ok) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+// M <= 63, digits staged in shared memory.  A CTA of 128 threads runs cpc
+// consecutive chains of one run (cpc <= 32, cpc * chain <= 2048):
+//  1. one bulk copy of the bit ranges of V_f and V_r those chains read (the
+//     chains are contiguous, so are their digits);
+//  2. all threads extract the digits u_j, w_m into 64-bit arrays;
+//  3. warp 0, one lane per chain, runs the recurrence of Sec. 3.2 from shared
+//     memory and stages the coefficients;
+//  4. all threads write the coefficients out.
+constexpr int kRT = 128;
+constexpr int kRCmax = 32;
+
+// 64 bits at bit `pos` of a staged word range (words outside [0, nw) read as zero)
+__device__ __forceinline__ uint64_t sbits64(const uint32_t *w, int64_t nw, int64_t pos) {
+  const int64_t i = pos >> 5;
+  const int sh = (int)(pos & 31);
+  const uint64_t w0 = (i >= 0 && i < nw) ? w[i] : 0u;
+  const uint64_t w1 = (i + 1 >= 0 && i + 1 < nw) ? w[i + 1] : 0u;
+  const uint64_t w2 = (i + 2 >= 0 && i + 2 < nw) ? w[i + 2] : 0u;
+  const uint64_t lo = w0 | (w1 << 32);
+  return sh ? ((lo >> sh) | (w2 << (64 - sh))) : lo;
+}
+
+__host__ __device__ __forceinline__ int recover_cpc(int64_t chain) {
+  int64_t c = 2048 / chain;
+  return (int)(c < 1 ? 1 : (c > kRCmax ? kRCmax : c));
+}
+// staged words of one digit string (multiple of four)
+__host__ __device__ __forceinline__ int64_t staged_words(int64_t chain, int M) {
+  return (((recover_cpc(chain) * chain + 2) * (int64_t)M + 31) / 32 + 12) & ~(int64_t)3;
+}
+// digits of one string, [step t in 0..chain][lane]: lanes read consecutive words
+__host__ __device__ __forceinline__ int64_t staged_digits(int64_t chain) {
+  return (chain + 1) * recover_cpc(chain);
+}
+__host__ __device__ __forceinline__ int64_t staged_bytes(int64_t chain, int M) {
+  return 2 * staged_words(chain, M) * 4 + 2 * staged_digits(chain) * 8 +
+         recover_cpc(chain) * chain * 2 * 8;
+}
+
+template <class Src>
+__global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
+  extern __shared__ __align__(16) uint32_t stg[];
+  __shared__ __align__(8) uint64_t bar;
+  int64_t local;
+  const RecoverArgs &a = src.locate(blockIdx.x, local);
+  int r = 0;
+  while (r + 1 < a.nruns && local >= a.rblocks[r]) {
+    local -= a.rblocks[r];
+    r++;
+  }
+  const RecoverRun &R = a.run[r];
+  int *status = a.status;
+  const int M = a.M, ol = a.ol;
+  const uint64_t mask = (1ull << M) - 1ull;
+  const int64_t n = R.n, chain = a.chain, nwords = a.nwords;
+  const int cpc = recover_cpc(chain);
+  const int tid = threadIdx.x;
+  const int64_t c0 = local * cpc;
+  const int64_t c1 = c0 + cpc < R.nchains ? c0 + cpc : R.nchains;
+  const int64_t j0 = c0 * chain;                        // first coefficient of the CTA
+  const int64_t jhi = c1 * chain < n ? c1 * chain : n;  // one past the last
+  // digits u_j, j in [j0, jhi]; w_m, m in [n - jhi, n - j0]
+  const int64_t ub0 = ((R.off_f + j0 * (int64_t)M) >> 5) & ~(int64_t)3;
+  const int64_t nu = ((((R.off_f + (jhi + 1) * (int64_t)M) >> 5) + 3 - ub0) + 3) & ~(int64_t)3;
+  const int64_t wb0 = ((R.off_r + (n - jhi) * (int64_t)M) >> 5) & ~(int64_t)3;
+  const int64_t nw = ((((R.off_r + (n - j0 + 1) * (int64_t)M) >> 5) + 3 - wb0) + 3) &
+                     ~(int64_t)3;
+  const int64_t capw = staged_words(chain, M), capd = staged_digits(chain);
+  if (nu > capw || nw > capw || ub0 < 0 || wb0 < 0 || (chain & (chain - 1)) != 0 || ol > 2) {
+    if (tid == 0) atomicExch(status, 3);  // not for a plan from make_recover_args
+    return;
+  }
+  uint32_t *su = stg, *sw = stg + capw;
+  // [t][lane] layouts: du(t, i) = u_(s_i + t), dw(t, i) = w_(n - s_i - t) with
+  // s_i = j0 + i chain (t = chain reaches the next chain's start), so(t, i) =
+  // coefficient s_i + t
+  uint64_t *du = reinterpret_cast<uint64_t *>(stg + 2 * capw);
+  uint64_t *dw = du + capd;
+  uint64_t *so = dw + capd;
+  // 1. the part of each word range inside the array arrives by bulk copy; the rest is zero
+  const int64_t cu = ub0 + nu <= nwords ? nu : (nwords > ub0 ? nwords - ub0 : 0);
+  const int64_t cw = wb0 + nw <= nwords ? nw : (nwords > wb0 ? nwords - wb0 : 0);
+  for (int64_t i = cu + tid; i < nu; i += kRT) su[i] = 0u;
+  for (int64_t i = cw + tid; i < nw; i += kRT) sw[i] = 0u;
+  if (tid == 0) {
+    stage_init(&bar);
+    stage_expect(&bar, (uint32_t)((cu + cw) * 4));
+    if (cu > 0) stage_copy(su, R.Vf + ub0, (uint32_t)(cu * 4), &bar);
+    if (cw > 0) stage_copy(sw, R.Vr + wb0, (uint32_t)(cw * 4), &bar);
+  }
+  __syncthreads();
+  if (!__syncthreads_and(stage_wait(&bar))) {
+    if (tid == 0) atomicExch(status, 1);
+    stage_wait(&bar);  // once more (bounded) for the copies in flight before leaving
+    return;
+  }
+  // 2. digits (chain and cpc are powers of two)
+  const int lc = __ffsll((long long)chain) - 1, lp = __ffs(cpc) - 1;
+  const int64_t pu = R.off_f - ub0 * 32, pw = R.off_r - wb0 * 32;  // staged bit offsets
+  for (int q = tid; q < (int)capd; q += kRT) {
+    const int t = q >> lp, i = q & (cpc - 1);
+    const int64_t j = j0 + ((int64_t)i << lc) + t;
+    const bool in = j <= jhi;
+    du[q] = in ? sbits64(su, nu, pu + j * (int64_t)M) & mask : 0ull;
+    dw[q] = in ? sbits64(sw, nw, pw + (n - j) * (int64_t)M) & mask : 0ull;
+  }
+  __syncthreads();
+  // 3. the chains (warp 0)
+  const int64_t gid = c0 + tid;
+  if (tid < 32 && gid < c1) {
+    const int64_t ln = tid;
+    auto u = [&](int64_t j) { return du[(j - j0 - (ln << lc)) * cpc + ln]; };
+    auto w = [&](int64_t m) { return dw[(n - m - j0 - (ln << lc)) * cpc + ln]; };
+    const int64_t s = gid * chain;
+    const int64_t e = (s + chain < n) ? s + chain : n;
+    uint64_t a_prev, a_cur, delta;
+    if (s == 0) {
+      a_prev = 0;
+      a_cur = u(0);
+      delta = 0;
+    } else {
+      const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
+      a_prev = load_d1(sd, a.seed_words, 0, M);
+      const uint64_t b_prev = load_d1(sd, a.seed_words, M, M);
+      a_cur = load_d1(sd + a.seed_words, a.seed_words, 0, M);
+      const uint64_t us = u(s);
+      const uint64_t dprev = (us - b_prev - a_cur) & mask;
+      if (dprev > 1) atomicExch(status, 2);
+      delta = (b_prev + a_cur + dprev - us) >> M;
+    }
+    uint64_t w_cur = w(n - s);
+    // step t reads du(t + 1, ln) and dw(t + 1, ln); eight steps are loaded ahead
+    const uint64_t *pdu = du + cpc + ln, *pdw = dw + cpc + ln;
+    uint64_t *po = so + 2 * ln;
+    constexpr int kAhead = 8;
+    uint64_t ub[kAhead], wb[kAhead];
+#pragma unroll
+    for (int q = 0; q < kAhead; q++) {
+      ub[q] = q < chain ? pdu[q * cpc] : 0ull;
+      wb[q] = q < chain ? pdw[q * cpc] : 0ull;
+    }
+    for (int64_t j = s; j < e; j++) {
+      const int t = (int)(j - s);
+      uint64_t *out = po + 2 * t * cpc;
+      const uint64_t u_next = ub[0], w_next = wb[0];
+#pragma unroll
+      for (int q = 0; q + 1 < kAhead; q++) {
+        ub[q] = ub[q + 1];
+        wb[q] = wb[q + 1];
+      }
+      ub[kAhead - 1] = t + kAhead < chain ? pdu[(t + kAhead) * cpc] : 0ull;
+      wb[kAhead - 1] = t + kAhead < chain ? pdw[(t + kAhead) * cpc] : 0ull;
+      if (j <= n - 2) {
+        const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
+        const uint64_t beta = (w_cur - a_prev - eps) & mask;
+        const uint64_t a_next = (u_next - beta - delta) & mask;
+        const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
+        if (dnext > 1) atomicExch(status, 2);
+        out[0] = a_cur | (beta << M);
+        out[1] = beta >> (64 - M);
+        a_prev = a_cur;
+        a_cur = a_next;
+        delta = dnext;
+        w_cur = w_next;
+      } else {
+        const uint64_t beta = (w_cur - a_prev) & mask;
+        out[0] = a_cur | (beta << M);
+        out[1] = beta >> (64 - M);
+      }
+    }
+  }
+  __syncthreads();
+  // 4. coefficients out
+  uint64_t *h = a.h;
+  uint64_t *hb = h + (R.kbase + R.kstride * j0) * ol;
+  const int64_t hs = R.kstride * ol;
+  for (int q = tid; q < (int)((jhi - j0) * ol); q += kRT) {
+    const int jj = ol == 2 ? q >> 1 : q;
+    const int l = q - jj * ol;
+    const int i = jj >> lc, t = jj & (int)(chain - 1);
+    hb[jj * hs + l] = so[((t << lp) + i) * 2 + l];
+  }
+}
+
 // 64 <= M <= 127
 template <class Src>
 __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
@@ -838,6 +1172,18 @@ int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, in
   a.ol = ol;
   a.status = status;
   if ((M + 31) / 32 > kMaxDigitWordsM) return -1;
+  if (M <= 63) {  // staged: CTAs of cpc chains that do not straddle runs
+    const int cpc = recover_cpc(chain);
+    blocks = 0;
+    for (int r = 0; r < nruns; r++) {
+      a.rblocks[r] = (runs[r].nchains + cpc - 1) / cpc;
+      blocks += a.rblocks[r];
+    }
+    const int64_t bytes = staged_bytes(chain, M);
+    if (bytes > 200 * 1024 || ol > 2) return -1;
+    a.smem = (int)bytes;
+    return 0;
+  }
   const int per = M <= 127 ? 128 : 64;
   blocks = (total + per - 1) / per;
   return 0;
@@ -846,10 +1192,28 @@ int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, in
 int recover_class(int M) { return M <= 63 ? 1 : (M <= 127 ? 2 : 3); }
 
 template <class Src>
-static void launch_recover_class(int cls, int64_t blocks, const Src &src, cudaStream_t s) {
-  if (cls == 1)
-    recover_kernel1<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
-  else if (cls == 2)
+static cudaError_t staged_attr(int smem) {
+  static int done[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem > 48 * 1024 && smem > done[dev]) {
+    e = cudaFuncSetAttribute(recover_staged1<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+    if (e != cudaSuccess) return e;
+    done[dev] = smem;
+  }
+  return cudaSuccess;
+}
+
+template <class Src>
+static void launch_recover_class(int cls, int64_t blocks, const Src &src, int smem,
+                                 cudaStream_t s) {
+  if (cls == 1) {
+    if (staged_attr<Src>(smem) == cudaSuccess)
+      recover_staged1<Src><<<(unsigned)blocks, kRT, smem, s>>>(src);
+  } else if (cls == 2)
     recover_kernel2<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
   else
     recover_wide<Src><<<(unsigned)blocks, 64, 0, s>>>(src);
@@ -863,15 +1227,15 @@ cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nrun
   if (make_recover_args(h, ol, runs, nruns, nwords, M, chain, seed_words, status, a, blocks) != 0)
     return cudaErrorInvalidValue;
   if (blocks == 0) return cudaSuccess;
-  launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, s);
+  launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, a.smem, s);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
-                                 int64_t blocks, cudaStream_t s) {
+                                 int64_t blocks, int smem, cudaStream_t s) {
   if (n == 0 || blocks == 0) return cudaSuccess;
-  launch_recover_class(cls, blocks, Many<RecoverArgs>{d, prefix, n}, s);
+  launch_recover_class(cls, blocks, Many<RecoverArgs>{d, prefix, n}, smem, s);
   note_launches(1);
   return cudaGetLastError();
 }
