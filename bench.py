@@ -312,6 +312,9 @@ def main_ours(args):
     # ---- batched workload: 4096 uneven products, one plan per dispatch mode, CUDA graph
     batched = run_batched(ks, dev, stream, flush, args.steps, args.warmup, world)
 
+    # ---- HBM-bound phases (pack, normalize, unpack) where the arrays exceed L2
+    hbm_phases = run_hbm_phases(ks, dev, stream, flush, hbm_gbs, peak_kind)
+
     # ---- roofline of the dominant phase of KS4
     r4 = results["KS4"]
     info = ks.plan_info(lf, lg, b, sg, 4, ks.ENGINE_AUTO)
@@ -366,9 +369,78 @@ def main_ours(args):
                 "d2h_bytes_per_step": int(lh * ol * 8)},
         "cpu_baseline": cpu,
         "batched": batched,
+        "hbm_phases": hbm_phases,
     }
     print(json.dumps(line))
     return 0
+
+
+HBM_WORKLOAD = {"workload": "zx_product_2pow20_u256", "len_f": 1 << 20, "len_g": 1 << 20,
+                "coeff_bits": 256, "is_signed": False, "seed_f": 55, "seed_g": 56}
+
+
+def phase_bytes(phase, info, lf, lg):
+    """Algorithmic bytes of one launch of a memory-bound phase: every input
+    element read once, every output element written once."""
+    nprod, nA, nB, ncols = info["nprod"], info["nA"], info["nB"], info["ncols"]
+    nw, nnorm, ol, il = info["nwords"], info["nnorm"], info["out_limbs"], info["in_limbs"]
+    if phase == "pack":  # coefficients in, int32 digits out
+        return (lf + lg) * il * 8 + nprod * (nA + nB) * 4
+    if phase == "normalize":  # column sums in (each once), 32-bit words out
+        return nprod * ncols * 8 + nnorm * nw * 4
+    if phase == "unpack":  # words in, coefficients out
+        return nnorm * nw * 4 + (lf + lg - 1) * ol * 8
+    return None
+
+
+def run_hbm_phases(ks, dev, stream, flush, hbm_gbs, peak_kind, reps=3):
+    """Per-phase achieved bandwidth of pack, normalize and unpack on one
+    2^20 x 256-bit product (the transform regime; every array is larger than
+    the 129 MB L2), from the library's per-phase CUDA events on the launching
+    stream, L2 flushed before each product."""
+    import torch
+    w = HBM_WORKLOAD
+    lf, lg, b = w["len_f"], w["len_g"], w["coeff_bits"]
+    f = ks_inputs.random_poly(lf, b, False, w["seed_f"])
+    g = ks_inputs.random_poly(lg, b, False, w["seed_g"])
+    tf = torch.from_numpy(f.view(np.int64)).to(dev)
+    tg = torch.from_numpy(g.view(np.int64)).to(dev)
+    ol = ks.out_limbs(lf, lg, b, False)
+    h = torch.empty((lf + lg - 1, ol), dtype=torch.int64, device=dev)
+    out = {"config": dict(w, l2="flushed before each product (256 MiB write)", reps=reps),
+           "peak_gbs": hbm_gbs, "peak_kind": peak_kind, "variants": {}}
+    for label, variant in (("KS1", 1), ("KS2", 2)):
+        info = ks.plan_info(lf, lg, b, False, variant, ks.ENGINE_AUTO)
+        ks.ks_mul(h, tf, tg, b, False, variant, stream)  # warm-up (workspace, tables)
+        torch.cuda.synchronize()
+        ks.profile_collect()
+        ks.profile_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            flush.zero_()
+            ks.ks_mul(h, tf, tg, b, False, variant, stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / reps
+        ks.profile_enable(False)
+        ks.status_sync(stream)
+        ph = ks.profile_collect()
+        res = {"engine": info["engine"], "product_ms_wall": wall * 1000.0}
+        for name in ("pack", "normalize", "unpack", "product"):
+            tot, cnt = ph.get(name, (0.0, 0))
+            if cnt == 0:
+                continue
+            ms = tot / cnt
+            byts = phase_bytes(name, info, lf, lg)
+            r = {"ms": ms}
+            if byts is not None:
+                gbs = byts / (ms / 1000.0) / 1e9
+                r.update({"bytes": int(byts), "achieved_gbs": gbs, "frac": gbs / hbm_gbs})
+            res[name] = r
+        out["variants"][label] = res
+    del tf, tg, h
+    ks.release_cache()
+    torch.cuda.empty_cache()
+    return out
 
 
 BATCH = {"workload": "uneven_batch_4096", "n": 4096, "seed": 20071231, "len": [8, 8192],

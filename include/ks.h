@@ -95,6 +95,12 @@ int64_t ks_workspace_bytes(int64_t len_f, int64_t len_g, int coeff_bits,
  * h must not overlap f or g; f may equal g.  Workspace comes from a cache
  * the library keeps per (device, stream) and grows on demand (so the first
  * call for a size allocates; later ones do not).  Asynchronous on `stream`.
+ * The phases that read only f and g (the exact seeds of Sec. 3.2's
+ * reconstruction, the prefix records of the signed correction) run on a
+ * helper stream the library creates on the first call per (device, stream),
+ * forked from and joined back into `stream` with events; as seen from
+ * `stream` the call is ordered like any other work on it, and it can be
+ * captured into a CUDA graph (the helper stream becomes a parallel branch).
  */
 int ks_mul(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
            int64_t len_g, int coeff_bits, int is_signed, int variant,
@@ -102,7 +108,8 @@ int ks_mul(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
 
 /*
  * As ks_mul, with an explicit engine and caller-owned device workspace of at
- * least ks_workspace_bytes() bytes (256-byte aligned).  Allocates nothing.
+ * least ks_workspace_bytes() bytes (256-byte aligned).  Allocates no device
+ * memory (it shares ks_mul's helper stream, created on first use).
  */
 int ks_mul_ex(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
               int64_t len_g, int coeff_bits, int is_signed, int variant,
@@ -269,7 +276,9 @@ const char *ks_last_cuda_error(void);
  * waits for those events and returns, per phase id (0 .. n-1, names from
  * ks_phase_name), the summed milliseconds and the number of records, then
  * clears them.  Phases: 0 pack, 1 product, 2 normalize, 3 unpack, 4 seeds,
- * 5 recover, 6 signed_fix, 7 reduce_mod.
+ * 5 recover, 6 signed_fix, 7 reduce_mod, 8 signed_prefix.  Seeds and
+ * signed_prefix read only f and g and run on a helper stream concurrently
+ * with phases 0-3 (their events are recorded on that stream).
  */
 long long ks_launch_count(void);
 

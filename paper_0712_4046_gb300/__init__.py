@@ -88,7 +88,7 @@ PLAN_FIELDS = ("variant", "engine", "N", "d", "nprod", "nA", "nB", "ncols", "nwo
                "off_digits", "off_cols", "off_words", "off_seeds", "seed_words", "nchains0",
                "nchains1")
 
-N_PHASES = 8
+N_PHASES = 9
 
 
 class KSError(RuntimeError):
@@ -263,6 +263,11 @@ def mul(f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO, stream
 
 def launch_count() -> int:
     return int(lib.ks_launch_count())
+
+
+def release_cache() -> None:
+    """Frees the workspaces the library has cached for the current device."""
+    lib.ks_release_cache()
 
 
 def profile_enable(on: bool = True) -> None:

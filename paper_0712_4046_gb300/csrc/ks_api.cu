@@ -12,7 +12,6 @@
 
 namespace ks {
 
-int64_t norm_tiles_for(int64_t nwords);
 size_t signed_prefix_bytes(int64_t lf, int64_t lg, int il);
 
 static thread_local char g_cuda_err[256] = "";
@@ -130,7 +129,7 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   }
   // a multiple of four: every normalized combination starts 16-byte aligned
   p.nwords = ((p.dn * p.ncols + 95) / 32 + 1 + 3) & ~(int64_t)3;
-  p.ntiles = norm_tiles_for(p.nwords);
+  p.ntiles = norm_tiles_for(p.nwords, p.dn);
   // digit magnitude: at most `pieces` fields meet a d-bit window
   const int64_t pieces = (b + p.d - 2) / p.N + 1;
   const double dmax = (double)pieces * (double)((1 << p.d) - 1);
@@ -179,13 +178,13 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   else
     off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
   p.off_cols = off;
-  off = align256(off + (size_t)p.nprod * p.ncols * 8);
+  // the normalization's look-back flags follow the column sums directly, so
+  // the clearing of the column sums clears them too
+  p.off_flags = off + (size_t)p.nprod * p.ncols * 8;
+  p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
+  off = align256(p.off_flags + (size_t)p.flag_bytes);
   p.off_words = off;
   off = align256(off + (size_t)p.nnorm * p.nwords * 4);
-  p.off_agg = off;
-  off = align256(off + (size_t)p.nnorm * p.ntiles);
-  p.off_cin = off;
-  off = align256(off + (size_t)p.nnorm * p.ntiles);
   p.off_seeds = off;
   off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
   p.off_seedacc = off;
@@ -307,17 +306,91 @@ bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *en
 }
 
 // --------------------------------------------------------------- execution
+// A helper stream and two events per (device, caller stream): the seeds and
+// the signed prefix records read only f and g, so they run on the helper
+// stream while the products run on the caller's, and are joined before the
+// reconstruction.  Created on first use (no device memory) and kept.
+struct Fork {
+  int dev;
+  cudaStream_t stream, side;
+  cudaEvent_t fork, join;
+};
+static std::mutex g_fork_mu;
+static std::vector<Fork> g_forks;
+
+static int fork_for(cudaStream_t s, Fork *out) {
+  int dev = 0;
+  KS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_fork_mu);
+  for (const Fork &x : g_forks)
+    if (x.dev == dev && x.stream == s) {
+      *out = x;
+      return KS_OK;
+    }
+  Fork x{dev, s, nullptr, nullptr, nullptr};
+  KS_CUDA(cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking));
+  KS_CUDA(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+  KS_CUDA(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
+  g_forks.push_back(x);
+  *out = x;
+  return KS_OK;
+}
+
 // h: exact product destination (Lh x out_limbs).  ws: workspace of >= p.total.
+// fork: run the input-only phases on a helper stream (false: all on s).
 static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_t *g, char *ws,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool fork = true) {
   int *status = status_ptr();
   if (status == nullptr) return KS_ECUDA;
   int32_t *dig = reinterpret_cast<int32_t *>(ws + p.off_digits);
   int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
-  uint8_t *agg = reinterpret_cast<uint8_t *>(ws + p.off_agg);
-  int8_t *cin = reinterpret_cast<int8_t *>(ws + p.off_cin);
+  uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
+  const int64_t nzero = (int64_t)p.nprod * p.ncols + p.flag_bytes / 8;  // sums + flags
+  uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
+
+  // reconstruction runs (Sec. 3.2; twice for Sec. 3.4)
+  RecoverRun runs[2];
+  if (p.variant == KS_3 || p.variant == KS_4) {
+    const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
+                   *V3 = words + 3 * p.nwords;
+    const int64_t N = p.N;
+    if (p.variant == KS_3) {
+      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
+    } else {
+      const bool odd = (p.lh & 1) == 1;
+      // even coefficients: 2E with (2ER or 2X OR); odd: 2X O with (2X OR or 2ER)
+      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
+                           p.nchains[0], seeds, 0};
+      if (p.nruns > 1)
+        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
+                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
+    }
+  }
+
+  // the phases that read only f and g: exact seeds, signed prefix records
+  const bool recon = p.variant == KS_3 || p.variant == KS_4;
+  Fork fk{};
+  cudaStream_t side = s;
+  if (fork && (recon || p.is_signed)) {
+    const int rc = fork_for(s, &fk);
+    if (rc != KS_OK) return rc;
+    side = fk.side;
+    KS_CUDA(cudaEventRecord(fk.fork, s));
+    KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
+  }
+  if (recon) {
+    PhaseTimer t(side, PH_SEEDS);
+    KS_CUDA(launch_seeds(seeds, p.seed_words,
+                         reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
+                         p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, side));
+  }
+  if (p.is_signed) {
+    PhaseTimer t(side, PH_SIGNED_PREFIX);
+    KS_CUDA(launch_signed_prefix(p.out_limbs, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, side));
+  }
+  if (side != s) KS_CUDA(cudaEventRecord(fk.join, side));
 
   // sub-product p: (reversed, sigma)
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
@@ -340,8 +413,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   if (p.engine == KS_ENGINE_TC) {
     {
       PhaseTimer t(s, PH_PACK);
-      KS_CUDA(launch_tc_pack(pa, p.tg, p.nprod, ws + p.off_digits, cols,
-                             (int64_t)p.nprod * p.ncols, s));
+      KS_CUDA(launch_tc_pack(pa, p.tg, p.nprod, ws + p.off_digits, cols, nzero, s));
     }
     PhaseTimer t(s, PH_PRODUCT);
     int64_t *C[4];
@@ -354,9 +426,10 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     }
     PhaseTimer t(s, PH_PRODUCT);
     if (p.engine == KS_ENGINE_SCHOOLBOOK) {
-      KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)p.nprod * p.ncols * 8, s));
+      KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)nzero * 8, s));
       KS_CUDA(launch_schoolbook(prods, p.nprod, s));
     } else {
+      KS_CUDA(cudaMemsetAsync(flags, 0, (size_t)p.flag_bytes, s));
       KS_CUDA(launch_ntt_products(prods, p.nprod, p.ntt_log, p.d, ws + p.off_ntt, s));
     }
   }
@@ -370,8 +443,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
     jobs[i].sigma = sigma;
     jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].agg = agg + (int64_t)i * p.ntiles;
-    jobs[i].cin = cin + (int64_t)i * p.ntiles;
+    jobs[i].flags = flags + 2 + (int64_t)i * p.ntiles;
   };
   switch (p.variant) {
     case KS_1: job(0, 0, -1, 1); break;
@@ -382,7 +454,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   }
   {
     PhaseTimer t(s, PH_NORMALIZE);
-    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, s));
+    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, flags, status, s));
   }
   const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
                  *V3 = words + 3 * p.nwords;
@@ -394,36 +466,16 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   } else if (p.variant == KS_2) {
     PhaseTimer t(s, PH_UNPACK);
     KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N}, s));
-  } else {
-    RecoverRun runs[2];
-    const int64_t N = p.N;
-    if (p.variant == KS_3) {
-      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
-    } else {
-      const bool odd = (p.lh & 1) == 1;
-      // even coefficients: 2E with (2ER or 2X OR); odd: 2X O with (2X OR or 2ER)
-      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
-                           p.nchains[0], seeds, 0};
-      if (p.nruns > 1)
-        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
-                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
-    }
-    {
-      PhaseTimer t(s, PH_SEEDS);
-      KS_CUDA(launch_seeds(seeds, p.seed_words,
-                           reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
-                           p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, s));
-    }
-    {
-      PhaseTimer t(s, PH_RECOVER);
-      KS_CUDA(launch_recover(h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words,
-                             status, s));
-    }
+  }
+  if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join, 0));
+  if (recon) {
+    PhaseTimer t(s, PH_RECOVER);
+    KS_CUDA(launch_recover(h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words, status,
+                           s));
   }
   if (p.is_signed) {
     PhaseTimer t(s, PH_SIGNED);
-    KS_CUDA(launch_signed_fix(h, ol, f, p.lf, g, p.lg, p.b, p.in_limbs,
-                              reinterpret_cast<uint64_t *>(ws + p.off_prefix), s));
+    KS_CUDA(launch_signed_apply(h, ol, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, s));
   }
   return KS_OK;
 }
@@ -663,9 +715,10 @@ int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t 
   char *ws = nullptr;
   rc = static_scratch_ptr(&ws);
   if (rc != KS_OK) return rc;
-  // run_plan clears the column sums (the only scratch that must start at
-  // zero) on `stream` before the products accumulate into them.
-  return run_plan(p, h, f, g, ws, static_cast<cudaStream_t>(stream));
+  // run_plan clears the scratch that must start at zero (the column sums,
+  // the normalization flags, the seed accumulators) on `stream` before use;
+  // everything runs on `stream` alone (no helper stream is created).
+  return run_plan(p, h, f, g, ws, static_cast<cudaStream_t>(stream), false);
 }
 
 int ks_status_sync(ks_stream_t stream) {
@@ -749,7 +802,7 @@ int ks_profile_collect(double *ms, long long *count, int n) {
 
 const char *ks_phase_name(int phase) {
   static const char *names[] = {"pack", "product", "normalize", "unpack", "seeds", "recover",
-                                "signed_fix", "reduce_mod"};
+                                "signed_fix", "reduce_mod", "signed_prefix"};
   return (phase >= 0 && phase < PH_COUNT) ? names[phase] : nullptr;
 }
 

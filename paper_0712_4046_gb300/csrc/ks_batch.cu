@@ -102,7 +102,8 @@ struct ks_plan {
   ks::List<ks::TcPackArgs> tcpack;
   ks::List<ks::SchoolArgs> school;
   ks::List<ks::TcArgs> tc;
-  ks::List<ks::NormArgs> norm_tiles, norm_jobs;
+  ks::List<ks::NormArgs> norm[2];        // digit width 16 and 28 (tensor cores)
+  unsigned int *norm_counter = nullptr;  // tiles claimed by each normalization launch
   ks::List<ks::UnpackArgs> unpack;
   ks::List<ks::SeedBArgs> seedb, seedb_finish;
   ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
@@ -117,6 +118,11 @@ struct ks_plan {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   int device = 0;
+  // the seeds and the signed prefix records read only the inputs: they run on
+  // a helper stream, forked after the clearing launch and joined before the
+  // reconstruction (in a captured graph: a parallel branch)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace ks {
@@ -148,6 +154,28 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     note_launches(1);
     KS_TRY(cudaGetLastError());
   }
+  const bool fork = P->side != nullptr && (P->seedb.n() || P->pref.n() || [&] {
+    for (int i = 0; i < 7; i++)
+      if (P->seedk[i].n()) return true;
+    return false;
+  }());
+  cudaStream_t side = fork ? P->side : s;
+  if (fork) {
+    KS_TRY(cudaEventRecord(P->ev_fork, s));
+    KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
+  }
+  if (P->seedb.n())
+    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb_finish.dprefix,
+                                      P->seedb.n(), P->seedb.blocks(),
+                                      P->seedb_finish.blocks(), side));
+  for (int i = 0; i < 7; i++)
+    if (P->seedk[i].n())
+      KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
+                                     P->seedk[i].n(), P->seedk[i].blocks(), side));
+  if (P->pref.n())
+    KS_TRY(launch_signed_prefix_batch(P->pref.d, P->pref.dprefix, P->pref.n(), P->pref.blocks(),
+                                      side));
+  if (fork) KS_TRY(cudaEventRecord(P->ev_join, side));
   if (P->pack.n())
     KS_TRY(launch_pack_batch(P->pack.d, P->pack.dprefix, P->pack.n(), P->pack.blocks(), s));
   if (P->tcpack.n())
@@ -158,28 +186,21 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
                                    P->school.blocks(), s));
   if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_chunks, s));
   for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
-  if (P->norm_tiles.n())
-    KS_TRY(launch_normalize_batch(P->norm_tiles.d, P->norm_tiles.dprefix, P->norm_jobs.dprefix,
-                                  P->norm_tiles.n(), P->norm_tiles.blocks(),
-                                  P->norm_jobs.blocks(), s));
+  for (int c = 0; c < 2; c++)
+    if (P->norm[c].n())
+      KS_TRY(launch_normalize_batch(c == 0 ? 16 : 28, P->norm[c].d, P->norm[c].dprefix,
+                                    P->norm[c].n(), P->norm[c].blocks(), P->norm_counter + c,
+                                    status_ptr(), s));
   if (P->unpack.n())
     KS_TRY(launch_unpack_batch(P->unpack.d, P->unpack.dprefix, P->unpack.n(),
                                P->unpack.blocks(), s));
-  if (P->seedb.n())
-    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb_finish.dprefix,
-                                      P->seedb.n(), P->seedb.blocks(),
-                                      P->seedb_finish.blocks(), s));
-  for (int i = 0; i < 7; i++)
-    if (P->seedk[i].n())
-      KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
-                                     P->seedk[i].n(), P->seedk[i].blocks(), s));
+  if (fork) KS_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
   for (int c = 0; c < 3; c++)
     if (P->recover[c].n())
       KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
                                   P->recover[c].n(), P->recover[c].blocks(), P->recover_smem, s));
-  if (P->pref.n())
-    KS_TRY(launch_signed_batch(P->pref.d, P->pref.dprefix, P->fix.d, P->fix.dprefix, P->pref.n(),
-                               P->pref.blocks(), P->fix.blocks(), s));
+  if (P->fix.n())
+    KS_TRY(launch_signed_apply_batch(P->fix.d, P->fix.dprefix, P->fix.n(), P->fix.blocks(), s));
   for (auto &j : P->singles)
     KS_TRY(launch_signed_fix(j.h, j.ol, j.f, j.lf, j.g, j.lg, j.b, j.il, j.prefix, s));
   return cudaSuccess;
@@ -191,8 +212,8 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   int32_t *dig = reinterpret_cast<int32_t *>(ws + p.off_digits);
   int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
-  uint8_t *agg = reinterpret_cast<uint8_t *>(ws + p.off_agg);
-  int8_t *cin = reinterpret_cast<int8_t *>(ws + p.off_cin);
+  uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
+  const int64_t nzero = (int64_t)p.nprod * p.ncols + p.flag_bytes / 8;  // sums + flags
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
   static const int kSig[5][4] = {{1}, {1}, {1, -1}, {1, 1}, {1, -1, 1, -1}};
@@ -216,17 +237,17 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     int64_t blocks;
     make_tc_pack_args(pa, p.tg, p.nprod, ws + p.off_digits, ta, blocks);
     P->tcpack.add(ta, blocks);
-    const int64_t nz = (int64_t)p.nprod * p.ncols;
-    P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nz}, (nz + 255) / 256);
+    P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
   } else {
     P->pack.add(pa, pack_blocks(pa));
     if (p.engine == KS_ENGINE_SCHOOLBOOK) {
       SchoolArgs sa;
       if (make_school_args(prods, p.nprod, sa) != 0) return KS_EINVAL;
       P->school.add(sa, sa.block_prefix[p.nprod]);
-      const int64_t nz = (int64_t)p.nprod * p.ncols;
-      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nz}, (nz + 255) / 256);
+      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
     } else {
+      const int64_t nf = p.flag_bytes / 8;
+      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(flags), nf}, (nf + 255) / 256);
       NttJob j{};
       for (int k = 0; k < p.nprod; k++) j.prods[k] = prods[k];
       j.nprod = p.nprod;
@@ -244,8 +265,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
     jobs[i].sigma = sigma;
     jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].agg = agg + (int64_t)i * p.ntiles;
-    jobs[i].cin = cin + (int64_t)i * p.ntiles;
+    jobs[i].flags = flags + 2 + (int64_t)i * p.ntiles;
   };
   switch (p.variant) {
     case KS_1: job(0, 0, -1, 1); break;
@@ -255,8 +275,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   }
   NormArgs na;
   if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
-  P->norm_tiles.add(na, (int64_t)p.nnorm * p.ntiles);
-  P->norm_jobs.add(na, p.nnorm);
+  P->norm[p.dn == 28 ? 1 : 0].add(na, norm_blocks(na));
   const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
                  *V3 = words + 3 * p.nwords;
   const int ol = p.out_limbs;
@@ -356,11 +375,21 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     offs[i] = total;
     total += align256(P->plans[i].total);
   }
-  P->ws_bytes = total < 256 ? 256 : total;
+  // one more 256-byte slot at the end: the normalization launches' tile counters
+  if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    ks_plan_destroy(P);
+    return KS_ECUDA;
+  }
+  P->ws_bytes = total + 256;
   if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
-    delete P;
+    P->ws = nullptr;
+    ks_plan_destroy(P);
     return KS_ENOMEM;
   }
+  P->norm_counter = reinterpret_cast<unsigned int *>(P->ws + total);
+  P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(P->norm_counter), 1}, 1);
   int *status = status_ptr();
   for (int64_t i = 0; i < n; i++) {
     const Plan &p = P->plans[i];
@@ -375,15 +404,14 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       P->tc.add(ta, ta.chunk_prefix[p.nprod]);
     }
     if (rc != KS_OK) {
-      cudaFree(P->ws);
-      delete P;
+      ks_plan_destroy(P);
       return rc;
     }
   }
   P->tc_chunks = P->tc.blocks();
   // descriptor arrays: one device allocation, filled from a pinned host copy
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
-              P->tc.bytes() + P->norm_tiles.bytes() + P->norm_jobs.bytes() + P->unpack.bytes() +
+              P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->unpack.bytes() +
               P->seedb.bytes() + P->seedb_finish.bytes() + P->pref.bytes() + P->fix.bytes();
   for (int i = 0; i < 7; i++) db += P->seedk[i].bytes();
   for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
@@ -398,10 +426,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->tcpack.place(h, d);
   P->school.place(h, d);
   P->tc.place(h, d);
-  P->norm_tiles.place(h, d);
-  P->norm_jobs.place(h, d);
-  // both normalization lists describe the same jobs; use the first array
-  P->norm_jobs.d = P->norm_tiles.d;
+  P->norm[0].place(h, d);
+  P->norm[1].place(h, d);
   P->unpack.place(h, d);
   P->seedb.place(h, d);
   P->seedb_finish.place(h, d);
@@ -488,6 +514,9 @@ void ks_plan_destroy(ks_plan *P) {
   if (P->ws) cudaFree(P->ws);
   if (P->desc) cudaFree(P->desc);
   if (P->hdesc) cudaFreeHost(P->hdesc);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->side) cudaStreamDestroy(P->side);
   cudaSetDevice(cur);
   delete P;
 }

@@ -51,7 +51,8 @@ struct Plan {
   // number-theoretic-transform engine
   int ntt_log = 0;      // transform length 2^ntt_log
   // workspace layout (byte offsets from the base)
-  size_t off_digits = 0, off_cols = 0, off_words = 0, off_agg = 0, off_cin = 0;
+  size_t off_digits = 0, off_cols = 0, off_flags = 0, off_words = 0;
+  int64_t flag_bytes = 0;  // right after the column sums: zeroed with them
   size_t off_seeds = 0, off_seedacc = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
@@ -169,26 +170,35 @@ struct NormJob {
   int64_t n2;
   int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k)
   uint32_t *out;
-  uint8_t *agg;       // per scan tile
-  int8_t *cin;        // per scan tile
+  uint32_t *flags;    // one look-back flag per scan tile (zero before the launch)
 };
 
-// Normalizes up to 4 column-sum combinations into two's complement words.
+// Normalizes up to 4 column-sum combinations into two's complement words in
+// one launch.  counter (one word) and the jobs' flags must be zero on entry.
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, cudaStream_t s);
+                             int64_t ntiles, unsigned int *counter, int *status,
+                             cudaStream_t s);
 
 struct NormArgs {
   NormJob job[4];
   int njobs;
+  int paired;         // jobs (0,1) and (2,3) are +- pairs of the same columns
   int d;
   int64_t nwords;
   int64_t ntiles;
 };
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
                    NormArgs &a);
-cudaError_t launch_normalize_batch(const NormArgs *d, const int64_t *prefix_tiles,
-                                   const int64_t *prefix_jobs, int n, int64_t tiles,
-                                   int64_t jobs, cudaStream_t s);
+int64_t norm_blocks(const NormArgs &a);
+// bytes of a product's flag region (a counter word, a spare, the tile flags)
+int64_t norm_flag_bytes(int njobs, int64_t ntiles);
+// one launch per digit width d (16 or 28) for the whole batch; the counter is
+// shared by the launch
+cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix, int n,
+                                   int64_t blocks, unsigned int *counter, int *status,
+                                   cudaStream_t s);
+// scan tiles of a combination of nwords words at digit width d
+int64_t norm_tiles_for(int64_t nwords, int d);
 
 // KS1 / KS2 unpack: h'_k = bits [off + kN, off + kN + width) of V (k even) or
 // V_odd (k odd).
@@ -310,12 +320,21 @@ struct FixArgs {
 bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
                       int64_t lg, int b, int in_limbs, uint64_t *prefix, PrefArgs &a,
                       FixArgs &fx, int64_t &pref_blocks, int64_t &fix_blocks);
-cudaError_t launch_signed_batch(const PrefArgs *pa, const int64_t *pref_prefix,
-                                const FixArgs *fa, const int64_t *fix_prefix, int n,
-                                int64_t pref_blocks, int64_t fix_blocks, cudaStream_t s);
+// The correction in two parts: the prefix records of f and g (inputs only),
+// then the correction of h; launch_signed_fix issues both in order.
+cudaError_t launch_signed_prefix(int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
+                                 int64_t lg, int b, int in_limbs, uint64_t *prefix,
+                                 cudaStream_t s);
+cudaError_t launch_signed_apply(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                                const uint64_t *g, int64_t lg, int b, int in_limbs,
+                                uint64_t *prefix, cudaStream_t s);
 cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
                               const uint64_t *g, int64_t lg, int b, int in_limbs,
                               uint64_t *prefix, cudaStream_t s);
+cudaError_t launch_signed_prefix_batch(const PrefArgs *pa, const int64_t *pref_prefix, int n,
+                                       int64_t pref_blocks, cudaStream_t s);
+cudaError_t launch_signed_apply_batch(const FixArgs *fa, const int64_t *fix_prefix, int n,
+                                      int64_t fix_blocks, cudaStream_t s);
 
 // (Z/pZ)[x]: out_k = h'_k mod p.
 cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh,
@@ -326,7 +345,7 @@ cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t 
 // CUDA-event timing on the caller's stream.
 void note_launches(int n);
 enum Phase { PH_PACK = 0, PH_PRODUCT, PH_NORMALIZE, PH_UNPACK, PH_SEEDS, PH_RECOVER, PH_SIGNED,
-             PH_MOD, PH_COUNT };
+             PH_MOD, PH_SIGNED_PREFIX, PH_COUNT };
 struct PhaseTimer {
   cudaStream_t s;
   int phase;
@@ -393,6 +412,40 @@ __device__ __forceinline__ int32_t digit_at(const PackOp &op, int64_t j, int64_t
       val += (int32_t)piece;
   }
   return val;
+}
+
+// Digits j0 .. j0 + K - 1 of one evaluation (the same values as digit_at):
+// one pair of divisions finds the coefficient fields that meet the K-digit
+// window, then each field adds its bits to the digits it overlaps
+// (compile-time digit width D, so the per-digit tests are register-only).
+template <int D, int K>
+__device__ __forceinline__ void digit_run(const PackOp &op, int64_t j0, int64_t N, int b,
+                                          int in_limbs, int flip, int32_t (&v)[K]) {
+#pragma unroll
+  for (int m = 0; m < K; m++) v[m] = 0;
+  const int64_t lo = j0 * D, hi = (j0 + K) * D;
+  const int64_t t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
+  int64_t t_hi = (hi - 1) / N;
+  if (t_hi > op.L - 1) t_hi = op.L - 1;
+  for (int64_t t = t_lo; t <= t_hi; t++) {
+    const int64_t pos = t * N;
+    const int64_t src = op.reversed ? (op.L - 1 - t) : t;
+    const uint64_t *c = op.poly + src * in_limbs;
+    const bool neg = op.sigma < 0 && (t & 1);
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+      const int64_t dlo = lo + (int64_t)m * D;
+      if (dlo + D <= pos || dlo >= pos + b) continue;
+      uint32_t piece;
+      if (pos >= dlo) {
+        const int sh = (int)(pos - dlo);
+        piece = coeff_slice(c, in_limbs, b, flip, 0, D - sh) << sh;
+      } else {
+        piece = coeff_slice(c, in_limbs, b, flip, (int)(dlo - pos), D);
+      }
+      v[m] += neg ? -(int32_t)piece : (int32_t)piece;
+    }
+  }
 }
 
 }  // namespace ks

@@ -16,8 +16,23 @@
 //  3. carry-lookahead: the carry into word j is in {-1, 0, 1}; word j maps an
 //     incoming carry c to floor((s_j + c) / 2^32), a function on the three
 //     carry values.  Functions compose associatively, so the carries are a
-//     parallel prefix: warp shuffles, then the block, then the tiles (one
-//     tile = 512 words per CTA), then a second pass applies them.
+//     parallel prefix: warp shuffles, then the block, then across tiles.
+//
+// One launch does all of it (a single-pass scan with decoupled look-back).
+// Every CTA takes the next tile index from a counter, so the tiles it looks
+// back on were claimed by CTAs that are already running.  It stages the
+// columns its tile needs in shared memory (one coalesced read of the column
+// sums; a thread's words are exactly its columns' bit span, so all slicing
+// offsets are compile-time constants of the digit width), forms s_j, scans
+// its tile, publishes the tile's transfer
+// function, and then one warp looks back over the preceding tiles' flags
+// (32 tiles per step) until it meets a tile that has published its carry-out;
+// it then publishes its own carry-out, and the CTA writes its words.  The ±
+// pair of a two- or four-point product (same c1, c2, opposite sigma) is done
+// by one CTA from one staged copy of c1 and c2, so those columns are read once.
+// Flags and the counter must be zero before the launch; every wait is bounded
+// (about one second), after which the kernel records status 1 and finishes
+// with carry 0.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -25,9 +40,28 @@ namespace ks {
 
 namespace {
 constexpr int kThreads = 128;
-constexpr int kWPT = 4;                     // words per thread
-constexpr int kTileWords = kThreads * kWPT; // words per tile
 constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
+constexpr uint32_t kFlagAgg = 1u << 8;      // the tile's transfer function is published
+constexpr uint32_t kFlagPre = 1u << 9;      // the tile's carry-out is published
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+// Per digit width D: every thread takes WPT words = 32 WPT bits = CPT columns
+// exactly (32 WPT = D CPT), so each column sits at a compile-time bit offset
+// from the thread's first word; BACK earlier columns still reach its first
+// word or the word before it (their slices span three words).
+template <int D>
+struct Geo;
+template <>
+struct Geo<16> {
+  static constexpr int WPT = 4, CPT = 8, BACK = 6;
+};
+template <>
+struct Geo<28> {
+  static constexpr int WPT = 7, CPT = 8, BACK = 3;
+};
+// staged columns of a tile: 128 CPT + BACK, one padding slot per 8 (banks)
+constexpr int kStage = (kThreads * 8 + 8) + (kThreads * 8 + 8) / 8 + 8;
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 
 // carry-transfer function: 2 bits per input carry c in {-1,0,1}, value c'+1
 __device__ __forceinline__ int apply_fn(uint32_t f, int c) {
@@ -40,6 +74,10 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f) {
   for (int c = -1; c <= 1; c++) h |= (uint32_t)(apply_fn(g, apply_fn(f, c)) + 1) << (2 * (c + 1));
   return h;
 }
+// two functions side by side (bits 0-5 and 8-13), composed lane-wise
+__device__ __forceinline__ uint32_t compose2(uint32_t g, uint32_t f) {
+  return compose(g & 63u, f & 63u) | (compose((g >> 8) & 63u, (f >> 8) & 63u) << 8);
+}
 __device__ __forceinline__ uint32_t word_fn(int64_t s) {
   uint32_t h = 0;
 #pragma unroll
@@ -47,193 +85,275 @@ __device__ __forceinline__ uint32_t word_fn(int64_t s) {
   return h;
 }
 
-__device__ __forceinline__ int64_t column(const NormJob &J, int64_t k) {
-  int64_t v = 0;
-  if (k < J.n1) v = J.c1[k];
-  if (J.c2 != nullptr && k < J.n2) v += (J.sigma > 0) ? J.c2[k] : -J.c2[k];
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-
-// T_j: the slices of all column values that land in word j.
-__device__ int64_t slice_sum(const NormJob &J, int d, int64_t j) {
-  if (j < 0) return 0;
-  const int64_t ncol = J.n1 > J.n2 ? J.n1 : J.n2;
-  int64_t kmin = (j >= 2) ? (32 * (j - 2) + d - 1) / d : 0;
-  int64_t kmax = (32 * j + 31) / d;
-  if (kmax > ncol - 1) kmax = ncol - 1;
-  int64_t T = 0;
-  for (int64_t k = kmin; k <= kmax; k++) {
-    const int64_t bit = (int64_t)d * k;
-    const int64_t q = bit >> 5;
-    if (q < j - 2 || q > j) continue;
-    const __int128 x = (__int128)column(J, k) << (int)(bit & 31);
-    if (q == j)
-      T += (int64_t)(uint32_t)x;
-    else if (q == j - 1)
-      T += (int64_t)(uint32_t)(x >> 32);
-    else
-      T += (int64_t)(int32_t)(uint32_t)(x >> 64);
-  }
-  return T;
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// s_j for the kWPT words of this thread, and their composed transfer function.
-__device__ uint32_t thread_words(const NormJob &J, int d, int64_t j0, int64_t s[kWPT]) {
-  int64_t Tprev = slice_sum(J, d, j0 - 1);
-  uint32_t agg = kIdentity;
-#pragma unroll
-  for (int w = 0; w < kWPT; w++) {
-    const int64_t T = slice_sum(J, d, j0 + w);
-    s[w] = (int64_t)(uint32_t)T + (Tprev >> 32);
-    Tprev = T;
-    agg = compose(word_fn(s[w]), agg);
+// Looks back from `tile` over the flags of the preceding tiles (one warp, 32
+// tiles per step) and returns the carry into `tile`; publishes the tile's
+// carry-out.  `total` is the tile's own transfer function.
+__device__ int look_back(uint32_t *flags, int64_t tile, uint32_t total, int lane, int *status) {
+  if (tile == 0) {
+    if (lane == 0) st_release(&flags[0], kFlagPre | (uint32_t)(apply_fn(total, 0) + 1));
+    return 0;
   }
-  return agg;
+  if (lane == 0) st_release(&flags[tile], kFlagAgg | total);
+  uint32_t acc = kIdentity;  // the functions of the tiles passed so far
+  int64_t top = tile - 1;
+  uint64_t t0 = 0;
+  int cin = 0;
+  while (true) {
+    const int64_t ti = top - lane;
+    // lanes before tile 0 read as "carry-out 0"; tile 0 always publishes one
+    const uint32_t v = ti >= 0 ? ld_acquire(&flags[ti]) : (kFlagPre | 1u);
+    const unsigned pre = __ballot_sync(0xffffffffu, (v & kFlagPre) != 0);
+    const unsigned ready = __ballot_sync(0xffffffffu, (v & (kFlagPre | kFlagAgg)) != 0);
+    const int fp = pre ? __ffs(pre) - 1 : 32;  // nearest tile with a carry-out
+    const unsigned need = fp == 32 ? 0xffffffffu : ((1u << fp) - 1u);
+    if ((ready & need) != need) {
+      if (t0 == 0) {
+        t0 = globaltimer();
+      } else if (globaltimer() - t0 > kWaitNs) {
+        if (lane == 0) atomicExch(status, 1);
+        cin = 0;
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    // compose the functions of lanes 0 .. fp-1 (lane 0 is the latest tile)
+    uint32_t f = lane < fp ? (v & 63u) : kIdentity;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o = __shfl_down_sync(0xffffffffu, f, off);
+      if (lane + off < 32) f = compose(f, o);
+    }
+    f = __shfl_sync(0xffffffffu, f, 0);
+    acc = compose(acc, f);
+    if (fp < 32) {
+      const uint32_t vp = __shfl_sync(0xffffffffu, v, fp);
+      cin = apply_fn(acc, (int)(vp & 3u) - 1);
+      break;
+    }
+    top -= 32;
+    t0 = 0;
+  }
+  if (lane == 0) st_release(&flags[tile], kFlagPre | (uint32_t)(apply_fn(total, cin) + 1));
+  return cin;
 }
 
-// Block-wide exclusive scan of transfer functions (thread order); returns the
-// exclusive prefix of this thread and writes the block total.
-__device__ uint32_t block_exclusive(uint32_t v, uint32_t *total) {
-  __shared__ uint32_t warp_tot[kThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = v;
+// s_j of a thread's WPT words from its BACK + CPT staged columns (x[i] is
+// column kstart - BACK + i); every offset and shift is a compile-time constant.
+template <int D>
+__device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + Geo<D>::CPT],
+                                             int64_t (&s)[Geo<D>::WPT]) {
+  constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
+  int64_t T[WPT + 1];  // T[w + 1]: slices landing in word j0 + w, w = -1 .. WPT-1
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl = compose(incl, o);
+  for (int w = 0; w <= WPT; w++) T[w] = 0;
+#pragma unroll
+  for (int i = 0; i < BACK + CPT; i++) {
+    const int c = i - BACK;                            // column offset from kstart
+    const int bit = D * c;                             // bit offset from word j0
+    const int q = bit >= 0 ? bit / 32 : -((-bit + 31) / 32);  // floor(bit / 32)
+    const int sh = bit - 32 * q;
+    const __int128 v = (__int128)x[i] << sh;
+    const int64_t sl0 = (int64_t)(uint32_t)v;
+    const int64_t sl1 = (int64_t)(uint32_t)(v >> 32);
+    const int64_t sl2 = (int64_t)(int32_t)(uint32_t)(v >> 64);
+    if (q >= -1 && q <= WPT - 1) T[q + 1] += sl0;
+    if (q + 1 >= -1 && q + 1 <= WPT - 1) T[q + 2] += sl1;
+    if (q + 2 >= -1 && q + 2 <= WPT - 1) T[q + 3] += sl2;
   }
-  uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = kIdentity;
-  if (lane == 31) warp_tot[wid] = incl;
+#pragma unroll
+  for (int w = 0; w < WPT; w++) s[w] = (int64_t)(uint32_t)T[w + 1] + (T[w] >> 32);
+}
+
+// counter: tiles claimed so far in this launch (zero before the launch)
+template <int D, class Src>
+__global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *counter,
+                                                        int *status) {
+  constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
+  constexpr int NX = BACK + CPT;
+  constexpr int TW = kThreads * WPT;  // words per tile
+  __shared__ int64_t s_c1[kStage];
+  __shared__ int64_t s_c2[kStage];
+  __shared__ uint32_t s_warp[kThreads / 32];
+  __shared__ int s_cin[2];
+  __shared__ unsigned int s_vid;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_vid = atomicAdd(counter, 1u);
   __syncthreads();
-  uint32_t wpre = kIdentity;
-  for (int w = 0; w < wid; w++) wpre = compose(warp_tot[w], wpre);
-  if (total != nullptr) {
-    uint32_t t = kIdentity;
-    for (int w = 0; w < kThreads / 32; w++) t = compose(warp_tot[w], t);
-    *total = t;
-  }
-  return compose(excl, wpre);
-}
-
-template <class Src>
-__global__ void __launch_bounds__(kThreads) norm_aggregate(Src src) {
   int64_t bid;
-  const NormArgs &a = src.locate(blockIdx.x, bid);
-  const NormJob &J = a.job[bid / a.ntiles];
-  const int64_t tile = bid % a.ntiles;
-  const int64_t j0 = tile * kTileWords + (int64_t)threadIdx.x * kWPT;
-  int64_t s[kWPT];
-  const uint32_t agg = thread_words(J, a.d, j0, s);
-  uint32_t total;
-  block_exclusive(agg, &total);
-  if (threadIdx.x == 0) J.agg[tile] = (uint8_t)total;
-}
+  const NormArgs &a = src.locate((int64_t)s_vid, bid);
+  const int64_t group = bid / a.ntiles;
+  const int64_t tile = bid - group * a.ntiles;
+  const int nsub = a.paired ? 2 : 1;
+  const NormJob &J0 = a.job[nsub * group];
+  const int64_t W0 = tile * TW;
+  const bool two = J0.c2 != nullptr;
 
-// One CTA per job: carries into every tile (the first tile gets 0), by a
-// parallel prefix of the tile functions (each thread composes a run of tiles,
-// then warp shuffles and one more level across the warps).
-template <class Src>
-__global__ void __launch_bounds__(1024) norm_tiles(Src src) {
-  int64_t jid;
-  const NormArgs &a = src.locate(blockIdx.x, jid);
-  const NormJob &J = a.job[jid];
-  __shared__ uint32_t wtot[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t per = (a.ntiles + 1023) / 1024;
-  const int64_t t0 = (int64_t)threadIdx.x * per;
-  uint32_t f = kIdentity;
-  for (int64_t t = t0; t < t0 + per && t < a.ntiles; t++) f = compose(J.agg[t], f);
-  uint32_t incl = f;
+  // stage the tile's columns kt .. kt + 128 CPT + BACK - 1 (kt = first column
+  // of thread 0 minus BACK), zero outside [0, n)
+  const int64_t kt = tile * (int64_t)(kThreads * CPT) - BACK;
+  constexpr int cnt = kThreads * CPT + BACK;
+  for (int i = tid; i < cnt; i += kThreads) {
+    const int64_t k = kt + i;
+    s_c1[pad8(i)] = (k >= 0 && k < J0.n1) ? J0.c1[k] : 0;
+    if (two) s_c2[pad8(i)] = (k >= 0 && k < J0.n2) ? J0.c2[k] : 0;
+  }
+  __syncthreads();
+
+  // s_j of this thread's words, for each sub-job; transfer functions side by side
+  const int64_t j0 = W0 + (int64_t)tid * WPT;
+  int64_t s[2][WPT];
+  uint32_t agg = kIdentity | (kIdentity << 8);
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+    if (u >= nsub) break;
+    const int sigma = a.job[nsub * group + u].sigma;
+    int64_t x[NX];
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      const int idx = pad8(tid * CPT + i);
+      int64_t v = s_c1[idx];
+      if (two) v += sigma > 0 ? s_c2[idx] : -s_c2[idx];
+      x[i] = v;
+    }
+    thread_words<D>(x, s[u]);
+    uint32_t f = kIdentity;
+#pragma unroll
+    for (int w = 0; w < WPT; w++) f = compose(word_fn(s[u][w]), f);
+    agg = u == 0 ? ((agg & ~63u) | f) : ((agg & 63u) | (f << 8));
+  }
+
+  // block-wide exclusive scan of the (paired) functions in thread order
+  uint32_t incl = agg;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl = compose(incl, o);
+    if (lane >= off) incl = compose2(incl, o);
   }
   uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = kIdentity;
-  if (lane == 31) wtot[wid] = incl;
+  if (lane == 0) excl = kIdentity | (kIdentity << 8);
+  if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
-  if (wid == 0) {
-    uint32_t v = wtot[lane];
-    uint32_t wi = v;
+  uint32_t wpre = kIdentity | (kIdentity << 8), total = kIdentity | (kIdentity << 8);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, wi, off);
-      if (lane >= off) wi = compose(wi, o);
-    }
-    uint32_t we = __shfl_up_sync(0xffffffffu, wi, 1);
-    if (lane == 0) we = kIdentity;
-    wtot[lane] = we;
+  for (int w = 0; w < kThreads / 32; w++) {
+    if (w < wid) wpre = compose2(s_warp[w], wpre);
+    total = compose2(s_warp[w], total);
+  }
+  const uint32_t pre = compose2(excl, wpre);
+
+  // warp u looks back for sub-job u
+  if (wid < nsub) {
+    const NormJob &J = a.job[nsub * group + wid];
+    const int c = look_back(J.flags, tile, (total >> (8 * wid)) & 63u, lane, status);
+    if (lane == 0) s_cin[wid] = c;
   }
   __syncthreads();
-  int c = apply_fn(compose(excl, wtot[wid]), 0);
-  for (int64_t t = t0; t < t0 + per && t < a.ntiles; t++) {
-    J.cin[t] = (int8_t)c;
-    c = apply_fn(J.agg[t], c);
+
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+    if (u >= nsub) break;
+    const NormJob &J = a.job[nsub * group + u];
+    int c = apply_fn((pre >> (8 * u)) & 63u, s_cin[u]);
+    uint32_t o[WPT];
+#pragma unroll
+    for (int w = 0; w < WPT; w++) {
+      const int64_t v = s[u][w] + c;
+      o[w] = (uint32_t)v;
+      c = (int)(v >> 32);
+    }
+    if (WPT == 4) {
+      // nwords is a multiple of four: the four words are all inside or all outside
+      if (j0 < a.nwords)
+        *reinterpret_cast<uint4 *>(J.out + j0) = make_uint4(o[0], o[1], o[2], o[3 % WPT]);
+    } else {
+#pragma unroll
+      for (int w = 0; w < WPT; w++)
+        if (j0 + w < a.nwords) J.out[j0 + w] = o[w];
+    }
   }
 }
 
-template <class Src>
-__global__ void __launch_bounds__(kThreads) norm_apply(Src src) {
-  int64_t bid;
-  const NormArgs &a = src.locate(blockIdx.x, bid);
-  const NormJob &J = a.job[bid / a.ntiles];
-  const int64_t tile = bid % a.ntiles;
-  const int64_t j0 = tile * kTileWords + (int64_t)threadIdx.x * kWPT;
-  int64_t s[kWPT];
-  const uint32_t agg = thread_words(J, a.d, j0, s);
-  const uint32_t pre = block_exclusive(agg, nullptr);
-  int c = apply_fn(pre, (int)J.cin[tile]);
-#pragma unroll
-  for (int w = 0; w < kWPT; w++) {
-    const int64_t v = s[w] + c;
-    if (j0 + w < a.nwords) J.out[j0 + w] = (uint32_t)v;
-    c = (int)(v >> 32);
-  }
-}
+template <int D>
+constexpr int tile_words() { return kThreads * Geo<D>::WPT; }
 
 }  // namespace
+
+int norm_tile_words(int d) { return d == 28 ? tile_words<28>() : tile_words<16>(); }
+
+int64_t norm_tiles_for(int64_t nwords, int d) {
+  const int tw = norm_tile_words(d);
+  return (nwords + tw - 1) / tw;
+}
 
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
                    NormArgs &a) {
   if (njobs < 1 || njobs > 4) return -1;
-  if (ntiles * kTileWords < nwords) return -1;
+  if (d != 16 && d != 28) return -1;
+  if (ntiles * norm_tile_words(d) < nwords || (nwords & 3) != 0) return -1;
   a = NormArgs{};
   for (int i = 0; i < njobs; i++) a.job[i] = jobs[i];
   a.njobs = njobs;
   a.d = d;
   a.nwords = nwords;
   a.ntiles = ntiles;
+  // the +- pairs of Sec. 3.3 / 3.4 share their inputs
+  bool paired = njobs % 2 == 0;
+  for (int i = 0; paired && i < njobs; i += 2) {
+    const NormJob &x = jobs[i], &y = jobs[i + 1];
+    paired = x.c2 != nullptr && x.c1 == y.c1 && x.c2 == y.c2 && x.n1 == y.n1 && x.n2 == y.n2;
+  }
+  a.paired = paired ? 1 : 0;
   return 0;
 }
 
+int64_t norm_blocks(const NormArgs &a) {
+  return (a.paired ? a.njobs / 2 : a.njobs) * a.ntiles;
+}
+
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, cudaStream_t s) {
+                             int64_t ntiles, unsigned int *counter, int *status, cudaStream_t s) {
   NormArgs a;
   if (make_norm_args(jobs, njobs, d, nwords, ntiles, a) != 0) return cudaErrorInvalidValue;
-  const One<NormArgs> one{a};
-  norm_aggregate<One<NormArgs>><<<(unsigned)(ntiles * njobs), kThreads, 0, s>>>(one);
-  norm_tiles<One<NormArgs>><<<njobs, 1024, 0, s>>>(one);
-  norm_apply<One<NormArgs>><<<(unsigned)(ntiles * njobs), kThreads, 0, s>>>(one);
-  note_launches(3);
+  const unsigned grid = (unsigned)norm_blocks(a);
+  if (d == 28)
+    norm_kernel<28, One<NormArgs>><<<grid, kThreads, 0, s>>>(One<NormArgs>{a}, counter, status);
+  else
+    norm_kernel<16, One<NormArgs>><<<grid, kThreads, 0, s>>>(One<NormArgs>{a}, counter, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
-// prefix_tiles: block prefix over njobs * ntiles; prefix_jobs: over njobs
-cudaError_t launch_normalize_batch(const NormArgs *d, const int64_t *prefix_tiles,
-                                   const int64_t *prefix_jobs, int n, int64_t tiles,
-                                   int64_t jobs, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  norm_aggregate<Many<NormArgs>><<<(unsigned)tiles, kThreads, 0, s>>>(
-      Many<NormArgs>{d, prefix_tiles, n});
-  norm_tiles<Many<NormArgs>><<<(unsigned)jobs, 1024, 0, s>>>(Many<NormArgs>{d, prefix_jobs, n});
-  norm_apply<Many<NormArgs>><<<(unsigned)tiles, kThreads, 0, s>>>(
-      Many<NormArgs>{d, prefix_tiles, n});
-  note_launches(3);
+cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix, int n,
+                                   int64_t blocks, unsigned int *counter, int *status,
+                                   cudaStream_t s) {
+  if (n == 0 || blocks == 0) return cudaSuccess;
+  const Many<NormArgs> src{da, prefix, n};
+  if (d == 28)
+    norm_kernel<28, Many<NormArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(src, counter, status);
+  else
+    norm_kernel<16, Many<NormArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(src, counter, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
-int64_t norm_tiles_for(int64_t nwords) { return (nwords + kTileWords - 1) / kTileWords; }
+// flag words of a product: one counter word, one spare, one flag per tile per job
+int64_t norm_flag_bytes(int njobs, int64_t ntiles) {
+  return ((8 + 4 * (int64_t)njobs * ntiles) + 7) & ~(int64_t)7;
+}
 
 }  // namespace ks

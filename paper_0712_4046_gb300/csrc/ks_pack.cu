@@ -21,30 +21,54 @@
 
 namespace ks {
 
+namespace {
+constexpr int kPackThreads = 256;
+constexpr int kRun = 8;                             // digits per thread
+constexpr int kCtaDigits = kPackThreads * kRun;     // digits per CTA
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int64_t ctas_for(int64_t ndig) {
+  return (ndig + kCtaDigits - 1) / kCtaDigits;
+}
+}  // namespace
+
+// One CTA makes 2048 consecutive digits of one operand: each thread a run of
+// eight (digit_run), staged in shared memory, then stored coalesced.
 template <class Src>
-__global__ void __launch_bounds__(256) pack_kernel(Src src) {
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
+  __shared__ int32_t st[kCtaDigits + kCtaDigits / 8];
   int64_t local;
   const PackArgs &a = src.locate(blockIdx.x, local);
-  int64_t j = local * 256 + threadIdx.x;
   int o = 0;
-  while (o < a.nops && j >= a.op[o].ndig) {
-    j -= a.op[o].ndig;
+  while (o < a.nops && local >= ctas_for(a.op[o].ndig)) {
+    local -= ctas_for(a.op[o].ndig);
     o++;
   }
   if (o >= a.nops) return;
-  a.op[o].out[j] = digit_at(a.op[o], j, a.N, a.b, a.d, a.in_limbs, a.flip);
+  const PackOp &op = a.op[o];
+  const int tid = threadIdx.x;
+  const int64_t jc = local * kCtaDigits;
+  int32_t v[kRun];
+  digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.b, a.in_limbs, a.flip, v);
+#pragma unroll
+  for (int m = 0; m < kRun; m++) st[pad8(kRun * tid + m)] = v[m];
+  __syncthreads();
+  for (int i = tid; i < kCtaDigits; i += kPackThreads) {
+    const int64_t j = jc + i;
+    if (j < op.ndig) op.out[j] = st[pad8(i)];
+  }
 }
 
 int64_t pack_blocks(const PackArgs &a) {
   int64_t total = 0;
-  for (int o = 0; o < a.nops; o++) total += a.op[o].ndig;
-  return (total + 255) / 256;
+  for (int o = 0; o < a.nops; o++) total += ctas_for(a.op[o].ndig);
+  return total;
 }
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
+  if (a.d != 16) return cudaErrorInvalidValue;  // the int32-digit engines use 16-bit digits
   const int64_t blocks = pack_blocks(a);
   if (blocks == 0) return cudaSuccess;
-  pack_kernel<One<PackArgs>><<<(unsigned)blocks, 256, 0, s>>>(One<PackArgs>{a});
+  pack_kernel<One<PackArgs>><<<(unsigned)blocks, kPackThreads, 0, s>>>(One<PackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -52,7 +76,8 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
 cudaError_t launch_pack_batch(const PackArgs *d, const int64_t *prefix, int n, int64_t blocks,
                               cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  pack_kernel<Many<PackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<PackArgs>{d, prefix, n});
+  pack_kernel<Many<PackArgs>><<<(unsigned)blocks, kPackThreads, 0, s>>>(
+      Many<PackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }

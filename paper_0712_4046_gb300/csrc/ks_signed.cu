@@ -481,39 +481,67 @@ bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const 
   return fast;
 }
 
-cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
-                              const uint64_t *g, int64_t lg, int b, int in_limbs,
-                              uint64_t *prefix, cudaStream_t s) {
+// The prefix records of f and g: they depend on the inputs only, so they may
+// run concurrently with the products.
+cudaError_t launch_signed_prefix(int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
+                                 int64_t lg, int b, int in_limbs, uint64_t *prefix,
+                                 cudaStream_t s) {
   if (ol > kMaxOl || in_limbs > kMaxIn) return cudaErrorInvalidValue;
   PrefArgs a;
   FixArgs fx;
   int64_t pb, fb;
-  if (make_signed_args(h, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb)) {
+  if (make_signed_args(nullptr, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb)) {
     pref_tile<One<PrefArgs>><<<(unsigned)pb, kPT, 0, s>>>(One<PrefArgs>{a});
-    signed_fix_fast<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
-    note_launches(2);
+    note_launches(1);
     return cudaGetLastError();
   }
   pref_block_totals<<<(unsigned)pb, kThreads, 0, s>>>(a);
   pref_scan_totals<<<2, 64, 0, s>>>(a);
   pref_apply<<<(unsigned)pb, kThreads, 0, s>>>(a);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+// The correction of h from the prefix records (after launch_signed_prefix).
+cudaError_t launch_signed_apply(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                                const uint64_t *g, int64_t lg, int b, int in_limbs,
+                                uint64_t *prefix, cudaStream_t s) {
+  if (ol > kMaxOl || in_limbs > kMaxIn) return cudaErrorInvalidValue;
+  PrefArgs a;
+  FixArgs fx;
+  int64_t pb, fb;
+  make_signed_args(h, ol, f, lf, g, lg, b, in_limbs, prefix, a, fx, pb, fb);
   if (in_limbs <= 8 && ol <= 17)
     signed_fix_fast<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
   else
     signed_fix_kernel<One<FixArgs>><<<(unsigned)fb, 128, 0, s>>>(One<FixArgs>{fx});
-  note_launches(4);
+  note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_signed_batch(const PrefArgs *pa, const int64_t *pref_prefix,
-                                const FixArgs *fa, const int64_t *fix_prefix, int n,
-                                int64_t pref_blocks, int64_t fix_blocks, cudaStream_t s) {
+cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
+                              const uint64_t *g, int64_t lg, int b, int in_limbs,
+                              uint64_t *prefix, cudaStream_t s) {
+  const cudaError_t e = launch_signed_prefix(ol, f, lf, g, lg, b, in_limbs, prefix, s);
+  if (e != cudaSuccess) return e;
+  return launch_signed_apply(h, ol, f, lf, g, lg, b, in_limbs, prefix, s);
+}
+
+cudaError_t launch_signed_prefix_batch(const PrefArgs *pa, const int64_t *pref_prefix, int n,
+                                       int64_t pref_blocks, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   pref_tile<Many<PrefArgs>><<<(unsigned)pref_blocks, kPT, 0, s>>>(
       Many<PrefArgs>{pa, pref_prefix, n});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_signed_apply_batch(const FixArgs *fa, const int64_t *fix_prefix, int n,
+                                      int64_t fix_blocks, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
   signed_fix_fast<Many<FixArgs>><<<(unsigned)fix_blocks, 128, 0, s>>>(
       Many<FixArgs>{fa, fix_prefix, n});
-  note_launches(2);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -241,9 +241,13 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     const PackOp &op = a.op[2 * q];
     const int64_t h0 = r * kPackSeg;
     const int64_t x0 = h0 - 127;
-    for (int i = tid; i < kPackSeg + 8; i += 256) {
-      const int64_t j = x0 - 1 + i;
-      raw[i] = j < 0 ? 0 : digit_at(op, j, a.N, a.b, 7, a.in_limbs, a.flip);
+    // digits x0 - 1 + i, i < kPackSeg + 8: runs of eight per thread (digits
+    // at negative positions come out as zero)
+    for (int i0 = 8 * tid; i0 < kPackSeg + 8; i0 += 8 * 256) {
+      int32_t v[8];
+      digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.b, a.in_limbs, a.flip, v);
+#pragma unroll
+      for (int m = 0; m < 8; m++) raw[i0 + m] = v[m];
     }
     __syncthreads();
     for (int i = tid; i < kPackSeg + 7; i += 256) dig[i] = __int2half_rn(recode7(raw[i + 1], raw[i]));
@@ -266,9 +270,17 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     const int64_t s0 = (r - a.segA) * 16;
     const int64_t rho0 = s0 - kPadB;
     const int64_t top = 128 * a.R - 1;  // digit index of reversed position 0
-    for (int m = tid; m < kPackSeg + 1; m += 256) {
-      const int64_t j = top - (128 * rho0 + m);
-      raw[m] = (j < 0 || j > top) ? 0 : digit_at(op, j, a.N, a.b, 7, a.in_limbs, a.flip);
+    // reversed digits j = top - (128 rho0 + m), m <= kPackSeg: runs of eight
+    // consecutive j per thread, zero outside [0, top]
+    for (int m0 = 8 * tid; m0 < kPackSeg + 1; m0 += 8 * 256) {
+      const int64_t jhi = top - (128 * rho0 + m0);  // j of m0; j of m0 + 7 is jhi - 7
+      int32_t v[8];
+      digit_run<7, 8>(op, jhi - 7, a.N, a.b, a.in_limbs, a.flip, v);
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int64_t j = jhi - u;
+        if (m0 + u < kPackSeg + 1) raw[m0 + u] = (j < 0 || j > top) ? 0 : v[7 - u];
+      }
     }
     __syncthreads();
     for (int m = tid; m < kPackSeg; m += 256) dig[m] = __int2half_rn(recode7(raw[m], raw[m + 1]));

@@ -10,22 +10,39 @@ namespace ks {
 // KS1: V = h(2^N), off = 0, width N.  KS2: V = P+ + P- = 2 h0(X^2) and
 // V_odd = P+ - P- = 2X h1(X^2); then both even and odd coefficients sit at
 // bit 1 + kN, width 2N (Sec. 3.3).
+// One CTA writes 1024 consecutive output limbs, four per thread (strided by
+// the block, so every store is coalesced and the four loads are independent).
+constexpr int kUnpackPer = 4;
 template <class Src>
 __global__ void __launch_bounds__(256) unpack_kernel(Src src) {
   int64_t local;
   const UnpackArgs &a = src.locate(blockIdx.x, local);
-  const int64_t idx = local * 256 + threadIdx.x;
-  if (idx >= a.lh * a.ol) return;
-  const int64_t k = idx / a.ol;
-  const int l = (int)(idx - k * a.ol);
-  const uint32_t *src_w = (a.V_odd != nullptr && (k & 1)) ? a.V_odd : a.V;
-  const int rem = a.width - 64 * l;
-  uint64_t v = 0;
-  if (rem > 0) {
-    v = get_bits64(src_w, a.nwords, a.off + k * a.N + 64 * (int64_t)l);
-    if (rem < 64) v &= (1ull << rem) - 1ull;
+  const int64_t total = a.lh * a.ol;
+  const int64_t base = local * (256 * kUnpackPer) + threadIdx.x;
+  const bool narrow = total < ((int64_t)1 << 31);  // 32-bit index arithmetic suffices
+#pragma unroll
+  for (int i = 0; i < kUnpackPer; i++) {
+    const int64_t idx = base + 256 * i;
+    if (idx >= total) break;
+    int64_t k;
+    int l;
+    if (narrow) {
+      const uint32_t q = (uint32_t)idx / (uint32_t)a.ol;
+      k = q;
+      l = (int)((uint32_t)idx - q * (uint32_t)a.ol);
+    } else {
+      k = idx / a.ol;
+      l = (int)(idx - k * a.ol);
+    }
+    const uint32_t *src_w = (a.V_odd != nullptr && (k & 1)) ? a.V_odd : a.V;
+    const int rem = a.width - 64 * l;
+    uint64_t v = 0;
+    if (rem > 0) {
+      v = get_bits64(src_w, a.nwords, a.off + k * a.N + 64 * (int64_t)l);
+      if (rem < 64) v &= (1ull << rem) - 1ull;
+    }
+    a.h[idx] = v;
   }
-  a.h[idx] = v;
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -35,7 +52,9 @@ static unsigned grid_for(int64_t n, int threads) {
   return (unsigned)b;
 }
 
-int64_t unpack_blocks(const UnpackArgs &a) { return (a.lh * a.ol + 255) / 256; }
+int64_t unpack_blocks(const UnpackArgs &a) {
+  return (a.lh * a.ol + 256 * kUnpackPer - 1) / (256 * kUnpackPer);
+}
 
 cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s) {
   unpack_kernel<One<UnpackArgs>><<<(unsigned)unpack_blocks(a), 256, 0, s>>>(One<UnpackArgs>{a});
