@@ -410,6 +410,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
     prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
   }
+  pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     {
       PhaseTimer t(s, PH_PACK);

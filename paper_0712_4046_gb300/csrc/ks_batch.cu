@@ -232,6 +232,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     pa.op[2 * k + 1] = PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB};
     prods[k] = Product{A, p.nA, B, p.nB, cols + (int64_t)k * p.ncols};
   }
+  pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     TcPackArgs ta;
     int64_t blocks;

@@ -73,13 +73,17 @@ struct PackOp {
   int sigma;     // +1: f(X); -1: f(-X) (odd coefficients negated)
   int32_t *out;
   int64_t ndig;
+  int narrow = 0;  // every bit position of this evaluation is below 2^31
 };
 
 struct PackArgs {
   PackOp op[kMaxOperands];
   int nops;
   int N, b, d, in_limbs, flip;
+  uint64_t ninv = 0;  // floor(2^64 / N) + 1: floor(x / N) = umulhi(x, ninv), x < 2^31
 };
+// Fills ninv and the per-operand narrow flags (after the operands are set).
+void pack_finish(PackArgs &a);
 
 // Signed digits of each evaluation (Sec. 3.1-3.4 evaluations at +-2^N and
 // the reversed polynomial), `d` bits per digit position.
@@ -138,6 +142,7 @@ struct TcPackArgs {
   PackOp op[kMaxOperands];
   int nprod;
   int N, b, in_limbs, flip;
+  uint64_t ninv;
   __half *E[4];
   __half *BRT[4];
   int64_t nE, rows, R, nA, nB;
@@ -418,19 +423,59 @@ __device__ __forceinline__ int32_t digit_at(const PackOp &op, int64_t j, int64_t
 // one pair of divisions finds the coefficient fields that meet the K-digit
 // window, then each field adds its bits to the digits it overlaps
 // (compile-time digit width D, so the per-digit tests are register-only).
+// floor(x / N) for 0 <= x < 2^31 from m = floor(2^64 / N) + 1: with
+// m = (2^64 + delta) / N, 1 <= delta <= N, x m / 2^64 exceeds x / N by less
+// than 2^-33 < 1 / N, so the high word is the exact quotient (N = 1: x).
+__device__ __forceinline__ int64_t div_by_n(int64_t x, int64_t N, uint64_t m) {
+  return N == 1 ? x : (int64_t)__umul64hi((uint64_t)x, m);
+}
+
+// The fields t of the digits jlo .. jhi (inclusive): [t_lo, t_hi] (empty if
+// t_hi < t_lo).
+template <int D>
+__device__ __forceinline__ void field_range(const PackOp &op, int64_t jlo, int64_t jhi,
+                                            int64_t N, uint64_t ninv, int b, int64_t &t_lo,
+                                            int64_t &t_hi) {
+  const int64_t lo = jlo * D, hi = (jhi + 1) * D;
+  if (op.narrow) {
+    t_lo = lo - b < 0 ? 0 : div_by_n(lo - b, N, ninv) + 1;
+    t_hi = hi - 1 < 0 ? -1 : div_by_n(hi - 1, N, ninv);
+  } else {
+    t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
+    t_hi = hi - 1 < 0 ? -1 : (hi - 1) / N;
+  }
+  if (t_hi > op.L - 1) t_hi = op.L - 1;
+}
+
+// Coefficients src0 .. src0 + n - 1 of an operand (n * in_limbs words) are
+// copied to shared memory by the CTA when they fit in `cap` words; returns
+// true (block-uniform) when they were.
+__device__ __forceinline__ bool stage_coeffs(const PackOp &op, int64_t t_lo, int64_t t_hi,
+                                             int in_limbs, uint64_t *sm, int cap,
+                                             int64_t &src0) {
+  const int64_t n = t_hi - t_lo + 1;
+  src0 = op.reversed ? op.L - 1 - t_hi : t_lo;
+  if (n <= 0 || n * in_limbs > cap) return false;
+  const uint64_t *g = op.poly + src0 * in_limbs;
+  const int words = (int)(n * in_limbs);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) sm[i] = g[i];
+  return true;
+}
+
 template <int D, int K>
-__device__ __forceinline__ void digit_run(const PackOp &op, int64_t j0, int64_t N, int b,
-                                          int in_limbs, int flip, int32_t (&v)[K]) {
+__device__ __forceinline__ void digit_run(const PackOp &op, int64_t j0, int64_t N, uint64_t ninv,
+                                          int b, int in_limbs, int flip, int32_t (&v)[K],
+                                          const uint64_t *base = nullptr, int64_t src0 = 0) {
 #pragma unroll
   for (int m = 0; m < K; m++) v[m] = 0;
-  const int64_t lo = j0 * D, hi = (j0 + K) * D;
-  const int64_t t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
-  int64_t t_hi = (hi - 1) / N;
-  if (t_hi > op.L - 1) t_hi = op.L - 1;
+  const int64_t lo = j0 * D;
+  int64_t t_lo, t_hi;
+  field_range<D>(op, j0, j0 + K - 1, N, ninv, b, t_lo, t_hi);
   for (int64_t t = t_lo; t <= t_hi; t++) {
     const int64_t pos = t * N;
     const int64_t src = op.reversed ? (op.L - 1 - t) : t;
-    const uint64_t *c = op.poly + src * in_limbs;
+    // the coefficient in global memory, or in the CTA's staged copy
+    const uint64_t *c = base ? base + (src - src0) * in_limbs : op.poly + src * in_limbs;
     const bool neg = op.sigma < 0 && (t & 1);
 #pragma unroll
     for (int m = 0; m < K; m++) {

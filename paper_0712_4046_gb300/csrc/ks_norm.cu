@@ -30,6 +30,9 @@
 // it then publishes its own carry-out, and the CTA writes its words.  The ±
 // pair of a two- or four-point product (same c1, c2, opposite sigma) is done
 // by one CTA from one staged copy of c1 and c2, so those columns are read once.
+// A tile whose composed transfer function is constant publishes its
+// carry-out before looking back (it does not depend on the carry in), which
+// keeps the look-back short whatever the number of tiles in flight.
 // Flags and the counter must be zero before the launch; every wait is bounded
 // (about one second), after which the kernel records status 1 and finishes
 // with carry 0.
@@ -78,12 +81,6 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f) {
 __device__ __forceinline__ uint32_t compose2(uint32_t g, uint32_t f) {
   return compose(g & 63u, f & 63u) | (compose((g >> 8) & 63u, (f >> 8) & 63u) << 8);
 }
-__device__ __forceinline__ uint32_t word_fn(int64_t s) {
-  uint32_t h = 0;
-#pragma unroll
-  for (int c = -1; c <= 1; c++) h |= (uint32_t)(((s + c) >> 32) + 1) << (2 * (c + 1));
-  return h;
-}
 
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -107,7 +104,13 @@ __device__ int look_back(uint32_t *flags, int64_t tile, uint32_t total, int lane
     if (lane == 0) st_release(&flags[0], kFlagPre | (uint32_t)(apply_fn(total, 0) + 1));
     return 0;
   }
-  if (lane == 0) st_release(&flags[tile], kFlagAgg | total);
+  // A tile whose transfer function is constant (some word in it absorbs any
+  // incoming carry, the usual case) knows its carry-out already: publish it
+  // at once, so that the next tile never has to look past this one.
+  const int out_m = apply_fn(total, -1), out_z = apply_fn(total, 0);
+  const bool constant = out_m == out_z && out_z == apply_fn(total, 1);
+  if (lane == 0)
+    st_release(&flags[tile], constant ? (kFlagPre | (uint32_t)(out_z + 1)) : (kFlagAgg | total));
   uint32_t acc = kIdentity;  // the functions of the tiles passed so far
   int64_t top = tile - 1;
   uint64_t t0 = 0;
@@ -148,7 +151,8 @@ __device__ int look_back(uint32_t *flags, int64_t tile, uint32_t total, int lane
     top -= 32;
     t0 = 0;
   }
-  if (lane == 0) st_release(&flags[tile], kFlagPre | (uint32_t)(apply_fn(total, cin) + 1));
+  if (lane == 0 && !constant)
+    st_release(&flags[tile], kFlagPre | (uint32_t)(apply_fn(total, cin) + 1));
   return cin;
 }
 
@@ -214,10 +218,13 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
   }
   __syncthreads();
 
-  // s_j of this thread's words, for each sub-job; transfer functions side by side
+  // s_j of this thread's words, for each sub-job, and the thread's transfer
+  // function (bits 0-5 sub-job 0, bits 8-13 sub-job 1), found by running the
+  // three possible incoming carries through its words
   const int64_t j0 = W0 + (int64_t)tid * WPT;
   int64_t s[2][WPT];
   uint32_t agg = kIdentity | (kIdentity << 8);
+  bool all_const = true;
 #pragma unroll
   for (int u = 0; u < 2; u++) {
     if (u >= nsub) break;
@@ -231,30 +238,48 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
       x[i] = v;
     }
     thread_words<D>(x, s[u]);
-    uint32_t f = kIdentity;
+    int64_t cm = -1, cz = 0, cp = 1;
 #pragma unroll
-    for (int w = 0; w < WPT; w++) f = compose(word_fn(s[u][w]), f);
+    for (int w = 0; w < WPT; w++) {
+      cm = (s[u][w] + cm) >> 32;
+      cz = (s[u][w] + cz) >> 32;
+      cp = (s[u][w] + cp) >> 32;
+    }
+    const uint32_t f = (uint32_t)(cm + 1) | ((uint32_t)(cz + 1) << 2) | ((uint32_t)(cp + 1) << 4);
+    all_const = all_const && cm == cz && cz == cp;
     agg = u == 0 ? ((agg & ~63u) | f) : ((agg & 63u) | (f << 8));
   }
+  // usual case: every thread's function is constant (some word of it absorbs
+  // any incoming carry); then a thread's carry in is its predecessor's
+  // constant carry out, and no composition is needed
+  const bool fast = __syncthreads_and(all_const) != 0;
 
-  // block-wide exclusive scan of the (paired) functions in thread order
-  uint32_t incl = agg;
+  uint32_t pre = kIdentity | (kIdentity << 8), total;
+  if (fast) {
+    if (lane == 31) s_warp[wid] = agg;
+    __syncthreads();
+    total = s_warp[kThreads / 32 - 1];  // thread 127's constant functions
+  } else {
+    // block-wide exclusive scan of the (paired) functions in thread order
+    uint32_t incl = agg;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl = compose2(incl, o);
-  }
-  uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = kIdentity | (kIdentity << 8);
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  uint32_t wpre = kIdentity | (kIdentity << 8), total = kIdentity | (kIdentity << 8);
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl = compose2(incl, o);
+    }
+    uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = kIdentity | (kIdentity << 8);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    uint32_t wpre = kIdentity | (kIdentity << 8);
+    total = kIdentity | (kIdentity << 8);
 #pragma unroll
-  for (int w = 0; w < kThreads / 32; w++) {
-    if (w < wid) wpre = compose2(s_warp[w], wpre);
-    total = compose2(s_warp[w], total);
+    for (int w = 0; w < kThreads / 32; w++) {
+      if (w < wid) wpre = compose2(s_warp[w], wpre);
+      total = compose2(s_warp[w], total);
+    }
+    pre = compose2(excl, wpre);
   }
-  const uint32_t pre = compose2(excl, wpre);
 
   // warp u looks back for sub-job u
   if (wid < nsub) {
@@ -264,11 +289,19 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
   }
   __syncthreads();
 
+  // predecessor's functions (fast path): the previous lane, or the previous
+  // warp's last lane; thread 0 takes the tile's carry in
+  const uint32_t prev_lane = __shfl_up_sync(0xffffffffu, agg, 1);
+  const uint32_t prev = lane > 0 ? prev_lane : (wid > 0 ? s_warp[wid - 1] : 0u);
 #pragma unroll
   for (int u = 0; u < 2; u++) {
     if (u >= nsub) break;
     const NormJob &J = a.job[nsub * group + u];
-    int c = apply_fn((pre >> (8 * u)) & 63u, s_cin[u]);
+    int c;
+    if (fast)
+      c = tid == 0 ? s_cin[u] : apply_fn((prev >> (8 * u)) & 63u, 0);
+    else
+      c = apply_fn((pre >> (8 * u)) & 63u, s_cin[u]);
     uint32_t o[WPT];
 #pragma unroll
     for (int w = 0; w < WPT; w++) {

@@ -16,11 +16,13 @@
 // Forward transforms are decimation in frequency (natural order in,
 // bit-reversed out), the pointwise product keeps the bit-reversed order, and
 // the inverse is decimation in time (bit-reversed in, natural out), so no
-// permutation pass exists.  A pass loads 4096 elements of one transform into
-// shared memory and runs up to 12 radix-2 stages there: the last pass takes
-// contiguous blocks, earlier passes take 2^k strided elements for 4096 / 2^k
-// consecutive offsets (coalesced).  Twiddles w^e come from two tables per
-// prime and direction, w^e = T1[e mod 2^13] * T2[e >> 13].
+// permutation pass exists.  A pass takes 4096 elements of one transform and
+// runs up to 12 radix-2 stages on them, three at a time in registers (radix
+// 8) with shared memory between: the last pass takes contiguous blocks,
+// earlier passes take 2^k strided elements for 4096 / 2^k consecutive offsets
+// (coalesced).  Twiddles w^e come from two tables per prime and direction,
+// w^e = T1[e mod 2^13] * T2[e >> 13], one lookup per unit of eight elements;
+// the unit's other twiddles are products with fixed roots of unity.
 #include <mutex>
 
 #include "ks_internal.cuh"
@@ -32,6 +34,7 @@ constexpr int kMaxLog = 27;
 constexpr int kT1 = 1 << 13;
 constexpr int kT2 = 1 << 14;
 constexpr int kTile = 4096;
+constexpr int kTileLog = 12;
 constexpr int kPassThreads = 512;
 constexpr uint32_t kP[2] = {2013265921u, 2281701377u};
 constexpr uint32_t kG[2] = {31u, 3u};
@@ -74,55 +77,166 @@ struct NttArgs {
 // array id -> prime: arrays are laid out [product][prime][side]
 __device__ __forceinline__ int prime_of(int a) { return (a >> 1) & 1; }
 
+// zeta[prime][dir][m] = W^(m 2^24) (Montgomery form), W the order-2^27 root of
+// the direction: the 8th roots of unity the radix-8 rounds need
+__constant__ uint32_t c_zeta[2][2][4];
+
+// One pass: stages s0 .. s0 + k - 1 of one transform on a tile of 2^k rows x
+// Wc consecutive offsets (4096 elements when the transform is large enough).
+// The stages go in rounds of up to three: a thread takes a unit of 2^g
+// elements (rows v0 + m 2^pp, one offset) and runs the round's g radix-2
+// stages on them in registers.  Within a unit every twiddle follows from one,
+// t = w^(J 2^s) (J the unit's offset in its half-block, s its first stage):
+// the first stage multiplies by t zeta_8^m, the second by t^2 zeta_4^m', the
+// third by t^4 (for g = 2: t zeta_4^m, then t^2; g = 1: t).  The first
+// round reads the transform in global memory, the last writes it back; the
+// rounds between exchange through shared memory (one padding word per 32).
+__device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
+
 template <bool kForward>
 __global__ void __launch_bounds__(kPassThreads) ntt_pass(NttArgs g) {
-  __shared__ uint32_t S[kTile];
+  __shared__ uint32_t S[kTile + kTile / 32];
   const int a = blockIdx.y * g.astride + g.aoff;
   const int r = prime_of(a);
+  const int dir = kForward ? 0 : 1;
   const uint32_t p = g.pc[r].p, pinv = g.pc[r].pinv;
-  const int64_t n = (int64_t)1 << g.L;
-  uint32_t *X = g.data + (int64_t)a * n;
+  uint32_t *X = g.data + ((int64_t)a << g.L);
   const int k = g.k;
-  const int64_t F = n >> (g.s0 + k);        // finest block width of this pass
-  const int Wc = (int)(F < (kTile >> k) ? F : (kTile >> k));  // consecutive offsets per CTA
-  const int V = 1 << k;
-  const int64_t wblocks = F / Wc;
-  const int64_t u = blockIdx.x / wblocks;
-  const int64_t w0 = (blockIdx.x % wblocks) * Wc;
-  const int64_t ubase = u * (n >> g.s0);
-  const int tot = V * Wc;
-  for (int i = threadIdx.x; i < tot; i += kPassThreads) {
-    const int v = i / Wc, wi = i % Wc;
-    S[v * Wc + wi] = X[ubase + v * F + w0 + wi];
-  }
-  __syncthreads();
+  // every extent is a power of two: F = 2^lf rows apart, Wc = 2^lw offsets
+  const int lf = g.L - g.s0 - k;
+  const int lw = lf < kTileLog - k ? lf : kTileLog - k;
+  const int wmask = (1 << lw) - 1;
+  const int64_t u = (int64_t)blockIdx.x >> (lf - lw);
+  const int64_t w0 = ((int64_t)blockIdx.x & ((((int64_t)1) << (lf - lw)) - 1)) << lw;
+  const int64_t gbase = (u << (g.L - g.s0)) + w0;
   const int shift = kMaxLog - g.L;  // exponents in units of the order-2^27 root
-  for (int rr = 0; rr < k; rr++) {
-    const int r_st = kForward ? rr : (k - 1 - rr);  // stage within the pass
-    const int s = g.s0 + r_st;
-    const int h = 1 << (k - 1 - r_st);
-    for (int b = threadIdx.x; b < tot / 2; b += kPassThreads) {
-      const int wi = b % Wc, vp = b / Wc;
-      const int vlo = ((vp >> (k - 1 - r_st)) << (k - r_st)) | (vp & (h - 1));
-      const int ilo = vlo * Wc + wi, ihi = (vlo + h) * Wc + wi;
-      const uint32_t j = (uint32_t)((vlo & (h - 1)) * F + w0 + wi);
-      const uint32_t e = (j << s) << shift;
-      const uint32_t tw = twiddle(r, kForward ? 0 : 1, e, p, pinv);
-      const uint32_t x = S[ilo], y = S[ihi];
-      if (kForward) {
-        S[ilo] = add_mod(x, y, p);
-        S[ihi] = mont_mul(sub_mod(x, y, p), tw, p, pinv);
+  const uint32_t z1 = c_zeta[r][dir][1], z2 = c_zeta[r][dir][2], z3 = c_zeta[r][dir][3];
+  const int nr = (k + 2) / 3;
+  for (int ri = 0; ri < nr; ri++) {
+    const int rr = kForward ? ri : nr - 1 - ri;
+    const int r0 = 3 * rr;                       // first stage of the round (in the pass)
+    const int gs = (k - r0) < 3 ? (k - r0) : 3;  // stages in the round
+    const int pp = k - r0 - gs;                  // rows between a unit's elements: 2^pp
+    const int nunits = 1 << (k - gs + lw);
+    const bool first = ri == 0, last = ri == nr - 1;
+    const int s = g.s0 + r0;                     // global stage of the round's first stage
+    for (int un = threadIdx.x; un < nunits; un += kPassThreads) {
+      const int wi = un & wmask;
+      const int vr = un >> lw;
+      const int vlow = vr & ((1 << pp) - 1);
+      const int v0 = ((vr >> pp) << (pp + gs)) | vlow;
+      const int ne = 1 << gs;
+      uint32_t x[8];
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        if (m < ne) {
+          const int v = v0 + (m << pp);
+          x[m] = first ? X[gbase + ((int64_t)v << lf) + wi] : S[sidx((v << lw) | wi)];
+        }
+      }
+      const uint32_t J = (uint32_t)(((int64_t)vlow << lf) + w0 + wi);
+      const uint32_t t = twiddle(r, dir, (J << s) << shift, p, pinv);
+      if (gs == 3) {
+        const uint32_t t2 = mont_mul(t, t, p, pinv), t4 = mont_mul(t2, t2, p, pinv);
+        const uint32_t tA[4] = {t, mont_mul(t, z1, p, pinv), mont_mul(t, z2, p, pinv),
+                                mont_mul(t, z3, p, pinv)};
+        const uint32_t tB[2] = {t2, mont_mul(t2, z2, p, pinv)};
+        if (kForward) {
+#pragma unroll
+          for (int m = 0; m < 4; m++) {
+            const uint32_t x0 = x[m], x1 = x[m + 4];
+            x[m] = add_mod(x0, x1, p);
+            x[m + 4] = mont_mul(sub_mod(x0, x1, p), tA[m], p, pinv);
+          }
+#pragma unroll
+          for (int m = 0; m < 8; m++) {
+            if ((m & 2) == 0) {
+              const uint32_t x0 = x[m], x1 = x[m + 2];
+              x[m] = add_mod(x0, x1, p);
+              x[m + 2] = mont_mul(sub_mod(x0, x1, p), tB[m & 1], p, pinv);
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < 8; m += 2) {
+            const uint32_t x0 = x[m], x1 = x[m + 1];
+            x[m] = add_mod(x0, x1, p);
+            x[m + 1] = mont_mul(sub_mod(x0, x1, p), t4, p, pinv);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 8; m += 2) {
+            const uint32_t x0 = x[m], y = mont_mul(x[m + 1], t4, p, pinv);
+            x[m] = add_mod(x0, y, p);
+            x[m + 1] = sub_mod(x0, y, p);
+          }
+#pragma unroll
+          for (int m = 0; m < 8; m++) {
+            if ((m & 2) == 0) {
+              const uint32_t x0 = x[m], y = mont_mul(x[m + 2], tB[m & 1], p, pinv);
+              x[m] = add_mod(x0, y, p);
+              x[m + 2] = sub_mod(x0, y, p);
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < 4; m++) {
+            const uint32_t x0 = x[m], y = mont_mul(x[m + 4], tA[m], p, pinv);
+            x[m] = add_mod(x0, y, p);
+            x[m + 4] = sub_mod(x0, y, p);
+          }
+        }
+      } else if (gs == 2) {
+        const uint32_t t2 = mont_mul(t, t, p, pinv);
+        const uint32_t tA[2] = {t, mont_mul(t, z2, p, pinv)};
+        if (kForward) {
+#pragma unroll
+          for (int m = 0; m < 2; m++) {
+            const uint32_t x0 = x[m], x1 = x[m + 2];
+            x[m] = add_mod(x0, x1, p);
+            x[m + 2] = mont_mul(sub_mod(x0, x1, p), tA[m], p, pinv);
+          }
+#pragma unroll
+          for (int m = 0; m < 4; m += 2) {
+            const uint32_t x0 = x[m], x1 = x[m + 1];
+            x[m] = add_mod(x0, x1, p);
+            x[m + 1] = mont_mul(sub_mod(x0, x1, p), t2, p, pinv);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 4; m += 2) {
+            const uint32_t x0 = x[m], y = mont_mul(x[m + 1], t2, p, pinv);
+            x[m] = add_mod(x0, y, p);
+            x[m + 1] = sub_mod(x0, y, p);
+          }
+#pragma unroll
+          for (int m = 0; m < 2; m++) {
+            const uint32_t x0 = x[m], y = mont_mul(x[m + 2], tA[m], p, pinv);
+            x[m] = add_mod(x0, y, p);
+            x[m + 2] = sub_mod(x0, y, p);
+          }
+        }
       } else {
-        const uint32_t yt = mont_mul(y, tw, p, pinv);
-        S[ilo] = add_mod(x, yt, p);
-        S[ihi] = sub_mod(x, yt, p);
+        if (kForward) {
+          const uint32_t x0 = x[0], x1 = x[1];
+          x[0] = add_mod(x0, x1, p);
+          x[1] = mont_mul(sub_mod(x0, x1, p), t, p, pinv);
+        } else {
+          const uint32_t x0 = x[0], y = mont_mul(x[1], t, p, pinv);
+          x[0] = add_mod(x0, y, p);
+          x[1] = sub_mod(x0, y, p);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        if (m < ne) {
+          const int v = v0 + (m << pp);
+          if (last)
+            X[gbase + ((int64_t)v << lf) + wi] = x[m];
+          else
+            S[sidx((v << lw) | wi)] = x[m];
+        }
       }
     }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < tot; i += kPassThreads) {
-    const int v = i / Wc, wi = i % Wc;
-    X[ubase + v * F + w0 + wi] = S[v * Wc + wi];
+    if (!last) __syncthreads();
   }
 }
 
@@ -136,7 +250,7 @@ struct LoadArgs {
   PrimeC pc[2];
 };
 
-__global__ void __launch_bounds__(256) ntt_load(LoadArgs g) {
+__global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs g) {
   const int64_t n = (int64_t)1 << g.L;
   const int64_t total = n * 4 * g.nprod;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -180,14 +294,12 @@ struct CrtArgs {
   uint32_t M;         // p1^-1 R mod p2
 };
 
-__global__ void __launch_bounds__(256) ntt_crt(CrtArgs g) {
+__global__ void __launch_bounds__(256) ntt_crt(const __grid_constant__ CrtArgs g) {
   const int64_t n = (int64_t)1 << g.L;
-  const int64_t total = g.ncols * g.nprod;
   const uint64_t P = (uint64_t)g.pc[0].p * g.pc[1].p;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx / g.ncols);
-    const int64_t k = idx - q * g.ncols;
+  const int q = blockIdx.y;  // product
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.ncols;
+       k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t z1 = g.data[(int64_t)(4 * q + 0) * n + k];
     const uint32_t z2 = g.data[(int64_t)(4 * q + 2) * n + k];
     const uint32_t c1 = mont_mul(z1, g.K[0], g.pc[0].p, g.pc[0].pinv);
@@ -251,6 +363,22 @@ int init_tables() {
     host_ready = true;
   }
   if (cudaMemcpyToSymbol(g_tw, host, sizeof(host)) != cudaSuccess) return -1;
+  // the 8th roots of unity W^(m 2^24), m < 4, per prime and direction
+  uint32_t zeta[2][2][4];
+  for (int r = 0; r < 2; r++) {
+    const uint64_t p = kP[r];
+    const uint64_t w = powmod(kG[r], (p - 1) >> kMaxLog, p);
+    const uint64_t wi = powmod(w, p - 2, p);
+    for (int dir = 0; dir < 2; dir++) {
+      const uint64_t z = powmod(dir == 0 ? w : wi, (uint64_t)1 << 24, p);
+      uint64_t x = 1;
+      for (int m = 0; m < 4; m++) {
+        zeta[r][dir][m] = to_mont(x, (uint32_t)p);
+        x = (unsigned __int128)x * z % p;
+      }
+    }
+  }
+  if (cudaMemcpyToSymbol(c_zeta, zeta, sizeof(zeta)) != cudaSuccess) return -1;
   done[dev] = true;
   return 0;
 }
@@ -355,10 +483,9 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   }
   const uint64_t p1inv = powmod(kP[0] % kP[1], kP[1] - 2, kP[1]);
   c.M = to_mont(p1inv, kP[1]);
-  tot = c.ncols * nprod;
-  blocks = (tot + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  ntt_crt<<<(unsigned)blocks, 256, 0, s>>>(c);
+  blocks = (c.ncols + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  ntt_crt<<<dim3((unsigned)blocks, (unsigned)nprod), 256, 0, s>>>(c);
   note_launches(3 + 2 * np);
   return cudaGetLastError();
 }

@@ -31,11 +31,16 @@ __host__ __device__ __forceinline__ int64_t ctas_for(int64_t ndig) {
 }
 }  // namespace
 
-// One CTA makes 2048 consecutive digits of one operand: each thread a run of
-// eight (digit_run), staged in shared memory, then stored coalesced.
+// One CTA makes 2048 consecutive digits of one operand: it copies the
+// coefficients they read into shared memory (when they fit), each thread
+// makes a run of eight (digit_run), and the digits are stored coalesced
+// through shared memory.
+constexpr int kStageWords = 3072;  // coefficient words staged per CTA (24 KB)
+
 template <class Src>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
   __shared__ int32_t st[kCtaDigits + kCtaDigits / 8];
+  __shared__ uint64_t cf[kStageWords];
   int64_t local;
   const PackArgs &a = src.locate(blockIdx.x, local);
   int o = 0;
@@ -47,14 +52,33 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
   const PackOp &op = a.op[o];
   const int tid = threadIdx.x;
   const int64_t jc = local * kCtaDigits;
+  // the coefficients this CTA's digits read, staged once (coalesced)
+  int64_t t_lo, t_hi, src0;
+  field_range<16>(op, jc, jc + kCtaDigits - 1, a.N, a.ninv, a.b, t_lo, t_hi);
+  const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kStageWords, src0);
+  __syncthreads();
   int32_t v[kRun];
-  digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.b, a.in_limbs, a.flip, v);
+  digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
+                      staged ? cf : nullptr, src0);
 #pragma unroll
   for (int m = 0; m < kRun; m++) st[pad8(kRun * tid + m)] = v[m];
   __syncthreads();
   for (int i = tid; i < kCtaDigits; i += kPackThreads) {
     const int64_t j = jc + i;
     if (j < op.ndig) op.out[j] = st[pad8(i)];
+  }
+}
+
+void pack_finish(PackArgs &a) {
+  a.ninv = a.N > 1 ? (uint64_t)(((unsigned __int128)1 << 64) / (unsigned)a.N) + 1 : 0;
+  for (int o = 0; o < a.nops; o++) {
+    PackOp &op = a.op[o];
+    // largest bit position a digit run or a field reaches (with a margin for
+    // the runs past the last digit: the tensor-core window rows reach about
+    // 2300 digits beyond it)
+    const int64_t top_digit = (op.ndig + 8192) * (int64_t)a.d;
+    const int64_t top_field = op.L * (int64_t)a.N + a.b;
+    op.narrow = (top_digit < ((int64_t)1 << 31) && top_field < ((int64_t)1 << 31)) ? 1 : 0;
   }
 }
 

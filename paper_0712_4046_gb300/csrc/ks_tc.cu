@@ -76,6 +76,7 @@ constexpr int kNumAcc = 4;
 constexpr int kTmemCols = kNT * kNumAcc;
 constexpr int kMaxItemChunks = 128;        // int32 sums: 128 * 10,616,832 < 2^31
 constexpr int kPackSeg = 2048;             // A window rows / reversed B digits per pack CTA
+constexpr int kPackStageWords = 2048;       // coefficient words a pack CTA stages (16 KB)
 // instruction descriptor, kind::f16: D = f32 (bits 4-5 = 1), A = B = f16
 // (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t kIdescM = (1u << 4) | ((uint32_t)(kTM >> 4) << 24);
@@ -224,6 +225,7 @@ template <class Src>
 __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
   __shared__ int32_t raw[kPackSeg + 8];
   __shared__ __align__(16) __half dig[kPackSeg + 8];
+  __shared__ uint64_t cf[kPackStageWords];  // the segment's coefficients, when they fit
   int64_t local;
   const TcPackArgs &a = src.locate(blockIdx.x, local);
   const int64_t per = a.segA + a.segB;
@@ -243,9 +245,14 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     const int64_t x0 = h0 - 127;
     // digits x0 - 1 + i, i < kPackSeg + 8: runs of eight per thread (digits
     // at negative positions come out as zero)
+    int64_t t_lo, t_hi, src0;
+    field_range<7>(op, x0 - 1, x0 + kPackSeg + 6, a.N, a.ninv, a.b, t_lo, t_hi);
+    const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
+    __syncthreads();
     for (int i0 = 8 * tid; i0 < kPackSeg + 8; i0 += 8 * 256) {
       int32_t v[8];
-      digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.b, a.in_limbs, a.flip, v);
+      digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
+                      staged ? cf : nullptr, src0);
 #pragma unroll
       for (int m = 0; m < 8; m++) raw[i0 + m] = v[m];
     }
@@ -272,10 +279,16 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     const int64_t top = 128 * a.R - 1;  // digit index of reversed position 0
     // reversed digits j = top - (128 rho0 + m), m <= kPackSeg: runs of eight
     // consecutive j per thread, zero outside [0, top]
+    int64_t t_lo, t_hi, src0;
+    field_range<7>(op, top - 128 * rho0 - kPackSeg - 7, top - 128 * rho0, a.N, a.ninv, a.b, t_lo,
+                   t_hi);
+    const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
+    __syncthreads();
     for (int m0 = 8 * tid; m0 < kPackSeg + 1; m0 += 8 * 256) {
       const int64_t jhi = top - (128 * rho0 + m0);  // j of m0; j of m0 + 7 is jhi - 7
       int32_t v[8];
-      digit_run<7, 8>(op, jhi - 7, a.N, a.b, a.in_limbs, a.flip, v);
+      digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
+                      staged ? cf : nullptr, src0);
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const int64_t j = jhi - u;
@@ -726,6 +739,7 @@ void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *bas
   a.b = pa.b;
   a.in_limbs = pa.in_limbs;
   a.flip = pa.flip;
+  a.ninv = pa.ninv;
   const size_t per = tc_operand_bytes(g);
   for (int q = 0; q < nprod; q++) {
     a.E[q] = reinterpret_cast<__half *>(base + q * per);
