@@ -178,9 +178,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   else
     off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
   p.off_cols = off;
-  // the normalization's look-back flags follow the column sums directly, so
-  // the clearing of the column sums clears them too
-  p.off_flags = off + (size_t)p.nprod * p.ncols * 8;
+  off = align256(off + (size_t)p.nprod * p.ncols * 8);
+  p.off_flags = off;
   p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
   off = align256(p.off_flags + (size_t)p.flag_bytes);
   p.off_words = off;
@@ -347,7 +346,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
-  const int64_t nzero = (int64_t)p.nprod * p.ncols + p.flag_bytes / 8;  // sums + flags
+  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
   uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
 
   // reconstruction runs (Sec. 3.2; twice for Sec. 3.4)
@@ -430,7 +429,6 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
       KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)nzero * 8, s));
       KS_CUDA(launch_schoolbook(prods, p.nprod, s));
     } else {
-      KS_CUDA(cudaMemsetAsync(flags, 0, (size_t)p.flag_bytes, s));
       KS_CUDA(launch_ntt_products(prods, p.nprod, p.ntt_log, p.d, ws + p.off_ntt, s));
     }
   }
@@ -444,7 +442,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
     jobs[i].sigma = sigma;
     jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].flags = flags + 2 + (int64_t)i * p.ntiles;
+    jobs[i].flags = flags + (int64_t)i * p.ntiles;
   };
   switch (p.variant) {
     case KS_1: job(0, 0, -1, 1); break;
@@ -455,7 +453,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   }
   {
     PhaseTimer t(s, PH_NORMALIZE);
-    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, flags, status, s));
+    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, s));
   }
   const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
                  *V3 = words + 3 * p.nwords;
@@ -717,7 +715,7 @@ int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t 
   rc = static_scratch_ptr(&ws);
   if (rc != KS_OK) return rc;
   // run_plan clears the scratch that must start at zero (the column sums,
-  // the normalization flags, the seed accumulators) on `stream` before use;
+  // the seed accumulators) on `stream` before use;
   // everything runs on `stream` alone (no helper stream is created).
   return run_plan(p, h, f, g, ws, static_cast<cudaStream_t>(stream), false);
 }

@@ -102,8 +102,8 @@ struct ks_plan {
   ks::List<ks::TcPackArgs> tcpack;
   ks::List<ks::SchoolArgs> school;
   ks::List<ks::TcArgs> tc;
-  ks::List<ks::NormArgs> norm[2];        // digit width 16 and 28 (tensor cores)
-  unsigned int *norm_counter = nullptr;  // tiles claimed by each normalization launch
+  ks::List<ks::NormArgs> norm[2];   // digit width 16 and 28 (tensor cores): tile pass
+  ks::List<ks::NormArgs> normc[2];  // the same descriptors, carry-pass block counts
   ks::List<ks::UnpackArgs> unpack;
   ks::List<ks::SeedBArgs> seedb, seedb_finish;
   ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
@@ -189,8 +189,8 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
   for (int c = 0; c < 2; c++)
     if (P->norm[c].n())
       KS_TRY(launch_normalize_batch(c == 0 ? 16 : 28, P->norm[c].d, P->norm[c].dprefix,
-                                    P->norm[c].n(), P->norm[c].blocks(), P->norm_counter + c,
-                                    status_ptr(), s));
+                                    P->normc[c].dprefix, P->norm[c].n(), P->norm[c].blocks(),
+                                    P->normc[c].blocks(), s));
   if (P->unpack.n())
     KS_TRY(launch_unpack_batch(P->unpack.d, P->unpack.dprefix, P->unpack.n(),
                                P->unpack.blocks(), s));
@@ -213,7 +213,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
-  const int64_t nzero = (int64_t)p.nprod * p.ncols + p.flag_bytes / 8;  // sums + flags
+  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
   static const int kSig[5][4] = {{1}, {1}, {1, -1}, {1, 1}, {1, -1, 1, -1}};
@@ -247,8 +247,6 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
       P->school.add(sa, sa.block_prefix[p.nprod]);
       P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
     } else {
-      const int64_t nf = p.flag_bytes / 8;
-      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(flags), nf}, (nf + 255) / 256);
       NttJob j{};
       for (int k = 0; k < p.nprod; k++) j.prods[k] = prods[k];
       j.nprod = p.nprod;
@@ -266,7 +264,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
     jobs[i].sigma = sigma;
     jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].flags = flags + 2 + (int64_t)i * p.ntiles;
+    jobs[i].flags = flags + (int64_t)i * p.ntiles;
   };
   switch (p.variant) {
     case KS_1: job(0, 0, -1, 1); break;
@@ -277,6 +275,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   NormArgs na;
   if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
   P->norm[p.dn == 28 ? 1 : 0].add(na, norm_blocks(na));
+  P->normc[p.dn == 28 ? 1 : 0].add(na, norm_carry_blocks(na));
   const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
                  *V3 = words + 3 * p.nwords;
   const int ol = p.out_limbs;
@@ -376,21 +375,18 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     offs[i] = total;
     total += align256(P->plans[i].total);
   }
-  // one more 256-byte slot at the end: the normalization launches' tile counters
   if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ECUDA;
   }
-  P->ws_bytes = total + 256;
+  P->ws_bytes = total < 256 ? 256 : total;
   if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
     P->ws = nullptr;
     ks_plan_destroy(P);
     return KS_ENOMEM;
   }
-  P->norm_counter = reinterpret_cast<unsigned int *>(P->ws + total);
-  P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(P->norm_counter), 1}, 1);
   int *status = status_ptr();
   for (int64_t i = 0; i < n; i++) {
     const Plan &p = P->plans[i];
@@ -412,7 +408,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->tc_chunks = P->tc.blocks();
   // descriptor arrays: one device allocation, filled from a pinned host copy
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
-              P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->unpack.bytes() +
+              P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->normc[0].bytes() +
+              P->normc[1].bytes() + P->unpack.bytes() +
               P->seedb.bytes() + P->seedb_finish.bytes() + P->pref.bytes() + P->fix.bytes();
   for (int i = 0; i < 7; i++) db += P->seedk[i].bytes();
   for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
@@ -427,8 +424,11 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->tcpack.place(h, d);
   P->school.place(h, d);
   P->tc.place(h, d);
-  P->norm[0].place(h, d);
-  P->norm[1].place(h, d);
+  for (int c = 0; c < 2; c++) {
+    P->norm[c].place(h, d);
+    P->normc[c].place(h, d);
+    P->normc[c].d = P->norm[c].d;  // both lists describe the same jobs
+  }
   P->unpack.place(h, d);
   P->seedb.place(h, d);
   P->seedb_finish.place(h, d);

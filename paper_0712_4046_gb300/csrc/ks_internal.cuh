@@ -52,7 +52,7 @@ struct Plan {
   int ntt_log = 0;      // transform length 2^ntt_log
   // workspace layout (byte offsets from the base)
   size_t off_digits = 0, off_cols = 0, off_flags = 0, off_words = 0;
-  int64_t flag_bytes = 0;  // right after the column sums: zeroed with them
+  int64_t flag_bytes = 0;  // the normalization's per-tile transfer functions
   size_t off_seeds = 0, off_seedacc = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
@@ -175,14 +175,13 @@ struct NormJob {
   int64_t n2;
   int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k)
   uint32_t *out;
-  uint32_t *flags;    // one look-back flag per scan tile (zero before the launch)
+  uint32_t *flags;    // one transfer function per scan tile (written by the tile pass)
 };
 
-// Normalizes up to 4 column-sum combinations into two's complement words in
-// one launch.  counter (one word) and the jobs' flags must be zero on entry.
+// Normalizes up to 4 column-sum combinations into two's complement words
+// (two launches: the tiles, then the carries between them).
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, unsigned int *counter, int *status,
-                             cudaStream_t s);
+                             int64_t ntiles, cudaStream_t s);
 
 struct NormArgs {
   NormJob job[4];
@@ -194,14 +193,14 @@ struct NormArgs {
 };
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
                    NormArgs &a);
-int64_t norm_blocks(const NormArgs &a);
-// bytes of a product's flag region (a counter word, a spare, the tile flags)
+int64_t norm_blocks(const NormArgs &a);        // CTAs of the tile pass
+int64_t norm_carry_blocks(const NormArgs &a);  // CTAs of the carry pass
+// bytes of a product's flag region (the tiles' transfer functions)
 int64_t norm_flag_bytes(int njobs, int64_t ntiles);
-// one launch per digit width d (16 or 28) for the whole batch; the counter is
-// shared by the launch
-cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix, int n,
-                                   int64_t blocks, unsigned int *counter, int *status,
-                                   cudaStream_t s);
+// the two launches for a whole batch, per digit width d (16 or 28)
+cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix_tiles,
+                                   const int64_t *prefix_carry, int n, int64_t tile_blocks,
+                                   int64_t carry_blocks, cudaStream_t s);
 // scan tiles of a combination of nwords words at digit width d
 int64_t norm_tiles_for(int64_t nwords, int d);
 
@@ -462,33 +461,86 @@ __device__ __forceinline__ bool stage_coeffs(const PackOp &op, int64_t t_lo, int
   return true;
 }
 
+// Limb i of a b-bit (biased) coefficient: the top limb is cut to the
+// coefficient's bits (inputs are sign-extended) and, for signed inputs, has
+// bit b-1 flipped (the bias 2^(b-1)); limbs past the top are zero.
+__device__ __forceinline__ uint64_t coeff_limb(const uint64_t *c, int i, int in_limbs, int b,
+                                               int flip) {
+  if (i >= in_limbs) return 0ull;
+  uint64_t v = c[i];
+  if (i == in_limbs - 1) {
+    const int top = b - 64 * i;  // 1 .. 64 bits in the top limb
+    if (top < 64) v &= (1ull << top) - 1ull;
+    if (flip) v ^= 1ull << (top - 1);
+  }
+  return v;
+}
+
+// Bits [x, x + 128) of a b-bit (biased) coefficient, as (lo, hi) 64-bit halves.
+__device__ __forceinline__ void coeff_bits128(const uint64_t *c, int x, int in_limbs, int b,
+                                              int flip, uint64_t &lo, uint64_t &hi) {
+  const int li = x >> 6, sh = x & 63;
+  const uint64_t w0 = coeff_limb(c, li, in_limbs, b, flip);
+  const uint64_t w1 = coeff_limb(c, li + 1, in_limbs, b, flip);
+  const uint64_t w2 = coeff_limb(c, li + 2, in_limbs, b, flip);
+  lo = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+  hi = sh ? (w1 >> sh) | (w2 << (64 - sh)) : w1;
+}
+
+// Digits j0 .. j0 + K - 1 of one evaluation (the same values as digit_at):
+// one pair of divisions finds the coefficient fields that meet the K-digit
+// window [lo, lo + K D); each field contributes the window's bits of its
+// coefficient placed at its offset (one 128-bit extraction), which split
+// into the K digits by compile-time shifts.
 template <int D, int K>
 __device__ __forceinline__ void digit_run(const PackOp &op, int64_t j0, int64_t N, uint64_t ninv,
                                           int b, int in_limbs, int flip, int32_t (&v)[K],
                                           const uint64_t *base = nullptr, int64_t src0 = 0) {
+  static_assert(D * K <= 128, "window of at most 128 bits");
+  constexpr int KD = D * K;
 #pragma unroll
   for (int m = 0; m < K; m++) v[m] = 0;
   const int64_t lo = j0 * D;
   int64_t t_lo, t_hi;
   field_range<D>(op, j0, j0 + K - 1, N, ninv, b, t_lo, t_hi);
   for (int64_t t = t_lo; t <= t_hi; t++) {
-    const int64_t pos = t * N;
     const int64_t src = op.reversed ? (op.L - 1 - t) : t;
     // the coefficient in global memory, or in the CTA's staged copy
     const uint64_t *c = base ? base + (src - src0) * in_limbs : op.poly + src * in_limbs;
     const bool neg = op.sigma < 0 && (t & 1);
+    // the field overlaps the window: -b < off < K D
+    const int off = (int)(t * N - lo);
+    uint64_t wlo, whi;
+    if (off >= 0) {
+      coeff_bits128(c, 0, in_limbs, b, flip, wlo, whi);
+      if (off >= 64) {
+        whi = wlo << (off - 64);
+        wlo = 0;
+      } else if (off > 0) {
+        whi = (whi << off) | (wlo >> (64 - off));
+        wlo <<= off;
+      }
+    } else {
+      coeff_bits128(c, -off, in_limbs, b, flip, wlo, whi);
+    }
+    if (KD < 64) {
+      wlo &= (1ull << (KD % 64)) - 1ull;
+      whi = 0;
+    } else if (KD < 128) {
+      whi &= (1ull << (KD % 64)) - 1ull;
+    }
 #pragma unroll
     for (int m = 0; m < K; m++) {
-      const int64_t dlo = lo + (int64_t)m * D;
-      if (dlo + D <= pos || dlo >= pos + b) continue;
-      uint32_t piece;
-      if (pos >= dlo) {
-        const int sh = (int)(pos - dlo);
-        piece = coeff_slice(c, in_limbs, b, flip, 0, D - sh) << sh;
-      } else {
-        piece = coeff_slice(c, in_limbs, b, flip, (int)(dlo - pos), D);
-      }
-      v[m] += neg ? -(int32_t)piece : (int32_t)piece;
+      const int sh = m * D;
+      uint64_t bits;
+      if (sh + D <= 64)
+        bits = wlo >> sh;
+      else if (sh >= 64)
+        bits = whi >> (sh - 64);
+      else
+        bits = (wlo >> sh) | (whi << (64 - sh));
+      const int32_t piece = (int32_t)(bits & ((1ull << D) - 1ull));
+      v[m] += neg ? -piece : piece;
     }
   }
 }

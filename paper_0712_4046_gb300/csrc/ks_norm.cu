@@ -18,24 +18,24 @@
 //     carry values.  Functions compose associatively, so the carries are a
 //     parallel prefix: warp shuffles, then the block, then across tiles.
 //
-// One launch does all of it (a single-pass scan with decoupled look-back).
-// Every CTA takes the next tile index from a counter, so the tiles it looks
-// back on were claimed by CTAs that are already running.  It stages the
-// columns its tile needs in shared memory (one coalesced read of the column
-// sums; a thread's words are exactly its columns' bit span, so all slicing
-// offsets are compile-time constants of the digit width), forms s_j, scans
-// its tile, publishes the tile's transfer
-// function, and then one warp looks back over the preceding tiles' flags
-// (32 tiles per step) until it meets a tile that has published its carry-out;
-// it then publishes its own carry-out, and the CTA writes its words.  The ±
-// pair of a two- or four-point product (same c1, c2, opposite sigma) is done
-// by one CTA from one staged copy of c1 and c2, so those columns are read once.
-// A tile whose composed transfer function is constant publishes its
-// carry-out before looking back (it does not depend on the carry in), which
-// keeps the look-back short whatever the number of tiles in flight.
-// Flags and the counter must be zero before the launch; every wait is bounded
-// (about one second), after which the kernel records status 1 and finishes
-// with carry 0.
+// Two launches, neither of which waits on another CTA:
+//
+//  * norm_tiles: every CTA takes one tile of words (one or both of a +- pair
+//    of combinations: same c1, c2, opposite sigma, so those columns are read
+//    once).  It stages the columns the tile needs in shared memory (one
+//    coalesced read of the column sums; a thread's words are exactly its
+//    columns' bit span, so all slicing offsets are compile-time constants of
+//    the digit width), forms s_j, resolves the carries inside the tile as if
+//    the carry into the tile were 0, writes the words, and records the tile's
+//    transfer function.  Usually every thread's function is constant (a word
+//    that absorbs any incoming carry), and then a thread's carry in is simply
+//    its predecessor's carry out.
+//  * norm_carry: the carry into each tile is the composition of the earlier
+//    tiles' functions applied to 0.  A CTA covers 256 tiles: it composes the
+//    functions of all tiles before its range (a block-wide ordered
+//    reduction), scans its own 256, and each thread adds its tile's carry in
+//    to the stored words -- an exact increment or decrement of the tile's
+//    value, which stops at the first word that absorbs it.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -43,10 +43,8 @@ namespace ks {
 
 namespace {
 constexpr int kThreads = 128;
+constexpr int kCarryThreads = 256;  // tiles per CTA of norm_carry
 constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
-constexpr uint32_t kFlagAgg = 1u << 8;      // the tile's transfer function is published
-constexpr uint32_t kFlagPre = 1u << 9;      // the tile's carry-out is published
-constexpr uint64_t kWaitNs = 1000000000ull;
 
 // Per digit width D: every thread takes WPT words = 32 WPT bits = CPT columns
 // exactly (32 WPT = D CPT), so each column sits at a compile-time bit offset
@@ -82,80 +80,6 @@ __device__ __forceinline__ uint32_t compose2(uint32_t g, uint32_t f) {
   return compose(g & 63u, f & 63u) | (compose((g >> 8) & 63u, (f >> 8) & 63u) << 8);
 }
 
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Looks back from `tile` over the flags of the preceding tiles (one warp, 32
-// tiles per step) and returns the carry into `tile`; publishes the tile's
-// carry-out.  `total` is the tile's own transfer function.
-__device__ int look_back(uint32_t *flags, int64_t tile, uint32_t total, int lane, int *status) {
-  if (tile == 0) {
-    if (lane == 0) st_release(&flags[0], kFlagPre | (uint32_t)(apply_fn(total, 0) + 1));
-    return 0;
-  }
-  // A tile whose transfer function is constant (some word in it absorbs any
-  // incoming carry, the usual case) knows its carry-out already: publish it
-  // at once, so that the next tile never has to look past this one.
-  const int out_m = apply_fn(total, -1), out_z = apply_fn(total, 0);
-  const bool constant = out_m == out_z && out_z == apply_fn(total, 1);
-  if (lane == 0)
-    st_release(&flags[tile], constant ? (kFlagPre | (uint32_t)(out_z + 1)) : (kFlagAgg | total));
-  uint32_t acc = kIdentity;  // the functions of the tiles passed so far
-  int64_t top = tile - 1;
-  uint64_t t0 = 0;
-  int cin = 0;
-  while (true) {
-    const int64_t ti = top - lane;
-    // lanes before tile 0 read as "carry-out 0"; tile 0 always publishes one
-    const uint32_t v = ti >= 0 ? ld_acquire(&flags[ti]) : (kFlagPre | 1u);
-    const unsigned pre = __ballot_sync(0xffffffffu, (v & kFlagPre) != 0);
-    const unsigned ready = __ballot_sync(0xffffffffu, (v & (kFlagPre | kFlagAgg)) != 0);
-    const int fp = pre ? __ffs(pre) - 1 : 32;  // nearest tile with a carry-out
-    const unsigned need = fp == 32 ? 0xffffffffu : ((1u << fp) - 1u);
-    if ((ready & need) != need) {
-      if (t0 == 0) {
-        t0 = globaltimer();
-      } else if (globaltimer() - t0 > kWaitNs) {
-        if (lane == 0) atomicExch(status, 1);
-        cin = 0;
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    // compose the functions of lanes 0 .. fp-1 (lane 0 is the latest tile)
-    uint32_t f = lane < fp ? (v & 63u) : kIdentity;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t o = __shfl_down_sync(0xffffffffu, f, off);
-      if (lane + off < 32) f = compose(f, o);
-    }
-    f = __shfl_sync(0xffffffffu, f, 0);
-    acc = compose(acc, f);
-    if (fp < 32) {
-      const uint32_t vp = __shfl_sync(0xffffffffu, v, fp);
-      cin = apply_fn(acc, (int)(vp & 3u) - 1);
-      break;
-    }
-    top -= 32;
-    t0 = 0;
-  }
-  if (lane == 0 && !constant)
-    st_release(&flags[tile], kFlagPre | (uint32_t)(apply_fn(total, cin) + 1));
-  return cin;
-}
-
 // s_j of a thread's WPT words from its BACK + CPT staged columns (x[i] is
 // column kstart - BACK + i); every offset and shift is a compile-time constant.
 template <int D>
@@ -183,23 +107,17 @@ __device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + G
   for (int w = 0; w < WPT; w++) s[w] = (int64_t)(uint32_t)T[w + 1] + (T[w] >> 32);
 }
 
-// counter: tiles claimed so far in this launch (zero before the launch)
 template <int D, class Src>
-__global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *counter,
-                                                        int *status) {
+__global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
   constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
   constexpr int NX = BACK + CPT;
   constexpr int TW = kThreads * WPT;  // words per tile
   __shared__ int64_t s_c1[kStage];
   __shared__ int64_t s_c2[kStage];
   __shared__ uint32_t s_warp[kThreads / 32];
-  __shared__ int s_cin[2];
-  __shared__ unsigned int s_vid;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_vid = atomicAdd(counter, 1u);
-  __syncthreads();
   int64_t bid;
-  const NormArgs &a = src.locate((int64_t)s_vid, bid);
+  const NormArgs &a = src.locate(blockIdx.x, bid);
   const int64_t group = bid / a.ntiles;
   const int64_t tile = bid - group * a.ntiles;
   const int nsub = a.paired ? 2 : 1;
@@ -281,16 +199,12 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
     pre = compose2(excl, wpre);
   }
 
-  // warp u looks back for sub-job u
-  if (wid < nsub) {
-    const NormJob &J = a.job[nsub * group + wid];
-    const int c = look_back(J.flags, tile, (total >> (8 * wid)) & 63u, lane, status);
-    if (lane == 0) s_cin[wid] = c;
-  }
-  __syncthreads();
+  // the tile's transfer functions, for the carry pass
+  if (tid == 0)
+    for (int u = 0; u < nsub; u++) a.job[nsub * group + u].flags[tile] = (total >> (8 * u)) & 63u;
 
   // predecessor's functions (fast path): the previous lane, or the previous
-  // warp's last lane; thread 0 takes the tile's carry in
+  // warp's last lane; thread 0 takes carry 0 (norm_carry adds the true one)
   const uint32_t prev_lane = __shfl_up_sync(0xffffffffu, agg, 1);
   const uint32_t prev = lane > 0 ? prev_lane : (wid > 0 ? s_warp[wid - 1] : 0u);
 #pragma unroll
@@ -299,9 +213,9 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
     const NormJob &J = a.job[nsub * group + u];
     int c;
     if (fast)
-      c = tid == 0 ? s_cin[u] : apply_fn((prev >> (8 * u)) & 63u, 0);
+      c = tid == 0 ? 0 : apply_fn((prev >> (8 * u)) & 63u, 0);
     else
-      c = apply_fn((pre >> (8 * u)) & 63u, s_cin[u]);
+      c = apply_fn((pre >> (8 * u)) & 63u, 0);
     uint32_t o[WPT];
 #pragma unroll
     for (int w = 0; w < WPT; w++) {
@@ -317,6 +231,73 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(Src src, unsigned int *c
 #pragma unroll
       for (int w = 0; w < WPT; w++)
         if (j0 + w < a.nwords) J.out[j0 + w] = o[w];
+    }
+  }
+}
+
+// Ordered block-wide composition: returns, in every thread, the composition
+// of the threads' functions in thread order (thread 0 innermost), and in
+// `excl` this thread's exclusive prefix.
+__device__ __forceinline__ uint32_t block_compose(uint32_t f, uint32_t &excl, uint32_t *s_warp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = f;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl = compose(incl, o);
+  }
+  uint32_t e = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) e = kIdentity;
+  __syncthreads();
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  uint32_t wpre = kIdentity, total = kIdentity;
+  for (int w = 0; w < kCarryThreads / 32; w++) {
+    if (w < wid) wpre = compose(s_warp[w], wpre);
+    total = compose(s_warp[w], total);
+  }
+  excl = compose(e, wpre);
+  return total;
+}
+
+// One CTA per 256 tiles of one group: carries into the tiles, added to the
+// stored words (tile t's words were written as if its carry in were 0).
+template <int D, class Src>
+__global__ void __launch_bounds__(kCarryThreads) norm_carry(Src src) {
+  constexpr int TW = kThreads * Geo<D>::WPT;
+  __shared__ uint32_t s_warp[kCarryThreads / 32];
+  int64_t bid;
+  const NormArgs &a = src.locate(blockIdx.x, bid);
+  const int64_t per = (a.ntiles + kCarryThreads - 1) / kCarryThreads;  // CTAs per group
+  const int64_t group = bid / per;
+  const int64_t t0 = (bid - group * per) * kCarryThreads;  // first tile of this CTA
+  const int nsub = a.paired ? 2 : 1;
+  const int tid = threadIdx.x;
+  for (int u = 0; u < nsub; u++) {
+    const NormJob &J = a.job[nsub * group + u];
+    // the composition of the functions of tiles 0 .. t0 - 1: each thread
+    // composes a contiguous run of them, then the runs are composed in order
+    const int64_t chunk = (t0 + kCarryThreads - 1) / kCarryThreads;
+    uint32_t f = kIdentity;
+    for (int64_t i = tid * chunk; i < (tid + 1) * chunk && i < t0; i++)
+      f = compose(J.flags[i] & 63u, f);
+    uint32_t excl;
+    const uint32_t before = block_compose(f, excl, s_warp);
+    const int c0 = apply_fn(before, 0);
+    // this CTA's tiles: exclusive prefix of their functions
+    const int64_t t = t0 + tid;
+    const uint32_t ft = t < a.ntiles ? (J.flags[t] & 63u) : kIdentity;
+    block_compose(ft, excl, s_warp);
+    int c = apply_fn(excl, c0);
+    if (t < a.ntiles && c != 0) {
+      const int64_t w0 = t * TW;
+      int64_t w1 = w0 + TW;
+      if (w1 > a.nwords) w1 = a.nwords;
+      for (int64_t j = w0; j < w1 && c != 0; j++) {
+        const int64_t v = (int64_t)J.out[j] + c;
+        J.out[j] = (uint32_t)v;
+        c = (int)(v >> 32);
+      }
     }
   }
 }
@@ -358,35 +339,46 @@ int64_t norm_blocks(const NormArgs &a) {
   return (a.paired ? a.njobs / 2 : a.njobs) * a.ntiles;
 }
 
+int64_t norm_carry_blocks(const NormArgs &a) {
+  return (a.paired ? a.njobs / 2 : a.njobs) * ((a.ntiles + kCarryThreads - 1) / kCarryThreads);
+}
+
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, unsigned int *counter, int *status, cudaStream_t s) {
+                             int64_t ntiles, cudaStream_t s) {
   NormArgs a;
   if (make_norm_args(jobs, njobs, d, nwords, ntiles, a) != 0) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)norm_blocks(a);
-  if (d == 28)
-    norm_kernel<28, One<NormArgs>><<<grid, kThreads, 0, s>>>(One<NormArgs>{a}, counter, status);
-  else
-    norm_kernel<16, One<NormArgs>><<<grid, kThreads, 0, s>>>(One<NormArgs>{a}, counter, status);
-  note_launches(1);
+  const One<NormArgs> one{a};
+  const unsigned g1 = (unsigned)norm_blocks(a), g2 = (unsigned)norm_carry_blocks(a);
+  if (d == 28) {
+    norm_tiles<28, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
+    norm_carry<28, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
+  } else {
+    norm_tiles<16, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
+    norm_carry<16, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
+  }
+  note_launches(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix, int n,
-                                   int64_t blocks, unsigned int *counter, int *status,
-                                   cudaStream_t s) {
-  if (n == 0 || blocks == 0) return cudaSuccess;
-  const Many<NormArgs> src{da, prefix, n};
-  if (d == 28)
-    norm_kernel<28, Many<NormArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(src, counter, status);
-  else
-    norm_kernel<16, Many<NormArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(src, counter, status);
-  note_launches(1);
+cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix_tiles,
+                                   const int64_t *prefix_carry, int n, int64_t tile_blocks,
+                                   int64_t carry_blocks, cudaStream_t s) {
+  if (n == 0 || tile_blocks == 0) return cudaSuccess;
+  const Many<NormArgs> t{da, prefix_tiles, n}, c{da, prefix_carry, n};
+  if (d == 28) {
+    norm_tiles<28, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
+    norm_carry<28, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
+  } else {
+    norm_tiles<16, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
+    norm_carry<16, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
+  }
+  note_launches(2);
   return cudaGetLastError();
 }
 
-// flag words of a product: one counter word, one spare, one flag per tile per job
+// flag words of a product: one transfer function per tile per job
 int64_t norm_flag_bytes(int njobs, int64_t ntiles) {
-  return ((8 + 4 * (int64_t)njobs * ntiles) + 7) & ~(int64_t)7;
+  return ((4 * (int64_t)njobs * ntiles) + 7) & ~(int64_t)7;
 }
 
 }  // namespace ks
