@@ -176,7 +176,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   if (engine == KS_ENGINE_TC)
     off = align256(off + (size_t)p.nprod * tc_operand_bytes(p.tg));
   else
-    off = align256(off + (size_t)p.nprod * (p.nA + p.nB) * 4);
+    off = align256(off + (size_t)p.nprod *
+                             (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3)) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
   p.off_flags = off;
@@ -305,14 +306,16 @@ bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *en
 }
 
 // --------------------------------------------------------------- execution
-// A helper stream and two events per (device, caller stream): the seeds and
+// A helper stream and three events per (device, caller stream): the seeds and
 // the signed prefix records read only f and g, so they run on the helper
-// stream while the products run on the caller's, and are joined before the
-// reconstruction.  Created on first use (no device memory) and kept.
+// stream, forked after the products (the persistent product kernels want
+// every SM) and overlapping the normalization and reconstruction; the seeds
+// are joined before the reconstruction, the prefix records before the signed
+// correction.  Created on first use (no device memory) and kept.
 struct Fork {
   int dev;
   cudaStream_t stream, side;
-  cudaEvent_t fork, join;
+  cudaEvent_t fork, join_seeds, join_prefix;
 };
 static std::mutex g_fork_mu;
 static std::vector<Fork> g_forks;
@@ -326,10 +329,11 @@ static int fork_for(cudaStream_t s, Fork *out) {
       *out = x;
       return KS_OK;
     }
-  Fork x{dev, s, nullptr, nullptr, nullptr};
+  Fork x{dev, s, nullptr, nullptr, nullptr, nullptr};
   KS_CUDA(cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking));
   KS_CUDA(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
-  KS_CUDA(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
+  KS_CUDA(cudaEventCreateWithFlags(&x.join_seeds, cudaEventDisableTiming));
+  KS_CUDA(cudaEventCreateWithFlags(&x.join_prefix, cudaEventDisableTiming));
   g_forks.push_back(x);
   *out = x;
   return KS_OK;
@@ -368,28 +372,13 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     }
   }
 
-  // the phases that read only f and g: exact seeds, signed prefix records
   const bool recon = p.variant == KS_3 || p.variant == KS_4;
   Fork fk{};
-  cudaStream_t side = s;
   if (fork && (recon || p.is_signed)) {
     const int rc = fork_for(s, &fk);
     if (rc != KS_OK) return rc;
-    side = fk.side;
-    KS_CUDA(cudaEventRecord(fk.fork, s));
-    KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
   }
-  if (recon) {
-    PhaseTimer t(side, PH_SEEDS);
-    KS_CUDA(launch_seeds(seeds, p.seed_words,
-                         reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
-                         p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, side));
-  }
-  if (p.is_signed) {
-    PhaseTimer t(side, PH_SIGNED_PREFIX);
-    KS_CUDA(launch_signed_prefix(p.out_limbs, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, side));
-  }
-  if (side != s) KS_CUDA(cudaEventRecord(fk.join, side));
+  const cudaStream_t side = fk.side != nullptr ? fk.side : s;
 
   // sub-product p: (reversed, sigma)
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
@@ -403,8 +392,9 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   pa.flip = p.is_signed;
   Product prods[4];
   for (int q = 0; q < p.nprod; q++) {
-    int32_t *A = dig + (int64_t)q * (p.nA + p.nB);
-    int32_t *B = A + p.nA;
+    // operands padded to multiples of four digits: every one 16-byte aligned
+    int32_t *A = dig + (int64_t)q * (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3));
+    int32_t *B = A + ((p.nA + 3) & ~(int64_t)3);
     pa.op[2 * q] = PackOp{f, p.lf, kRev[p.variant][q], kSig[p.variant][q], A, p.nA};
     pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
     prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
@@ -432,6 +422,25 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
       KS_CUDA(launch_ntt_products(prods, p.nprod, p.ntt_log, p.d, ws + p.off_ntt, s));
     }
   }
+
+  // the phases that read only f and g (exact seeds, signed prefix records),
+  // on the helper stream from here on
+  if (side != s) {
+    KS_CUDA(cudaEventRecord(fk.fork, s));
+    KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
+  }
+  if (recon) {
+    PhaseTimer t(side, PH_SEEDS);
+    KS_CUDA(launch_seeds(seeds, p.seed_words,
+                         reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
+                         p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, side));
+  }
+  if (side != s) KS_CUDA(cudaEventRecord(fk.join_seeds, side));
+  if (p.is_signed) {
+    PhaseTimer t(side, PH_SIGNED_PREFIX);
+    KS_CUDA(launch_signed_prefix(p.out_limbs, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, side));
+  }
+  if (side != s) KS_CUDA(cudaEventRecord(fk.join_prefix, side));
 
   // normalized combinations
   NormJob jobs[4];
@@ -466,12 +475,13 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     PhaseTimer t(s, PH_UNPACK);
     KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N}, s));
   }
-  if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join, 0));
   if (recon) {
+    if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join_seeds, 0));
     PhaseTimer t(s, PH_RECOVER);
     KS_CUDA(launch_recover(h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words, status,
                            s));
   }
+  if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join_prefix, 0));
   if (p.is_signed) {
     PhaseTimer t(s, PH_SIGNED);
     KS_CUDA(launch_signed_apply(h, ol, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, s));

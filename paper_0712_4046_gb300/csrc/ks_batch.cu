@@ -119,10 +119,11 @@ struct ks_plan {
   cudaStream_t graph_stream = nullptr;
   int device = 0;
   // the seeds and the signed prefix records read only the inputs: they run on
-  // a helper stream, forked after the clearing launch and joined before the
-  // reconstruction (in a captured graph: a parallel branch)
+  // a helper stream, forked after the products (whose persistent kernels want
+  // every SM) and joined before the reconstruction and the signed correction
+  // respectively (in a captured graph: a parallel branch)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
 };
 
 namespace ks {
@@ -154,6 +155,16 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     note_launches(1);
     KS_TRY(cudaGetLastError());
   }
+  if (P->pack.n())
+    KS_TRY(launch_pack_batch(P->pack.d, P->pack.dprefix, P->pack.n(), P->pack.blocks(), s));
+  if (P->tcpack.n())
+    KS_TRY(launch_tc_pack_batch(P->tcpack.d, P->tcpack.dprefix, P->tcpack.n(),
+                                P->tcpack.blocks(), s));
+  if (P->school.n())
+    KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
+                                   P->school.blocks(), s));
+  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_chunks, s));
+  for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
   const bool fork = P->side != nullptr && (P->seedb.n() || P->pref.n() || [&] {
     for (int i = 0; i < 7; i++)
       if (P->seedk[i].n()) return true;
@@ -172,20 +183,11 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     if (P->seedk[i].n())
       KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
                                      P->seedk[i].n(), P->seedk[i].blocks(), side));
+  if (fork) KS_TRY(cudaEventRecord(P->ev_join, side));
   if (P->pref.n())
     KS_TRY(launch_signed_prefix_batch(P->pref.d, P->pref.dprefix, P->pref.n(), P->pref.blocks(),
                                       side));
-  if (fork) KS_TRY(cudaEventRecord(P->ev_join, side));
-  if (P->pack.n())
-    KS_TRY(launch_pack_batch(P->pack.d, P->pack.dprefix, P->pack.n(), P->pack.blocks(), s));
-  if (P->tcpack.n())
-    KS_TRY(launch_tc_pack_batch(P->tcpack.d, P->tcpack.dprefix, P->tcpack.n(),
-                                P->tcpack.blocks(), s));
-  if (P->school.n())
-    KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
-                                   P->school.blocks(), s));
-  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_chunks, s));
-  for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
+  if (fork) KS_TRY(cudaEventRecord(P->ev_join2, side));
   for (int c = 0; c < 2; c++)
     if (P->norm[c].n())
       KS_TRY(launch_normalize_batch(c == 0 ? 16 : 28, P->norm[c].d, P->norm[c].dprefix,
@@ -199,6 +201,7 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     if (P->recover[c].n())
       KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
                                   P->recover[c].n(), P->recover[c].blocks(), P->recover_smem, s));
+  if (fork) KS_TRY(cudaStreamWaitEvent(s, P->ev_join2, 0));
   if (P->fix.n())
     KS_TRY(launch_signed_apply_batch(P->fix.d, P->fix.dprefix, P->fix.n(), P->fix.blocks(), s));
   for (auto &j : P->singles)
@@ -226,8 +229,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   pa.flip = p.is_signed;
   Product prods[4];
   for (int k = 0; k < p.nprod; k++) {
-    int32_t *A = dig + (int64_t)k * (p.nA + p.nB);
-    int32_t *B = A + p.nA;
+    // operands padded to multiples of four digits: every one 16-byte aligned
+    int32_t *A = dig + (int64_t)k * (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3));
+    int32_t *B = A + ((p.nA + 3) & ~(int64_t)3);
     pa.op[2 * k] = PackOp{q.f, p.lf, kRev[p.variant][k], kSig[p.variant][k], A, p.nA};
     pa.op[2 * k + 1] = PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB};
     prods[k] = Product{A, p.nA, B, p.nB, cols + (int64_t)k * p.ncols};
@@ -377,7 +381,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   }
   if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ECUDA;
   }
@@ -517,6 +522,7 @@ void ks_plan_destroy(ks_plan *P) {
   if (P->hdesc) cudaFreeHost(P->hdesc);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->ev_join2) cudaEventDestroy(P->ev_join2);
   if (P->side) cudaStreamDestroy(P->side);
   cudaSetDevice(cur);
   delete P;

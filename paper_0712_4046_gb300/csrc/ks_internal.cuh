@@ -457,7 +457,20 @@ __device__ __forceinline__ bool stage_coeffs(const PackOp &op, int64_t t_lo, int
   if (n <= 0 || n * in_limbs > cap) return false;
   const uint64_t *g = op.poly + src0 * in_limbs;
   const int words = (int)(n * in_limbs);
-  for (int i = threadIdx.x; i < words; i += blockDim.x) sm[i] = g[i];
+  // four loads in flight per thread (read-only path), then the stores
+  for (int i0 = threadIdx.x; i0 < words; i0 += 4 * blockDim.x) {
+    uint64_t r[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = i0 + u * blockDim.x;
+      r[u] = i < words ? __ldg(g + i) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = i0 + u * blockDim.x;
+      if (i < words) sm[i] = r[u];
+    }
+  }
   return true;
 }
 

@@ -129,10 +129,25 @@ __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
   // of thread 0 minus BACK), zero outside [0, n)
   const int64_t kt = tile * (int64_t)(kThreads * CPT) - BACK;
   constexpr int cnt = kThreads * CPT + BACK;
-  for (int i = tid; i < cnt; i += kThreads) {
-    const int64_t k = kt + i;
-    s_c1[pad8(i)] = (k >= 0 && k < J0.n1) ? J0.c1[k] : 0;
-    if (two) s_c2[pad8(i)] = (k >= 0 && k < J0.n2) ? J0.c2[k] : 0;
+  constexpr int kIt = (cnt + kThreads - 1) / kThreads;
+  {
+    // all of a thread's loads first (read-only path), then the stores
+    int64_t r1[kIt], r2[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; it++) {
+      const int i = tid + it * kThreads;
+      const int64_t k = kt + i;
+      r1[it] = (i < cnt && k >= 0 && k < J0.n1) ? __ldg(J0.c1 + k) : 0;
+      r2[it] = (two && i < cnt && k >= 0 && k < J0.n2) ? __ldg(J0.c2 + k) : 0;
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; it++) {
+      const int i = tid + it * kThreads;
+      if (i < cnt) {
+        s_c1[pad8(i)] = r1[it];
+        s_c2[pad8(i)] = r2[it];
+      }
+    }
   }
   __syncthreads();
 

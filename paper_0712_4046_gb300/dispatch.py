@@ -61,6 +61,10 @@ def default_grid():
     for L, b in ((64, 16), (256, 48), (1024, 64), (4096, 32), (512, 256)):
         for batch in (16, 256):
             shapes.append((L, L, b, 0, batch))
+    # the large batches of the batched executor
+    for L, b, s in ((64, 16, 0), (256, 48, 1), (1024, 64, 0), (512, 256, 1)):
+        for batch in (1024, 4096):
+            shapes.append((L, L, b, s, batch))
     return shapes
 
 
