@@ -399,6 +399,9 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
     prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
   }
+  // squaring (f = g, equal lengths): the int32-digit engines pack every
+  // evaluation once and multiply its digits by themselves
+  if (f == g && p.lf == p.lg && p.engine != KS_ENGINE_TC) squaring_pack(pa, prods, p.nprod);
   pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     {

@@ -236,6 +236,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     pa.op[2 * k + 1] = PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB};
     prods[k] = Product{A, p.nA, B, p.nB, cols + (int64_t)k * p.ncols};
   }
+  // squaring (f = g, equal lengths): the int32-digit engines pack every
+  // evaluation once and multiply its digits by themselves
+  if (q.f == q.g && p.lf == p.lg && p.engine != KS_ENGINE_TC) squaring_pack(pa, prods, p.nprod);
   pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     TcPackArgs ta;

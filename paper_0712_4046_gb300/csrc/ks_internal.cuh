@@ -85,6 +85,11 @@ struct PackArgs {
 // Fills ninv and the per-operand narrow flags (after the operands are set).
 void pack_finish(PackArgs &a);
 
+struct Product;
+// Squaring: keeps only the f-side operand of each sub-product (2 q) and makes
+// every sub-product read it on both sides.
+void squaring_pack(PackArgs &a, Product *prods, int nprod);
+
 // Signed digits of each evaluation (Sec. 3.1-3.4 evaluations at +-2^N and
 // the reversed polynomial), `d` bits per digit position.
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);

@@ -32,10 +32,11 @@
 //    its predecessor's carry out.
 //  * norm_carry: the carry into each tile is the composition of the earlier
 //    tiles' functions applied to 0.  A CTA covers 256 tiles: it composes the
-//    functions of all tiles before its range (a block-wide ordered
-//    reduction), scans its own 256, and each thread adds its tile's carry in
-//    to the stored words -- an exact increment or decrement of the tile's
-//    value, which stops at the first word that absorbs it.
+//    functions of the tiles before its range, 256 at a time backwards until
+//    the composition is constant (block-wide ordered reductions), scans its
+//    own 256, and each thread adds its tile's carry in to the stored words --
+//    an exact increment or decrement of the tile's value, which stops at the
+//    first word that absorbs it.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -290,14 +291,18 @@ __global__ void __launch_bounds__(kCarryThreads) norm_carry(Src src) {
   const int tid = threadIdx.x;
   for (int u = 0; u < nsub; u++) {
     const NormJob &J = a.job[nsub * group + u];
-    // the composition of the functions of tiles 0 .. t0 - 1: each thread
-    // composes a contiguous run of them, then the runs are composed in order
-    const int64_t chunk = (t0 + kCarryThreads - 1) / kCarryThreads;
-    uint32_t f = kIdentity;
-    for (int64_t i = tid * chunk; i < (tid + 1) * chunk && i < t0; i++)
-      f = compose(J.flags[i] & 63u, f);
-    uint32_t excl;
-    const uint32_t before = block_compose(f, excl, s_warp);
+    // the composition of the functions of tiles 0 .. t0 - 1, walked back from
+    // t0 in windows of 256 (one flag per thread, composed in order); it stops
+    // at the first window after which the composition is constant (usually the
+    // first: some tile absorbs any incoming carry), or at tile 0
+    uint32_t before = kIdentity, excl;
+    for (int64_t w1 = t0; w1 > 0; w1 -= kCarryThreads) {
+      const int64_t w0 = w1 - kCarryThreads;
+      const int64_t i = w0 + tid;
+      const uint32_t f = i >= 0 ? (J.flags[i] & 63u) : kIdentity;
+      before = compose(before, block_compose(f, excl, s_warp));
+      if (apply_fn(before, -1) == apply_fn(before, 1)) break;  // constant (monotone)
+    }
     const int c0 = apply_fn(before, 0);
     // this CTA's tiles: exclusive prefix of their functions
     const int64_t t = t0 + tid;

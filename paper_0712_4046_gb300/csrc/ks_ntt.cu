@@ -247,6 +247,7 @@ struct LoadArgs {
   uint32_t *data;
   int L;
   int nprod;
+  int square;  // A = B: only the first side is loaded and transformed
   PrimeC pc[2];
 };
 
@@ -258,6 +259,7 @@ __global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs
     const int a = (int)(idx >> g.L);
     const int64_t i = idx & (n - 1);
     const int q = a >> 2, r = (a >> 1) & 1, side = a & 1;
+    if (g.square && side == 1) continue;
     const uint32_t p = g.pc[r].p;
     int32_t d = 0;
     if (side == 0) {
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs
 }
 
 __global__ void __launch_bounds__(256) ntt_pointwise(uint32_t *data, int L, int nprod, PrimeC p0,
-                                                     PrimeC p1) {
+                                                     PrimeC p1, int square) {
   const int64_t n = (int64_t)1 << L;
   const int64_t total = n * 2 * nprod;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -279,7 +281,8 @@ __global__ void __launch_bounds__(256) ntt_pointwise(uint32_t *data, int L, int 
     const int64_t i = idx & (n - 1);
     const PrimeC pc = (qr & 1) ? p1 : p0;
     uint32_t *X = data + (int64_t)(2 * qr) * n;
-    X[i] = mont_mul(X[i], X[n + i], pc.p, pc.pinv);
+    const uint32_t x = X[i];
+    X[i] = mont_mul(x, square ? x : X[n + i], pc.p, pc.pinv);
   }
 }
 
@@ -425,6 +428,9 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   }
   la.nA = prods[0].nA;
   la.nB = prods[0].nB;
+  // squaring: both operands are the same digits
+  const int square = (prods[0].A == prods[0].B && prods[0].nA == prods[0].nB) ? 1 : 0;
+  la.square = square;
   la.data = data;
   la.L = log_n;
   la.nprod = nprod;
@@ -442,20 +448,21 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   g.L = log_n;
   g.pc[0] = pc0;
   g.pc[1] = pc1;
-  for (int i = 0; i < np; i++) {  // forward: all 4 * nprod arrays
+  for (int i = 0; i < np; i++) {  // forward: all 4 * nprod arrays (squaring: the first sides)
     g.s0 = s0[i];
     g.k = kk[i];
-    g.astride = 1;
+    g.astride = square ? 2 : 1;
     g.aoff = 0;
     const int64_t F = n >> (s0[i] + kk[i]);
     const int64_t Wc = F < (kTile >> kk[i]) ? F : (kTile >> kk[i]);
     const int64_t ctas = ((int64_t)1 << s0[i]) * (F / Wc);
-    ntt_pass<true><<<dim3((unsigned)ctas, (unsigned)(4 * nprod)), kPassThreads, 0, s>>>(g);
+    ntt_pass<true><<<dim3((unsigned)ctas, (unsigned)((square ? 2 : 4) * nprod)), kPassThreads, 0,
+                     s>>>(g);
   }
   tot = n * 2 * nprod;
   blocks = (tot + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  ntt_pointwise<<<(unsigned)blocks, 256, 0, s>>>(data, log_n, nprod, pc0, pc1);
+  ntt_pointwise<<<(unsigned)blocks, 256, 0, s>>>(data, log_n, nprod, pc0, pc1, square);
   for (int i = np - 1; i >= 0; i--) {  // inverse: the product arrays (side 0)
     g.s0 = s0[i];
     g.k = kk[i];

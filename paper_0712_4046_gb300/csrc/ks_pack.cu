@@ -58,8 +58,12 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
   const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kStageWords, src0);
   __syncthreads();
   int32_t v[kRun];
-  digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
-                      staged ? cf : nullptr, src0);
+  // two call sites, so that the staged one reads shared memory as such
+  if (staged)
+    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
+                        cf, src0);
+  else
+    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
 #pragma unroll
   for (int m = 0; m < kRun; m++) st[pad8(kRun * tid + m)] = v[m];
   __syncthreads();
@@ -67,6 +71,14 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
     const int64_t j = jc + i;
     if (j < op.ndig) op.out[j] = st[pad8(i)];
   }
+}
+
+void squaring_pack(PackArgs &a, Product *prods, int nprod) {
+  for (int q = 0; q < nprod; q++) {
+    a.op[q] = a.op[2 * q];
+    prods[q].B = prods[q].A;
+  }
+  a.nops = nprod;
 }
 
 void pack_finish(PackArgs &a) {

@@ -251,8 +251,10 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     __syncthreads();
     for (int i0 = 8 * tid; i0 < kPackSeg + 8; i0 += 8 * 256) {
       int32_t v[8];
-      digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
-                      staged ? cf : nullptr, src0);
+      if (staged)
+        digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+      else
+        digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
 #pragma unroll
       for (int m = 0; m < 8; m++) raw[i0 + m] = v[m];
     }
@@ -287,8 +289,10 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     for (int m0 = 8 * tid; m0 < kPackSeg + 1; m0 += 8 * 256) {
       const int64_t jhi = top - (128 * rho0 + m0);  // j of m0; j of m0 + 7 is jhi - 7
       int32_t v[8];
-      digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
-                      staged ? cf : nullptr, src0);
+      if (staged)
+        digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+      else
+        digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const int64_t j = jhi - u;

@@ -22,6 +22,7 @@ def main(argv=None) -> int:
     ap.add_argument("--signed", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=20071229)
+    ap.add_argument("--square", action="store_true", help="g = f (the same buffer)")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import numpy as np
@@ -34,7 +35,9 @@ def main(argv=None) -> int:
     f = ks_inputs.random_poly(lf, args.bits, args.signed, args.seed)
     g = ks_inputs.random_poly(lg, args.bits, args.signed, args.seed + 1)
     tf = torch.from_numpy(f.view(np.int64)).cuda()
-    tg = torch.from_numpy(g.view(np.int64)).cuda()
+    tg = tf if args.square else torch.from_numpy(g.view(np.int64)).cuda()
+    if args.square:
+        lg = lf
     for _ in range(args.reps):
         h = ks.mul(tf, tg, args.bits, args.signed, args.variant, args.engine)
     ks.status_sync()
