@@ -8,7 +8,8 @@ Contents:
 
 * ``schoolbook.c`` -- the plain definition h_k = sum_{i+j=k} f_i g_j over exact
   multi-limb integers (Harvey, Sec. 3), multithreaded over k, plus the
-  (Z/pZ)[x] product of Sec. 4.  Loaded here through ctypes.
+  (Z/pZ)[x] product of Sec. 4 and the plain bivariate product in
+  (Z/pZ)[x, y] of Sec. 2.  Loaded here through ctypes.
 * ``pyref`` -- a pure-Python twin of the same definition for tiny sizes.
 * ``ks_steps`` -- a step model that runs each Kronecker-substitution variant
   (Sec. 3.1-3.4) on Python integers in any base, exposing the intermediates
@@ -54,6 +55,8 @@ def _load():
         lib.oracle_coeffs.restype = ci
         lib.oracle_mul_mod.argtypes = [u64p, u64p, i64, u64p, i64, ctypes.c_uint64, ci]
         lib.oracle_mul_mod.restype = ci
+        lib.oracle_mul_biv_mod.argtypes = [u64p, u64p, u64p, i64, i64, ctypes.c_uint64, ci]
+        lib.oracle_mul_biv_mod.restype = ci
         _lib = lib
     return _lib
 
@@ -123,3 +126,19 @@ def mul_mod(f: np.ndarray, g: np.ndarray, p: int, threads: int | None = None) ->
     if rc != 0:
         raise ValueError("oracle_mul_mod failed: %d" % rc)
     return h.reshape(-1, 1)
+
+
+def mul_biv_mod(f: np.ndarray, g: np.ndarray, p: int, threads: int | None = None) -> np.ndarray:
+    """The plain product in (Z/pZ)[x, y] (Sec. 2): f, g are (ly, lx) uint64 arrays
+    of residues, row i the coefficients of y^i; returns (2 ly - 1, 2 lx - 1)."""
+    f = np.ascontiguousarray(f, dtype=np.uint64)
+    g = np.ascontiguousarray(g, dtype=np.uint64)
+    if f.ndim != 2 or f.shape != g.shape:
+        raise ValueError("f and g must be (ly, lx) arrays of the same shape")
+    ly, lx = f.shape
+    h = np.zeros((2 * ly - 1, 2 * lx - 1), dtype=np.uint64)
+    rc = _load().oracle_mul_biv_mod(_ptr(h), _ptr(f), _ptr(g), lx, ly, p,
+                                    threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_mul_biv_mod failed: %d" % rc)
+    return h

@@ -13,7 +13,8 @@
  * as an exact integer, by the schoolbook double loop over multi-limb
  * integers, one coefficient at a time.  No blocking, no reordering, no
  * substitution.  The modular entry point follows the paper's application
- * (Sec. 4): h_k mod p for residues in [0, p).
+ * (Sec. 4): h_k mod p for residues in [0, p).  The bivariate entry point is
+ * the plain product in (Z/pZ)[x, y], the setting of Sec. 2.
  *
  * Encoding: coefficient i of f is fl = ceil(b/64) little-endian uint64 limbs;
  * signed values are two's complement sign-extended over the limbs.  Each
@@ -208,6 +209,70 @@ int oracle_mul_mod(uint64_t *h, const uint64_t *f, int64_t lf,
   for (int t = 1; t < nthreads; t++, started++)
     if (pthread_create(&th[t], NULL, mworker, &jobs[t]) != 0) { rc = -3; break; }
   if (rc == 0) mworker(&jobs[0]);
+  for (int t = 1; t < started; t++) pthread_join(th[t], NULL);
+  return rc;
+}
+
+/* ---- (Z/pZ)[x, y]: the plain bivariate product (Harvey, Sec. 2) ----
+ *
+ * f and g have ly rows of lx residues in [0, p): row i holds the coefficients
+ * of f_i(x), the coefficient of y^i.  h has 2 ly - 1 rows of 2 lx - 1:
+ *
+ *     h[k][m] = sum_{i + i' = k} sum_{j + j' = m} f[i][j] g[i'][j']  mod p,
+ *
+ * one term at a time, each reduced mod p through a 128-bit product.
+ * Multithreaded over the rows k of h. */
+
+typedef struct {
+  uint64_t *h;
+  const uint64_t *f, *g;
+  int64_t lx, ly;
+  uint64_t p;
+  int64_t begin, stride;
+} bjob_t;
+
+static void *bworker(void *arg) {
+  bjob_t *J = (bjob_t *)arg;
+  const int64_t hy = 2 * J->ly - 1, hx = 2 * J->lx - 1;
+  for (int64_t k = J->begin; k < hy; k += J->stride) {
+    for (int64_t m = 0; m < hx; m++) {
+      uint64_t acc = 0;
+      for (int64_t i = 0; i < J->ly; i++) {
+        const int64_t i2 = k - i;
+        if (i2 < 0 || i2 >= J->ly) continue;
+        for (int64_t j = 0; j < J->lx; j++) {
+          const int64_t j2 = m - j;
+          if (j2 < 0 || j2 >= J->lx) continue;
+          const uint64_t t =
+              (uint64_t)(((u128)J->f[i * J->lx + j] * J->g[i2 * J->lx + j2]) % J->p);
+          acc = (uint64_t)(((u128)acc + t) % J->p);
+        }
+      }
+      J->h[k * hx + m] = acc;
+    }
+  }
+  return NULL;
+}
+
+int oracle_mul_biv_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx, int64_t ly,
+                       uint64_t p, int nthreads) {
+  if (lx < 1 || ly < 1 || p < 2) return -1;
+  for (int64_t i = 0; i < lx * ly; i++)
+    if (f[i] >= p || g[i] >= p) return -1;
+  const int64_t hy = 2 * ly - 1;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if (hy < nthreads) nthreads = (int)hy;
+  pthread_t th[256];
+  bjob_t jobs[256];
+  for (int t = 0; t < nthreads; t++) {
+    bjob_t J = {h, f, g, lx, ly, p, t, nthreads};
+    jobs[t] = J;
+  }
+  int started = 1, rc = 0;
+  for (int t = 1; t < nthreads; t++, started++)
+    if (pthread_create(&th[t], NULL, bworker, &jobs[t]) != 0) { rc = -3; break; }
+  if (rc == 0) bworker(&jobs[0]);
   for (int t = 1; t < started; t++) pthread_join(th[t], NULL);
   return rc;
 }
