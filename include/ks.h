@@ -135,6 +135,25 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
                int64_t len_g, uint64_t p, int variant, ks_stream_t stream);
 
 /*
+ * Bivariate product in (Z/pZ)[x, y] (Sec. 2): f and g are device arrays of
+ * ly rows of lx residues in [0, p) (row i, entry j: the coefficient of
+ * x^j y^i); h receives 2 ly - 1 rows of 2 lx - 1 residues.  2 <= p < 2^63.
+ * The variant is the polynomial-ring substitution of the paper:
+ *   KS_1  y = x^N, N = 2 lx - 1, one product of length (ly - 1) N + lx (Sec. 2.1)
+ *   KS_2  y = +-x^N, N = lx, two products of length lx ly (Sec. 2.3; p odd)
+ *   KS_3  y = x^N and x^-N, N = lx, two products of length lx ly (Sec. 2.2)
+ *   KS_4  y = +-x^N, +-x^-N, N = ceil(lx / 2), four products of length
+ *         N (ly - 1) + lx (Sec. 2.4; p odd)
+ *   KS_AUTO  KS_2 for odd p, else KS_1.
+ * Each univariate product runs through ks_mul_mod (whose own substitution
+ * is chosen as for KS_AUTO).  Workspace is cached per (device, stream).
+ * KS_EINVAL for bad arguments (KS_2 / KS_4 with even p); KS_ERANGE beyond
+ * lx, ly <= 2^26 and lx ly <= 2^28.  Asynchronous on `stream`.
+ */
+int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx,
+                         int64_t ly, uint64_t p, int variant, ks_stream_t stream);
+
+/*
  * ks_mul_static -- ks_mul without any allocation.  (The paper has no
  * counterpart; this entry point is a deployment convenience.)
  *

@@ -47,6 +47,7 @@ _sig("ks_mul", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
 _sig("ks_mul_ex", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp, _i64, _vp)
 _sig("ks_mul_host", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp)
 _sig("ks_mul_mod", _ci, _vp, _vp, _i64, _vp, _i64, _u64, _ci, _vp)
+_sig("ks_mul_bivariate_mod", _ci, _vp, _vp, _vp, _i64, _i64, _u64, _ci, _vp)
 _sig("ks_mul_batch", _ci, ctypes.POINTER(KSProblem), _i64, _vp)
 _sig("ks_plan_create", _ci, ctypes.POINTER(_vp), ctypes.POINTER(KSProblem), _i64, _ci)
 _sig("ks_plan_execute", _ci, _vp, _vp)
@@ -185,6 +186,18 @@ def ks_mul_static(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
 def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
     _check(lib.ks_mul_mod(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], p, variant,
                           _stream_ptr(stream)), "ks_mul_mod")
+
+
+def ks_mul_bivariate_mod(h, f, g, p, variant=KS_AUTO, stream=None):
+    """(Z/pZ)[x, y] product (Sec. 2): f, g are (ly, lx) device tensors of residues
+    (row i, column j: the coefficient of x^j y^i); h is (2 ly - 1, 2 lx - 1)."""
+    if f.dim() != 2 or tuple(f.shape) != tuple(g.shape):
+        raise ValueError("f and g must be (ly, lx) tensors of the same shape")
+    ly, lx = f.shape
+    if tuple(h.shape) != (2 * ly - 1, 2 * lx - 1):
+        raise ValueError("h must be (2 ly - 1, 2 lx - 1)")
+    _check(lib.ks_mul_bivariate_mod(_dptr(h), _dptr(f), _dptr(g), lx, ly, p, variant,
+                                    _stream_ptr(stream)), "ks_mul_bivariate_mod")
 
 
 def _problems(problems):

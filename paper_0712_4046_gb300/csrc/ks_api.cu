@@ -699,6 +699,78 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
   return KS_OK;
 }
 
+int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx,
+                         int64_t ly, uint64_t p_mod, int variant, ks_stream_t stream) {
+  if (!h || !f || !g || lx < 1 || ly < 1 || p_mod < 2 || p_mod >= (1ull << 63)) return KS_EINVAL;
+  if (variant == KS_AUTO) variant = (p_mod & 1) ? KS_2 : KS_1;
+  if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
+  if ((variant == KS_2 || variant == KS_4) && (p_mod & 1) == 0) return KS_EINVAL;  // halving
+  if (lx > ((int64_t)1 << 26) || ly > ((int64_t)1 << 26) || lx * ly > ((int64_t)1 << 28))
+    return KS_ERANGE;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // evaluation spacing N, evaluation length LF, products (Sec. 2.1 - 2.4)
+  int64_t N, LF;
+  int nprod;
+  switch (variant) {
+    case KS_1: N = 2 * lx - 1; LF = (ly - 1) * N + lx; nprod = 1; break;
+    case KS_2:
+    case KS_3: N = lx; LF = lx * ly; nprod = 2; break;
+    default: N = (lx + 1) / 2; LF = N * (ly - 1) + lx; nprod = 4; break;
+  }
+  const int64_t LP = 2 * LF - 1;
+  const size_t ebytes = align256((size_t)LF * 8), pbytes = align256((size_t)LP * 8);
+  void *buf = nullptr;
+  int rc = cached_buffer(3, s, (size_t)(2 * nprod) * ebytes + (size_t)nprod * pbytes, &buf);
+  if (rc != KS_OK) return rc;
+  char *base = static_cast<char *>(buf);
+  uint64_t *E[8], *P[4];
+  for (int i = 0; i < 2 * nprod; i++) E[i] = reinterpret_cast<uint64_t *>(base + i * ebytes);
+  for (int q = 0; q < nprod; q++)
+    P[q] = reinterpret_cast<uint64_t *>(base + 2 * nprod * ebytes + q * pbytes);
+  // product q multiplies E[2q] (from f) by E[2q + 1] (from g): (reversed, alternating)
+  static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
+  static const int kAlt[5][4] = {{0}, {0}, {0, 1}, {0, 0}, {0, 1, 0, 1}};
+  BivEvalArgs ea{};
+  ea.n = 2 * nprod;
+  for (int q = 0; q < nprod; q++)
+    for (int side = 0; side < 2; side++)
+      ea.e[2 * q + side] = BivEval{side ? g : f, E[2 * q + side], lx, ly, N, LF,
+                                   kRev[variant][q], kAlt[variant][q], p_mod};
+  KS_CUDA(launch_biv_eval(ea, LF, s));
+  for (int q = 0; q < nprod; q++) {
+    rc = ks_mul_mod(P[q], E[2 * q], LF, E[2 * q + 1], LF, p_mod, KS_AUTO, stream);
+    if (rc != KS_OK) return rc;
+  }
+  switch (variant) {
+    case KS_1:
+      KS_CUDA(launch_biv_readoff(BivReadArgs{h, P[0], nullptr, lx, ly, N, p_mod}, s));
+      break;
+    case KS_2:
+      KS_CUDA(launch_biv_readoff(BivReadArgs{h, P[0], P[1], lx, ly, N, p_mod}, s));
+      break;
+    case KS_3:
+      KS_CUDA(launch_biv_recover(BivRecoverArgs{h, BivSeq{P[0], nullptr, 1, 0, LP},
+                                                BivSeq{P[1], nullptr, 1, 0, LP}, 2 * ly - 1, lx,
+                                                2 * lx - 1, lx, 0, 1, p_mod},
+                                 s));
+      break;
+    default:
+      // even rows from (P1 + P2)/2 and (P3 + P4)/2, odd rows from the halved
+      // differences shifted by N (Sec. 2.4), each at spacing 2N
+      KS_CUDA(launch_biv_recover(BivRecoverArgs{h, BivSeq{P[0], P[1], 1, 0, LP},
+                                                BivSeq{P[2], P[3], 1, 0, LP}, ly, 2 * N,
+                                                2 * lx - 1, lx, 0, 2, p_mod},
+                                 s));
+      if (ly > 1)
+        KS_CUDA(launch_biv_recover(BivRecoverArgs{h, BivSeq{P[0], P[1], -1, N, LP},
+                                                  BivSeq{P[2], P[3], -1, N, LP}, ly - 1, 2 * N,
+                                                  2 * lx - 1, lx, 1, 2, p_mod},
+                                   s));
+      break;
+  }
+  return KS_OK;
+}
+
 int ks_mul_batch(const ks_problem *probs, int64_t n, ks_stream_t stream) {
   if (n < 0 || (n > 0 && probs == nullptr)) return KS_EINVAL;
   if (n == 0) return KS_OK;

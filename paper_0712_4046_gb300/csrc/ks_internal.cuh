@@ -345,6 +345,40 @@ cudaError_t launch_signed_prefix_batch(const PrefArgs *pa, const int64_t *pref_p
 cudaError_t launch_signed_apply_batch(const FixArgs *fa, const int64_t *fix_prefix, int n,
                                       int64_t fix_blocks, cudaStream_t s);
 
+// (Z/pZ)[x, y] by the substitutions of Sec. 2 (ks_biv.cu).
+constexpr int kMaxBivEvals = 8;
+struct BivEval {  // one evaluation of f or g at +-x^N or +-x^-N
+  const uint64_t *f;
+  uint64_t *out;
+  int64_t lx, ly, N, len;
+  int reversed, alternate;
+  uint64_t p;
+};
+struct BivEvalArgs {
+  BivEval e[kMaxBivEvals];
+  int n;
+};
+struct BivReadArgs {  // KS_1 / KS_2 read-off of the rows of h
+  uint64_t *h;
+  const uint64_t *P1, *P2;
+  int64_t lx, ly, N;
+  uint64_t p;
+};
+struct BivSeq {  // P1, or (P1 + sign P2) / 2, read from index shift on
+  const uint64_t *P1, *P2;
+  int sign;
+  int64_t shift, len;
+};
+struct BivRecoverArgs {  // KS_3 / KS_4 reciprocal recovery of n blocks
+  uint64_t *h;
+  BivSeq A, B;
+  int64_t n, M, ell, lx, row0, rstep;
+  uint64_t p;
+};
+cudaError_t launch_biv_eval(const BivEvalArgs &a, int64_t maxlen, cudaStream_t s);
+cudaError_t launch_biv_readoff(const BivReadArgs &a, cudaStream_t s);
+cudaError_t launch_biv_recover(const BivRecoverArgs &a, cudaStream_t s);
+
 // (Z/pZ)[x]: out_k = h'_k mod p.
 cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh,
                               uint64_t p, cudaStream_t s);
