@@ -311,6 +311,8 @@ def main_ours(args):
         batched = run_batched(ks, dev, stream, flush, args.steps, args.warmup, world)
         # ---- HBM-bound phases (pack, normalize, unpack) where the arrays exceed L2
         hbm_phases = run_hbm_phases(ks, dev, stream, flush, hbm_gbs, peak_kind)
+        # ---- the polynomial-ring variants of Sec. 2 on one (Z/pZ)[x, y] product
+        bivariate = run_bivariate(ks, dev, stream, flush, args.steps, args.warmup)
     clocks = clk.summary()
 
     # ---- e2e through the host-buffer entry point (pinned buffers)
@@ -388,9 +390,49 @@ def main_ours(args):
         "cpu_baseline": cpu,
         "batched": batched,
         "hbm_phases": hbm_phases,
+        "bivariate": bivariate,
     }
     print(json.dumps(line))
     return 0
+
+
+BIV_WORKLOAD = {"workload": "biv_mod_p61_256x256", "lx": 256, "ly": 256, "p": (1 << 61) - 1,
+                "seed_f": 61, "seed_g": 62}
+
+
+def run_bivariate(ks, dev, stream, flush, steps, warmup):
+    """One product in (Z/pZ)[x, y] (l_x = l_y = 256, p = 2^61 - 1) by each of
+    the four substitutions of Sec. 2, CUDA events on the bench stream, L2
+    flushed before each product."""
+    import torch
+    w = BIV_WORKLOAD
+    lx, ly, p = w["lx"], w["ly"], w["p"]
+    f = ks_inputs.random_residues(lx * ly, p, w["seed_f"]).reshape(ly, lx)
+    g = ks_inputs.random_residues(lx * ly, p, w["seed_g"]).reshape(ly, lx)
+    tf = torch.from_numpy(f.view(np.int64)).to(dev)
+    tg = torch.from_numpy(g.view(np.int64)).to(dev)
+    h = torch.empty((2 * ly - 1, 2 * lx - 1), dtype=torch.int64, device=dev)
+    out = {"config": dict(w, l2="flushed before each product (256 MiB write)")}
+    ref = None
+    for label, variant in (("KS1", 1), ("KS2", 2), ("KS3", 3), ("KS4", 4)):
+        for _ in range(max(1, warmup)):
+            ks.ks_mul_bivariate_mod(h, tf, tg, p, variant, stream)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            ks.ks_mul_bivariate_mod(h, tf, tg, p, variant, stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ks.status_sync(stream)
+        ms = sum(a.elapsed_time(z) for a, z in evs) / steps
+        cur = h.cpu()
+        same = True if ref is None else bool(torch.equal(cur, ref))
+        ref = cur if ref is None else ref
+        out[label] = {"ms": ms, "products_per_s": 1000.0 / ms, "same_as_KS1": same}
+    return out
 
 
 HBM_WORKLOAD = {"workload": "zx_product_2pow20_u256", "len_f": 1 << 20, "len_g": 1 << 20,
