@@ -292,8 +292,9 @@ struct RecoverArgs {
   uint64_t *h;
   int ol;
   int *status;
-  int64_t rblocks[2];  // M <= 63: CTAs of 32 chains per run
+  int64_t rblocks[2];  // M <= 63: CTAs of cpc chains per run
   int smem;            // M <= 63: staged digit words of one CTA (bytes)
+  int cpc;             // M <= 63: chains per CTA (a power of two, 8 .. 32)
 };
 int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
                       int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,

@@ -892,21 +892,22 @@ __device__ __forceinline__ uint64_t sbits64(const uint32_t *w, int64_t nw, int64
   return sh ? ((lo >> sh) | (w2 << (64 - sh))) : lo;
 }
 
+// the most chains per CTA for this chain length (2048 / chain, at most 32)
 __host__ __device__ __forceinline__ int recover_cpc(int64_t chain) {
   int64_t c = 2048 / chain;
   return (int)(c < 1 ? 1 : (c > kRCmax ? kRCmax : c));
 }
 // staged words of one digit string (multiple of four)
-__host__ __device__ __forceinline__ int64_t staged_words(int64_t chain, int M) {
-  return (((recover_cpc(chain) * chain + 2) * (int64_t)M + 31) / 32 + 12) & ~(int64_t)3;
+__host__ __device__ __forceinline__ int64_t staged_words(int64_t chain, int M, int cpc) {
+  return (((cpc * chain + 2) * (int64_t)M + 31) / 32 + 12) & ~(int64_t)3;
 }
 // digits of one string, [step t in 0..chain][lane]: lanes read consecutive words
-__host__ __device__ __forceinline__ int64_t staged_digits(int64_t chain) {
-  return (chain + 1) * recover_cpc(chain);
+__host__ __device__ __forceinline__ int64_t staged_digits(int64_t chain, int cpc) {
+  return (chain + 1) * cpc;
 }
-__host__ __device__ __forceinline__ int64_t staged_bytes(int64_t chain, int M) {
-  return 2 * staged_words(chain, M) * 4 + 2 * staged_digits(chain) * 8 +
-         recover_cpc(chain) * chain * 2 * 8;
+__host__ __device__ __forceinline__ int64_t staged_bytes(int64_t chain, int M, int cpc) {
+  return 2 * staged_words(chain, M, cpc) * 4 + 2 * staged_digits(chain, cpc) * 8 +
+         cpc * chain * 2 * 8;
 }
 
 template <class Src>
@@ -925,7 +926,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
   const int M = a.M, ol = a.ol;
   const uint64_t mask = (1ull << M) - 1ull;
   const int64_t n = R.n, chain = a.chain, nwords = a.nwords;
-  const int cpc = recover_cpc(chain);
+  const int cpc = a.cpc;
   const int tid = threadIdx.x;
   const int64_t c0 = local * cpc;
   const int64_t c1 = c0 + cpc < R.nchains ? c0 + cpc : R.nchains;
@@ -937,7 +938,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
   const int64_t wb0 = ((R.off_r + (n - jhi) * (int64_t)M) >> 5) & ~(int64_t)3;
   const int64_t nw = ((((R.off_r + (n - j0 + 1) * (int64_t)M) >> 5) + 3 - wb0) + 3) &
                      ~(int64_t)3;
-  const int64_t capw = staged_words(chain, M), capd = staged_digits(chain);
+  const int64_t capw = staged_words(chain, M, cpc), capd = staged_digits(chain, cpc);
   if (nu > capw || nw > capw || ub0 < 0 || wb0 < 0 || (chain & (chain - 1)) != 0 || ol > 2) {
     if (tid == 0) atomicExch(status, 3);  // not for a plan from make_recover_args
     return;
@@ -1192,13 +1193,17 @@ int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, in
   a.status = status;
   if ((M + 31) / 32 > kMaxDigitWordsM) return -1;
   if (M <= 63) {  // staged: CTAs of cpc chains that do not straddle runs
-    const int cpc = recover_cpc(chain);
+    // fewer chains per CTA (down to 8) until there are two CTAs per SM: the
+    // staging, digit extraction and output of a CTA then go faster
+    int cpc = recover_cpc(chain);
+    while (cpc > 8 && (total + cpc - 1) / cpc < 2 * 152) cpc >>= 1;
+    a.cpc = cpc;
     blocks = 0;
     for (int r = 0; r < nruns; r++) {
       a.rblocks[r] = (runs[r].nchains + cpc - 1) / cpc;
       blocks += a.rblocks[r];
     }
-    const int64_t bytes = staged_bytes(chain, M);
+    const int64_t bytes = staged_bytes(chain, M, cpc);
     if (bytes > 200 * 1024 || ol > 2) return -1;
     a.smem = (int)bytes;
     return 0;
