@@ -81,6 +81,7 @@ struct PackArgs {
   int nops;
   int N, b, d, in_limbs, flip;
   uint64_t ninv = 0;  // floor(2^64 / N) + 1: floor(x / N) = umulhi(x, ninv), x < 2^31
+  int fields = 0;     // > 0: coefficient fields per CTA of the field-centric path (N >= b)
 };
 // Fills ninv and the per-operand narrow flags (after the operands are set).
 void pack_finish(PackArgs &a);

@@ -25,32 +25,90 @@ namespace {
 constexpr int kPackThreads = 256;
 constexpr int kRun = 8;                             // digits per thread
 constexpr int kCtaDigits = kPackThreads * kRun;     // digits per CTA
+constexpr int kStageWords = 3072;                   // coefficient words staged per CTA (24 KB)
+constexpr int kFieldDigits = 6144;                  // digits of a field-centric CTA (24 KB)
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 __host__ __device__ __forceinline__ int64_t ctas_for(int64_t ndig) {
   return (ndig + kCtaDigits - 1) / kCtaDigits;
 }
+__host__ __device__ __forceinline__ int64_t op_ctas(const PackArgs &a, const PackOp &op) {
+  return a.fields > 0 ? (op.L + a.fields - 1) / a.fields : ctas_for(op.ndig);
+}
 }  // namespace
 
-// One CTA makes 2048 consecutive digits of one operand: it copies the
-// coefficients they read into shared memory (when they fit), each thread
-// makes a run of eight (digit_run), and the digits are stored coalesced
-// through shared memory.
-constexpr int kStageWords = 3072;  // coefficient words staged per CTA (24 KB)
-
+// Two ways to a CTA's digits, chosen per plan (block-uniform):
+//
+//  * digit-centric (any N): a CTA makes 2048 consecutive digits; it copies the
+//    coefficients they read into shared memory (when they fit), each thread
+//    makes a run of eight (digit_run), and the digits are stored coalesced
+//    through shared memory.
+//  * field-centric (N >= b, the fields do not overlap): a CTA takes `fields`
+//    consecutive coefficient fields and owns the digits from the first one's
+//    start to the next CTA's; it stages those coefficients (and the earlier
+//    ones whose tails reach its first digit), each thread adds the
+//    16-bit pieces of one field into shared digit accumulators (+- by the sign
+//    of the evaluation point), and the CTA stores its digit range coalesced.
+//    Digits between fields cost nothing but their store.
 template <class Src>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
-  __shared__ int32_t st[kCtaDigits + kCtaDigits / 8];
-  __shared__ uint64_t cf[kStageWords];
+  __shared__ __align__(16) uint64_t raw[kStageWords + kFieldDigits / 2];
   int64_t local;
   const PackArgs &a = src.locate(blockIdx.x, local);
   int o = 0;
-  while (o < a.nops && local >= ctas_for(a.op[o].ndig)) {
-    local -= ctas_for(a.op[o].ndig);
+  while (o < a.nops && local >= op_ctas(a, a.op[o])) {
+    local -= op_ctas(a, a.op[o]);
     o++;
   }
   if (o >= a.nops) return;
   const PackOp &op = a.op[o];
   const int tid = threadIdx.x;
+  uint64_t *cf = raw;
+  if (a.fields > 0) {
+    int32_t *sd = reinterpret_cast<int32_t *>(raw + kStageWords);
+    const int64_t N = a.N;
+    const int64_t c0 = local * a.fields;
+    const int64_t c1 = c0 + a.fields < op.L ? c0 + a.fields : op.L;  // one past the last field
+    const int64_t D0 = (c0 * N) >> 4;
+    const int64_t D1 = c1 < op.L ? (c1 * N) >> 4 : op.ndig;
+    const int nd = (int)(D1 - D0);
+    for (int i = tid; i < nd; i += kPackThreads) sd[i] = 0;
+    // every field that meets digit D0: the earlier ones only with their tails
+    // (more than one when N < 16)
+    int64_t src0;
+    const int64_t e0 = 16 * D0 - a.b;
+    const int64_t t_lo = e0 < 0 ? 0 : e0 / N + 1;
+    const bool staged = stage_coeffs(op, t_lo, c1 - 1, a.in_limbs, cf, kStageWords, src0);
+    __syncthreads();
+    const int b = a.b, il = a.in_limbs, flip = a.flip;
+    const int64_t t = t_lo + tid;  // this thread's field
+    if (t < c1) {
+      const int64_t pos = t * N;
+      const int64_t src = op.reversed ? (op.L - 1 - t) : t;
+      const uint64_t *c = staged ? cf + (src - src0) * il : op.poly + src * il;
+      const bool neg = op.sigma < 0 && (t & 1);
+      int64_t d = pos >> 4;
+      int64_t dend = (pos + b - 1) >> 4;
+      if (d < D0) d = D0;
+      if (dend > D1 - 1) dend = D1 - 1;
+      for (; d <= dend; d++) {
+        const int x = (int)(16 * d - pos);  // the coefficient's bit at the digit's bit 0
+        uint32_t piece;
+        if (x >= 0) {
+          const int li = x >> 6, sh = x & 63;
+          const uint64_t w0 = coeff_limb(c, li, il, b, flip);
+          const uint64_t w1 = sh + 16 > 64 ? coeff_limb(c, li + 1, il, b, flip) : 0ull;
+          piece = (uint32_t)(((w0 >> sh) | (sh ? w1 << (64 - sh) : 0ull)) & 0xFFFFull);
+        } else {
+          piece = (uint32_t)((coeff_limb(c, 0, il, b, flip) << (-x)) & 0xFFFFull);
+        }
+        if (piece) atomicAdd(&sd[d - D0], neg ? -(int32_t)piece : (int32_t)piece);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nd; i += kPackThreads) op.out[D0 + i] = sd[i];
+    return;
+  }
+  int32_t *st = reinterpret_cast<int32_t *>(raw + kStageWords);
   const int64_t jc = local * kCtaDigits;
   // the coefficients this CTA's digits read, staged once (coalesced)
   int64_t t_lo, t_hi, src0;
@@ -83,6 +141,19 @@ void squaring_pack(PackArgs &a, Product *prods, int nprod) {
 
 void pack_finish(PackArgs &a) {
   a.ninv = a.N > 1 ? (uint64_t)(((unsigned __int128)1 << 64) / (unsigned)a.N) + 1 : 0;
+  // field-centric CTAs when the fields do not overlap: as many fields as keep
+  // the CTA's digits (about fields N / 16 + 2) and its staged coefficients
+  // (fields + 1 of them) in shared memory, at most one per thread but one
+  a.fields = 0;
+  if (a.d == 16 && a.N >= a.b) {
+    // fields before a CTA's first that can still reach its first digit
+    const int64_t extra = (16 + a.b - 1) / a.N + 1;
+    int64_t c = (int64_t)(kFieldDigits - 2) * 16 / a.N;
+    const int64_t cw = kStageWords / a.in_limbs - extra;
+    if (cw < c) c = cw;
+    if (c > kPackThreads - extra) c = kPackThreads - extra;
+    if (c >= 16) a.fields = (int)c;
+  }
   for (int o = 0; o < a.nops; o++) {
     PackOp &op = a.op[o];
     // largest bit position a digit run or a field reaches (with a margin for
@@ -96,7 +167,7 @@ void pack_finish(PackArgs &a) {
 
 int64_t pack_blocks(const PackArgs &a) {
   int64_t total = 0;
-  for (int o = 0; o < a.nops; o++) total += ctas_for(a.op[o].ndig);
+  for (int o = 0; o < a.nops; o++) total += op_ctas(a, a.op[o]);
   return total;
 }
 
