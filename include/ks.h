@@ -135,6 +135,21 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
                int64_t len_g, uint64_t p, int variant, ks_stream_t stream);
 
 /*
+ * h = f * g for coefficients of different sizes: f has bits_f-bit
+ * coefficients (in_limbs ceil(bits_f / 64)), g has bits_g-bit ones (signed
+ * or unsigned as for ks_mul, both the same).  The narrower operand is taken
+ * as a B-bit one, B = max(bits_f, bits_g) (re-encoded with ceil(B / 64)
+ * limbs, sign- or zero-extended, when its limb count differs), and the
+ * product is ks_mul's with coeff_bits = B: exact, with the evaluation
+ * exponents of B-bit operands (not the smaller ones b_f + b_g allows).  h has
+ * ks_out_limbs(len_f, len_g, B, is_signed) limbs per coefficient.  The
+ * re-encoded copy lives in a cache kept per (device, stream).  Asynchronous.
+ */
+int ks_mul_bits(uint64_t *h, const uint64_t *f, int64_t len_f, int bits_f,
+                const uint64_t *g, int64_t len_g, int bits_g, int is_signed,
+                int variant, ks_stream_t stream);
+
+/*
  * Bivariate product in (Z/pZ)[x, y] (Sec. 2): f and g are device arrays of
  * ly rows of lx residues in [0, p) (row i, entry j: the coefficient of
  * x^j y^i); h receives 2 ly - 1 rows of 2 lx - 1 residues.  2 <= p < 2^63.

@@ -48,6 +48,7 @@ _sig("ks_mul_ex", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp, _i64,
 _sig("ks_mul_host", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _ci, _vp)
 _sig("ks_mul_mod", _ci, _vp, _vp, _i64, _vp, _i64, _u64, _ci, _vp)
 _sig("ks_mul_bivariate_mod", _ci, _vp, _vp, _vp, _i64, _i64, _u64, _ci, _vp)
+_sig("ks_mul_bits", _ci, _vp, _vp, _i64, _ci, _vp, _i64, _ci, _ci, _ci, _vp)
 _sig("ks_mul_batch", _ci, ctypes.POINTER(KSProblem), _i64, _vp)
 _sig("ks_plan_create", _ci, ctypes.POINTER(_vp), ctypes.POINTER(KSProblem), _i64, _ci)
 _sig("ks_plan_execute", _ci, _vp, _vp)
@@ -186,6 +187,13 @@ def ks_mul_static(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
 def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
     _check(lib.ks_mul_mod(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], p, variant,
                           _stream_ptr(stream)), "ks_mul_mod")
+
+
+def ks_mul_bits(h, f, bits_f, g, bits_g, is_signed, variant=KS_AUTO, stream=None):
+    """h = f g with bits_f-bit coefficients in f and bits_g-bit ones in g (device
+    tensors of shape (L, ceil(bits / 64))); h has out_limbs(.., max(bits), ..) limbs."""
+    _check(lib.ks_mul_bits(_dptr(h), _dptr(f), f.shape[0], bits_f, _dptr(g), g.shape[0], bits_g,
+                           int(is_signed), variant, _stream_ptr(stream)), "ks_mul_bits")
 
 
 def ks_mul_bivariate_mod(h, f, g, p, variant=KS_AUTO, stream=None):

@@ -699,6 +699,27 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
   return KS_OK;
 }
 
+int ks_mul_bits(uint64_t *h, const uint64_t *f, int64_t len_f, int bits_f, const uint64_t *g,
+                int64_t len_g, int bits_g, int is_signed, int variant, ks_stream_t stream) {
+  if (bits_f < 1 || bits_g < 1 || bits_f > KS_MAX_COEFF_BITS || bits_g > KS_MAX_COEFF_BITS ||
+      len_f < 1 || len_g < 1 || !h || !f || !g)
+    return KS_EINVAL;
+  const int B = bits_f > bits_g ? bits_f : bits_g;
+  const int il = (B + 63) / 64, ilf = (bits_f + 63) / 64, ilg = (bits_g + 63) / 64;
+  if (ilf == il && ilg == il)  // same limb layout: a bits_g-bit value is a B-bit value
+    return ks_mul(h, f, len_f, g, len_g, B, is_signed, variant, stream);
+  // re-encode the narrower operand with il limbs
+  const bool wf = ilf < il;
+  const int64_t len = wf ? len_f : len_g;
+  void *buf = nullptr;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = cached_buffer(4, s, (size_t)len * il * 8, &buf);
+  if (rc != KS_OK) return rc;
+  uint64_t *w = static_cast<uint64_t *>(buf);
+  KS_CUDA(launch_widen(w, wf ? f : g, len, wf ? ilf : ilg, il, is_signed, s));
+  return ks_mul(h, wf ? w : f, len_f, wf ? g : w, len_g, B, is_signed, variant, stream);
+}
+
 int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx,
                          int64_t ly, uint64_t p_mod, int variant, ks_stream_t stream) {
   if (!h || !f || !g || lx < 1 || ly < 1 || p_mod < 2 || p_mod >= (1ull << 63)) return KS_EINVAL;

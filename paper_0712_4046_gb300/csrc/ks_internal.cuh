@@ -86,6 +86,10 @@ struct PackArgs {
 // Fills ninv and the per-operand narrow flags (after the operands are set).
 void pack_finish(PackArgs &a);
 
+// Coefficients of il limbs re-encoded with ol >= il limbs (sign- or zero-extended).
+cudaError_t launch_widen(uint64_t *out, const uint64_t *in, int64_t len, int il, int ol,
+                         int is_signed, cudaStream_t s);
+
 struct Product;
 // Squaring: keeps only the f-side operand of each sub-product (2 q) and makes
 // every sub-product read it on both sides.

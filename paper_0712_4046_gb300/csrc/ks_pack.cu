@@ -131,6 +131,34 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
   }
 }
 
+// out (len x ol limbs) = in (len x il limbs, il <= ol), each coefficient
+// extended with its sign (signed) or with zeros: the same integers, wider.
+__global__ void __launch_bounds__(256) widen_kernel(uint64_t *out, const uint64_t *in, int64_t len,
+                                                    int il, int ol, int is_signed) {
+  const int64_t total = len * ol;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / ol;
+    const int l = (int)(idx - i * ol);
+    uint64_t v;
+    if (l < il)
+      v = in[i * il + l];
+    else
+      v = (is_signed && (in[i * il + il - 1] >> 63)) ? ~0ull : 0ull;
+    out[idx] = v;
+  }
+}
+
+cudaError_t launch_widen(uint64_t *out, const uint64_t *in, int64_t len, int il, int ol,
+                         int is_signed, cudaStream_t s) {
+  int64_t blocks = (len * ol + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  widen_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, in, len, il, ol, is_signed);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 void squaring_pack(PackArgs &a, Product *prods, int nprod) {
   for (int q = 0; q < nprod; q++) {
     a.op[q] = a.op[2 * q];
