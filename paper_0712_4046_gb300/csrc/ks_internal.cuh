@@ -434,39 +434,6 @@ __device__ __forceinline__ uint32_t coeff_slice(const uint64_t *c, int in_limbs,
   return (uint32_t)(v & ((1ull << len) - 1ull));
 }
 
-// Signed digit j (bits [jd, jd + d)) of one evaluation: the sum over the
-// coefficients t whose field [tN, tN + b) meets the window of +- (their bits
-// inside it), with the sign -1 for odd t at the point -2^N (Sec. 3.3, 3.4).
-__device__ __forceinline__ int32_t digit_at(const PackOp &op, int64_t j, int64_t N, int b, int d,
-                                            int in_limbs, int flip) {
-  const int64_t lo = j * d;
-  int64_t t_lo = lo - b < 0 ? 0 : (lo - b) / N + 1;
-  int64_t t_hi = (lo + d - 1) / N;
-  if (t_hi > op.L - 1) t_hi = op.L - 1;
-  int32_t val = 0;
-  for (int64_t t = t_lo; t <= t_hi; t++) {
-    const int64_t pos = t * N;
-    const int64_t src = op.reversed ? (op.L - 1 - t) : t;
-    const uint64_t *c = op.poly + src * in_limbs;
-    uint32_t piece;
-    if (pos >= lo) {
-      const int sh = (int)(pos - lo);
-      piece = coeff_slice(c, in_limbs, b, flip, 0, d - sh) << sh;
-    } else {
-      piece = coeff_slice(c, in_limbs, b, flip, (int)(lo - pos), d);
-    }
-    if (op.sigma < 0 && (t & 1))
-      val -= (int32_t)piece;
-    else
-      val += (int32_t)piece;
-  }
-  return val;
-}
-
-// Digits j0 .. j0 + K - 1 of one evaluation (the same values as digit_at):
-// one pair of divisions finds the coefficient fields that meet the K-digit
-// window, then each field adds its bits to the digits it overlaps
-// (compile-time digit width D, so the per-digit tests are register-only).
 // floor(x / N) for 0 <= x < 2^31 from m = floor(2^64 / N) + 1: with
 // m = (2^64 + delta) / N, 1 <= delta <= N, x m / 2^64 exceeds x / N by less
 // than 2^-33 < 1 / N, so the high word is the exact quotient (N = 1: x).
@@ -545,8 +512,10 @@ __device__ __forceinline__ void coeff_bits128(const uint64_t *c, int x, int in_l
   hi = sh ? (w1 >> sh) | (w2 << (64 - sh)) : w1;
 }
 
-// Digits j0 .. j0 + K - 1 of one evaluation (the same values as digit_at):
-// one pair of divisions finds the coefficient fields that meet the K-digit
+// Digits j0 .. j0 + K - 1 of one evaluation.  Digit j (bits [jd, jd + d)) is
+// the sum over the coefficients t whose field [tN, tN + b) meets the window of
+// +- their bits inside it, with the sign -1 for odd t at the point -2^N
+// (Sec. 3.3, 3.4).  One pair of divisions finds the coefficient fields that meet the K-digit
 // window [lo, lo + K D); each field contributes the window's bits of its
 // coefficient placed at its offset (one 128-bit extraction), which split
 // into the K digits by compile-time shifts.

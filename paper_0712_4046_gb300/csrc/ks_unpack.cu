@@ -762,73 +762,6 @@ __device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, 
   return r < a.nruns;
 }
 
-// M <= 63
-template <class Src>
-__global__ void __launch_bounds__(128) recover_kernel1(Src src) {
-  int64_t local;
-  const RecoverArgs &a = src.locate(blockIdx.x, local);
-  uint64_t *h = a.h;
-  const int ol = a.ol;
-  int *status = a.status;
-  int64_t gid = local * 128 + threadIdx.x;
-  int r;
-  if (!chain_index(a, gid, r)) return;
-  const RecoverRun &R = a.run[r];
-  const int M = a.M;
-  const uint64_t mask = (1ull << M) - 1ull;
-  const int64_t n = R.n;
-  const int64_t s = gid * a.chain;
-  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
-  uint64_t a_prev, a_cur, delta;
-  if (s == 0) {
-    a_prev = 0;
-    a_cur = load_d1(R.Vf, a.nwords, R.off_f, M);
-    delta = 0;
-  } else {
-    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
-    a_prev = load_d1(sd, a.seed_words, 0, M);
-    const uint64_t b_prev = load_d1(sd, a.seed_words, M, M);
-    a_cur = load_d1(sd + a.seed_words, a.seed_words, 0, M);
-    const uint64_t us = load_d1(R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
-    const uint64_t dprev = (us - b_prev - a_cur) & mask;
-    if (dprev > 1) atomicExch(status, 2);
-    delta = (b_prev + a_cur + dprev - us) >> M;
-  }
-  uint64_t w_cur = load_d1(R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
-  constexpr int kAhead = 8;  // digits are loaded kAhead steps ahead of their use
-  for (int64_t j0 = s; j0 < e; j0 += kAhead) {
-    uint64_t ub[kAhead], wb[kAhead];
-#pragma unroll
-    for (int q = 0; q < kAhead; q++) {
-      const int64_t j = j0 + q;
-      ub[q] = load_d1(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
-      wb[q] = load_d1(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
-    }
-#pragma unroll
-    for (int q = 0; q < kAhead; q++) {
-      const int64_t j = j0 + q;
-      if (j >= e) break;
-      uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
-      if (j <= n - 2) {
-        const uint64_t w_next = wb[q];
-        const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
-        const uint64_t beta = (w_cur - a_prev - eps) & mask;
-        const uint64_t u_next = ub[q];
-        const uint64_t a_next = (u_next - beta - delta) & mask;
-        const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
-        if (dnext > 1) atomicExch(status, 2);
-        write_h1(out, ol, a_cur, beta, M);
-        a_prev = a_cur;
-        a_cur = a_next;
-        delta = dnext;
-        w_cur = w_next;
-      } else {
-        write_h1(out, ol, a_cur, (w_cur - a_prev) & mask, M);
-      }
-    }
-  }
-}
-
 // ---- bulk copies into shared memory (one thread issues, all wait, bounded)
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
