@@ -1165,15 +1165,18 @@ static cudaError_t staged_attr(int smem) {
 }
 
 template <class Src>
-static void launch_recover_class(int cls, int64_t blocks, const Src &src, int smem,
-                                 cudaStream_t s) {
+static cudaError_t launch_recover_class(int cls, int64_t blocks, const Src &src, int smem,
+                                        cudaStream_t s) {
   if (cls == 1) {
-    if (staged_attr<Src>(smem) == cudaSuccess)
-      recover_staged1<Src><<<(unsigned)blocks, kRT, smem, s>>>(src);
+    const cudaError_t e = staged_attr<Src>(smem);
+    if (e != cudaSuccess) return e;
+    recover_staged1<Src><<<(unsigned)blocks, kRT, smem, s>>>(src);
   } else if (cls == 2)
     recover_kernel2<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
   else
     recover_wide<Src><<<(unsigned)blocks, 64, 0, s>>>(src);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
@@ -1184,17 +1187,13 @@ cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nrun
   if (make_recover_args(h, ol, runs, nruns, nwords, M, chain, seed_words, status, a, blocks) != 0)
     return cudaErrorInvalidValue;
   if (blocks == 0) return cudaSuccess;
-  launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, a.smem, s);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, a.smem, s);
 }
 
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
                                  int64_t blocks, int smem, cudaStream_t s) {
   if (n == 0 || blocks == 0) return cudaSuccess;
-  launch_recover_class(cls, blocks, Many<RecoverArgs>{d, prefix, n}, smem, s);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_recover_class(cls, blocks, Many<RecoverArgs>{d, prefix, n}, smem, s);
 }
 
 // ------------------------------------------------------------------ mod p

@@ -141,3 +141,18 @@ def test_config5b_64_products_mod_mersenne61(ks):
                 want = sum(fi[t] * gi[k - t] for t in range(lo, hi + 1)) % p
                 assert got[k] == want, (i, k)
     ks.status_sync()
+
+
+@pytest.mark.parametrize("variant,L,b,signed,engine", [
+    (3, 300000, 8, False, 2),   # chains of 256: one CTA per seed, 64-bit coefficients
+    (4, 300000, 20, True, 2),   # chains of 128 in both runs of Sec. 3.4
+    (4, 524288, 48, False, 3),  # tensor-core products, chains of 128
+    (3, 524288, 100, True, 2),  # multi-word seeds, chains of 256
+])
+def test_long_reconstruction_chains(ks, variant, L, b, signed, engine):
+    # runs of more than 2^18 coefficients take longer chains, whose seeds no
+    # longer fit the blocked seed kernel's window
+    f, g = random_case(L, L, b, signed, L + 3 * b + variant)
+    got = gpu_mul(ks, f, g, b, signed, variant, engine)
+    fingerprint_check(got, f, g, signed, variant + b, nchecks=2)
+    sampled_check(got, f, g, b, signed, 8, L + variant)
