@@ -156,19 +156,24 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
+// one MMA (kind::f16, fp32 accumulate), issued by lane 0 of a warp that executes the
+// call in uniform control flow
+__device__ __forceinline__ void mma_f16_lane0(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate, uint32_t lane) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\t"
+      "{\n\t.reg .pred p, e;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "setp.eq.u32 e, %5, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(lane)
       : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+__device__ __forceinline__ void mma_commit_lane0(uint64_t *bar, uint32_t lane) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
+      "{\n\t.reg .pred e;\n\t"
+      "setp.eq.u32 e, %1, 0;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+          smem_u32(bar)), "r"(lane)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -534,76 +539,82 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: one chunk = clearing MMA + trimmed MMAs
-    if (lane == 0) {
-      int stage = 0, acc = 0, islot = 0;
-      uint32_t phase = 0, aphase = 0, iphase = 0;
-      bool aborted = false, issued = false;
-      const uint64_t zdesc = sdesc(smem_u32(smem + kStages * kStage), 128u, 128u);
-      for (;;) {
-        if (!mbar_wait(&bar_ifull[islot], iphase) || *abort_v) {
+    // ---------------- MMA issuer: one chunk = clearing MMA + trimmed MMAs.  The
+    // whole warp walks the items and chunks, so the descriptors are computed in
+    // warp-uniform control flow; lane 0 alone issues each MMA and commit (the
+    // predicate sits inside the instruction's asm block).
+    int stage = 0, acc = 0, islot = 0;
+    uint32_t phase = 0, aphase = 0, iphase = 0;
+    bool aborted = false, issued = false;
+    const uint32_t lane_u = (uint32_t)lane;
+    const uint64_t zdesc = sdesc(smem_u32(smem + kStages * kStage), 128u, 128u);
+    for (;;) {
+      const bool iok = mbar_wait(&bar_ifull[islot], iphase);
+      if (__any_sync(0xffffffffu, !iok || *abort_v)) {
+        aborted = true;
+        break;
+      }
+      TcSlot it;
+      slot_load(it, &slots[islot]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_iempty[islot]);
+      if (++islot == kItemSlots) {
+        islot = 0;
+        iphase ^= 1;
+      }
+      if (it.done) break;
+      for (int c = it.c0; c < it.c1; c++) {
+        const bool ok = mbar_wait(&bar_full[stage], phase) && mbar_wait(&bar_tempty[acc], aphase ^ 1);
+        if (__any_sync(0xffffffffu, !ok || *abort_v)) {
           aborted = true;
           break;
         }
-        TcSlot it;
-        slot_load(it, &slots[islot]);
-        mbar_arrive(&bar_iempty[islot]);
-        if (++islot == kItemSlots) {
-          islot = 0;
-          iphase ^= 1;
-        }
-        if (it.done) break;
-        for (int c = it.c0; c < it.c1; c++) {
-          if (!mbar_wait(&bar_full[stage], phase) || !mbar_wait(&bar_tempty[acc], aphase ^ 1) ||
-              *abort_v) {
-            aborted = true;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a0 = smem_u32(smem + stage * kStage), b0 = a0 + kStageA;
-          const uint32_t dt = tmem + (uint32_t)(acc * kNT);
-          mma_f16(dt, zdesc, sdesc(b0, (uint32_t)kPlaneB, 128u),
-                  kIdescM | ((uint32_t)(kNT >> 3) << 17), 0u);
-          const int64_t d0 = it.dlo + (int64_t)c * kKS;
-          // block columns n' of offset delta: [P0 + 128 - delta - R, P0 + 128 - delta) clipped
-          const int64_t top = it.P0 + kNT - d0;
-          int jmax = kKS;
-          if (d0 + jmax - 1 > it.dhi) jmax = (int)(it.dhi - d0 + 1);
-          for (int j = 0; j < jmax; j++) {
-            int64_t lo = top - j - it.R;
-            int64_t hi = top - j;
-            if (lo < 0) lo = 0;
-            if (hi > kNT) hi = kNT;
-            const uint32_t lo16 = (uint32_t)lo & ~15u;
-            const uint32_t hi16 = ((uint32_t)hi + 15u) & ~15u;
-            const uint32_t idesc = kIdescM | (((hi16 - lo16) >> 3) << 17);
-            const uint32_t aj = a0 + (uint32_t)(16 * j) * 128u;
-            const uint32_t bj = b0 + ((uint32_t)j + lo16) * 16u;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + stage * kStage), b0 = a0 + kStageA;
+        const uint32_t dt = tmem + (uint32_t)(acc * kNT);
+        mma_f16_lane0(dt, zdesc, sdesc(b0, (uint32_t)kPlaneB, 128u),
+                      kIdescM | ((uint32_t)(kNT >> 3) << 17), 0u, lane_u);
+        const int64_t d0 = it.dlo + (int64_t)c * kKS;
+        // block columns n' of offset delta: [P0 + 128 - delta - R, P0 + 128 - delta) clipped
+        const int64_t top = it.P0 + kNT - d0;
+        int jmax = kKS;
+        if (d0 + jmax - 1 > it.dhi) jmax = (int)(it.dhi - d0 + 1);
+        for (int j = 0; j < jmax; j++) {
+          int64_t lo = top - j - it.R;
+          int64_t hi = top - j;
+          if (lo < 0) lo = 0;
+          if (hi > kNT) hi = kNT;
+          const uint32_t lo16 = (uint32_t)lo & ~15u;
+          const uint32_t hi16 = ((uint32_t)hi + 15u) & ~15u;
+          const uint32_t idesc = kIdescM | (((hi16 - lo16) >> 3) << 17);
+          // the K steps advance A by two core matrices (256 bytes) and B by two
+          // planes; the start-address field of a descriptor is the address / 16
+          const uint64_t ad = sdesc(a0 + (uint32_t)(16 * j) * 128u, 128u, 128u);
+          const uint64_t bd = sdesc(b0 + ((uint32_t)j + lo16) * 16u, (uint32_t)kPlaneB, 128u);
 #pragma unroll
-            for (int k = 0; k < 8; k++)
-              mma_f16(dt + lo16, sdesc(aj + (uint32_t)(2 * k) * 128u, 128u, 128u),
-                      sdesc(bj + (uint32_t)(2 * k) * kPlaneB, (uint32_t)kPlaneB, 128u), idesc, 1u);
-          }
-          mma_commit(&bar_empty[stage]);
-          mma_commit(&bar_tfull[acc]);
-          issued = true;
-          if (++stage == kStages) {
-            stage = 0;
-            phase ^= 1;
-          }
-          if (++acc == kNumAcc) {
-            acc = 0;
-            aphase ^= 1;
-          }
+          for (int k = 0; k < 8; k++)
+            mma_f16_lane0(dt + lo16, ad + (uint64_t)(16 * k), bd + (uint64_t)((2 * k * kPlaneB) >> 4),
+                          idesc, 1u, lane_u);
         }
-        if (aborted) break;
+        mma_commit_lane0(&bar_empty[stage], lane_u);
+        mma_commit_lane0(&bar_tfull[acc], lane_u);
+        issued = true;
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+        if (++acc == kNumAcc) {
+          acc = 0;
+          aphase ^= 1;
+        }
       }
-      if (aborted) {
-        *abort_v = 1;
-        if (issued) {  // every MMA issued so far completes before the memory is released
-          mma_commit(&bar_drain);
-          mbar_wait(&bar_drain, 0);
-        }
+      if (aborted) break;
+    }
+    if (aborted) {
+      if (lane == 0) *abort_v = 1;
+      if (issued) {  // every MMA issued so far completes before the memory is released
+        mma_commit_lane0(&bar_drain, lane_u);
+        mbar_wait(&bar_drain, 0);
       }
     }
   } else {
