@@ -113,7 +113,7 @@ struct ks_plan {
   ks::List<ks::FixArgs> fix;
   std::vector<ks::NttJob> ntt;
   std::vector<ks::SingleJob> singles;
-  int64_t tc_chunks = 0;
+  int64_t tc_work = 0;
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -163,7 +163,7 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
   if (P->school.n())
     KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
                                    P->school.blocks(), s));
-  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_chunks, s));
+  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, s));
   for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
   const bool fork = P->side != nullptr && (P->seedb.n() || P->pref.n() || [&] {
     for (int i = 0; i < 7; i++)
@@ -406,14 +406,14 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       for (int k = 0; k < p.nprod; k++)
         C[k] = reinterpret_cast<int64_t *>(ws + p.off_cols) + (int64_t)k * p.ncols;
       make_tc_args(p.tg, p.nprod, ws + p.off_digits, C, status, ta);
-      P->tc.add(ta, ta.chunk_prefix[p.nprod]);
+      P->tc.add(ta, ta.work_prefix[p.nprod]);
     }
     if (rc != KS_OK) {
       ks_plan_destroy(P);
       return rc;
     }
   }
-  P->tc_chunks = P->tc.blocks();
+  P->tc_work = P->tc.blocks();
   // descriptor arrays: one device allocation, filled from a pinned host copy
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
               P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->normc[0].bytes() +

@@ -136,7 +136,7 @@ struct TcProduct {
   const __half *BRT;
   int64_t rows;
   int64_t dmax, R, T;  // largest delta, rows of B, tiles
-  int64_t chunks;  // accumulation chunks over all output tiles
+  int64_t work;    // block offsets over all output tiles (the kernel's split unit)
   int64_t *C;
   int64_t ncols;
 };
@@ -144,7 +144,7 @@ struct TcProduct {
 struct TcArgs {
   TcProduct p[4];
   int nprod;
-  int64_t chunk_prefix[5];  // chunks of the sub-products before each one
+  int64_t work_prefix[5];  // block offsets of the sub-products before each one
   int *status;
 };
 
@@ -166,7 +166,7 @@ void make_tc_pack_args(const PackArgs &pa, const TcGeom &g, int nprod, char *bas
                        int64_t nzero = 0);
 cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int n,
                                  int64_t blocks, cudaStream_t s);
-int64_t tc_chunks(const TcGeom &g);  // accumulation chunks of one sub-product
+int64_t tc_work(const TcGeom &g);  // block offsets over the output tiles of one sub-product
 void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
                   TcArgs &a);
 // the prefix (in chunks) over the descriptors splits evenly over one CTA per SM

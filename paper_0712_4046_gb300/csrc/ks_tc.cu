@@ -38,13 +38,19 @@
 // with one MMA of an all-zero A strip that clears the whole accumulator.  The
 // B planes carry 16 zero rows on each side, enough for the rounding.
 //
+// Split.  An MMA costs about the same whatever its trimmed N, so the unit of
+// work is one block offset of one tile (eight MMAs), and the CTAs take equal
+// contiguous ranges of the offsets of all tiles.  A CTA's share may start and
+// end inside a tile; its chunks are runs of up to kKS offsets from wherever
+// that share starts.
+//
 // Pipeline (one CTA per SM, persistent over work items of (sub-product,
-// output tile, run of chunks)): warp 0 copies the operands of each chunk into
-// a ring of three shared memory stages (cp.async.bulk completing on an
-// mbarrier), warp 1 issues the MMAs of a chunk into one of two tensor memory
-// accumulators and commits them to the stage's "empty" and the accumulator's
-// "full" barrier, and eight epilogue warps read each accumulator out while
-// the tensor core fills the other one.  Every mbarrier wait is bounded (about
+// output tile, run of block offsets)): warp 0 copies the operands of each
+// chunk into a ring of kStages shared memory stages (cp.async.bulk completing
+// on an mbarrier), warp 1 issues the MMAs of a chunk into one of kNumAcc
+// tensor memory accumulators and commits them to the stage's "empty" and the
+// accumulator's "full" barrier, and eight epilogue warps read each
+// accumulator out while the tensor core fills the next one.  Every mbarrier wait is bounded (about
 // one second of %globaltimer); on expiry the CTA records KS status 1, waits
 // (bounded) for its own copies and MMAs, releases its tensor memory and
 // returns.
@@ -330,23 +336,21 @@ __host__ __device__ __forceinline__ void tc_tile(int64_t dmax, int64_t R, int64_
   nch = (dhi - dlo) / kKS + 1;
 }
 
-// Chunks of the tiles before tile t, in closed form: with kKS = 16 dividing
-// 128 the chunk count of a tile is 8 t + 8 while dlo = 0 and dhi = 128 t + 127,
-// constant while exactly one of them is clipped, and K - 8 t once both are.
-static_assert(kKS == 16, "the closed form assumes 16 offsets per chunk");
-__host__ __device__ __forceinline__ int64_t tc_chunk_prefix(int64_t dmax, int64_t R, int64_t t) {
-  const int64_t tA = (R - 1) / 128;                    // dlo = 0 up to tile tA
-  const int64_t tB = dmax >= 127 ? (dmax - 127) / 128 : -1;  // dhi unclipped up to tB
-  const int64_t lo = tA < tB ? tA : tB, hi = tA < tB ? tB : tA;
-  int64_t P = 0;
-  const int64_t m = t < lo + 1 ? t : lo + 1;
-  if (m > 0) P += 4 * m * (m + 1);
-  int64_t a = lo + 1, b = t < hi + 1 ? t : hi + 1;
-  if (b > a) P += (b - a) * (tA < tB ? (R + 126) / 16 + 1 : dmax / 16 + 1);
-  a = hi + 1;
-  b = t;
-  if (b > a) P += (b - a) * ((dmax + R - 1) / 16 + 1) - 4 * (a + b - 1) * (b - a);
-  return P;
+// The unit of work is one block offset of one output tile (eight MMAs of
+// N <= 128; their cost hardly depends on N).  Offsets of the tiles before tile
+// t, in closed form: the sum over t' < t of
+// min(dmax, 128 t' + 127) - max(0, 128 t' - R + 1) + 1, each bound linear in
+// t' on one side of its clipping point.
+__host__ __device__ __forceinline__ int64_t tc_offset_prefix(int64_t dmax, int64_t R, int64_t t) {
+  const int64_t T = (dmax + R + kNT - 1) / kNT;
+  if (t > T) t = T;
+  if (t <= 0) return 0;
+  const int64_t na = dmax >= kNT - 1 ? (dmax - (kNT - 1)) / kNT + 1 : 0;  // dhi unclipped
+  const int64_t m = t < na ? t : na;
+  const int64_t s_hi = (kNT / 2) * m * (m - 1) + (kNT - 1) * m + (t - m) * dmax;
+  const int64_t n0 = (R - 1) / kNT + 1;  // dlo = 0
+  const int64_t s_lo = t > n0 ? (kNT / 2) * (n0 + t - 1) * (t - n0) - (R - 1) * (t - n0) : 0;
+  return s_hi - s_lo + t;
 }
 
 // one work item, as the producer hands it to the MMA issuer and the epilogue
@@ -359,31 +363,32 @@ struct __align__(16) TcSlot {
 };
 constexpr int kItemSlots = 4;
 
-// The item that holds global chunk `s`: its descriptor, sub-product and tile
-// (a binary search over the closed-form tile prefix), and the chunks of that
-// tile from s up to at most s_end.
+// The CTAs split the offsets of all tiles evenly.  tc_decode gives the item
+// that starts at offset position s: that offset and the ones after it in the
+// same tile, up to position s_end and at most kMaxItemChunks chunks of kKS
+// offsets; `next` is the position after the item.  Requires s < s_end.
 template <class Src>
-__device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it) {
+__device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it, int64_t &next) {
   int64_t local;
   const TcArgs &a = src.locate(s, local);
   int q = 0;
-  while (q + 1 < a.nprod && local >= a.chunk_prefix[q + 1]) q++;
+  while (q + 1 < a.nprod && local >= a.work_prefix[q + 1]) q++;
   const TcProduct &P = a.p[q];
-  const int64_t L = local - a.chunk_prefix[q];
+  const int64_t L = local - a.work_prefix[q];
   int64_t tlo = 0, thi = P.T - 1;  // last tile whose prefix is <= L
   while (tlo < thi) {
     const int64_t mid = (tlo + thi + 1) >> 1;
-    if (tc_chunk_prefix(P.dmax, P.R, mid) <= L)
+    if (tc_offset_prefix(P.dmax, P.R, mid) <= L)
       tlo = mid;
     else
       thi = mid - 1;
   }
   int64_t dlo, dhi, nch;
   tc_tile(P.dmax, P.R, tlo, dlo, dhi, nch);
-  const int64_t c = L - tc_chunk_prefix(P.dmax, P.R, tlo);
-  int64_t c1 = nch;
-  if (c1 - c > s_end - s) c1 = c + (s_end - s);
-  if (c1 - c > kMaxItemChunks) c1 = c + kMaxItemChunks;
+  const int64_t da = dlo + (L - tc_offset_prefix(P.dmax, P.R, tlo));
+  int64_t db = da + (s_end - s) - 1;
+  if (db > dhi) db = dhi;
+  if (db > da + (int64_t)kKS * kMaxItemChunks - 1) db = da + (int64_t)kKS * kMaxItemChunks - 1;
   it.E = P.E;
   it.BRT = P.BRT;
   it.C = P.C;
@@ -393,12 +398,13 @@ __device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it) 
   it.R = P.R;
   it.ncols = P.ncols;
   it.P0 = tlo * kNT;
-  it.dlo = dlo;
-  it.dhi = dhi;
-  it.c0 = (int)c;
-  it.c1 = (int)c1;
+  it.dlo = da;
+  it.dhi = db;
+  it.c0 = 0;
+  it.c1 = (int)((db - da) / kKS + 1);
   it.pad = 0;
   it.done = 0;
+  next = s + (db - da + 1);
 }
 
 __device__ __forceinline__ void slot_store(TcSlot *dst, const TcSlot &v) {
@@ -476,14 +482,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       int stage = 0, islot = 0;
       uint32_t phase = 0, iphase = 0, armed = 0, armed_par = 0;
       bool aborted = false;
-      // this CTA's even share of the chunk sequence
+      // this CTA's even share of the offsets
       const int64_t s_beg = total * blockIdx.x / gridDim.x;
       const int64_t s_end = total * (blockIdx.x + 1) / gridDim.x;
       for (int64_t s = s_beg;;) {
         TcSlot it;
+        int64_t next = s_end;
         const bool have = s < s_end;
         if (have)
-          tc_decode(src, s, s_end, it);
+          tc_decode(src, s, s_end, it, next);
         else
           it.done = 1;
         if (!mbar_wait(&bar_iempty[islot], iphase ^ 1) || *abort_v) {
@@ -497,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
           iphase ^= 1;
         }
         if (!have) break;
-        s += it.c1 - it.c0;
+        s = next;
         if (status_sh == nullptr) status_sh = it.status;
         for (int c = it.c0; c < it.c1; c++) {
           if (!mbar_wait(&bar_empty[stage], phase ^ 1) || *abort_v) {
@@ -813,7 +820,7 @@ static cudaError_t tc_attr(int *sms) {
   return cudaSuccess;
 }
 
-int64_t tc_chunks(const TcGeom &g) { return tc_chunk_prefix(g.dmax, g.R, g.T); }
+int64_t tc_work(const TcGeom &g) { return tc_offset_prefix(g.dmax, g.R, g.T); }
 
 void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
                   TcArgs &a) {
@@ -821,7 +828,7 @@ void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int
   a.nprod = nprod;
   a.status = status;
   const size_t per = tc_operand_bytes(g);
-  a.chunk_prefix[0] = 0;
+  a.work_prefix[0] = 0;
   for (int q = 0; q < nprod; q++) {
     TcProduct &P = a.p[q];
     P.E = reinterpret_cast<const __half *>(base + q * per);
@@ -831,10 +838,10 @@ void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int
     P.dmax = g.dmax;
     P.R = g.R;
     P.T = g.T;
-    P.chunks = tc_chunks(g);
+    P.work = tc_work(g);
     P.C = C[q];
     P.ncols = g.ncols;
-    a.chunk_prefix[q + 1] = a.chunk_prefix[q] + P.chunks;
+    a.work_prefix[q + 1] = a.work_prefix[q] + P.work;
   }
 }
 
@@ -845,22 +852,22 @@ cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base, int64_t *
   if (e != cudaSuccess) return e;
   TcArgs a;
   make_tc_args(g, nprod, base, C, status, a);
-  const int64_t chunks = a.chunk_prefix[nprod];
-  if (chunks <= 0) return cudaSuccess;
-  const int64_t grid = chunks < sms ? chunks : sms;
-  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, chunks);
+  const int64_t work = a.work_prefix[nprod];
+  if (work <= 0) return cudaSuccess;
+  const int64_t grid = work < sms ? work : sms;
+  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, work);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t chunks,
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t work,
                             cudaStream_t s) {
-  if (n == 0 || chunks == 0) return cudaSuccess;
+  if (n == 0 || work == 0) return cudaSuccess;
   int sms = 0;
   cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
-  const int64_t grid = chunks < sms ? chunks : sms;
-  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, chunks);
+  const int64_t grid = work < sms ? work : sms;
+  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, work);
   note_launches(1);
   return cudaGetLastError();
 }
