@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one tc_kernel launch on this workload's KS4
 # product, from the ncu capture summarised in
 # profiles/tc_kernel_zx_product_16384_s48_ks4.md (re-taken whenever the kernel changes)
-TC_KERNEL_DRAM_BYTES = 6001664
+TC_KERNEL_DRAM_BYTES = 6001408
 # 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC
 IMAD_PER_SM_CLK = 64
 SMS = 152
