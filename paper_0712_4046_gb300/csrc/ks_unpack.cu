@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(256) seed_blocked64(Src src) {
   int64_t thi = kmax < lf - 1 ? kmax : lf - 1;
   const int64_t s_lo = tlo + slice * kSlice;
   const int64_t s_hi = s_lo + kSlice - 1 < thi ? s_lo + kSlice - 1 : thi;
+  if (s_lo > s_hi) return;  // the group's t range ends before this slice (uniform)
   if (split) {
     uint4 *sf = reinterpret_cast<uint4 *>(sraw);
     uint4 *sg = sf + kST;
@@ -332,29 +333,30 @@ __global__ void __launch_bounds__(256) seed_blocked64(Src src) {
         }
       }
     }
-    // reduce over the 64 threads of each seed through shared memory:
-    // red[seed][value][sub], then one thread per (seed, value) sums 64 entries
+    // sums over the 64 threads of each seed: a shuffle tree in each of its two
+    // warps, then red[seed][value][warp]
     __syncthreads();
     unsigned long long *red = reinterpret_cast<unsigned long long *>(sraw);
+    const int half = (tid >> 5) & 1, lane = tid & 31;
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const int sd = sq + 4 * u;
-      red[(sd * 3 + 0) * 64 + sub] = ll[u];
-      red[(sd * 3 + 1) * 64 + sub] = hh[u];
-      red[(sd * 3 + 2) * 64 + sub] = ss[u];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        ll[u] += __shfl_xor_sync(0xffffffffu, ll[u], off);
+        hh[u] += __shfl_xor_sync(0xffffffffu, hh[u], off);
+        ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], off);
+      }
+      if (lane == 0) {
+        const int sd = sq + 4 * u;
+        red[(sd * 3 + 0) * 2 + half] = ll[u];
+        red[(sd * 3 + 1) * 2 + half] = hh[u];
+        red[(sd * 3 + 2) * 2 + half] = ss[u];
+      }
     }
-    __syncthreads();
-    unsigned long long tot = 0;
-    if (tid < kSG * 3) {
-      const unsigned long long *rr = red + tid * 64;
-#pragma unroll 16
-      for (int i = 0; i < 64; i++) tot += rr[(i + tid) & 63];
-    }
-    __syncthreads();
-    if (tid < kSG * 3) red[tid] = tot;
     __syncthreads();
     if (tid < nS) {
-      const unsigned long long l = red[tid * 3], hv = red[tid * 3 + 1], sv = red[tid * 3 + 2];
+      const unsigned long long *q = red + tid * 6;
+      const unsigned long long l = q[0] + q[1], hv = q[2] + q[3], sv = q[4] + q[5];
       // ll + (ss - ll - hh) 2^24 + hh 2^48 as 128 bits (the middle term is non-negative)
       const uint64_t mid = sv - l - hv;
       const uint64_t ml = mid << 24, mh = mid >> 40;
