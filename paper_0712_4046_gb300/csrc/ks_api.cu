@@ -373,6 +373,17 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   }
 
   const bool recon = p.variant == KS_3 || p.variant == KS_4;
+  // the exact seeds; from the blocked kernel the reconstruction reads (and carries)
+  // their column sums directly
+  SeedPlan sp;
+  if (recon) {
+    if (make_seed_plan(seeds, p.seed_words,
+                       reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs, p.nruns,
+                       p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
+      return KS_ERANGE;
+    if (sp.kind == 1)
+      for (int r = 0; r < p.nruns; r++) runs[r].seed_acc = sp.bl.acc;
+  }
   Fork fk{};
   if (fork && (recon || p.is_signed)) {
     const int rc = fork_for(s, &fk);
@@ -434,9 +445,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   }
   if (recon) {
     PhaseTimer t(side, PH_SEEDS);
-    KS_CUDA(launch_seeds(seeds, p.seed_words,
-                         reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs,
-                         p.nruns, p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, side));
+    KS_CUDA(launch_seed_plan(sp, side));
   }
   if (side != s) KS_CUDA(cudaEventRecord(fk.join_seeds, side));
   if (p.is_signed) {

@@ -105,7 +105,7 @@ struct ks_plan {
   ks::List<ks::NormArgs> norm[2];   // digit width 16 and 28 (tensor cores): tile pass
   ks::List<ks::NormArgs> normc[2];  // the same descriptors, carry-pass block counts
   ks::List<ks::UnpackArgs> unpack;
-  ks::List<ks::SeedBArgs> seedb, seedb_finish;
+  ks::List<ks::SeedBArgs> seedb;
   ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
   ks::List<ks::RecoverArgs> recover[3];
   int recover_smem = 0;  // class 1: the largest staged-digit buffer of the batch
@@ -176,9 +176,8 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
   }
   if (P->seedb.n())
-    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb_finish.dprefix,
-                                      P->seedb.n(), P->seedb.blocks(),
-                                      P->seedb_finish.blocks(), side));
+    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb.n(),
+                                      P->seedb.blocks(), side));
   for (int i = 0; i < 7; i++)
     if (P->seedk[i].n())
       KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
@@ -310,8 +309,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
                        p.chain, q.f, p.lf, q.g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
       return KS_ERANGE;
     if (sp.kind == 1) {
+      // the reconstruction reads the seeds from the column sums themselves
+      for (int r = 0; r < p.nruns; r++) runs[r].seed_acc = sp.bl.acc;
       P->seedb.add(sp.bl, sp.blocks);
-      P->seedb_finish.add(sp.bl, sp.finish_blocks);
       const int64_t nz = sp.nseeds * 6;
       P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(sp.bl.acc), nz}, (nz + 255) / 256);
     } else if (sp.kind != 0) {
@@ -418,7 +418,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
               P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->normc[0].bytes() +
               P->normc[1].bytes() + P->unpack.bytes() +
-              P->seedb.bytes() + P->seedb_finish.bytes() + P->pref.bytes() + P->fix.bytes();
+              P->seedb.bytes() + P->pref.bytes() + P->fix.bytes();
   for (int i = 0; i < 7; i++) db += P->seedk[i].bytes();
   for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
   P->desc_bytes = db;
@@ -439,8 +439,6 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   }
   P->unpack.place(h, d);
   P->seedb.place(h, d);
-  P->seedb_finish.place(h, d);
-  P->seedb_finish.d = P->seedb.d;
   for (int i = 0; i < 7; i++) P->seedk[i].place(h, d);
   for (int c = 0; c < 3; c++) P->recover[c].place(h, d);
   P->pref.place(h, d);

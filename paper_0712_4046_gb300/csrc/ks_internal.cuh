@@ -13,6 +13,7 @@ namespace ks {
 // ---------------------------------------------------------------- limits
 constexpr int kMaxOperands = 8;      // 4 sub-products x 2 sides
 constexpr int kMaxSeedWords = 136;   // exact seeds: (2b + e) bits, b <= 2048
+constexpr int kAccSeedWords = 8;     // seed words of the blocked (b <= 64) seed path, at most
 constexpr int kMaxDigitWordsM = 72;  // reconstruction digit: M <= 2304 bits
 
 // ---------------------------------------------------------------- planning
@@ -240,6 +241,9 @@ struct RecoverRun {
   int64_t nchains;
   const uint32_t *seeds;   // 2 values per chain c >= 1 (seed_words words each)
   int64_t seed_base;       // index of this run's first seed value
+  // when set, the seeds are read (and carried) from these 64-bit column sums,
+  // 6 per value, instead of from `seeds` (the blocked seed kernel's output)
+  const unsigned long long *seed_acc;
 };
 
 // Exact coefficients h'_k (biased, unsigned) for the chain starts.
@@ -270,20 +274,15 @@ struct SeedPlan {
   int kind = 0;  // 0 none, 1 blocked, 2 one 64-bit word, 100 + words: templated
   SeedArgs a;
   SeedBArgs bl;
-  int64_t blocks = 0, finish_blocks = 0, nseeds = 0;
+  int64_t blocks = 0, nseeds = 0;
 };
 // seed_acc: scratch of 6 64-bit words per seed (the b <= 64 blocked path).
 int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
                    const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
                    const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp);
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s);
-cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
-                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
-                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs,
-                         int flip, cudaStream_t s);
-cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks,
-                                       const int64_t *prefix_finish, int n, int64_t blocks,
-                                       int64_t finish_blocks, cudaStream_t s);
+cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks, int n,
+                                       int64_t blocks, cudaStream_t s);
 cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
                                     int64_t blocks, cudaStream_t s);
 

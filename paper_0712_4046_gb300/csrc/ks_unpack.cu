@@ -440,24 +440,6 @@ __global__ void __launch_bounds__(256) seed_blocked64(Src src) {
   }
 }
 
-// word sums (6 x 64-bit per seed) -> carried 32-bit seed words
-template <class Src>
-__global__ void __launch_bounds__(128) seed_finish(Src src) {
-  int64_t local;
-  const SeedBArgs &a = src.locate(blockIdx.x, local);
-  const int64_t i = local * 128 + threadIdx.x;
-  if (i >= a.nseeds) return;
-  uint32_t *seeds = a.seeds;
-  const int seed_words = a.seed_words;
-  const unsigned long long *acc = a.acc;
-  unsigned long long carry = 0;
-  for (int w = 0; w < seed_words; w++) {
-    const unsigned long long v = (w < 6 ? acc[i * 6 + w] : 0ull) + carry;
-    seeds[i * seed_words + w] = (uint32_t)v;
-    carry = v >> 32;
-  }
-}
-
 int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
                    const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
                    const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp) {
@@ -482,7 +464,7 @@ int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc
   a.flip = flip;
   sp.blocks = n;
   // blocked path when the seeds of a group lie close enough together
-  bool blocked = b <= 64;
+  bool blocked = b <= 64 && seed_words <= kAccSeedWords;
   for (int r = 0; r < nruns && blocked; r++)
     if (runs[r].kstride * (chain * (kSG / 2) + 1) + kST > kSW) blocked = false;
   if (blocked) {
@@ -511,7 +493,6 @@ int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc
     sb.flip = flip;
     sp.kind = 1;
     sp.blocks = groups * sb.slices;
-    sp.finish_blocks = (n + 127) / 128;
     return 0;
   }
   const int nw = (b + 31) / 32;
@@ -547,8 +528,7 @@ cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const One<SeedBArgs> one{sp.bl};
     seed_blocked64<One<SeedBArgs>><<<(unsigned)sp.blocks, 256, 0, s>>>(one);
-    seed_finish<One<SeedBArgs>><<<(unsigned)sp.finish_blocks, 128, 0, s>>>(one);
-    note_launches(2);
+    note_launches(1);
   } else {
     launch_seed_kind(sp.kind, sp.blocks, One<SeedArgs>{sp.a}, s);
     note_launches(1);
@@ -557,15 +537,12 @@ cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
 }
 
 // batches: blocked (kind 1) products, then per kind the others
-cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks,
-                                       const int64_t *prefix_finish, int n, int64_t blocks,
-                                       int64_t finish_blocks, cudaStream_t s) {
+cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks, int n,
+                                       int64_t blocks, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   seed_blocked64<Many<SeedBArgs>><<<(unsigned)blocks, 256, 0, s>>>(
       Many<SeedBArgs>{d, prefix_blocks, n});
-  seed_finish<Many<SeedBArgs>><<<(unsigned)finish_blocks, 128, 0, s>>>(
-      Many<SeedBArgs>{d, prefix_finish, n});
-  note_launches(2);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -577,16 +554,6 @@ cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *
   return cudaGetLastError();
 }
 
-cudaError_t launch_seeds(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
-                         const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f,
-                         int64_t lf, const uint64_t *g, int64_t lg, int b, int in_limbs, int flip,
-                         cudaStream_t s) {
-  SeedPlan sp;
-  if (make_seed_plan(seeds, seed_words, seed_acc, runs, nruns, chain, f, lf, g, lg, b, in_limbs,
-                     flip, sp) != 0)
-    return cudaErrorInvalidValue;
-  return launch_seed_plan(sp, s);
-}
 
 // ------------------------------------------------------------------ recover
 // Sec. 3.2: from the base-X digits u_i of fwd = sum c_i X^i and w_i of
@@ -717,6 +684,25 @@ __device__ __forceinline__ D2 load_d2(const uint32_t *V, int64_t nwords, int64_t
   r.lo = get_bits64(V, nwords, pos);
   r.hi = get_bits64(V, nwords, pos + 64) & hi_mask(M);
   return r;
+}
+// Seed value i of a run as kAccSeedWords 32-bit words (the top ones zero): the
+// finished seed words, or carried from the blocked seed kernel's 64-bit column sums
+// (nw <= kAccSeedWords there).
+__device__ __forceinline__ void seed_value(const RecoverRun &R, int64_t i, int nw,
+                                           uint32_t (&out)[kAccSeedWords]) {
+  if (R.seed_acc != nullptr) {
+    const unsigned long long *acc = R.seed_acc + i * 6;
+    unsigned long long carry = 0;
+#pragma unroll
+    for (int w = 0; w < kAccSeedWords; w++) {
+      const unsigned long long v = (w < 6 ? acc[w] : 0ull) + carry;
+      out[w] = w < nw ? (uint32_t)v : 0u;
+      carry = v >> 32;
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < kAccSeedWords; w++) out[w] = w < nw ? R.seeds[i * nw + w] : 0u;
+  }
 }
 // (a - b - c) mod 2^M, c in {0, 1}
 __device__ __forceinline__ D2 sub_d2(D2 a, D2 b, uint64_t c, int M) {
@@ -927,10 +913,12 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
       a_cur = u(0);
       delta = 0;
     } else {
-      const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
-      a_prev = load_d1(sd, a.seed_words, 0, M);
-      const uint64_t b_prev = load_d1(sd, a.seed_words, M, M);
-      a_cur = load_d1(sd + a.seed_words, a.seed_words, 0, M);
+      uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
+      seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
+      seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
+      a_prev = load_d1(s0, kAccSeedWords, 0, M);
+      const uint64_t b_prev = load_d1(s0, kAccSeedWords, M, M);
+      a_cur = load_d1(s1, kAccSeedWords, 0, M);
       const uint64_t us = u(s);
       const uint64_t dprev = (us - b_prev - a_cur) & mask;
       if (dprev > 1) atomicExch(status, 2);
@@ -1014,10 +1002,12 @@ __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
     a_cur = load_d2(R.Vf, a.nwords, R.off_f, M);
     delta = 0;
   } else {
-    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
-    a_prev = load_d2(sd, a.seed_words, 0, M);
-    const D2 b_prev = load_d2(sd, a.seed_words, M, M);
-    a_cur = load_d2(sd + a.seed_words, a.seed_words, 0, M);
+    uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
+    seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
+    seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
+    a_prev = load_d2(s0, kAccSeedWords, 0, M);
+    const D2 b_prev = load_d2(s0, kAccSeedWords, M, M);
+    a_cur = load_d2(s1, kAccSeedWords, 0, M);
     const D2 us = load_d2(R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
     const D2 dprev = sub_d2(sub_d2(us, b_prev, 0, M), a_cur, 0, M);
     if (dprev.hi != 0 || dprev.lo > 1) atomicExch(status, 2);
@@ -1072,11 +1062,20 @@ __global__ void __launch_bounds__(64) recover_wide(Src src) {
     dig_load(a_cur, R.Vf, a.nwords, R.off_f, M);
     delta = 0;
   } else {
-    const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
     Dig b_prev, us, dp;
-    dig_load_local(a_prev, sd, a.seed_words, 0, M);
-    dig_load_local(b_prev, sd, a.seed_words, M, M);
-    dig_load_local(a_cur, sd + a.seed_words, a.seed_words, 0, M);
+    if (R.seed_acc != nullptr) {
+      uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
+      seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
+      seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
+      dig_load_local(a_prev, s0, kAccSeedWords, 0, M);
+      dig_load_local(b_prev, s0, kAccSeedWords, M, M);
+      dig_load_local(a_cur, s1, kAccSeedWords, 0, M);
+    } else {
+      const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
+      dig_load_local(a_prev, sd, a.seed_words, 0, M);
+      dig_load_local(b_prev, sd, a.seed_words, M, M);
+      dig_load_local(a_cur, sd + a.seed_words, a.seed_words, 0, M);
+    }
     dig_load(us, R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
     Dig t1;
     dig_sub(t1, us, b_prev, 0, M);
