@@ -180,6 +180,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
                              (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3)) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
+  p.off_seedacc = off;  // right after the column sums: one clearing pass covers both
+  off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_flags = off;
   p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
   off = align256(p.off_flags + (size_t)p.flag_bytes);
@@ -187,8 +189,6 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   off = align256(off + (size_t)p.nnorm * p.nwords * 4);
   p.off_seeds = off;
   off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
-  p.off_seedacc = off;
-  off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_prefix = off;
   if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.in_limbs));
   p.off_hp = off;  // exact product for ks_mul_mod (sized by the caller)
@@ -350,7 +350,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
-  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
+  int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
   uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
 
   // reconstruction runs (Sec. 3.2; twice for Sec. 3.4)
@@ -381,8 +381,15 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
                        reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs, p.nruns,
                        p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
       return KS_ERANGE;
-    if (sp.kind == 1)
+    if (sp.kind == 1) {
       for (int r = 0; r < p.nruns; r++) runs[r].seed_acc = sp.bl.acc;
+      // the blocked kernel's column sums follow the products' in the workspace, and
+      // the seeds run after the products: the products' clearing pass covers them
+      if (p.engine != KS_ENGINE_NTT) {
+        nzero = (int64_t)((p.off_seedacc - p.off_cols) / 8) + sp.nseeds * 6;
+        sp.acc_cleared = true;
+      }
+    }
   }
   Fork fk{};
   if (fork && (recon || p.is_signed)) {

@@ -275,6 +275,7 @@ struct SeedPlan {
   SeedArgs a;
   SeedBArgs bl;
   int64_t blocks = 0, nseeds = 0;
+  bool acc_cleared = false;  // kind 1: the column sums are already zero (no clearing launch)
 };
 // seed_acc: scratch of 6 64-bit words per seed (the b <= 64 blocked path).
 int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,

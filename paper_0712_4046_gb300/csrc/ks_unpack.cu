@@ -524,8 +524,10 @@ static void launch_seed_kind(int kind, int64_t blocks, const Src &src, cudaStrea
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
   if (sp.nseeds == 0) return cudaSuccess;
   if (sp.kind == 1) {
-    cudaError_t e = cudaMemsetAsync(sp.bl.acc, 0, (size_t)sp.nseeds * 6 * 8, s);
-    if (e != cudaSuccess) return e;
+    if (!sp.acc_cleared) {
+      cudaError_t e = cudaMemsetAsync(sp.bl.acc, 0, (size_t)sp.nseeds * 6 * 8, s);
+      if (e != cudaSuccess) return e;
+    }
     const One<SeedBArgs> one{sp.bl};
     seed_blocked64<One<SeedBArgs>><<<(unsigned)sp.blocks, 256, 0, s>>>(one);
     note_launches(1);
