@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -98,7 +99,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        # the raw samples go to a scratch file (set KS_CLOCKS_DIR to keep them);
+        # the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("KS_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 "ks_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

@@ -679,10 +679,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       }
       if (aborted) break;
       // Four neighbouring digits (lanes 4g .. 4g + 3, weights 128^w) form one
-      // 28-bit-digit column sum.  A two-round butterfly over each group of
+      // 28-bit-digit column sum.  A two-step butterfly over each group of
       // four block columns gives lane 4g + u the whole sum of column i + u:
-      // round 1 (lanes u, u ^ 1) pairs the columns i + (u & 1) and
-      // i + 2 + (u & 1), round 2 (lanes u, u ^ 2) completes column i + u.
+      // step 1 (lanes u, u ^ 1) pairs the columns i + (u & 1) and
+      // i + 2 + (u & 1), step 2 (lanes u, u ^ 2) completes column i + u.
       // The tile's 4096 column sums (block column p = P0 + row, 32 per row)
       // are contiguous in C: they are staged in shared memory and added with
       // one bulk reduction.
