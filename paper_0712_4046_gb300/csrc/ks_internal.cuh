@@ -263,9 +263,7 @@ struct SeedBArgs {  // blocked path (b <= 64): groups x t-slices, 64-bit word su
   int64_t chain;
   int64_t groups[2];
   int64_t slices, nseeds;
-  unsigned long long *acc;
-  uint32_t *seeds;
-  int seed_words;
+  unsigned long long *acc;  // 6 per seed; the reconstruction carries them into seed words
   const uint64_t *f, *g;
   int64_t lf, lg;
   int b, in_limbs, flip;

@@ -482,8 +482,6 @@ int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc
     sb.slices = (lmin + kSW + kSlice - 1) / kSlice;
     sb.nseeds = n;
     sb.acc = seed_acc;
-    sb.seeds = seeds;
-    sb.seed_words = seed_words;
     sb.f = f;
     sb.g = g;
     sb.lf = lf;
