@@ -191,3 +191,64 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     monkeypatch.setattr(S, "eval_pm", wrong_pm)
     with pytest.raises(AssertionError):
         test_ks2_example_replay()
+
+
+def _rand_recoverable(n, X, rng):
+    """Coefficients 0 <= c_i < X (X - 1) (the range Sec. 3.2 recovers) and their fwd, rev."""
+    c = [rng.randrange(X * (X - 1)) for _ in range(n)]
+    fwd = sum(ci * X ** i for i, ci in enumerate(c))
+    rev = sum(ci * X ** i for i, ci in enumerate(reversed(c)))
+    return c, fwd, rev
+
+
+@pytest.mark.parametrize("X", [10, 16, 2 ** 7, 2 ** 20])
+def test_recover_runs_downward_on_the_reversed_problem(X):
+    # x^(n-1) h(1/x) has coefficients c_(n-1-i): its fwd is rev and its rev is fwd,
+    # so the same recurrence with the two swapped yields the c_i from the top down
+    rng = random.Random(X)
+    for n in (1, 2, 3, 17, 64):
+        c, fwd, rev = _rand_recoverable(n, X, rng)
+        assert S.recover(fwd, rev, n, X).h == c
+        assert S.recover(rev, fwd, n, X).h == c[::-1]
+
+
+def _seeded_chain(fwd, rev, n, X, s, length, seed_prev, seed_cur):
+    """Sec. 3.2's recurrence started at index s >= 1 from the exact values
+    c_(s-1), c_s instead of from index 0: alpha_(s-1), beta_(s-1), alpha_s follow
+    from the seeds, delta_(s-1) = u_s - beta_(s-1) - alpha_s (mod X) is 0 or 1, and
+    the steps j = s .. s + length - 1 give c_j."""
+    u = [S.digit(fwd, i, X) for i in range(n + 1)]
+    w = [S.digit(rev, n - j, X) for j in range(n + 1)]
+    a_prev, b_prev = seed_prev % X, seed_prev // X
+    a_cur = seed_cur % X
+    d_prev = (u[s] - b_prev - a_cur) % X
+    assert d_prev in (0, 1)
+    delta = (b_prev + a_cur + d_prev - u[s]) // X
+    out = []
+    for j in range(s, min(s + length, n)):
+        if j <= n - 2:
+            eps = 1 if a_cur > w[j + 1] else 0
+            beta = (w[j] - a_prev - eps) % X
+            a_next = (u[j + 1] - beta - delta) % X
+            t = beta + a_next + delta - u[j + 1]
+            assert t % X == 0 and t // X in (0, 1)
+            out.append(a_cur + X * beta)
+            a_prev, a_cur, delta = a_cur, a_next, t // X
+        else:
+            out.append(a_cur + X * ((w[j] - a_prev) % X))
+    return out
+
+
+@pytest.mark.parametrize("X", [10, 2 ** 7, 2 ** 31])
+def test_one_seed_pair_starts_a_chain_each_way(X):
+    # the exact pair (c_(s-1), c_s) starts the chain [s, s + m) upward and, on the
+    # reversed problem, the chain [s - m, s) downward: every other seed pair suffices
+    rng = random.Random(X + 1)
+    n, m = 96, 16
+    c, fwd, rev = _rand_recoverable(n, X, rng)
+    for s in range(m, n, 2 * m):
+        up = _seeded_chain(fwd, rev, n, X, s, m, c[s - 1], c[s])
+        assert up == c[s:s + m]
+        # reversed index r = n - 1 - i: the pair becomes (c~_(n-s-1), c~_(n-s)) = (c_s, c_(s-1))
+        down = _seeded_chain(rev, fwd, n, X, n - s, m, c[s], c[s - 1])
+        assert down == c[s - m:s][::-1]
