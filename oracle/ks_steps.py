@@ -214,6 +214,44 @@ def ks_mul_unsigned(f: list[int], g: list[int], b: int, variant: int, base: int 
     return VARIANTS[variant](f, g, base ** N)
 
 
+def variant_N_bits(variant: int, bf: int, bg: int, e: int) -> int:
+    """N for coefficient sizes bf (f) and bg (g).  The coefficients of h are below
+    min(Lf, Lg) 2^(bf + bg), so bf + bg takes the place of 2b in Sec. 3.1-3.4."""
+    s = bf + bg + e
+    if variant == 1:
+        return s
+    if variant in (2, 3):
+        return (s + 1) // 2
+    if variant == 4:
+        return (s + 3) // 4
+    raise ValueError("variant must be 1..4")
+
+
+def ks_mul_unsigned_bits(f: list[int], g: list[int], bf: int, bg: int, variant: int,
+                         base: int = 2) -> Run:
+    """One variant for coefficients of at most bf (f) and bg (g) base-digits."""
+    if min(f) < 0 or min(g) < 0:
+        raise ValueError("the paper's variants take non-negative coefficients")
+    e = ceil_log(min(len(f), len(g)), base)
+    return VARIANTS[variant](f, g, base ** variant_N_bits(variant, bf, bg, e))
+
+
+def ks_mul_signed_bits(f: list[int], g: list[int], bf: int, bg: int, variant: int) -> list[int]:
+    """Signed coefficients, f in [-2^(bf-1), 2^(bf-1)) and g in [-2^(bg-1), 2^(bg-1)):
+    the bias reading with one bias per operand, cf = 2^(bf-1) and cg = 2^(bg-1);
+    h = h' - cg (f U_g) - cf (U_f g) - cf cg (U_f U_g)."""
+    cf, cg = 1 << (bf - 1), 1 << (bg - 1)
+    hb = ks_mul_unsigned_bits([x + cf for x in f], [x + cg for x in g], bf, bg, variant).h
+    lf, lg = len(f), len(g)
+    out = []
+    for k in range(lf + lg - 1):
+        lo, hi = max(0, k - lg + 1), min(k, lf - 1)
+        lo2, hi2 = max(0, k - lf + 1), min(k, lg - 1)
+        out.append(hb[k] - cg * sum(f[lo:hi + 1]) - cf * sum(g[lo2:hi2 + 1])
+                   - cf * cg * (hi - lo + 1))
+    return out
+
+
 def ks_mul_signed(f: list[int], g: list[int], b: int, variant: int) -> list[int]:
     """Signed coefficients in [-2^(b-1), 2^(b-1)) by the bias reading (see module doc)."""
     c = 1 << (b - 1)

@@ -252,3 +252,32 @@ def test_one_seed_pair_starts_a_chain_each_way(X):
         # reversed index r = n - 1 - i: the pair becomes (c~_(n-s-1), c~_(n-s)) = (c_s, c_(s-1))
         down = _seeded_chain(rev, fwd, n, X, n - s, m, c[s], c[s - 1])
         assert down == c[s - m:s][::-1]
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("bf,bg", [(1, 30), (7, 64), (40, 3), (33, 33)])
+def test_unequal_bit_sizes_match_schoolbook(variant, bf, bg):
+    # N from bf + bg in place of 2b: random, all-ones-maximal and signed operands
+    rng = random.Random(97 * bf + bg + variant)
+    for lf, lg in ((1, 1), (5, 3), (17, 40), (64, 64)):
+        f = [rng.randrange(1 << bf) for _ in range(lf)]
+        g = [rng.randrange(1 << bg) for _ in range(lg)]
+        assert S.ks_mul_unsigned_bits(f, g, bf, bg, variant).h == pyref.poly_mul(f, g)
+        fm, gm = [(1 << bf) - 1] * lf, [(1 << bg) - 1] * lg
+        assert S.ks_mul_unsigned_bits(fm, gm, bf, bg, variant).h == pyref.poly_mul(fm, gm)
+        fs = [rng.randrange(-(1 << (bf - 1)), 1 << (bf - 1)) for _ in range(lf)]
+        gs = [rng.randrange(-(1 << (bg - 1)), 1 << (bg - 1)) for _ in range(lg)]
+        assert S.ks_mul_signed_bits(fs, gs, bf, bg, variant) == pyref.poly_mul(fs, gs)
+
+
+def test_unequal_bit_sizes_N_is_tight_for_ks1():
+    # one bit less than bf + bg + e and the all-maximal product no longer fits its fields
+    bf, bg, L = 9, 21, 8
+    f, g = [(1 << bf) - 1] * L, [(1 << bg) - 1] * L
+    e = S.ceil_log(L, 2)
+    N = S.variant_N_bits(1, bf, bg, e)
+    assert N == bf + bg + e == S.variant_N(1, 15, e)
+    assert S.ks1(f, g, 2 ** N).h == pyref.poly_mul(f, g)
+    assert S.ks1(f, g, 2 ** (N - 1)).h != pyref.poly_mul(f, g)
+    # and the unequal-size N is smaller than the equal-size one at max(bf, bg)
+    assert N < S.variant_N(1, max(bf, bg), e)
