@@ -20,9 +20,17 @@ Readings of the paper used here (the paper is silent or garbled on them):
 * Four-point pairing: when Lh is even, the even-index half of rev h holds the
   odd coefficients of h, so the even coefficients come from (E, OR) and the
   odd ones from (O, ER).
-* Signed coefficients (the paper treats non-negative ones only): bias each
-  coefficient by c = 2^(b-1) to make it non-negative, multiply, and subtract
-  c (f U_g + U_f g) + c^2 U_f U_g, with U the all-ones polynomial.
+* Signed coefficients (the paper treats non-negative ones only), two readings:
+  - bias: bias each coefficient by c = 2^(b-1) to make it non-negative,
+    multiply, and subtract c (f U_g + U_f g) + c^2 U_f U_g, with U the
+    all-ones polynomial;
+  - offset: evaluate the signed coefficients as they are (the evaluations of
+    Sec. 3.3 are signed anyway), then add K U_h(Y) to every integer that the
+    coefficients are read from (K = 2^(bf + bg - 2 + e), Y the digit base of
+    that integer), which shifts every coefficient into [0, 2K] -- the
+    non-negative range the read-off and the reconstruction of Sec. 3 need --
+    and subtract K from each coefficient read.  |h_k| <= min(Lf, Lg)
+    2^(bf - 1) 2^(bg - 1) <= K.
 """
 from __future__ import annotations
 
@@ -267,4 +275,138 @@ def ks_mul_signed(f: list[int], g: list[int], b: int, variant: int) -> list[int]
         wg = sum(g[lo2:hi2 + 1])                     # (U_f * g)_k
         cnt = hi - lo + 1                            # (U_f * U_g)_k
         out.append(hb[k] - c * (wf + wg) - c * c * cnt)
+    return out
+
+
+def signed_N(variant: int, bf: int, bg: int, e: int) -> int:
+    """N of the offset reading.  The shifted coefficients lie in [0, 2^(s-1)],
+    s = bf + bg + e, one bit below the unsigned bound 2^s, so the Propositions'
+    N still holds, except for the reciprocal variant at s = 2 (bf = bg = 1,
+    e = 0), where X (X - 1) = 2 is not above 2^(s-1) = 2: there N = 2."""
+    N = variant_N_bits(variant, bf, bg, e)
+    if variant == 3 and bf + bg + e <= 2:
+        N = 2
+    return N
+
+
+def ones(n: int, Y: int) -> int:
+    """U_n(Y) = 1 + Y + ... + Y^(n-1)."""
+    return sum(Y ** i for i in range(n))
+
+
+def ks_mul_signed_offset(f: list[int], g: list[int], bf: int, bg: int, variant: int) -> Run:
+    """Signed coefficients, f in [-2^(bf-1), 2^(bf-1)), g in [-2^(bg-1), 2^(bg-1)),
+    by the offset reading (module doc): the variant's evaluations and products
+    on the signed values, K U(Y) added to what the coefficients are read from,
+    the unsigned read-off or reconstruction, K subtracted.  Returns the Run with
+    h the signed coefficients and `halves` holding the shifted integers."""
+    lf, lg = len(f), len(g)
+    lh = lf + lg - 1
+    e = ceil_log(min(lf, lg), 2)
+    N = signed_N(variant, bf, bg, e)
+    K = 1 << (bf + bg - 2 + e)
+    X = 1 << N
+    if variant == 1:
+        P = evaluate(f, X) * evaluate(g, X)
+        Ps = P + K * ones(lh, X)
+        hs = [digit(Ps, k, X) for k in range(lh)]
+        return Run(1, X, [c - K for c in hs], {}, {"P": P}, {"P'": Ps})
+    Y = X * X
+    n0, n1 = (lh + 1) // 2, lh // 2
+    if variant == 2:
+        Fp, Fm = eval_pm(f, X)
+        Gp, Gm = eval_pm(g, X)
+        Pp, Pm = Fp * Gp, Fm * Gm
+        E, O = (Pp + Pm) // 2, (Pp - Pm) // (2 * X)
+        Es, Os = E + K * ones(n0, Y), O + K * ones(n1, Y)
+        hs = [digit(Es, k // 2, Y) if k % 2 == 0 else digit(Os, k // 2, Y) for k in range(lh)]
+        return Run(2, X, [c - K for c in hs], {}, {"P+": Pp, "P-": Pm}, {"E'": Es, "O'": Os})
+    if variant == 3:
+        P = evaluate(f, X) * evaluate(g, X)
+        R = evaluate(f[::-1], X) * evaluate(g[::-1], X)
+        Ps, Rs = P + K * ones(lh, X), R + K * ones(lh, X)
+        rec = recover(Ps, Rs, lh, X)
+        return Run(3, X, [c - K for c in rec.h], {}, {"P": P, "R": R}, {"P'": Ps, "R'": Rs},
+                   [rec])
+    Fp, Fm = eval_pm(f, X)
+    Gp, Gm = eval_pm(g, X)
+    Frp, Frm = eval_pm(f[::-1], X)
+    Grp, Grm = eval_pm(g[::-1], X)
+    Pp, Pm, Rp, Rm = Fp * Gp, Fm * Gm, Frp * Grp, Frm * Grm
+    E, O = (Pp + Pm) // 2, (Pp - Pm) // (2 * X)
+    ER, OR = (Rp + Rm) // 2, (Rp - Rm) // (2 * X)
+    # each holds the coefficients of one parity class of h or of rev h
+    Es, Os = E + K * ones(n0, Y), O + K * ones(n1, Y)
+    ERs, ORs = ER + K * ones(n0, Y), OR + K * ones(n1, Y)
+    even_pair = (Es, ERs) if lh % 2 == 1 else (Es, ORs)
+    odd_pair = (Os, ORs) if lh % 2 == 1 else (Os, ERs)
+    hs = [0] * lh
+    recs = [recover(even_pair[0], even_pair[1], n0, Y)]
+    hs[0::2] = recs[0].h
+    if n1 > 0:
+        recs.append(recover(odd_pair[0], odd_pair[1], n1, Y))
+        hs[1::2] = recs[1].h
+    return Run(4, X, [c - K for c in hs], {},
+               {"P+": Pp, "P-": Pm, "R+": Rp, "R-": Rm},
+               {"E'": Es, "O'": Os, "ER'": ERs, "OR'": ORs}, recs)
+
+
+def recover_chains(fwd: int, rev: int, n: int, X: int, m: int, exact: list[int]) -> list[int]:
+    """The reconstruction of Sec. 3.2 split into chains of m coefficients that
+    need no predecessor: chain c covers [c m, (c + 1) m).  An odd chain runs
+    upward from s = c m, an even one downward from s = (c + 1) m, both started
+    by the exact pair (c_(s-1), c_s) taken from `exact` (a downward chain is the
+    same recurrence on the reversed problem x^(n-1) h(1/x), whose fwd is rev and
+    whose rev is fwd).  An even chain whose s would reach n runs downward from
+    n without a seed (the reversed problem's start at index 0).  Each pair of
+    exact values therefore starts two chains."""
+    u = [digit(fwd, i, X) for i in range(n + 1)]
+    w = [digit(rev, n - j, X) for j in range(n + 1)]
+    out = [None] * n
+
+    def chain(du, dw, length, seed, last_at):
+        # du[t], dw[t]: the chain's own digits u, w at step t (t = 0 .. length)
+        if seed is None:
+            a_prev, a_cur, delta = 0, du[0], 0
+        else:
+            sp, sc = seed
+            a_prev, b_prev, a_cur = sp % X, sp // X, sc % X
+            d_prev = (du[0] - b_prev - a_cur) % X
+            assert d_prev in (0, 1)
+            delta = (b_prev + a_cur + d_prev - du[0]) // X
+        w_cur = dw[0]
+        res = []
+        for t in range(length):
+            if t != last_at:
+                eps = 1 if a_cur > dw[t + 1] else 0
+                beta = (w_cur - a_prev - eps) % X
+                a_next = (du[t + 1] - beta - delta) % X
+                d_next = (beta + a_next + delta - du[t + 1]) // X
+                assert d_next in (0, 1)
+                res.append(a_cur + X * beta)
+                a_prev, a_cur, delta, w_cur = a_cur, a_next, d_next, dw[t + 1]
+            else:
+                res.append(a_cur + X * ((w_cur - a_prev) % X))
+        return res
+
+    nch = (n + m - 1) // m
+    for c in range(nch):
+        lo, hi = c * m, min((c + 1) * m, n)
+        if c % 2 == 1:                       # upward from s = c m
+            s = lo
+            du = [u[s + t] for t in range(hi - s + 1)]
+            dw = [w[s + t] for t in range(hi - s + 1)]
+            vals = chain(du, dw, hi - s, (exact[s - 1], exact[s]),
+                         (n - 1 - s) if hi == n else -1)
+            for t, v in enumerate(vals):
+                out[s + t] = v
+        else:                                # downward from s = (c + 1) m, or from n
+            s = hi
+            seeded = s <= n - 1
+            du = [w[s - t] for t in range(s - lo + 1)]
+            dw = [u[s - t] for t in range(s - lo + 1)]
+            seed = (exact[s], exact[s - 1]) if seeded else None
+            vals = chain(du, dw, s - lo, seed, (s - 1) if lo == 0 else -1)
+            for t, v in enumerate(vals):
+                out[s - 1 - t] = v
     return out

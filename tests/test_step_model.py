@@ -281,3 +281,88 @@ def test_unequal_bit_sizes_N_is_tight_for_ks1():
     assert S.ks1(f, g, 2 ** (N - 1)).h != pyref.poly_mul(f, g)
     # and the unequal-size N is smaller than the equal-size one at max(bf, bg)
     assert N < S.variant_N(1, max(bf, bg), e)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("bf,bg", [(1, 1), (2, 2), (8, 8), (48, 48), (64, 64), (5, 17), (1, 30)])
+def test_signed_offset_reading(variant, bf, bg):
+    # signed evaluations, K U(Y) added to the integers read, K subtracted: the schoolbook
+    # product on random operands and on the extremes (the largest positive h_k is
+    # min(Lf, Lg) 2^(bf-1) 2^(bg-1) = K exactly when every pair is (-2^(bf-1), -2^(bg-1)))
+    rng = random.Random(31 * bf + bg + 7 * variant)
+    lo_f, hi_f = -(1 << (bf - 1)), (1 << (bf - 1)) - 1
+    lo_g, hi_g = -(1 << (bg - 1)), (1 << (bg - 1)) - 1
+    for lf, lg in SHAPES:
+        f = [rng.randint(lo_f, hi_f) for _ in range(lf)]
+        g = [rng.randint(lo_g, hi_g) for _ in range(lg)]
+        r = S.ks_mul_signed_offset(f, g, bf, bg, variant)
+        assert r.h == pyref.poly_mul(f, g), (lf, lg)
+        for rec in r.recoveries:
+            _check_recovery_invariants(rec, r.X if variant == 3 else r.X * r.X)
+        for a, c in [(lo_f, lo_g), (lo_f, hi_g), (hi_f, lo_g), (hi_f, hi_g)]:
+            fe, ge = [a] * lf, [c] * lg
+            assert S.ks_mul_signed_offset(fe, ge, bf, bg, variant).h == pyref.poly_mul(fe, ge)
+
+
+def test_signed_offset_range_fits_every_read():
+    # the shifted coefficients lie in [0, 2K]; the top is reached by the all-minimum
+    # product, and it must fit what each variant reads: a field of N (Sec. 3.1) or 2N
+    # (Sec. 3.3) bits, and c < X (X - 1) for the reconstruction (Sec. 3.2: beta < X - 1)
+    r = S.ks_mul_signed_offset([-1], [-1, -1, -1], 1, 1, 3)
+    assert r.h == [1, 1, 1]
+    for bf in range(1, 9):
+        for bg in range(1, 9):
+            for e in range(0, 7):
+                top = 2 << (bf + bg - 2 + e)          # 2K
+                N = [S.signed_N(v, bf, bg, e) for v in (1, 2, 3, 4)]
+                assert top < 1 << N[0]
+                assert top < 1 << (2 * N[1])
+                X3, Y4 = 1 << N[2], 1 << (2 * N[3])
+                assert top < X3 * (X3 - 1), (bf, bg, e)
+                assert top < Y4 * (Y4 - 1)
+    # at bf = bg = 1, e = 0 the reciprocal variant's own N = 1 gives X (X - 1) = 2 = 2K
+    assert S.variant_N_bits(3, 1, 1, 0) == 1 and S.signed_N(3, 1, 1, 0) == 2
+
+
+@pytest.mark.parametrize("X", [10, 2 ** 7, 2 ** 28, 2 ** 56])
+@pytest.mark.parametrize("n,m", [(1, 4), (3, 4), (4, 4), (5, 4), (8, 4), (9, 4), (12, 4),
+                                 (13, 4), (64, 8), (100, 16), (97, 32)])
+def test_chains_alternate_down_and_up(X, n, m):
+    # chain c covers [c m, (c+1) m): odd chains upward, even chains downward, one exact
+    # pair (c_(s-1), c_s) at every s = m (2j + 1) starting two chains; the top chain
+    # runs down from n without a seed
+    rng = random.Random(X + 13 * n + m)
+    c, fwd, rev = _rand_recoverable(n, X, rng)
+    assert S.recover_chains(fwd, rev, n, X, m, c) == c
+    # the chains read the exact values only at the pair positions
+    used = {s + d for s in range(m, n, 2 * m) for d in (-1, 0)}
+    masked = [c[i] if i in used else None for i in range(n)]
+    assert S.recover_chains(fwd, rev, n, X, m, masked) == c
+
+
+def test_chains_fail_with_a_wrong_seed():
+    rng = random.Random(5)
+    X, n, m = 2 ** 20, 64, 8
+    c, fwd, rev = _rand_recoverable(n, X, rng)
+    bad = list(c)
+    bad[m] += 1                          # the first pair's c_s off by one
+    try:
+        out = S.recover_chains(fwd, rev, n, X, m, bad)
+    except AssertionError:
+        return                           # a carry check caught it
+    assert out != c
+
+
+def test_planted_offset_slip_fails(monkeypatch):
+    # shifting one coefficient too few (U_(n-1) for U_n) breaks the pins
+    good = S.ones
+    monkeypatch.setattr(S, "ones", lambda n, Y: good(max(n - 1, 0), Y))
+    rng = random.Random(11)
+    f = [rng.randint(-128, 127) for _ in range(9)]
+    g = [rng.randint(-128, 127) for _ in range(7)]
+    for v in (1, 2, 3, 4):
+        try:
+            bad = S.ks_mul_signed_offset(f, g, 8, 8, v).h != pyref.poly_mul(f, g)
+        except AssertionError:
+            bad = True
+        assert bad, v
