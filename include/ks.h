@@ -21,8 +21,12 @@
  *     ks_out_limbs(...) limbs;
  *   - unsigned coefficients lie in [0, 2^b); signed ones in
  *     [-2^(b-1), 2^(b-1)), two's complement, sign-extended over the limbs
- *     (Sec. 3 treats non-negative coefficients; signed ones are handled by a
- *     bias of 2^(b-1) and an exact correction, see ks_mul);
+ *     (Sec. 3 treats non-negative coefficients; for signed ones the variants
+ *     evaluate the signed coefficients as they are -- Sec. 3.3's evaluations
+ *     are signed anyway -- and read every coefficient shifted by
+ *     K = 2^(2b-2+e) >= |h_k|, which puts it in the non-negative range the
+ *     read-off and the reconstruction of Sec. 3 need; K is subtracted on
+ *     output);
  *   - h holds len_f + len_g - 1 coefficients in the same encoding.
  *
  * Pointers: "device" means memory the current CUDA device can address
@@ -31,8 +35,10 @@
  * void*, NULL = the legacy default stream) and is asynchronous unless stated.
  *
  * Errors: every call returns a ks_status; nothing is thrown across the ABI.
- * Asynchronous device-side failures (a bounded wait that gave up) are
- * reported by ks_status_sync().  On any error the output is unspecified.
+ * Asynchronous device-side failures (a bounded wait that gave up, a failed
+ * range check of the reconstruction) are reported by ks_status_sync() for
+ * the single-product calls and by ks_plan_status() for a plan.  On any error
+ * the output is unspecified.
  */
 #ifndef KS_H
 #define KS_H
@@ -95,9 +101,9 @@ int64_t ks_workspace_bytes(int64_t len_f, int64_t len_g, int coeff_bits,
  * h must not overlap f or g; f may equal g.  Workspace comes from a cache
  * the library keeps per (device, stream) and grows on demand (so the first
  * call for a size allocates; later ones do not).  Asynchronous on `stream`.
- * The phases that read only f and g (the exact seeds of Sec. 3.2's
- * reconstruction, the prefix records of the signed correction) run on a
- * helper stream the library creates on the first call per (device, stream),
+ * The phase that reads only f and g (the exact seeds of Sec. 3.2's
+ * reconstruction) runs on a helper stream the library creates on the first
+ * call per (device, stream),
  * forked from and joined back into `stream` with events; as seen from
  * `stream` the call is ordered like any other work on it, and it can be
  * captured into a CUDA graph (the helper stream becomes a parallel branch).
@@ -240,6 +246,15 @@ enum { KS_DISPATCH_AUTO = 0, KS_DISPATCH_KS1 = 1, KS_DISPATCH_TABLE = 2, KS_DISP
 int ks_plan_create(ks_plan **plan, const ks_problem *probs, int64_t n, int dispatch_mode);
 int ks_plan_execute(ks_plan *plan, ks_stream_t stream);
 int ks_plan_capture(ks_plan *plan, ks_stream_t stream);
+/*
+ * The plan's own device status word (Sec. 3.2's reconstruction checks its
+ * carries delta, epsilon in {0, 1}; every device wait of the plan's kernels is
+ * bounded): waits for the stream of the plan's last execute, reads the word,
+ * clears it and returns KS_OK, KS_ETIMEOUT (a bounded wait gave up) or
+ * KS_ERANGE (a range check failed).  KS_EINVAL for NULL; KS_ECUDA if the
+ * wait or the copy fails.  Other plans and single calls do not touch it.
+ */
+int ks_plan_status(ks_plan *plan);
 /* Kernel launches of the last non-graph execute; device bytes the plan holds. */
 long long ks_plan_launches(const ks_plan *plan);
 int64_t ks_plan_workspace_bytes(const ks_plan *plan);
@@ -310,11 +325,19 @@ const char *ks_last_cuda_error(void);
  * waits for those events and returns, per phase id (0 .. n-1, names from
  * ks_phase_name), the summed milliseconds and the number of records, then
  * clears them.  Phases: 0 pack, 1 product, 2 normalize, 3 unpack, 4 seeds,
- * 5 recover, 6 signed_fix, 7 reduce_mod, 8 signed_prefix.  Seeds and
- * signed_prefix read only f and g and run on a helper stream concurrently
- * with phases 0-3 (their events are recorded on that stream).
+ * 5 recover, 6 reduce_mod.  Seeds read only f and g and run on a helper
+ * stream concurrently with the normalization (their events are recorded on
+ * that stream).
  */
 long long ks_launch_count(void);
+
+/*
+ * Host-side fault injection for tests (no counterpart in the paper): the next
+ * n device allocations the library makes (cached workspaces, plans) fail as
+ * if the device were out of memory, so the calls return KS_ENOMEM.  No device
+ * is touched by the failure.  n <= 0 clears it.
+ */
+void ks_debug_fail_allocs(int n);
 
 /*
  * The plan ks_mul_ex would run, as int64 fields (n of them are written):
@@ -322,7 +345,7 @@ long long ks_launch_count(void);
  * f-side operand, 6 digits of each g-side operand, 7 column sums per
  * sub-product, 8 words per normalized value, 9 normalized values,
  * 10 reconstruction digit bits M (0 for KS_1 / KS_2), 11 chain length,
- * 12 seed coefficients, 13 output limbs, 14 input limbs, 15 workspace bytes,
+ * 12 exact seed values (two per seed pair of each run), 13 output limbs, 14 input limbs, 15 workspace bytes,
  * 16 log2 of the transform length (NTT engine, else 0), 17-20 workspace byte
  * offsets of the digits, column sums, normalized words and seeds, 21 words
  * per seed, 22-23 reconstruction chains of the two runs.

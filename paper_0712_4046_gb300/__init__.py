@@ -57,6 +57,8 @@ _sig("ks_plan_launches", ctypes.c_longlong, _vp)
 _sig("ks_plan_workspace_bytes", _i64, _vp)
 _sig("ks_plan_choice", _ci, _vp, _i64, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
 _sig("ks_plan_destroy", None, _vp)
+_sig("ks_plan_status", _ci, _vp)
+_sig("ks_debug_fail_allocs", None, _ci)
 
 DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
 
@@ -90,7 +92,7 @@ PLAN_FIELDS = ("variant", "engine", "N", "d", "nprod", "nA", "nB", "ncols", "nwo
                "off_digits", "off_cols", "off_words", "off_seeds", "seed_words", "nchains0",
                "nchains1")
 
-N_PHASES = 9
+N_PHASES = 7
 
 
 class KSError(RuntimeError):
@@ -120,6 +122,55 @@ def _dptr(t):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _limbs(bits: int) -> int:
+    return (int(bits) + 63) // 64
+
+
+def _check_poly(t, rows, limbs, name) -> None:
+    """A polynomial tensor of the layout the C ABI reads: (rows, limbs), 8-byte
+    elements, contiguous.  Checked before any device pointer is taken, so a
+    wrongly shaped tensor never reaches the kernels."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s: expected a torch tensor" % name)
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("%s: expected dtype int64 or uint64, got %s" % (name, t.dtype))
+    if t.dim() != 2:
+        raise ValueError("%s: expected a 2-d tensor (coefficients, limbs), got %d-d"
+                         % (name, t.dim()))
+    want_rows = t.shape[0] if rows is None else rows
+    if tuple(t.shape) != (want_rows, limbs) or t.shape[0] < 1:
+        raise ValueError("%s: expected shape (%s, %d), got %s"
+                         % (name, want_rows if rows is not None else "L >= 1", limbs,
+                            tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s: expected a contiguous tensor" % name)
+
+
+def _check_device(*ts) -> None:
+    """All tensors on the current CUDA device (the C ABI works there, and its
+    streams, caches and status word are per device)."""
+    import torch
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("expected CUDA tensors")
+    dev = torch.cuda.current_device()
+    for t in ts:
+        if t.device.index != dev:
+            raise ValueError("tensor on cuda:%d, but the current device is cuda:%d; "
+                             "call inside torch.cuda.device(...)" % (t.device.index, dev))
+
+
+def _check_product(h, f, g, bits_f, bits_g, is_signed) -> None:
+    if bits_f < 1 or bits_g < 1:
+        raise ValueError("coefficient bits must be >= 1")
+    _check_poly(f, None, _limbs(bits_f), "f")
+    _check_poly(g, None, _limbs(bits_g), "g")
+    ol = out_limbs(f.shape[0], g.shape[0], max(bits_f, bits_g), is_signed)
+    _check_poly(h, f.shape[0] + g.shape[0] - 1, ol, "h")
+    _check_device(h, f, g)
 
 
 def out_limbs(len_f: int, len_g: int, coeff_bits: int, is_signed: bool) -> int:
@@ -152,11 +203,14 @@ def choose(len_f, len_g, coeff_bits, is_signed):
 
 def ks_mul(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
     """h = f * g with device tensors (L, limbs); h preallocated (Lh, out_limbs)."""
+    _check_product(h, f, g, coeff_bits, coeff_bits, is_signed)
     _check(lib.ks_mul(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
                       int(is_signed), variant, _stream_ptr(stream)), "ks_mul")
 
 
 def ks_mul_ex(h, f, g, coeff_bits, is_signed, variant, engine, workspace, stream=None):
+    _check_product(h, f, g, coeff_bits, coeff_bits, is_signed)
+    _check_device(workspace)
     _check(lib.ks_mul_ex(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
                          int(is_signed), variant, engine, _dptr(workspace),
                          workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
@@ -170,6 +224,12 @@ def ks_mul_host(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_A
     for a in (h, f, g):
         if not (isinstance(a, np.ndarray) and a.dtype == np.uint64 and a.flags.c_contiguous):
             raise ValueError("expected C-contiguous uint64 numpy arrays")
+    il = _limbs(coeff_bits)
+    if f.ndim != 2 or g.ndim != 2 or f.shape[1] != il or g.shape[1] != il:
+        raise ValueError("f and g must be (L, %d) arrays" % il)
+    ol = out_limbs(f.shape[0], g.shape[0], coeff_bits, is_signed)
+    if h.shape != (f.shape[0] + g.shape[0] - 1, ol):
+        raise ValueError("h must be (%d, %d)" % (f.shape[0] + g.shape[0] - 1, ol))
     _check(lib.ks_mul_host(h.ctypes.data, f.ctypes.data, f.shape[0], g.ctypes.data, g.shape[0],
                            coeff_bits, int(is_signed), variant, engine, _stream_ptr(stream)),
            "ks_mul_host")
@@ -180,11 +240,17 @@ def ks_mul_static(h, f, g, coeff_bits, is_signed, variant=KS_AUTO, stream=None):
     device array inside the library (STATIC_SCRATCH_BYTES), for callers that
     may not allocate device memory at call time.  Calls sharing the array must
     not overlap on the GPU; larger problems raise KSError (KS_ERANGE)."""
+    _check_product(h, f, g, coeff_bits, coeff_bits, is_signed)
     _check(lib.ks_mul_static(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], coeff_bits,
                              int(is_signed), variant, _stream_ptr(stream)), "ks_mul_static")
 
 
 def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
+    """(Z/pZ)[x] product: residues in [0, p), one limb each; h is (Lf + Lg - 1, 1)."""
+    _check_poly(f, None, 1, "f")
+    _check_poly(g, None, 1, "g")
+    _check_poly(h, f.shape[0] + g.shape[0] - 1, 1, "h")
+    _check_device(h, f, g)
     _check(lib.ks_mul_mod(_dptr(h), _dptr(f), f.shape[0], _dptr(g), g.shape[0], p, variant,
                           _stream_ptr(stream)), "ks_mul_mod")
 
@@ -192,6 +258,7 @@ def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
 def ks_mul_bits(h, f, bits_f, g, bits_g, is_signed, variant=KS_AUTO, stream=None):
     """h = f g with bits_f-bit coefficients in f and bits_g-bit ones in g (device
     tensors of shape (L, ceil(bits / 64))); h has out_limbs(.., max(bits), ..) limbs."""
+    _check_product(h, f, g, bits_f, bits_g, is_signed)
     _check(lib.ks_mul_bits(_dptr(h), _dptr(f), f.shape[0], bits_f, _dptr(g), g.shape[0], bits_g,
                            int(is_signed), variant, _stream_ptr(stream)), "ks_mul_bits")
 
@@ -199,11 +266,16 @@ def ks_mul_bits(h, f, bits_f, g, bits_g, is_signed, variant=KS_AUTO, stream=None
 def ks_mul_bivariate_mod(h, f, g, p, variant=KS_AUTO, stream=None):
     """(Z/pZ)[x, y] product (Sec. 2): f, g are (ly, lx) device tensors of residues
     (row i, column j: the coefficient of x^j y^i); h is (2 ly - 1, 2 lx - 1)."""
+    import torch
     if f.dim() != 2 or tuple(f.shape) != tuple(g.shape):
         raise ValueError("f and g must be (ly, lx) tensors of the same shape")
     ly, lx = f.shape
     if tuple(h.shape) != (2 * ly - 1, 2 * lx - 1):
         raise ValueError("h must be (2 ly - 1, 2 lx - 1)")
+    for t, n in ((h, "h"), (f, "f"), (g, "g")):
+        if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+            raise ValueError("%s: expected a contiguous int64 or uint64 tensor" % n)
+    _check_device(h, f, g)
     _check(lib.ks_mul_bivariate_mod(_dptr(h), _dptr(f), _dptr(g), lx, ly, p, variant,
                                     _stream_ptr(stream)), "ks_mul_bivariate_mod")
 
@@ -211,6 +283,7 @@ def ks_mul_bivariate_mod(h, f, g, p, variant=KS_AUTO, stream=None):
 def _problems(problems):
     arr = (KSProblem * len(problems))()
     for i, q in enumerate(problems):
+        _check_product(q["h"], q["f"], q["g"], q["coeff_bits"], q["coeff_bits"], q["is_signed"])
         arr[i] = KSProblem(_dptr(q["h"]).value, _dptr(q["f"]).value, _dptr(q["g"]).value,
                            q["f"].shape[0], q["g"].shape[0], q["coeff_bits"],
                            int(q["is_signed"]), q.get("variant", KS_AUTO),
@@ -239,6 +312,11 @@ class Plan:
 
     def capture(self, stream):
         _check(lib.ks_plan_capture(self.ptr, _stream_ptr(stream)), "ks_plan_capture")
+
+    def status(self) -> None:
+        """Waits for the plan's last execute and raises KSError if its device
+        status word records a failure (a bounded wait that gave up, a range check)."""
+        _check(lib.ks_plan_status(self.ptr), "ks_plan_status")
 
     def launches(self) -> int:
         return int(lib.ks_plan_launches(self.ptr))
@@ -270,6 +348,8 @@ def status_sync(stream=None) -> None:
 def mul(f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO, stream=None):
     """Allocating convenience wrapper: returns h = f * g as a new device tensor."""
     import torch
+    _check_poly(f, None, _limbs(coeff_bits), "f")
+    _check_poly(g, None, _limbs(coeff_bits), "g")
     ol = out_limbs(f.shape[0], g.shape[0], coeff_bits, is_signed)
     h = torch.empty((f.shape[0] + g.shape[0] - 1, ol), dtype=torch.int64, device=f.device)
     if engine == ENGINE_AUTO:
@@ -280,6 +360,12 @@ def mul(f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO, stream
                          dtype=torch.int64, device=f.device)
         ks_mul_ex(h, f, g, coeff_bits, is_signed, variant, engine, ws, stream)
     return h
+
+
+def debug_fail_allocs(n: int) -> None:
+    """Host-side fault injection: the library's next n device allocations fail
+    (the calls return KS_ENOMEM); 0 clears it."""
+    lib.ks_debug_fail_allocs(int(n))
 
 
 def launch_count() -> int:

@@ -12,8 +12,6 @@
 
 namespace ks {
 
-size_t signed_prefix_bytes(int64_t lf, int64_t lg, int il);
-
 static thread_local char g_cuda_err[256] = "";
 
 static int cuda_fail(cudaError_t e) {
@@ -87,6 +85,15 @@ int variant_N(int variant, int b, int e) {
   }
 }
 
+// N for signed inputs (the offset reading): every coefficient is read shifted
+// into [0, 2^(2b-1+e)], one bit below the unsigned bound, so the
+// Propositions' N holds, except for the reciprocal variant at 2b + e = 2,
+// where X (X - 1) = 2 does not exceed the shifted top 2: there N = 2.
+int signed_N(int variant, int b, int e) {
+  const int N = variant_N(variant, b, e);
+  return (variant == KS_3 && 2 * b + e <= 2) ? 2 : N;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine) {
@@ -104,7 +111,9 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.b = b;
   p.is_signed = is_signed ? 1 : 0;
   p.e = ceil_log2(lf < lg ? lf : lg);
-  p.N = variant_N(variant, b, p.e);
+  p.N = is_signed ? signed_N(variant, b, p.e) : variant_N(variant, b, p.e);
+  // signed: every coefficient is read shifted by K = 2^(2b-2+e) >= |h_k|
+  p.kb = is_signed ? 2 * b - 2 + p.e : -1;
   p.in_limbs = (b + 63) / 64;
   p.out_limbs = (2 * b + p.e + p.is_signed + 63) / 64;
   p.d = engine == KS_ENGINE_TC ? 7 : 16;
@@ -164,11 +173,16 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     while (c2 < p.chain) c2 <<= 1;
     p.chain = c2;
     p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
-    p.nseeds = 0;
-    for (int r = 0; r < p.nruns; r++) {
-      p.nchains[r] = (p.run_n[r] + p.chain - 1) / p.chain;
-      p.nseeds += 2 * (p.nchains[r] - 1);
-    }
+    for (int r = 0; r < p.nruns; r++) p.nchains[r] = (p.run_n[r] + p.chain - 1) / p.chain;
+    // one seed cluster per pair position s = chain (2j + 1) of the longer run:
+    // (h_(s-1), h_s) for Sec. 3.2, (h_(2s-2), h_(2s-1), h_(2s), h_(2s+1)) for
+    // Sec. 3.4 (both runs' pairs at once)
+    const int a = variant == KS_3 ? 1 : 2;
+    p.C = 2 * a;
+    p.ncl = run_pairs(p.run_n[0], p.chain);
+    p.k00 = a * p.chain - a;
+    p.kstep = 2 * a * p.chain;
+    p.nseeds = p.ncl * p.C;
   }
   // workspace layout
   size_t off = 0;
@@ -180,17 +194,16 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
                              (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3)) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
-  p.off_seedacc = off;  // right after the column sums: one clearing pass covers both
-  off = align256(off + (size_t)p.nseeds * 6 * 8);
+  p.off_seedacc = off;  // narrow seeds: six words per (value, slice), each written once
+  if (b <= 64 && p.nseeds > 0)
+    off = align256(off + (size_t)p.nseeds * seed_slices(lf, lg, p.C) * 6 * 8);
   p.off_flags = off;
   p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
   off = align256(p.off_flags + (size_t)p.flag_bytes);
   p.off_words = off;
   off = align256(off + (size_t)p.nnorm * p.nwords * 4);
   p.off_seeds = off;
-  off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
-  p.off_prefix = off;
-  if (p.is_signed) off = align256(off + signed_prefix_bytes(lf, lg, p.in_limbs));
+  if (b > 64) off = align256(off + (size_t)p.nseeds * p.seed_words * 4);
   p.off_hp = off;  // exact product for ks_mul_mod (sized by the caller)
   p.off_ntt = off;
   if (engine == KS_ENGINE_NTT) off = align256(off + ntt_workspace_bytes(p.ntt_log, p.nprod));
@@ -306,16 +319,14 @@ bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *en
 }
 
 // --------------------------------------------------------------- execution
-// A helper stream and three events per (device, caller stream): the seeds and
-// the signed prefix records read only f and g, so they run on the helper
-// stream, forked after the products (the persistent product kernels want
-// every SM) and overlapping the normalization and reconstruction; the seeds
-// are joined before the reconstruction, the prefix records before the signed
-// correction.  Created on first use (no device memory) and kept.
+// A helper stream and two events per (device, caller stream): the exact seeds
+// read only f and g, so they run on the helper stream, forked after the
+// products and overlapping the normalization; they are joined before the
+// reconstruction.  Created on first use (no device memory) and kept.
 struct Fork {
   int dev;
   cudaStream_t stream, side;
-  cudaEvent_t fork, join_seeds, join_prefix;
+  cudaEvent_t fork, join;
 };
 static std::mutex g_fork_mu;
 static std::vector<Fork> g_forks;
@@ -329,18 +340,89 @@ static int fork_for(cudaStream_t s, Fork *out) {
       *out = x;
       return KS_OK;
     }
-  Fork x{dev, s, nullptr, nullptr, nullptr, nullptr};
+  Fork x{dev, s, nullptr, nullptr, nullptr};
   KS_CUDA(cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking));
   KS_CUDA(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
-  KS_CUDA(cudaEventCreateWithFlags(&x.join_seeds, cudaEventDisableTiming));
-  KS_CUDA(cudaEventCreateWithFlags(&x.join_prefix, cudaEventDisableTiming));
+  KS_CUDA(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
   g_forks.push_back(x);
   *out = x;
   return KS_OK;
 }
 
+// The reconstruction runs of a plan (Sec. 3.2; twice for Sec. 3.4) over its
+// normalized combinations.
+int plan_runs(const Plan &p, const uint32_t *words, RecoverRun *runs) {
+  const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
+                 *V3 = words + 3 * p.nwords;
+  const int64_t N = p.N;
+  if (p.variant == KS_3) {
+    runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], 0, 1};
+    return 1;
+  }
+  // even coefficients: 2E with (2ER or 2X OR); odd: 2X O with (2X OR or 2ER)
+  const bool odd = (p.lh & 1) == 1;
+  runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2, p.nchains[0],
+                       0, 2};
+  if (p.nruns > 1)
+    runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
+                         p.nchains[1], 1, 3};
+  return p.nruns;
+}
+
+// The normalization jobs of a plan: which column sums combine into which
+// value, and the shift pattern of signed coefficients in each.
+void plan_norm_jobs(const Plan &p, int64_t *cols, uint32_t *words, uint32_t *flags,
+                    NormJob *jobs) {
+  auto job = [&](int i, int c1, int c2, int sigma) {
+    jobs[i] = NormJob{};
+    jobs[i].c1 = cols + (int64_t)c1 * p.ncols;
+    jobs[i].n1 = p.ncols;
+    jobs[i].c2 = c2 >= 0 ? cols + (int64_t)c2 * p.ncols : nullptr;
+    jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
+    jobs[i].sigma = sigma;
+    jobs[i].out = words + (int64_t)i * p.nwords;
+    jobs[i].flags = flags + (int64_t)i * p.ntiles;
+  };
+  // K U(Y) on the value a job holds: one bit at kb + (offset of each coefficient)
+  auto shift = [&](int i, int64_t start, int64_t stride, int64_t count) {
+    if (p.kb < 0 || count <= 0) return;
+    jobs[i].pstart = start + p.kb;
+    jobs[i].pstride = stride;
+    jobs[i].pcount = count;
+  };
+  const int64_t N = p.N, n0 = (p.lh + 1) / 2, n1 = p.lh / 2;
+  switch (p.variant) {
+    case KS_1:  // h(X): coefficient k at bit kN
+      job(0, 0, -1, 1);
+      shift(0, 0, N, p.lh);
+      break;
+    case KS_2:  // P+ + P- = 2 h0(X^2), P+ - P- = 2X h1(X^2)
+      job(0, 0, 1, 1);
+      job(1, 0, 1, -1);
+      shift(0, 1, 2 * N, n0);
+      shift(1, 1 + N, 2 * N, n1);
+      break;
+    case KS_3:  // P = h(X), R = rev h(X)
+      job(0, 0, -1, 1);
+      job(1, 1, -1, 1);
+      shift(0, 0, N, p.lh);
+      shift(1, 0, N, p.lh);
+      break;
+    case KS_4:  // 2E, 2X O, 2ER, 2X OR (ER: ceil(Lh/2) coefficients, OR: floor(Lh/2))
+      job(0, 0, 1, 1);
+      job(1, 0, 1, -1);
+      job(2, 2, 3, 1);
+      job(3, 2, 3, -1);
+      shift(0, 1, 2 * N, n0);
+      shift(1, 1 + N, 2 * N, n1);
+      shift(2, 1, 2 * N, n0);
+      shift(3, 1 + N, 2 * N, n1);
+      break;
+  }
+}
+
 // h: exact product destination (Lh x out_limbs).  ws: workspace of >= p.total.
-// fork: run the input-only phases on a helper stream (false: all on s).
+// fork: run the input-only phase on a helper stream (false: all on s).
 static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_t *g, char *ws,
                     cudaStream_t s, bool fork = true) {
   int *status = status_ptr();
@@ -350,49 +432,20 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
-  int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
-  uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
-
-  // reconstruction runs (Sec. 3.2; twice for Sec. 3.4)
-  RecoverRun runs[2];
-  if (p.variant == KS_3 || p.variant == KS_4) {
-    const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
-                   *V3 = words + 3 * p.nwords;
-    const int64_t N = p.N;
-    if (p.variant == KS_3) {
-      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
-    } else {
-      const bool odd = (p.lh & 1) == 1;
-      // even coefficients: 2E with (2ER or 2X OR); odd: 2X O with (2X OR or 2ER)
-      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
-                           p.nchains[0], seeds, 0};
-      if (p.nruns > 1)
-        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
-                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
-    }
-  }
+  unsigned long long *seed_acc = reinterpret_cast<unsigned long long *>(ws + p.off_seedacc);
+  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
 
   const bool recon = p.variant == KS_3 || p.variant == KS_4;
-  // the exact seeds; from the blocked kernel the reconstruction reads (and carries)
-  // their column sums directly
+  RecoverRun runs[2];
   SeedPlan sp;
   if (recon) {
-    if (make_seed_plan(seeds, p.seed_words,
-                       reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs, p.nruns,
-                       p.chain, f, p.lf, g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
+    plan_runs(p, words, runs);
+    if (make_seed_plan(f, p.lf, p.b, g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl, p.C,
+                       seed_acc, seeds, p.seed_words, sp) != 0)
       return KS_ERANGE;
-    if (sp.kind == 1) {
-      for (int r = 0; r < p.nruns; r++) runs[r].seed_acc = sp.bl.acc;
-      // the blocked kernel's column sums follow the products' in the workspace, and
-      // the seeds run after the products: the products' clearing pass covers them
-      if (p.engine != KS_ENGINE_NTT) {
-        nzero = (int64_t)((p.off_seedacc - p.off_cols) / 8) + sp.nseeds * 6;
-        sp.acc_cleared = true;
-      }
-    }
   }
   Fork fk{};
-  if (fork && (recon || p.is_signed)) {
+  if (fork && recon && sp.kind != 0) {
     const int rc = fork_for(s, &fk);
     if (rc != KS_OK) return rc;
   }
@@ -444,68 +497,62 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     }
   }
 
-  // the phases that read only f and g (exact seeds, signed prefix records),
-  // on the helper stream from here on
-  if (side != s) {
-    KS_CUDA(cudaEventRecord(fk.fork, s));
-    KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
+  // the exact seeds read only f and g: on the helper stream, forked after the
+  // products (the persistent product kernels want every SM, and share their
+  // SMs' shared-memory bandwidth with no one), overlapping the normalization
+  if (recon && sp.kind != 0) {
+    if (side != s) {
+      KS_CUDA(cudaEventRecord(fk.fork, s));
+      KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
+    }
+    {
+      PhaseTimer t(side, PH_SEEDS);
+      KS_CUDA(launch_seed_plan(sp, side));
+    }
+    if (side != s) KS_CUDA(cudaEventRecord(fk.join, side));
   }
-  if (recon) {
-    PhaseTimer t(side, PH_SEEDS);
-    KS_CUDA(launch_seed_plan(sp, side));
-  }
-  if (side != s) KS_CUDA(cudaEventRecord(fk.join_seeds, side));
-  if (p.is_signed) {
-    PhaseTimer t(side, PH_SIGNED_PREFIX);
-    KS_CUDA(launch_signed_prefix(p.out_limbs, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, side));
-  }
-  if (side != s) KS_CUDA(cudaEventRecord(fk.join_prefix, side));
 
-  // normalized combinations
+  // normalized combinations (with the shift of signed coefficients)
   NormJob jobs[4];
-  auto job = [&](int i, int c1, int c2, int sigma) {
-    jobs[i].c1 = cols + (int64_t)c1 * p.ncols;
-    jobs[i].n1 = p.ncols;
-    jobs[i].c2 = c2 >= 0 ? cols + (int64_t)c2 * p.ncols : nullptr;
-    jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
-    jobs[i].sigma = sigma;
-    jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].flags = flags + (int64_t)i * p.ntiles;
-  };
-  switch (p.variant) {
-    case KS_1: job(0, 0, -1, 1); break;
-    case KS_2: job(0, 0, 1, 1); job(1, 0, 1, -1); break;        // P+ + P-, P+ - P-
-    case KS_3: job(0, 0, -1, 1); job(1, 1, -1, 1); break;       // P, R
-    case KS_4: job(0, 0, 1, 1); job(1, 0, 1, -1);               // 2E, 2X O
-               job(2, 2, 3, 1); job(3, 2, 3, -1); break;        // 2ER, 2X OR
-  }
+  plan_norm_jobs(p, cols, words, flags, jobs);
   {
     PhaseTimer t(s, PH_NORMALIZE);
     KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, s));
   }
-  const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
-                 *V3 = words + 3 * p.nwords;
-
+  const uint32_t *V0 = words, *V1 = words + p.nwords;
   const int ol = p.out_limbs;
   if (p.variant == KS_1) {
     PhaseTimer t(s, PH_UNPACK);
-    KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N}, s));
+    KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N, p.kb}, s));
   } else if (p.variant == KS_2) {
     PhaseTimer t(s, PH_UNPACK);
-    KS_CUDA(launch_unpack(UnpackArgs{h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N}, s));
+    KS_CUDA(
+        launch_unpack(UnpackArgs{h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N, p.kb}, s));
   }
   if (recon) {
-    if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join_seeds, 0));
+    if (side != s && sp.kind != 0) KS_CUDA(cudaStreamWaitEvent(s, fk.join, 0));
+    RecoverArgs ra;
+    int64_t blocks = 0;
+    if (make_recover_args(h, ol, p.kb, runs, p.nruns, p.nwords, p.M, p.chain, p.C,
+                          sp.narrow() ? seed_acc : nullptr, sp.a.slices, seeds, p.seed_words,
+                          status, ra, blocks) != 0)
+      return KS_ERANGE;
     PhaseTimer t(s, PH_RECOVER);
-    KS_CUDA(launch_recover(h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words, status,
-                           s));
-  }
-  if (side != s) KS_CUDA(cudaStreamWaitEvent(s, fk.join_prefix, 0));
-  if (p.is_signed) {
-    PhaseTimer t(s, PH_SIGNED);
-    KS_CUDA(launch_signed_apply(h, ol, f, p.lf, g, p.lg, p.b, p.in_limbs, prefix, s));
+    KS_CUDA(launch_recover(ra, blocks, s));
   }
   return KS_OK;
+}
+
+// --------------------------------------------------------------- allocation
+// Every device allocation of the library goes through here, so that a test can
+// make the next n of them fail on the host (ks_debug_fail_allocs) and check
+// that the caller gets KS_ENOMEM; no device is involved in the failure.
+static std::atomic<int> g_fail_allocs{0};
+cudaError_t alloc_device(void **p, size_t bytes) {
+  int n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
 }
 
 // --------------------------------------------------------------- caches
@@ -534,7 +581,7 @@ static int cached_buffer(int kind, cudaStream_t s, size_t bytes, void **out) {
       c.ptr = nullptr;
       c.bytes = 0;
       void *p = nullptr;
-      KS_CUDA(cudaMalloc(&p, bytes));
+      KS_CUDA(alloc_device(&p, bytes));
       c.ptr = p;
       c.bytes = bytes;
       *out = p;
@@ -542,7 +589,7 @@ static int cached_buffer(int kind, cudaStream_t s, size_t bytes, void **out) {
     }
   }
   void *p = nullptr;
-  KS_CUDA(cudaMalloc(&p, bytes < 256 ? 256 : bytes));
+  KS_CUDA(alloc_device(&p, bytes < 256 ? 256 : bytes));
   g_cache.push_back(CacheEntry{dev, s, kind, p, bytes < 256 ? 256 : bytes});
   *out = p;
   return KS_OK;
@@ -871,6 +918,8 @@ const char *ks_strerror(int status) {
 
 const char *ks_last_cuda_error(void) { return g_cuda_err; }
 
+void ks_debug_fail_allocs(int n) { g_fail_allocs.store(n < 0 ? 0 : n); }
+
 long long ks_launch_count(void) { return g_launches.load(); }
 
 int ks_plan_info(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed, int variant,
@@ -923,7 +972,7 @@ int ks_profile_collect(double *ms, long long *count, int n) {
 
 const char *ks_phase_name(int phase) {
   static const char *names[] = {"pack", "product", "normalize", "unpack", "seeds", "recover",
-                                "signed_fix", "reduce_mod", "signed_prefix"};
+                                "reduce_mod"};
   return (phase >= 0 && phase < PH_COUNT) ? names[phase] : nullptr;
 }
 

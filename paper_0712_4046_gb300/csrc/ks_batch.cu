@@ -9,8 +9,8 @@
 // the INT32 and tensor-core products (the tensor-core kernel is persistent
 // over the work items of every sub-product of every product, so the four
 // sub-products of a four-point product are independent items), carry
-// normalization, unpack, seeds and reconstruction per word-size class, and the
-// signed correction -- about fifteen launches whatever the batch size.
+// normalization, unpack, seeds and reconstruction per word-size class -- about
+// a dozen launches whatever the batch size.
 // Products routed to the transform engine (large ones) run their transform
 // launches individually inside the same sequence.  The first execute on a
 // stream captures the sequence into a CUDA graph; later executes replay it.
@@ -25,6 +25,7 @@
 namespace ks {
 
 int *status_ptr();
+cudaError_t alloc_device(void **p, size_t bytes);
 int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *variant,
                 int *engine);
 bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *engines);
@@ -76,14 +77,6 @@ struct NttJob {
   int nprod, log_n, d;
   char *scratch;
 };
-struct SingleJob {  // products whose signed correction needs the long-prefix path
-  uint64_t *h;
-  int ol;
-  const uint64_t *f, *g;
-  int64_t lf, lg;
-  int b, il;
-  uint64_t *prefix;
-};
 }  // namespace
 
 }  // namespace ks
@@ -105,43 +98,26 @@ struct ks_plan {
   ks::List<ks::NormArgs> norm[2];   // digit width 16 and 28 (tensor cores): tile pass
   ks::List<ks::NormArgs> normc[2];  // the same descriptors, carry-pass block counts
   ks::List<ks::UnpackArgs> unpack;
-  ks::List<ks::SeedBArgs> seedb;
-  ks::List<ks::SeedArgs> seedk[7];  // kinds 2, 102, 104, 108, 116, 132, 164
+  ks::List<ks::SeedArgs> seeds[ks::kSeedKinds];  // per kernel kind (kSeedKindList)
   ks::List<ks::RecoverArgs> recover[3];
   int recover_smem = 0;  // class 1: the largest staged-digit buffer of the batch
-  ks::List<ks::PrefArgs> pref;
-  ks::List<ks::FixArgs> fix;
   std::vector<ks::NttJob> ntt;
-  std::vector<ks::SingleJob> singles;
   int64_t tc_work = 0;
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
+  cudaStream_t last_stream = nullptr;  // where the last execute ran (ks_plan_status)
   int device = 0;
-  // the seeds and the signed prefix records read only the inputs: they run on
-  // a helper stream, forked after the products (whose persistent kernels want
-  // every SM) and joined before the reconstruction and the signed correction
-  // respectively (in a captured graph: a parallel branch)
+  int *status = nullptr;  // the plan's device status word (the first bytes of ws)
+  // the seeds read only the inputs: they run on a helper stream, forked after
+  // the products and joined before the reconstruction (in a captured graph: a
+  // parallel branch)
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace ks {
 namespace {
-int seed_kind_index(int kind) {
-  switch (kind) {
-    case 2: return 0;
-    case 102: return 1;
-    case 104: return 2;
-    case 108: return 3;
-    case 116: return 4;
-    case 132: return 5;
-    case 164: return 6;
-  }
-  return -1;
-}
-const int kSeedKinds[7] = {2, 102, 104, 108, 116, 132, 164};
-
 #define KS_TRY(call)                                  \
   do {                                                \
     cudaError_t e_ = (call);                          \
@@ -165,28 +141,21 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
                                    P->school.blocks(), s));
   if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, s));
   for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
-  const bool fork = P->side != nullptr && (P->seedb.n() || P->pref.n() || [&] {
-    for (int i = 0; i < 7; i++)
-      if (P->seedk[i].n()) return true;
-    return false;
-  }());
+  // the seeds read only the inputs: on the helper stream, forked after the
+  // products, joined before the reconstruction
+  bool any_seeds = false;
+  for (int i = 0; i < kSeedKinds; i++) any_seeds = any_seeds || P->seeds[i].n() > 0;
+  const bool fork = P->side != nullptr && any_seeds;
   cudaStream_t side = fork ? P->side : s;
   if (fork) {
     KS_TRY(cudaEventRecord(P->ev_fork, s));
     KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
   }
-  if (P->seedb.n())
-    KS_TRY(launch_seeds_blocked_batch(P->seedb.d, P->seedb.dprefix, P->seedb.n(),
-                                      P->seedb.blocks(), side));
-  for (int i = 0; i < 7; i++)
-    if (P->seedk[i].n())
-      KS_TRY(launch_seeds_kind_batch(kSeedKinds[i], P->seedk[i].d, P->seedk[i].dprefix,
-                                     P->seedk[i].n(), P->seedk[i].blocks(), side));
+  for (int i = 0; i < kSeedKinds; i++)
+    if (P->seeds[i].n())
+      KS_TRY(launch_seeds_batch(kSeedKindList[i], P->seeds[i].d, P->seeds[i].dprefix,
+                                P->seeds[i].n(), P->seeds[i].blocks(), side));
   if (fork) KS_TRY(cudaEventRecord(P->ev_join, side));
-  if (P->pref.n())
-    KS_TRY(launch_signed_prefix_batch(P->pref.d, P->pref.dprefix, P->pref.n(), P->pref.blocks(),
-                                      side));
-  if (fork) KS_TRY(cudaEventRecord(P->ev_join2, side));
   for (int c = 0; c < 2; c++)
     if (P->norm[c].n())
       KS_TRY(launch_normalize_batch(c == 0 ? 16 : 28, P->norm[c].d, P->norm[c].dprefix,
@@ -200,11 +169,6 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     if (P->recover[c].n())
       KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
                                   P->recover[c].n(), P->recover[c].blocks(), P->recover_smem, s));
-  if (fork) KS_TRY(cudaStreamWaitEvent(s, P->ev_join2, 0));
-  if (P->fix.n())
-    KS_TRY(launch_signed_apply_batch(P->fix.d, P->fix.dprefix, P->fix.n(), P->fix.blocks(), s));
-  for (auto &j : P->singles)
-    KS_TRY(launch_signed_fix(j.h, j.ol, j.f, j.lf, j.g, j.lg, j.b, j.il, j.prefix, s));
   return cudaSuccess;
 }
 }  // namespace
@@ -263,81 +227,39 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     }
   }
   NormJob jobs[4];
-  auto job = [&](int i, int c1, int c2, int sigma) {
-    jobs[i].c1 = cols + (int64_t)c1 * p.ncols;
-    jobs[i].n1 = p.ncols;
-    jobs[i].c2 = c2 >= 0 ? cols + (int64_t)c2 * p.ncols : nullptr;
-    jobs[i].n2 = c2 >= 0 ? p.ncols : 0;
-    jobs[i].sigma = sigma;
-    jobs[i].out = words + (int64_t)i * p.nwords;
-    jobs[i].flags = flags + (int64_t)i * p.ntiles;
-  };
-  switch (p.variant) {
-    case KS_1: job(0, 0, -1, 1); break;
-    case KS_2: job(0, 0, 1, 1); job(1, 0, 1, -1); break;
-    case KS_3: job(0, 0, -1, 1); job(1, 1, -1, 1); break;
-    case KS_4: job(0, 0, 1, 1); job(1, 0, 1, -1); job(2, 2, 3, 1); job(3, 2, 3, -1); break;
-  }
+  plan_norm_jobs(p, cols, words, flags, jobs);
   NormArgs na;
   if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
   P->norm[p.dn == 28 ? 1 : 0].add(na, norm_blocks(na));
   P->normc[p.dn == 28 ? 1 : 0].add(na, norm_carry_blocks(na));
-  const uint32_t *V0 = words, *V1 = words + p.nwords, *V2 = words + 2 * p.nwords,
-                 *V3 = words + 3 * p.nwords;
+  const uint32_t *V0 = words, *V1 = words + p.nwords;
   const int ol = p.out_limbs;
   if (p.variant == KS_1 || p.variant == KS_2) {
     UnpackArgs ua = p.variant == KS_1
-                        ? UnpackArgs{q.h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N}
-                        : UnpackArgs{q.h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N};
+                        ? UnpackArgs{q.h, ol, p.lh, V0, nullptr, p.nwords, 0, p.N, p.N, p.kb}
+                        : UnpackArgs{q.h, ol, p.lh, V0, V1, p.nwords, 1, p.N, 2 * p.N, p.kb};
     P->unpack.add(ua, unpack_blocks(ua));
   } else {
     RecoverRun runs[2];
-    const int64_t N = p.N;
-    if (p.variant == KS_3) {
-      runs[0] = RecoverRun{V0, 0, V1, 0, p.lh, 0, 1, p.nchains[0], seeds, 0};
-    } else {
-      const bool odd = (p.lh & 1) == 1;
-      runs[0] = RecoverRun{V0, 1, odd ? V2 : V3, odd ? 1 : N + 1, p.run_n[0], 0, 2,
-                           p.nchains[0], seeds, 0};
-      if (p.nruns > 1)
-        runs[1] = RecoverRun{V1, N + 1, odd ? V3 : V2, odd ? N + 1 : 1, p.run_n[1], 1, 2,
-                             p.nchains[1], seeds, 2 * (p.nchains[0] - 1)};
-    }
+    plan_runs(p, words, runs);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws + p.off_seedacc);
     SeedPlan sp;
-    if (make_seed_plan(seeds, p.seed_words,
-                       reinterpret_cast<unsigned long long *>(ws + p.off_seedacc), runs, p.nruns,
-                       p.chain, q.f, p.lf, q.g, p.lg, p.b, p.in_limbs, p.is_signed, sp) != 0)
+    if (make_seed_plan(q.f, p.lf, p.b, q.g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl,
+                       p.C, acc, seeds, p.seed_words, sp) != 0)
       return KS_ERANGE;
-    if (sp.kind == 1) {
-      // the reconstruction reads the seeds from the column sums themselves
-      for (int r = 0; r < p.nruns; r++) runs[r].seed_acc = sp.bl.acc;
-      P->seedb.add(sp.bl, sp.blocks);
-      const int64_t nz = sp.nseeds * 6;
-      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(sp.bl.acc), nz}, (nz + 255) / 256);
-    } else if (sp.kind != 0) {
+    if (sp.kind != 0) {
       const int i = seed_kind_index(sp.kind);
       if (i < 0) return KS_ERANGE;
-      P->seedk[i].add(sp.a, sp.blocks);
+      P->seeds[i].add(sp.a, sp.blocks);
     }
     RecoverArgs ra;
     int64_t blocks;
-    if (make_recover_args(q.h, ol, runs, p.nruns, p.nwords, p.M, p.chain, p.seed_words, status,
+    if (make_recover_args(q.h, ol, p.kb, runs, p.nruns, p.nwords, p.M, p.chain, p.C,
+                          sp.narrow() ? acc : nullptr, sp.a.slices, seeds, p.seed_words, status,
                           ra, blocks) != 0)
       return KS_ERANGE;
     P->recover[recover_class(p.M) - 1].add(ra, blocks);
     if (ra.smem > P->recover_smem) P->recover_smem = ra.smem;
-  }
-  if (p.is_signed) {
-    PrefArgs pr;
-    FixArgs fx;
-    int64_t pb, fb;
-    uint64_t *prefix = reinterpret_cast<uint64_t *>(ws + p.off_prefix);
-    if (make_signed_args(q.h, ol, q.f, p.lf, q.g, p.lg, p.b, p.in_limbs, prefix, pr, fx, pb, fb)) {
-      P->pref.add(pr, pb);
-      P->fix.add(fx, fb);
-    } else {
-      P->singles.push_back(SingleJob{q.h, ol, q.f, q.g, p.lf, p.lg, p.b, p.in_limbs, prefix});
-    }
   }
   return KS_OK;
 }
@@ -384,21 +306,26 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   }
   if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ECUDA;
   }
-  P->ws_bytes = total < 256 ? 256 : total;
-  if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+  // the plan's status word, then every product's workspace
+  P->ws_bytes = 256 + total;
+  if (alloc_device(reinterpret_cast<void **>(&P->ws), P->ws_bytes) != cudaSuccess) {
     P->ws = nullptr;
     ks_plan_destroy(P);
     return KS_ENOMEM;
   }
-  int *status = status_ptr();
+  P->status = reinterpret_cast<int *>(P->ws);
+  if (cudaMemset(P->status, 0, 256) != cudaSuccess) {
+    ks_plan_destroy(P);
+    return KS_ECUDA;
+  }
+  int *status = P->status;
   for (int64_t i = 0; i < n; i++) {
     const Plan &p = P->plans[i];
-    char *ws = P->ws + offs[i];
+    char *ws = P->ws + 256 + offs[i];
     int rc = add_product(P, p, probs[i], ws, status);
     if (rc == KS_OK && p.engine == KS_ENGINE_TC) {
       TcArgs ta;
@@ -418,11 +345,12 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
               P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->normc[0].bytes() +
               P->normc[1].bytes() + P->unpack.bytes() +
-              P->seedb.bytes() + P->pref.bytes() + P->fix.bytes();
-  for (int i = 0; i < 7; i++) db += P->seedk[i].bytes();
+              0;
+  for (int i = 0; i < kSeedKinds; i++) db += P->seeds[i].bytes();
   for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
   P->desc_bytes = db;
-  if (cudaMalloc(&P->desc, db) != cudaSuccess || cudaMallocHost(&P->hdesc, db) != cudaSuccess) {
+  if (alloc_device(reinterpret_cast<void **>(&P->desc), db) != cudaSuccess ||
+      cudaMallocHost(&P->hdesc, db) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ENOMEM;
   }
@@ -438,11 +366,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     P->normc[c].d = P->norm[c].d;  // both lists describe the same jobs
   }
   P->unpack.place(h, d);
-  P->seedb.place(h, d);
-  for (int i = 0; i < 7; i++) P->seedk[i].place(h, d);
+  for (int i = 0; i < kSeedKinds; i++) P->seeds[i].place(h, d);
   for (int c = 0; c < 3; c++) P->recover[c].place(h, d);
-  P->pref.place(h, d);
-  P->fix.place(h, d);
   if (cudaMemcpy(P->desc, P->hdesc, db, cudaMemcpyHostToDevice) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ECUDA;
@@ -457,6 +382,7 @@ int ks_plan_execute(ks_plan *P, ks_stream_t stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return KS_EINVAL;
   const long long before = ks_launch_count();
+  P->last_stream = s;
   if (P->graph != nullptr && P->graph_stream == s) {
     if (cudaGraphLaunch(P->graph, s) != cudaSuccess) return KS_ECUDA;
     return KS_OK;
@@ -498,6 +424,27 @@ int ks_plan_capture(ks_plan *P, ks_stream_t stream) {
   return KS_OK;
 }
 
+int ks_plan_status(ks_plan *P) {
+  if (P == nullptr || P->status == nullptr) return KS_EINVAL;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return KS_ECUDA;
+  if (cur != P->device && cudaSetDevice(P->device) != cudaSuccess) return KS_ECUDA;
+  int rc = KS_OK, v = 0;
+  cudaStream_t s = P->last_stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpyAsync(&v, P->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = KS_ECUDA;
+  } else if (v != 0) {
+    rc = v == 1 ? KS_ETIMEOUT : KS_ERANGE;
+    if (cudaMemsetAsync(P->status, 0, sizeof(int), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = KS_ECUDA;
+  }
+  if (cur != P->device) cudaSetDevice(cur);
+  return rc;
+}
+
 long long ks_plan_launches(const ks_plan *P) { return P ? P->launches : -1; }
 
 int64_t ks_plan_workspace_bytes(const ks_plan *P) {
@@ -523,7 +470,6 @@ void ks_plan_destroy(ks_plan *P) {
   if (P->hdesc) cudaFreeHost(P->hdesc);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
-  if (P->ev_join2) cudaEventDestroy(P->ev_join2);
   if (P->side) cudaStreamDestroy(P->side);
   cudaSetDevice(cur);
   delete P;

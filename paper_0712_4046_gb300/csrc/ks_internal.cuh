@@ -13,7 +13,7 @@ namespace ks {
 // ---------------------------------------------------------------- limits
 constexpr int kMaxOperands = 8;      // 4 sub-products x 2 sides
 constexpr int kMaxSeedWords = 136;   // exact seeds: (2b + e) bits, b <= 2048
-constexpr int kAccSeedWords = 8;     // seed words of the blocked (b <= 64) seed path, at most
+constexpr int kAccSeedWords = 8;     // words of a narrow seed value (six column sums, mod 2^192)
 constexpr int kMaxDigitWordsM = 72;  // reconstruction digit: M <= 2304 bits
 
 // ---------------------------------------------------------------- planning
@@ -41,6 +41,7 @@ struct Plan {
   int64_t ncols = 0;    // column sums per sub-product
   int64_t nwords = 0;   // 32-bit words per normalized combination
   int nnorm = 0;        // normalized combinations (1, 2, 2, 4)
+  int kb = -1;           // signed: coefficients are read shifted by K = 2^kb
   // reconstruction (Sec. 3.2; run twice for Sec. 3.4)
   int M = 0;            // digit bits: N (KS3) or 2N (KS4)
   int nruns = 0;
@@ -48,13 +49,16 @@ struct Plan {
   int64_t chain = 0;
   int64_t nchains[2] = {0, 0};
   int seed_words = 0;
-  int64_t nseeds = 0;
+  int C = 0;            // seed values per cluster: 2 (KS3) or 4 (KS4)
+  int64_t ncl = 0;      // seed clusters (the pairs of the longest run)
+  int64_t k00 = 0, kstep = 0;  // first h index of cluster j: k00 + kstep j
+  int64_t nseeds = 0;   // seed values: ncl C
   // number-theoretic-transform engine
   int ntt_log = 0;      // transform length 2^ntt_log
   // workspace layout (byte offsets from the base)
   size_t off_digits = 0, off_cols = 0, off_flags = 0, off_words = 0;
   int64_t flag_bytes = 0;  // the normalization's per-tile transfer functions
-  size_t off_seeds = 0, off_seedacc = 0, off_prefix = 0, off_hp = 0, off_status = 0, off_ntt = 0;
+  size_t off_seeds = 0, off_seedacc = 0, off_hp = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
 };
@@ -65,6 +69,7 @@ int variant_N(int variant, int b, int e);
 int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant,
               int engine);
 int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine);
+int signed_N(int variant, int b, int e);
 
 // ---------------------------------------------------------------- kernels
 struct PackOp {
@@ -184,9 +189,12 @@ struct NormJob {
   int64_t n1;
   const int64_t *c2;  // may be null
   int64_t n2;
-  int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k)
+  int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k) + sum_i 2^(pstart + i pstride)
   uint32_t *out;
   uint32_t *flags;    // one transfer function per scan tile (written by the tile pass)
+  // the shift of signed coefficients: one bit per coefficient read from this
+  // value (K U(Y) with K = 2^kb); pcount = 0 for none
+  int64_t pstart = 0, pstride = 1, pcount = 0;
 };
 
 // Normalizes up to 4 column-sum combinations into two's complement words
@@ -215,8 +223,17 @@ cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *pre
 // scan tiles of a combination of nwords words at digit width d
 int64_t norm_tiles_for(int64_t nwords, int d);
 
+struct RecoverRun;
+// The reconstruction runs of a plan over its normalized values (returns nruns),
+// and its normalization jobs (which column sums combine, the shift pattern).
+int plan_runs(const Plan &p, const uint32_t *words, RecoverRun *runs);
+void plan_norm_jobs(const Plan &p, int64_t *cols, uint32_t *words, uint32_t *flags,
+                    NormJob *jobs);
+
 // KS1 / KS2 unpack: h'_k = bits [off + kN, off + kN + width) of V (k even) or
 // V_odd (k odd).
+// Signed coefficients arrive shifted by K = 2^kb (kb < 0: unsigned, no shift);
+// the unpack subtracts it.
 struct UnpackArgs {
   uint64_t *h;
   int ol;
@@ -225,65 +242,88 @@ struct UnpackArgs {
   const uint32_t *V_odd;
   int64_t nwords, off, N;
   int width;
+  int kb;
 };
 cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s);
 int64_t unpack_blocks(const UnpackArgs &a);
 cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int n,
                                 int64_t blocks, cudaStream_t s);
 
+// One run of the reconstruction of Sec. 3.2 (KS3: one run over h; KS4: one
+// run over the even-index and one over the odd-index coefficients): the digit
+// strings fwd = sum c_i X^i (Vf, from bit off_f) and rev = sum c_(n-1-i) X^i
+// (Vr, from bit off_r) of its n coefficients, c_i = h'_(kbase + kstride i).
+// The run is cut into chains of `chain` coefficients, chain c covering
+// [c chain, (c + 1) chain): an odd chain runs upward from s = c chain, an even
+// one downward from s = (c + 1) chain -- the same recurrence on the reversed
+// problem x^(n-1) h(1/x), whose fwd is rev and whose rev is fwd -- so one exact
+// pair (c_(s-1), c_s) at every s = chain (2j + 1) starts two chains.  An even
+// chain whose s would reach n runs downward from n without seeds.  The pair
+// j of this run is cluster j of the seed kernel, values slot_prev (c_(s-1))
+// and slot_cur (c_s).
 struct RecoverRun {
   const uint32_t *Vf;
   int64_t off_f;
   const uint32_t *Vr;
   int64_t off_r;
-  int64_t n;           // coefficients in this run
+  int64_t n;               // coefficients in this run
   int64_t kbase, kstride;  // h index of run coefficient i: kbase + kstride * i
-  int64_t nchains;
-  const uint32_t *seeds;   // 2 values per chain c >= 1 (seed_words words each)
-  int64_t seed_base;       // index of this run's first seed value
-  // when set, the seeds are read (and carried) from these 64-bit column sums,
-  // 6 per value, instead of from `seeds` (the blocked seed kernel's output)
-  const unsigned long long *seed_acc;
+  int64_t nchains;         // ceil(n / chain)
+  int slot_prev, slot_cur;
 };
+// Chain c of a run: its direction, start s, length, and whether it is seeded.
+__host__ __device__ __forceinline__ void chain_geom(int64_t n, int64_t chain, int64_t c,
+                                                    bool &up, int64_t &s, int64_t &len,
+                                                    bool &seeded) {
+  const int64_t lo = c * chain;
+  const int64_t hi = lo + chain < n ? lo + chain : n;
+  up = (c & 1) != 0;
+  s = up ? lo : hi;
+  len = hi - lo;
+  seeded = up || hi <= n - 1;
+}
+// seed pairs of a run: every s = chain (2j + 1) <= n - 1
+__host__ __device__ __forceinline__ int64_t run_pairs(int64_t n, int64_t chain) {
+  return n - 1 >= chain ? (n - 1 - chain) / (2 * chain) + 1 : 0;
+}
 
-// Exact coefficients h'_k (biased, unsigned) for the chain starts.
+// Exact values h'_k (h_k + K for signed inputs, K = 2^kb) for the chain
+// starts: ncl clusters of C consecutive k, cluster j starting at
+// k0 = k00 + kstep j.  Value r of cluster j is value index j C + r.
 struct SeedArgs {
-  RecoverRun run[2];
-  int nruns;
-  int64_t chain;
-  uint32_t *seeds;
+  const uint64_t *f, *g;
+  int64_t lf, lg;
+  int bf, bg, ilf, ilg;  // coefficient bits and limbs of each operand
+  int sgn;               // two's complement inputs
+  int kb;                // K = 2^kb is added (sgn), else kb < 0
+  int64_t k00, kstep, ncl;
+  int C;
+  int64_t slices, tslice;   // narrow path: items per cluster, indices t per item
+  // narrow path: per (value, slice) six 32-bit words of the slice's partial
+  // (value v, slice s at acc + (v slices + s) 6)
+  unsigned long long *acc;
+  uint32_t *seeds;          // wide path: seed_words words per value
   int seed_words;
-  const uint64_t *f, *g;
-  int64_t lf, lg;
-  int b, in_limbs, flip;
-};
-struct SeedBArgs {  // blocked path (b <= 64): groups x t-slices, 64-bit word sums
-  RecoverRun run[2];
-  int nruns;
-  int64_t chain;
-  int64_t groups[2];
-  int64_t slices, nseeds;
-  unsigned long long *acc;  // 6 per seed; the reconstruction carries them into seed words
-  const uint64_t *f, *g;
-  int64_t lf, lg;
-  int b, in_limbs, flip;
 };
 struct SeedPlan {
-  int kind = 0;  // 0 none, 1 blocked, 2 one 64-bit word, 100 + words: templated
+  // 0 none; 1-6 narrow (both operands <= 64 bits; by path and cluster size);
+  // 100 + words: wide
+  int kind = 0;
   SeedArgs a;
-  SeedBArgs bl;
-  int64_t blocks = 0, nseeds = 0;
-  bool acc_cleared = false;  // kind 1: the column sums are already zero (no clearing launch)
+  int64_t blocks = 0, nvalues = 0;
+  bool narrow() const { return kind >= 1 && kind < 100; }
 };
-// seed_acc: scratch of 6 64-bit words per seed (the b <= 64 blocked path).
-int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
-                   const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
-                   const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp);
+// items per seed cluster of the narrow path (slices of its t range)
+int64_t seed_slices(int64_t lf, int64_t lg, int C);
+int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int64_t lg, int bg,
+                   int sgn, int kb, int64_t k00, int64_t kstep, int64_t ncl, int C,
+                   unsigned long long *acc, uint32_t *seeds, int seed_words, SeedPlan &sp);
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s);
-cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks, int n,
-                                       int64_t blocks, cudaStream_t s);
-cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
-                                    int64_t blocks, cudaStream_t s);
+cudaError_t launch_seeds_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
+                               int64_t blocks, cudaStream_t s);
+int seed_kind_index(int kind);  // 0 .. kSeedKinds - 1, or -1
+constexpr int kSeedKinds = 12;  // six narrow kinds, then wide classes of 2 .. 64 words
+extern const int kSeedKindList[kSeedKinds];
 
 struct RecoverArgs {
   RecoverRun run[2];
@@ -291,63 +331,30 @@ struct RecoverArgs {
   int64_t nwords;
   int M;
   int64_t chain;
-  int seed_words;
   uint64_t *h;
   int ol;
+  int kb;              // signed: subtract K = 2^kb from every coefficient
   int *status;
+  // the exact seed values: value index (pair C + slot)
+  int C;
+  const unsigned long long *seed_acc;  // narrow seeds: six words per (value, slice)
+  int64_t seed_slices;
+  const uint32_t *seeds;               // wide seeds: seed_words words per value
+  int seed_words;
   int64_t rblocks[2];  // M <= 63: CTAs of cpc chains per run
   int smem;            // M <= 63: staged digit words of one CTA (bytes)
   int cpc;             // M <= 63: chains per CTA (a power of two, 8 .. 32)
 };
-int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
-                      int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,
+int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int nruns,
+                      int64_t nwords, int M, int64_t chain, int C,
+                      const unsigned long long *seed_acc, int64_t seed_slices,
+                      const uint32_t *seeds, int seed_words, int *status, RecoverArgs &a,
                       int64_t &blocks);
 int recover_class(int M);
-cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
-                           int64_t nwords, int M, int64_t chain, int seed_words,
-                           int *status, cudaStream_t s);
+cudaError_t launch_recover(const RecoverArgs &a, int64_t blocks, cudaStream_t s);
 // smem: the largest RecoverArgs::smem of the batch (class 1)
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
                                  int64_t blocks, int smem, cudaStream_t s);
-
-// Signed inputs: h_k = h'_k - 2^(b-1) (W_f,k + W_g,k) - 2^(2b-2) cnt_k mod 2^(64 ol).
-struct PrefArgs {
-  const uint64_t *x[2];
-  int64_t L[2];
-  int64_t nblocks[2];
-  int il;
-  uint64_t *P[2];    // per element: il x (lo, hi), then the negative count
-  uint64_t *bt;      // per block: the same record, block totals -> exclusive offsets
-};
-struct FixArgs {
-  uint64_t *h;
-  int ol;
-  int64_t lf, lg;
-  int b, il;
-  const uint64_t *pf, *pg;  // prefix records
-  const uint64_t *f, *g;    // the coefficients
-  const uint64_t *tf, *tg;  // unused (null)
-};
-// true when the short path applies (lengths <= 16384, in_limbs <= 8, ol <= 17):
-// one scanning CTA per polynomial (pref_blocks = 2), then the correction
-bool make_signed_args(uint64_t *h, int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
-                      int64_t lg, int b, int in_limbs, uint64_t *prefix, PrefArgs &a,
-                      FixArgs &fx, int64_t &pref_blocks, int64_t &fix_blocks);
-// The correction in two parts: the prefix records of f and g (inputs only),
-// then the correction of h; launch_signed_fix issues both in order.
-cudaError_t launch_signed_prefix(int ol, const uint64_t *f, int64_t lf, const uint64_t *g,
-                                 int64_t lg, int b, int in_limbs, uint64_t *prefix,
-                                 cudaStream_t s);
-cudaError_t launch_signed_apply(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
-                                const uint64_t *g, int64_t lg, int b, int in_limbs,
-                                uint64_t *prefix, cudaStream_t s);
-cudaError_t launch_signed_fix(uint64_t *h, int ol, const uint64_t *f, int64_t lf,
-                              const uint64_t *g, int64_t lg, int b, int in_limbs,
-                              uint64_t *prefix, cudaStream_t s);
-cudaError_t launch_signed_prefix_batch(const PrefArgs *pa, const int64_t *pref_prefix, int n,
-                                       int64_t pref_blocks, cudaStream_t s);
-cudaError_t launch_signed_apply_batch(const FixArgs *fa, const int64_t *fix_prefix, int n,
-                                      int64_t fix_blocks, cudaStream_t s);
 
 // (Z/pZ)[x, y] by the substitutions of Sec. 2 (ks_biv.cu).
 constexpr int kMaxBivEvals = 8;
@@ -391,8 +398,8 @@ cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t 
 // Kernel launches issued by the library (host counter), and optional per-phase
 // CUDA-event timing on the caller's stream.
 void note_launches(int n);
-enum Phase { PH_PACK = 0, PH_PRODUCT, PH_NORMALIZE, PH_UNPACK, PH_SEEDS, PH_RECOVER, PH_SIGNED,
-             PH_MOD, PH_SIGNED_PREFIX, PH_COUNT };
+enum Phase { PH_PACK = 0, PH_PRODUCT, PH_NORMALIZE, PH_UNPACK, PH_SEEDS, PH_RECOVER, PH_MOD,
+             PH_COUNT };
 struct PhaseTimer {
   cudaStream_t s;
   int phase;
@@ -513,7 +520,9 @@ __device__ __forceinline__ void coeff_bits128(const uint64_t *c, int x, int in_l
 // Digits j0 .. j0 + K - 1 of one evaluation.  Digit j (bits [jd, jd + d)) is
 // the sum over the coefficients t whose field [tN, tN + b) meets the window of
 // +- their bits inside it, with the sign -1 for odd t at the point -2^N
-// (Sec. 3.3, 3.4).  One pair of divisions finds the coefficient fields that meet the K-digit
+// (Sec. 3.3, 3.4).  Signed coefficients (flip) are two's complement: bit
+// b - 1 weighs -2^(b-1), so the evaluation is exact on the signed values
+// themselves (the digits of a piece stay within +-(2^D - 1)).  One pair of divisions finds the coefficient fields that meet the K-digit
 // window [lo, lo + K D); each field contributes the window's bits of its
 // coefficient placed at its offset (one 128-bit extraction), which split
 // into the K digits by compile-time shifts.
@@ -566,6 +575,17 @@ __device__ __forceinline__ void digit_run(const PackOp &op, int64_t j0, int64_t 
         bits = (wlo >> sh) | (whi << (64 - sh));
       const int32_t piece = (int32_t)(bits & ((1ull << D) - 1ull));
       v[m] += neg ? -piece : piece;
+    }
+    if (flip) {
+      // signed input: the pieces above are those of c + 2^(b-1) (bit b-1
+      // flipped); the field's top bit takes the bias back, with the field's sign
+      const int top = off + b - 1;
+#pragma unroll
+      for (int m = 0; m < K; m++)
+        if (top >= m * D && top < m * D + D) {
+          const int32_t bias = (int32_t)1 << (top - m * D);
+          v[m] += neg ? bias : -bias;
+        }
     }
   }
 }

@@ -83,9 +83,14 @@ __device__ __forceinline__ uint32_t compose2(uint32_t g, uint32_t f) {
 
 // s_j of a thread's WPT words from its BACK + CPT staged columns (x[i] is
 // column kstart - BACK + i); every offset and shift is a compile-time constant.
+//
+// J's shift pattern (one bit at pstart + i pstride, i < pcount: the K U(Y) of
+// signed coefficients) is added to T before the fold, so that its carries
+// travel with the others.
 template <int D>
 __device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + Geo<D>::CPT],
-                                             int64_t (&s)[Geo<D>::WPT]) {
+                                             int64_t (&s)[Geo<D>::WPT], const NormJob &J,
+                                             int64_t j0) {
   constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
   int64_t T[WPT + 1];  // T[w + 1]: slices landing in word j0 + w, w = -1 .. WPT-1
 #pragma unroll
@@ -103,6 +108,20 @@ __device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + G
     if (q >= -1 && q <= WPT - 1) T[q + 1] += sl0;
     if (q + 1 >= -1 && q + 1 <= WPT - 1) T[q + 2] += sl1;
     if (q + 2 >= -1 && q + 2 <= WPT - 1) T[q + 3] += sl2;
+  }
+  if (J.pcount > 0) {
+    // pattern bits in words j0 - 1 .. j0 + WPT - 1, bits [b0, b1)
+    const int64_t b0 = 32 * (j0 - 1), b1 = 32 * (j0 + WPT);
+    int64_t i = b0 > J.pstart ? (b0 - J.pstart + J.pstride - 1) / J.pstride : 0;
+    for (; i < J.pcount; i++) {
+      const int64_t rel = J.pstart + i * J.pstride - b0;
+      if (rel >= b1 - b0) break;
+      const int w = (int)(rel >> 5);
+      const int64_t bit = (int64_t)1 << (rel & 31);
+#pragma unroll
+      for (int q = 0; q <= WPT; q++)
+        if (q == w) T[q] += bit;
+    }
   }
 #pragma unroll
   for (int w = 0; w < WPT; w++) s[w] = (int64_t)(uint32_t)T[w + 1] + (T[w] >> 32);
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
       if (two) v += sigma > 0 ? s_c2[idx] : -s_c2[idx];
       x[i] = v;
     }
-    thread_words<D>(x, s[u]);
+    thread_words<D>(x, s[u], a.job[nsub * group + u], j0);
     int64_t cm = -1, cz = 0, cp = 1;
 #pragma unroll
     for (int w = 0; w < WPT; w++) {

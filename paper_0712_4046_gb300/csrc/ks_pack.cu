@@ -14,8 +14,10 @@
 // sub-product engines take these signed digits as they are, and the single
 // carry normalization after the products resolves every carry at once.
 //
-// Signed inputs are biased to unsigned b-bit values by flipping bit b-1
-// (c + 2^(b-1)); the exact correction is applied after unpacking.
+// Signed inputs are two's complement b-bit values: bit b-1 of a coefficient
+// weighs -2^(b-1).  The pieces are taken from c + 2^(b-1) (bit b-1 flipped,
+// non-negative) and the digit holding the field's top bit takes 2^(b-1) back,
+// so the digits evaluate the signed polynomial itself.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -101,7 +103,12 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
         } else {
           piece = (uint32_t)((coeff_limb(c, 0, il, b, flip) << (-x)) & 0xFFFFull);
         }
-        if (piece) atomicAdd(&sd[d - D0], neg ? -(int32_t)piece : (int32_t)piece);
+        int32_t val = (int32_t)piece;
+        if (flip) {  // the bias of a signed coefficient leaves at its top bit
+          const int top = (int)(pos + b - 1 - 16 * d);
+          if (top >= 0 && top < 16) val -= (int32_t)1 << top;
+        }
+        if (val) atomicAdd(&sd[d - D0], neg ? -val : val);
       }
     }
     __syncthreads();

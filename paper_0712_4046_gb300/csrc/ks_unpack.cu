@@ -6,7 +6,8 @@
 namespace ks {
 
 // ------------------------------------------------------------------ unpack
-// h'_k = bits [off + kN, off + kN + width) of V (or of V_odd for odd k).
+// h'_k = bits [off + kN, off + kN + width) of V (or of V_odd for odd k), and
+// h_k = h'_k - 2^kb for signed inputs (kb >= 0).
 // KS1: V = h(2^N), off = 0, width N.  KS2: V = P+ + P- = 2 h0(X^2) and
 // V_odd = P+ - P- = 2X h1(X^2); then both even and odd coefficients sit at
 // bit 1 + kN, width 2N (Sec. 3.3).
@@ -36,10 +37,23 @@ __global__ void __launch_bounds__(256) unpack_kernel(Src src) {
     }
     const uint32_t *src_w = (a.V_odd != nullptr && (k & 1)) ? a.V_odd : a.V;
     const int rem = a.width - 64 * l;
+    const int64_t pos = a.off + k * a.N;
     uint64_t v = 0;
     if (rem > 0) {
-      v = get_bits64(src_w, a.nwords, a.off + k * a.N + 64 * (int64_t)l);
+      v = get_bits64(src_w, a.nwords, pos + 64 * (int64_t)l);
       if (rem < 64) v &= (1ull << rem) - 1ull;
+    }
+    const int kb = a.kb;
+    if (kb >= 0) {
+      // field - 2^kb, limb l, two's complement: the field is at most 2^(kb+1)
+      // (bits kb, kb + 1 lie inside it), so a limb above K's borrows exactly
+      // when the field's bits [kb, 64 l) are all zero
+      if (64 * l <= kb) {
+        if (kb < 64 * l + 64) v -= 1ull << (kb - 64 * l);
+      } else {
+        const uint64_t top = get_bits64(src_w, a.nwords, pos + kb) & (64 * l - kb >= 2 ? 3ull : 1ull);
+        if (top == 0) v -= 1ull;
+      }
     }
     a.h[idx] = v;
   }
@@ -70,491 +84,6 @@ cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int 
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ seeds
-// Exact h'_k = sum_t f'_t g'_(k-t) (biased, non-negative b-bit inputs) for the
-// chain starts of the reconstruction: one CTA per coefficient.  A thread
-// multiplies its terms word by word (NW 32-bit words per coefficient, a
-// compile-time size so the words stay in registers) and keeps 64-bit per-word
-// sums; the CTA adds those into shared 64-bit word sums and one thread
-// propagates the carries.
-namespace {
-constexpr int kSeedThreads = 128;
-}  // namespace
-
-template <int NW>
-__device__ __forceinline__ void coeff_words(const uint64_t *c, int in_limbs, int b, int flip,
-                                            uint32_t *w) {
-#pragma unroll
-  for (int i = 0; i < NW; i++) {
-    const int rem = b - 32 * i;
-    w[i] = rem > 0 ? coeff_slice(c, in_limbs, b, flip, 32 * i, rem < 32 ? rem : 32) : 0u;
-  }
-}
-
-template <int NW, class Src>
-__global__ void __launch_bounds__(kSeedThreads) seed_kernel(Src src) {
-  __shared__ unsigned long long colsum[kMaxSeedWords];
-  int64_t sid;
-  const SeedArgs &a = src.locate(blockIdx.x, sid);
-  uint32_t *seeds = a.seeds;
-  const int seed_words = a.seed_words;
-  const uint64_t *f = a.f, *g = a.g;
-  const int64_t lf = a.lf, lg = a.lg;
-  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
-  int r = 0;
-  int64_t per_run = 2 * (a.run[0].nchains - 1);
-  while (r + 1 < a.nruns && sid >= per_run) {
-    sid -= per_run;
-    r++;
-    per_run = 2 * (a.run[r].nchains - 1);
-  }
-  const RecoverRun &R = a.run[r];
-  const int64_t c = sid / 2 + 1;
-  const int64_t i = c * a.chain - 1 + (sid & 1);
-  const int64_t k = R.kbase + R.kstride * i;
-  for (int w = threadIdx.x; w < seed_words; w += blockDim.x) colsum[w] = 0ull;
-  __syncthreads();
-
-  unsigned long long loc[2 * NW];
-#pragma unroll
-  for (int w = 0; w < 2 * NW; w++) loc[w] = 0ull;
-  int64_t t_lo = k - (lg - 1);
-  if (t_lo < 0) t_lo = 0;
-  const int64_t t_hi = k < lf - 1 ? k : lf - 1;
-  for (int64_t t = t_lo + threadIdx.x; t <= t_hi; t += blockDim.x) {
-    uint32_t fw[NW], gw[NW], pr[2 * NW];
-    coeff_words<NW>(f + t * in_limbs, in_limbs, b, flip, fw);
-    coeff_words<NW>(g + (k - t) * in_limbs, in_limbs, b, flip, gw);
-#pragma unroll
-    for (int w = 0; w < 2 * NW; w++) pr[w] = 0u;
-#pragma unroll
-    for (int x = 0; x < NW; x++) {
-      uint64_t carry = 0;
-#pragma unroll
-      for (int y = 0; y < NW; y++) {
-        const uint64_t tt = (uint64_t)fw[x] * gw[y] + pr[x + y] + carry;
-        pr[x + y] = (uint32_t)tt;
-        carry = tt >> 32;
-      }
-      pr[x + NW] = (uint32_t)carry;
-    }
-#pragma unroll
-    for (int w = 0; w < 2 * NW; w++) loc[w] += pr[w];
-  }
-#pragma unroll
-  for (int w = 0; w < 2 * NW; w++)
-    if (w < seed_words && loc[w]) atomicAdd(&colsum[w], loc[w]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t *out = seeds + (R.seed_base + sid) * seed_words;
-    unsigned long long carry = 0;
-    for (int w = 0; w < seed_words; w++) {
-      const unsigned long long v = colsum[w] + carry;
-      out[w] = (uint32_t)v;
-      carry = v >> 32;
-    }
-  }
-}
-
-// b <= 64: each coefficient is one 64-bit word; products are 128-bit and a
-// thread keeps a 192-bit running sum in three registers.
-template <class Src>
-__global__ void __launch_bounds__(kSeedThreads) seed_kernel64(Src src) {
-  __shared__ unsigned long long colsum[kMaxSeedWords];
-  int64_t sid;
-  const SeedArgs &a = src.locate(blockIdx.x, sid);
-  uint32_t *seeds = a.seeds;
-  const int seed_words = a.seed_words;
-  const uint64_t *f = a.f, *g = a.g;
-  const int64_t lf = a.lf, lg = a.lg;
-  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
-  int r = 0;
-  int64_t per_run = 2 * (a.run[0].nchains - 1);
-  while (r + 1 < a.nruns && sid >= per_run) {
-    sid -= per_run;
-    r++;
-    per_run = 2 * (a.run[r].nchains - 1);
-  }
-  const RecoverRun &R = a.run[r];
-  const int64_t c = sid / 2 + 1;
-  const int64_t i = c * a.chain - 1 + (sid & 1);
-  const int64_t k = R.kbase + R.kstride * i;
-  for (int w = threadIdx.x; w < seed_words; w += blockDim.x) colsum[w] = 0ull;
-  __syncthreads();
-  const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
-  const uint64_t fl = flip ? (1ull << (b - 1)) : 0ull;
-  uint64_t a0 = 0, a1 = 0, a2 = 0;
-  int64_t t_lo = k - (lg - 1);
-  if (t_lo < 0) t_lo = 0;
-  const int64_t t_hi = k < lf - 1 ? k : lf - 1;
-  for (int64_t t = t_lo + threadIdx.x; t <= t_hi; t += blockDim.x) {
-    const uint64_t x = (f[t * in_limbs] & mask) ^ fl;
-    const uint64_t y = (g[(k - t) * in_limbs] & mask) ^ fl;
-    const uint64_t lo = x * y, hi = __umul64hi(x, y);
-    a0 += lo;
-    const uint64_t c1 = a0 < lo;
-    const uint64_t h1 = hi + c1;  // hi <= 2^64 - 2
-    a1 += h1;
-    a2 += a1 < h1;
-  }
-  const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
-                          (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
-#pragma unroll
-  for (int w = 0; w < 6; w++)
-    if (w < seed_words && w6[w]) atomicAdd(&colsum[w], (unsigned long long)w6[w]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t *out = seeds + (R.seed_base + sid) * seed_words;
-    unsigned long long carry = 0;
-    for (int w = 0; w < seed_words; w++) {
-      const unsigned long long v = colsum[w] + carry;
-      out[w] = (uint32_t)v;
-      carry = v >> 32;
-    }
-  }
-}
-
-// Blocked seeds, b <= 64: a CTA computes kSG consecutive seeds of one run.
-// For each chunk of kST indices t it stages f'_t and the window of g' those
-// seeds need in shared memory (the seeds' k differ by at most kSW - kST), so
-// every input word is read from L2 once per CTA rather than once per seed.
-// 16 threads per seed accumulate 192-bit sums over a strided part of the chunk.
-namespace {
-constexpr int kSG = 16;
-constexpr int kST = 512;
-constexpr int kSW = 2048;
-constexpr int64_t kSlice = 2048;  // indices t per CTA
-__device__ __forceinline__ int64_t seed_k(const RecoverRun &R, int64_t chain, int64_t sid) {
-  const int64_t c = sid / 2 + 1;
-  return R.kbase + R.kstride * (c * chain - 1 + (sid & 1));
-}
-}  // namespace
-
-// 32 x 32 -> 64-bit multiply-add (one instruction)
-__device__ __forceinline__ void mad_wide(unsigned long long &acc, uint32_t x, uint32_t y) {
-  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(y));
-}
-
-// b <= 48: values split into 24-bit halves, x = xl + 2^24 xh, with xs = xl + xh;
-// x y = xl yl + (xs ys - xl yl - xh yh) 2^24 + xh yh 2^48, three multiply-adds per
-// pair whose sums over one slice (2048 t, 32 per thread) stay below 2^56.
-// Thread (sub, sq): t = sub, sub + 64, ... of each chunk, seeds sq + 4 r (r < 4),
-// one load of x serving four seeds.
-__device__ __forceinline__ uint4 split24(uint64_t v) {
-  const uint32_t lo = (uint32_t)(v & 0xFFFFFFull), hi = (uint32_t)(v >> 24);
-  return make_uint4(lo, hi, lo + hi, 0u);
-}
-
-template <class Src>
-__global__ void __launch_bounds__(256) seed_blocked64(Src src) {
-  __shared__ __align__(16) uint8_t sraw[kST * 16 + kSW * 16];
-  __shared__ unsigned long long colsum[kSG][6];
-  int64_t bid;
-  const SeedBArgs &a = src.locate(blockIdx.x, bid);
-  unsigned long long *acc = a.acc;
-  const uint64_t *f = a.f, *g = a.g;
-  const int64_t lf = a.lf, lg = a.lg;
-  const int b = a.b, in_limbs = a.in_limbs, flip = a.flip;
-  const int64_t slice = bid % a.slices;
-  int64_t gid = bid / a.slices;
-  int r = 0;
-  while (r + 1 < a.nruns && gid >= a.groups[r]) {
-    gid -= a.groups[r];
-    r++;
-  }
-  const RecoverRun &R = a.run[r];
-  const int64_t nseeds = 2 * (R.nchains - 1);
-  const int64_t sid0 = gid * kSG;
-  const int nS = (int)(nseeds - sid0 < kSG ? nseeds - sid0 : kSG);
-  const int tid = threadIdx.x;
-  for (int i = tid; i < kSG * 6; i += 256) (&colsum[0][0])[i] = 0ull;
-  const int64_t kmin = seed_k(R, a.chain, sid0);
-  const int64_t kmax = seed_k(R, a.chain, sid0 + nS - 1);
-  const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
-  const uint64_t fl = flip ? (1ull << (b - 1)) : 0ull;
-  const bool split = b <= 48;
-  // this CTA's slice of the t range
-  int64_t tlo = kmin - lg + 1 > 0 ? kmin - lg + 1 : 0;
-  int64_t thi = kmax < lf - 1 ? kmax : lf - 1;
-  const int64_t s_lo = tlo + slice * kSlice;
-  const int64_t s_hi = s_lo + kSlice - 1 < thi ? s_lo + kSlice - 1 : thi;
-  if (s_lo > s_hi) return;  // the group's t range ends before this slice (uniform)
-  if (split) {
-    uint4 *sf = reinterpret_cast<uint4 *>(sraw);
-    uint4 *sg = sf + kST;
-    const int sub = tid & 63, sq = tid >> 6;
-    int64_t kk[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) kk[u] = sq + 4 * u < nS ? seed_k(R, a.chain, sid0 + sq + 4 * u) : -1;
-    unsigned long long ll[4] = {0, 0, 0, 0}, hh[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
-    for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
-      const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
-      const int64_t jlo = kmin - t0 - T + 1;
-      const int W = (int)(kmax - kmin + T);
-      // every global load of the chunk is issued before any of them is used
-      uint64_t vf[kST / 256], vg[kSW / 256];
-#pragma unroll
-      for (int m = 0; m < kST / 256; m++) {
-        const int i = tid + 256 * m;
-        vf[m] = i < T ? f[(t0 + i) * in_limbs] : 0ull;
-      }
-#pragma unroll
-      for (int m = 0; m < kSW / 256; m++) {
-        const int i = tid + 256 * m;
-        const int64_t j = jlo + i;
-        vg[m] = (i < W && j >= 0 && j < lg) ? g[j * in_limbs] : 0ull;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int m = 0; m < kST / 256; m++) {
-        const int i = tid + 256 * m;
-        if (i < T) sf[i] = split24((vf[m] & mask) ^ fl);
-      }
-#pragma unroll
-      for (int m = 0; m < kSW / 256; m++) {
-        const int i = tid + 256 * m;
-        const int64_t j = jlo + i;
-        if (i < W) sg[i] = split24((j >= 0 && j < lg) ? ((vg[m] & mask) ^ fl) : 0ull);
-      }
-      __syncthreads();
-      int base[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) base[u] = kk[u] >= 0 ? (int)(kk[u] - t0 - jlo) : 0;
-      for (int i = sub; i < T; i += 64) {
-        const uint4 x = sf[i];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (kk[u] >= 0) {
-            const uint4 y = sg[base[u] - i];
-            mad_wide(ll[u], x.x, y.x);
-            mad_wide(hh[u], x.y, y.y);
-            mad_wide(ss[u], x.z, y.z);
-          }
-        }
-      }
-    }
-    // sums over the 64 threads of each seed: a shuffle tree in each of its two
-    // warps, then red[seed][value][warp]
-    __syncthreads();
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(sraw);
-    const int half = (tid >> 5) & 1, lane = tid & 31;
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        ll[u] += __shfl_xor_sync(0xffffffffu, ll[u], off);
-        hh[u] += __shfl_xor_sync(0xffffffffu, hh[u], off);
-        ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], off);
-      }
-      if (lane == 0) {
-        const int sd = sq + 4 * u;
-        red[(sd * 3 + 0) * 2 + half] = ll[u];
-        red[(sd * 3 + 1) * 2 + half] = hh[u];
-        red[(sd * 3 + 2) * 2 + half] = ss[u];
-      }
-    }
-    __syncthreads();
-    if (tid < nS) {
-      const unsigned long long *q = red + tid * 6;
-      const unsigned long long l = q[0] + q[1], hv = q[2] + q[3], sv = q[4] + q[5];
-      // ll + (ss - ll - hh) 2^24 + hh 2^48 as 128 bits (the middle term is non-negative)
-      const uint64_t mid = sv - l - hv;
-      const uint64_t ml = mid << 24, mh = mid >> 40;
-      const uint64_t hl = hv << 48, hhi = hv >> 16;
-      uint64_t lo = l + ml;
-      uint64_t hi = mh + hhi + (lo < ml);
-      lo += hl;
-      hi += lo < hl;
-      colsum[tid][0] = (uint32_t)lo;
-      colsum[tid][1] = (uint32_t)(lo >> 32);
-      colsum[tid][2] = (uint32_t)hi;
-      colsum[tid][3] = (uint32_t)(hi >> 32);
-    }
-  } else {
-    uint64_t *sf = reinterpret_cast<uint64_t *>(sraw);
-    uint64_t *sg = sf + kST;
-    const int sl = tid >> 4, sub = tid & 15;
-    const int64_t kk = sl < nS ? seed_k(R, a.chain, sid0 + sl) : -1;
-    uint64_t a0 = 0, a1 = 0, a2 = 0;
-    for (int64_t t0 = s_lo; t0 <= s_hi; t0 += kST) {
-      const int T = (int)(s_hi - t0 + 1 < kST ? s_hi - t0 + 1 : kST);
-      const int64_t jlo = kmin - t0 - T + 1;
-      const int W = (int)(kmax - kmin + T);
-      __syncthreads();
-      for (int i = tid; i < T; i += 256) sf[i] = (f[(t0 + i) * in_limbs] & mask) ^ fl;
-      for (int i = tid; i < W; i += 256) {
-        const int64_t j = jlo + i;
-        sg[i] = (j >= 0 && j < lg) ? ((g[j * in_limbs] & mask) ^ fl) : 0ull;
-      }
-      __syncthreads();
-      if (kk >= 0) {
-        // four independent 192-bit partial sums keep several products in flight
-        uint64_t b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
-        const int base = (int)(kk - t0 - jlo);  // sg index of t = t0
-        int i = sub;
-        for (; i + 48 < T; i += 64) {
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const uint64_t x = sf[i + 16 * u];
-            const uint64_t y = sg[base - i - 16 * u];
-            const uint64_t lo = x * y, hi = __umul64hi(x, y);
-            b0[u] += lo;
-            const uint64_t h1 = hi + (b0[u] < lo);
-            b1[u] += h1;
-            b2[u] += b1[u] < h1;
-          }
-        }
-        for (; i < T; i += 16) {
-          const uint64_t x = sf[i];
-          const uint64_t y = sg[base - i];
-          const uint64_t lo = x * y, hi = __umul64hi(x, y);
-          b0[0] += lo;
-          const uint64_t h1 = hi + (b0[0] < lo);
-          b1[0] += h1;
-          b2[0] += b1[0] < h1;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          a0 += b0[u];
-          const uint64_t c0 = a0 < b0[u];
-          const uint64_t m = b1[u] + c0;
-          const uint64_t c1 = m < c0;
-          a1 += m;
-          a2 += b2[u] + c1 + (a1 < m);
-        }
-      }
-    }
-    if (kk >= 0) {
-      const uint32_t w6[6] = {(uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1,
-                              (uint32_t)(a1 >> 32), (uint32_t)a2, (uint32_t)(a2 >> 32)};
-#pragma unroll
-      for (int w = 0; w < 6; w++)
-        if (w6[w]) atomicAdd(&colsum[sl][w], (unsigned long long)w6[w]);
-    }
-  }
-  __syncthreads();
-  if (tid < nS * 6) {
-    const int sidx = tid / 6, w = tid % 6;
-    const unsigned long long v = colsum[sidx][w];
-    if (v) atomicAdd(acc + (R.seed_base + sid0 + sidx) * 6 + w, v);
-  }
-}
-
-int make_seed_plan(uint32_t *seeds, int seed_words, unsigned long long *seed_acc,
-                   const RecoverRun *runs, int nruns, int64_t chain, const uint64_t *f, int64_t lf,
-                   const uint64_t *g, int64_t lg, int b, int in_limbs, int flip, SeedPlan &sp) {
-  sp = SeedPlan{};
-  int64_t n = 0;
-  for (int r = 0; r < nruns; r++) n += 2 * (runs[r].nchains - 1);
-  sp.nseeds = n;
-  if (n == 0) return 0;
-  if (seed_words > kMaxSeedWords) return -1;
-  SeedArgs &a = sp.a;
-  for (int r = 0; r < nruns; r++) a.run[r] = runs[r];
-  a.nruns = nruns;
-  a.chain = chain;
-  a.seeds = seeds;
-  a.seed_words = seed_words;
-  a.f = f;
-  a.g = g;
-  a.lf = lf;
-  a.lg = lg;
-  a.b = b;
-  a.in_limbs = in_limbs;
-  a.flip = flip;
-  sp.blocks = n;
-  // blocked path when the seeds of a group lie close enough together
-  bool blocked = b <= 64 && seed_words <= kAccSeedWords;
-  for (int r = 0; r < nruns && blocked; r++)
-    if (runs[r].kstride * (chain * (kSG / 2) + 1) + kST > kSW) blocked = false;
-  if (blocked) {
-    SeedBArgs &sb = sp.bl;
-    int64_t groups = 0;
-    for (int r = 0; r < nruns; r++) {
-      sb.run[r] = runs[r];
-      sb.groups[r] = (2 * (runs[r].nchains - 1) + kSG - 1) / kSG;
-      groups += sb.groups[r];
-    }
-    sb.nruns = nruns;
-    sb.chain = chain;
-    const int64_t lmin = lf < lg ? lf : lg;
-    // a group's t range is at most min(Lf, Lg) plus the spread of its k (< kSW)
-    sb.slices = (lmin + kSW + kSlice - 1) / kSlice;
-    sb.nseeds = n;
-    sb.acc = seed_acc;
-    sb.f = f;
-    sb.g = g;
-    sb.lf = lf;
-    sb.lg = lg;
-    sb.b = b;
-    sb.in_limbs = in_limbs;
-    sb.flip = flip;
-    sp.kind = 1;
-    sp.blocks = groups * sb.slices;
-    return 0;
-  }
-  const int nw = (b + 31) / 32;
-  if (b <= 64) {
-    sp.kind = 2;
-  } else {
-    int cls = 2;
-    while (cls < nw) cls *= 2;
-    if (cls > 64) return -1;
-    sp.kind = 100 + cls;  // word-count class of the templated kernel
-  }
-  return 0;
-}
-
-template <class Src>
-static void launch_seed_kind(int kind, int64_t blocks, const Src &src, cudaStream_t s) {
-  const unsigned grid = (unsigned)blocks;
-  switch (kind) {
-    case 2: seed_kernel64<Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 102: seed_kernel<2, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 104: seed_kernel<4, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 108: seed_kernel<8, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 116: seed_kernel<16, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 132: seed_kernel<32, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-    case 164: seed_kernel<64, Src><<<grid, kSeedThreads, 0, s>>>(src); break;
-  }
-}
-
-cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
-  if (sp.nseeds == 0) return cudaSuccess;
-  if (sp.kind == 1) {
-    if (!sp.acc_cleared) {
-      cudaError_t e = cudaMemsetAsync(sp.bl.acc, 0, (size_t)sp.nseeds * 6 * 8, s);
-      if (e != cudaSuccess) return e;
-    }
-    const One<SeedBArgs> one{sp.bl};
-    seed_blocked64<One<SeedBArgs>><<<(unsigned)sp.blocks, 256, 0, s>>>(one);
-    note_launches(1);
-  } else {
-    launch_seed_kind(sp.kind, sp.blocks, One<SeedArgs>{sp.a}, s);
-    note_launches(1);
-  }
-  return cudaGetLastError();
-}
-
-// batches: blocked (kind 1) products, then per kind the others
-cudaError_t launch_seeds_blocked_batch(const SeedBArgs *d, const int64_t *prefix_blocks, int n,
-                                       int64_t blocks, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  seed_blocked64<Many<SeedBArgs>><<<(unsigned)blocks, 256, 0, s>>>(
-      Many<SeedBArgs>{d, prefix_blocks, n});
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
-                                    int64_t blocks, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  launch_seed_kind(kind, blocks, Many<SeedArgs>{d, prefix, n}, s);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-
 // ------------------------------------------------------------------ recover
 // Sec. 3.2: from the base-X digits u_i of fwd = sum c_i X^i and w_i of
 // rev = sum c_(n-1-i) X^i (fwd = sum_{i<=n} u_i X^i, rev = sum_{i<=n}
@@ -567,11 +96,14 @@ cudaError_t launch_seeds_kind_batch(int kind, const SeedArgs *d, const int64_t *
 //   delta_(j+1) = (beta_j + alpha_(j+1) + delta_j - u_(j+1)) / X  in {0, 1}
 //
 // and finally beta_(n-1) = w_(n-1) - alpha_(n-2) (mod X).  The recurrence is
-// sequential; chains of `chain` steps run in parallel, chain c starting at
-// s = c * chain from the exact seeds h'_(s-1), h'_s: alpha_(s-1), alpha_s,
-// beta_(s-1) follow directly, and delta_(s-1) = u_s - beta_(s-1) - alpha_s
-// (mod X, necessarily 0 or 1) gives delta_s = (beta_(s-1) + alpha_s +
-// delta_(s-1) - u_s) / X.
+// sequential; chains of `chain` steps run in parallel.  A chain starting at s
+// from the exact values c_(s-1), c_s: alpha_(s-1), alpha_s, beta_(s-1) follow
+// directly, and delta_(s-1) = u_s - beta_(s-1) - alpha_s (mod X, necessarily 0
+// or 1) gives delta_s = (beta_(s-1) + alpha_s + delta_(s-1) - u_s) / X.  The
+// same recurrence on the reversed problem x^(n-1) h(1/x) (fwd and rev
+// exchanged) runs downward, so every exact pair starts one chain each way (see
+// RecoverRun).  Signed inputs arrive shifted by K = 2^kb, which the output
+// subtracts.
 namespace {
 
 // digit arithmetic on W 32-bit words, values in [0, 2^M)
@@ -632,40 +164,6 @@ __device__ __forceinline__ uint32_t dig_add_carry(const Dig &a, const Dig &b, ui
   if (top == 32) return (uint32_t)carry;
   return (topw >> top) & 1u;
 }
-// out limbs of alpha + 2^M beta
-__device__ void write_coeff(uint64_t *out, int ol, const Dig &al, const Dig &be, int M) {
-  const int W = (M + 31) / 32;
-  for (int l = 0; l < ol; l++) {
-    uint64_t v = 0;
-    for (int half = 0; half < 2; half++) {
-      const int64_t p0 = 64 * (int64_t)l + 32 * half;  // bit position of this 32-bit chunk
-      uint64_t chunk = 0;
-      // from alpha: bits [p0, p0+32) below M
-      if (p0 < M) {
-        const int wi = (int)(p0 >> 5);
-        uint32_t x = al.w[wi];
-        chunk |= x;  // alpha's bits above M are zero
-      }
-      // from beta: bits [p0 - M, p0 - M + 32)
-      const int64_t q = p0 - M;
-      if (q + 32 > 0 && q < (int64_t)32 * W) {
-        const int64_t wi = q >= 0 ? (q >> 5) : -1;
-        const int sh = (int)(q & 31);
-        const uint64_t lo = (wi >= 0 && wi < W) ? be.w[wi] : 0u;
-        const uint64_t hi = (wi + 1 >= 0 && wi + 1 < W) ? be.w[wi + 1] : 0u;
-        const uint64_t pair = lo | (hi << 32);
-        uint32_t part;
-        if (q >= 0)
-          part = (uint32_t)(pair >> sh);
-        else
-          part = (uint32_t)(((uint64_t)be.w[0]) << (int)(-q));  // -q < 32
-        chunk |= part;
-      }
-      v |= (chunk & 0xffffffffull) << (32 * half);
-    }
-    out[l] = v;
-  }
-}
 }  // namespace
 
 // Digits of at most 63 bits live in one 64-bit register; digits of 64..127
@@ -685,23 +183,28 @@ __device__ __forceinline__ D2 load_d2(const uint32_t *V, int64_t nwords, int64_t
   r.hi = get_bits64(V, nwords, pos + 64) & hi_mask(M);
   return r;
 }
-// Seed value i of a run as kAccSeedWords 32-bit words (the top ones zero): the
-// finished seed words, or carried from the blocked seed kernel's 64-bit column sums
-// (nw <= kAccSeedWords there).
-__device__ __forceinline__ void seed_value(const RecoverRun &R, int64_t i, int nw,
+// Seed value v as kAccSeedWords 32-bit words: the narrow seed kernel's slice
+// partials added as six 64-bit column sums and carried (mod 2^192: the top
+// words are zero), or the wide seed kernel's words.
+__device__ __forceinline__ void seed_value(const RecoverArgs &a, int64_t v,
                                            uint32_t (&out)[kAccSeedWords]) {
-  if (R.seed_acc != nullptr) {
-    const unsigned long long *acc = R.seed_acc + i * 6;
+  if (a.seed_acc != nullptr) {
+    const unsigned long long *acc = a.seed_acc + v * a.seed_slices * 6;
+    unsigned long long col[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t sl = 0; sl < a.seed_slices; sl++)
+#pragma unroll
+      for (int w = 0; w < 6; w++) col[w] += acc[sl * 6 + w];
     unsigned long long carry = 0;
 #pragma unroll
     for (int w = 0; w < kAccSeedWords; w++) {
-      const unsigned long long v = (w < 6 ? acc[w] : 0ull) + carry;
-      out[w] = w < nw ? (uint32_t)v : 0u;
-      carry = v >> 32;
+      const unsigned long long x = (w < 6 ? col[w] : 0ull) + carry;
+      out[w] = w < 6 ? (uint32_t)x : 0u;
+      carry = x >> 32;
     }
   } else {
+    const int nw = a.seed_words;
 #pragma unroll
-    for (int w = 0; w < kAccSeedWords; w++) out[w] = w < nw ? R.seeds[i * nw + w] : 0u;
+    for (int w = 0; w < kAccSeedWords; w++) out[w] = w < nw ? a.seeds[v * nw + w] : 0u;
   }
 }
 // (a - b - c) mod 2^M, c in {0, 1}
@@ -726,19 +229,29 @@ __device__ __forceinline__ uint64_t carry_d2(D2 a, D2 b, uint64_t c, int M) {
 __device__ __forceinline__ bool gt_d2(D2 a, D2 b) {
   return a.hi != b.hi ? a.hi > b.hi : a.lo > b.lo;
 }
-// out limbs of alpha + 2^M beta, alpha, beta < 2^M
-__device__ __forceinline__ void write_h1(uint64_t *out, int ol, uint64_t a, uint64_t be, int M) {
-  out[0] = a | (be << M);
-  if (ol > 1) out[1] = be >> (64 - M);
-  for (int l = 2; l < ol; l++) out[l] = 0;
+// limb l of K = 2^kb (kb < 0: no shift)
+__device__ __forceinline__ uint64_t k_limb(int kb, int l) {
+  return (kb >= 0 && (kb >> 6) == l) ? 1ull << (kb & 63) : 0ull;
 }
-__device__ __forceinline__ void write_h2(uint64_t *out, int ol, D2 a, D2 be, int M) {
+// out[l] = limb l of the value minus K, two's complement over ol limbs
+__device__ __forceinline__ uint64_t sub_k(uint64_t v, int kb, int l, uint64_t &borrow) {
+  const uint64_t k = k_limb(kb, l);
+  const uint64_t d1 = v - k;
+  const uint64_t b1 = v < k;
+  const uint64_t d2 = d1 - borrow;
+  const uint64_t b2 = d1 < borrow;
+  borrow = b1 | b2;
+  return d2;
+}
+// out limbs of alpha + 2^M beta - K, alpha, beta < 2^M (64 <= M < 128)
+__device__ __forceinline__ void write_h2(uint64_t *out, int ol, D2 a, D2 be, int M, int kb) {
   uint64_t s[5] = {a.lo, a.hi, 0, 0, 0};
-  const int r = M & 63;  // beta starts in limb 1 (64 <= M < 128)
+  const int r = M & 63;  // beta starts in limb 1
   s[1] |= be.lo << r;
   s[2] |= (r ? (be.lo >> (64 - r)) : 0ull) | (be.hi << r);
   s[3] |= r ? (be.hi >> (64 - r)) : 0ull;
-  for (int l = 0; l < ol; l++) out[l] = l < 5 ? s[l] : 0ull;
+  uint64_t borrow = 0;
+  for (int l = 0; l < ol; l++) out[l] = sub_k(l < 5 ? s[l] : 0ull, kb, l, borrow);
 }
 
 __device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, int &r) {
@@ -748,6 +261,44 @@ __device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, 
     r++;
   }
   return r < a.nruns;
+}
+
+// The strings a chain walks.  Step t of chain c reads DU(t + 1) and DW(t + 1):
+//   upward from s:   DU(t) = u_(s+t) = digit s + t of fwd,
+//                    DW(t) = w_(s+t) = digit n - s - t of rev;
+//   downward from s: DU(t) = w_(s-t) = digit n - s + t of rev,
+//                    DW(t) = u_(s-t) = digit s - t of fwd
+// (the reversed problem: fwd and rev exchanged, s -> n - s), so DU walks one
+// string up from pA and DW the other down from pB.  The chain's step t is the
+// reversed or plain run's coefficient pA + t; the last coefficient of the run
+// (pA + t = n - 1) takes beta = w - alpha_prev.  Step t outputs run coefficient
+// s + t (upward) or s - 1 - t (downward).
+struct ChainLane {
+  const uint32_t *A, *B;
+  int64_t offA, offB, pA, pB, s, len;
+  bool up, seeded;
+  int64_t vprev, vcur;  // seed value indices (seeded chains)
+};
+__device__ __forceinline__ ChainLane chain_lane(const RecoverArgs &a, const RecoverRun &R,
+                                                int64_t c) {
+  ChainLane L;
+  chain_geom(R.n, a.chain, c, L.up, L.s, L.len, L.seeded);
+  L.A = L.up ? R.Vf : R.Vr;
+  L.offA = L.up ? R.off_f : R.off_r;
+  L.B = L.up ? R.Vr : R.Vf;
+  L.offB = L.up ? R.off_r : R.off_f;
+  L.pA = L.up ? L.s : R.n - L.s;
+  L.pB = L.up ? R.n - L.s : L.s;
+  // pair j starts the downward chain 2j and the upward chain 2j + 1; the
+  // downward chain sees the pair reversed: (c_s, c_(s-1))
+  const int64_t pair = L.up ? (c - 1) >> 1 : c >> 1;
+  const int64_t vp = pair * a.C + R.slot_prev, vc = pair * a.C + R.slot_cur;
+  L.vprev = L.up ? vp : vc;
+  L.vcur = L.up ? vc : vp;
+  return L;
+}
+__device__ __forceinline__ int64_t lane_coeff(const ChainLane &L, int64_t t) {
+  return L.up ? L.s + t : L.s - 1 - t;
 }
 
 // ---- bulk copies into shared memory (one thread issues, all wait, bounded)
@@ -792,13 +343,14 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar) {
 }
 
 // M <= 63, digits staged in shared memory.  A CTA of 128 threads runs cpc
-// consecutive chains of one run (cpc <= 32, cpc * chain <= 2048):
-//  1. one bulk copy of the bit ranges of V_f and V_r those chains read (the
-//     chains are contiguous, so are their digits);
-//  2. all threads extract the digits u_j, w_m into 64-bit arrays;
+// consecutive chains of one run (cpc <= 32, cpc * chain <= 2048), which
+// cover the coefficients [j0, jhi) without gaps:
+//  1. one bulk copy of the bit ranges of V_f and V_r holding u_j and w_j,
+//     j0 <= j <= jhi (upward and downward chains read the same digits);
+//  2. all threads extract each chain's DU(t), DW(t) into [t][lane] arrays;
 //  3. warp 0, one lane per chain, runs the recurrence of Sec. 3.2 from shared
-//     memory and stages the coefficients;
-//  4. all threads write the coefficients out.
+//     memory and stages the coefficients in [position][lane] order;
+//  4. all threads write the coefficients out (minus K for signed inputs).
 constexpr int kRT = 128;
 constexpr int kRCmax = 32;
 
@@ -822,7 +374,7 @@ __host__ __device__ __forceinline__ int recover_cpc(int64_t chain) {
 __host__ __device__ __forceinline__ int64_t staged_words(int64_t chain, int M, int cpc) {
   return (((cpc * chain + 2) * (int64_t)M + 31) / 32 + 12) & ~(int64_t)3;
 }
-// digits of one string, [step t in 0..chain][lane]: lanes read consecutive words
+// digits of one string, [step t in 0..chain][lane]
 __host__ __device__ __forceinline__ int64_t staged_digits(int64_t chain, int cpc) {
   return (chain + 1) * cpc;
 }
@@ -844,7 +396,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
   }
   const RecoverRun &R = a.run[r];
   int *status = a.status;
-  const int M = a.M, ol = a.ol;
+  const int M = a.M, ol = a.ol, kb = a.kb;
   const uint64_t mask = (1ull << M) - 1ull;
   const int64_t n = R.n, chain = a.chain, nwords = a.nwords;
   const int cpc = a.cpc;
@@ -865,12 +417,9 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
     return;
   }
   uint32_t *su = stg, *sw = stg + capw;
-  // [t][lane] layouts: du(t, i) = u_(s_i + t), dw(t, i) = w_(n - s_i - t) with
-  // s_i = j0 + i chain (t = chain reaches the next chain's start), so(t, i) =
-  // coefficient s_i + t
   uint64_t *du = reinterpret_cast<uint64_t *>(stg + 2 * capw);
   uint64_t *dw = du + capd;
-  uint64_t *so = dw + capd;
+  uint64_t *so = dw + capd;  // so(position p, lane i): coefficient of lane i at offset p
   // 1. the part of each word range inside the array arrives by bulk copy; the rest is zero
   const int64_t cu = ub0 + nu <= nwords ? nu : (nwords > ub0 ? nwords - ub0 : 0);
   const int64_t cw = wb0 + nw <= nwords ? nw : (nwords > wb0 ? nwords - wb0 : 0);
@@ -882,201 +431,261 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
     if (cu > 0) stage_copy(su, R.Vf + ub0, (uint32_t)(cu * 4), &bar);
     if (cw > 0) stage_copy(sw, R.Vr + wb0, (uint32_t)(cw * 4), &bar);
   }
+  // the seeds of this thread's chain, while the copies fly
+  const int64_t c_me = c0 + tid;
+  const bool chain_lane_me = tid < 32 && c_me < c1;
+  uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
+  ChainLane Lm;
+  if (chain_lane_me) {
+    Lm = chain_lane(a, R, c_me);
+    if (Lm.seeded) {
+      seed_value(a, Lm.vprev, s0);
+      seed_value(a, Lm.vcur, s1);
+    }
+  }
   __syncthreads();
   if (!__syncthreads_and(stage_wait(&bar))) {
     if (tid == 0) atomicExch(status, 1);
     stage_wait(&bar);  // once more (bounded) for the copies in flight before leaving
     return;
   }
-  // 2. digits (chain and cpc are powers of two)
+  // 2. each chain's digits (chain and cpc are powers of two)
   const int lc = __ffsll((long long)chain) - 1, lp = __ffs(cpc) - 1;
   const int64_t pu = R.off_f - ub0 * 32, pw = R.off_r - wb0 * 32;  // staged bit offsets
   for (int q = tid; q < (int)capd; q += kRT) {
     const int t = q >> lp, i = q & (cpc - 1);
-    const int64_t j = j0 + ((int64_t)i << lc) + t;
-    const bool in = j <= jhi;
-    du[q] = in ? sbits64(su, nu, pu + j * (int64_t)M) & mask : 0ull;
-    dw[q] = in ? sbits64(sw, nw, pw + (n - j) * (int64_t)M) & mask : 0ull;
+    const int64_t c = c0 + i;
+    uint64_t x = 0, y = 0;
+    if (c < c1) {
+      bool up, seeded;
+      int64_t s, len;
+      chain_geom(n, chain, c, up, s, len, seeded);
+      if (t <= len) {
+        const int64_t j = up ? s + t : s - t;  // in [j0, jhi]
+        const uint64_t uj = sbits64(su, nu, pu + j * (int64_t)M) & mask;
+        const uint64_t wj = sbits64(sw, nw, pw + (n - j) * (int64_t)M) & mask;
+        x = up ? uj : wj;
+        y = up ? wj : uj;
+      }
+    }
+    du[q] = x;
+    dw[q] = y;
   }
   __syncthreads();
   // 3. the chains (warp 0)
-  const int64_t gid = c0 + tid;
-  if (tid < 32 && gid < c1) {
-    const int64_t ln = tid;
-    auto u = [&](int64_t j) { return du[(j - j0 - (ln << lc)) * cpc + ln]; };
-    auto w = [&](int64_t m) { return dw[(n - m - j0 - (ln << lc)) * cpc + ln]; };
-    const int64_t s = gid * chain;
-    const int64_t e = (s + chain < n) ? s + chain : n;
+  if (chain_lane_me) {
+    const int ln = tid;
+    const ChainLane &L = Lm;
     uint64_t a_prev, a_cur, delta;
-    if (s == 0) {
+    if (!L.seeded) {  // downward from n: the reversed problem's start at index 0
       a_prev = 0;
-      a_cur = u(0);
+      a_cur = du[ln];
       delta = 0;
     } else {
-      uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
-      seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
-      seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
       a_prev = load_d1(s0, kAccSeedWords, 0, M);
       const uint64_t b_prev = load_d1(s0, kAccSeedWords, M, M);
       a_cur = load_d1(s1, kAccSeedWords, 0, M);
-      const uint64_t us = u(s);
+      const uint64_t us = du[ln];
       const uint64_t dprev = (us - b_prev - a_cur) & mask;
       if (dprev > 1) atomicExch(status, 2);
       delta = (b_prev + a_cur + dprev - us) >> M;
     }
-    uint64_t w_cur = w(n - s);
-    // step t reads du(t + 1, ln) and dw(t + 1, ln); eight steps are loaded ahead
+    uint64_t w_cur = dw[ln];
+    // step t reads du(t + 1, ln) and dw(t + 1, ln): eight steps' digits are
+    // loaded at once, then the eight steps run with compile-time indices.  A
+    // step keeps only the recurrence on its critical path (alpha, the carries);
+    // it stores (alpha_j, beta_j), and the output phase forms the coefficient.
+    // delta_(j+1) = [beta_j + delta_j > u_(j+1)]: alpha_(j+1) wrapped below
+    // zero exactly then.  (delta, epsilon are 0 or 1 by construction once the
+    // start is consistent, which the seed check above verified.)  The run's
+    // last coefficient (beta_(n-1) = w_(n-1) - alpha_(n-2)) can only be a
+    // chain's final step and is taken after the loop.
     const uint64_t *pdu = du + cpc + ln, *pdw = dw + cpc + ln;
+    const int len = (int)L.len;
+    const int64_t last = n - 1 - L.pA;  // step of the run's last coefficient
+    const int steps = last == len - 1 ? len - 1 : len;
     uint64_t *po = so + 2 * ln;
-    constexpr int kAhead = 8;
-    uint64_t ub[kAhead], wb[kAhead];
+    const int pstride = 2 * cpc;  // so words between consecutive positions
+    const int pos0 = L.up ? 0 : len - 1, pdir = L.up ? pstride : -pstride;
+    for (int t0 = 0; t0 < steps; t0 += 8) {
+      uint64_t U[8], Wn[8];
 #pragma unroll
-    for (int q = 0; q < kAhead; q++) {
-      ub[q] = q < chain ? pdu[q * cpc] : 0ull;
-      wb[q] = q < chain ? pdw[q * cpc] : 0ull;
-    }
-    for (int64_t j = s; j < e; j++) {
-      const int t = (int)(j - s);
-      uint64_t *out = po + 2 * t * cpc;
-      const uint64_t u_next = ub[0], w_next = wb[0];
-#pragma unroll
-      for (int q = 0; q + 1 < kAhead; q++) {
-        ub[q] = ub[q + 1];
-        wb[q] = wb[q + 1];
+      for (int q = 0; q < 8; q++) {
+        const bool in = t0 + q < (int)chain;  // rows up to chain exist
+        U[q] = in ? pdu[(t0 + q) * cpc] : 0ull;
+        Wn[q] = in ? pdw[(t0 + q) * cpc] : 0ull;
       }
-      ub[kAhead - 1] = t + kAhead < chain ? pdu[(t + kAhead) * cpc] : 0ull;
-      wb[kAhead - 1] = t + kAhead < chain ? pdw[(t + kAhead) * cpc] : 0ull;
-      if (j <= n - 2) {
-        const uint64_t eps = a_cur > w_next ? 1ull : 0ull;
+      uint64_t *out = po + pos0 * pstride + t0 * pdir;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        if (t0 + q >= steps) break;
+        const uint64_t eps = a_cur > Wn[q] ? 1ull : 0ull;
         const uint64_t beta = (w_cur - a_prev - eps) & mask;
-        const uint64_t a_next = (u_next - beta - delta) & mask;
-        const uint64_t dnext = (beta + a_next + delta - u_next) >> M;
-        if (dnext > 1) atomicExch(status, 2);
-        out[0] = a_cur | (beta << M);
-        out[1] = beta >> (64 - M);
+        const uint64_t a_next = (U[q] - beta - delta) & mask;
+        const uint64_t dnext = beta + delta > U[q] ? 1ull : 0ull;
+        out[0] = a_cur;
+        out[1] = beta;
+        out += pdir;
         a_prev = a_cur;
         a_cur = a_next;
         delta = dnext;
-        w_cur = w_next;
-      } else {
-        const uint64_t beta = (w_cur - a_prev) & mask;
-        out[0] = a_cur | (beta << M);
-        out[1] = beta >> (64 - M);
+        w_cur = Wn[q];
       }
+    }
+    if (steps < len) {
+      uint64_t *out = po + (pos0 + (int64_t)steps * (L.up ? 1 : -1)) * pstride;
+      out[0] = a_cur;
+      out[1] = (w_cur - a_prev) & mask;
     }
   }
   __syncthreads();
-  // 4. coefficients out
+  // 4. coefficients alpha + 2^M beta out, minus K
   uint64_t *h = a.h;
-  uint64_t *hb = h + (R.kbase + R.kstride * j0) * ol;
-  const int64_t hs = R.kstride * ol;
   for (int q = tid; q < (int)((jhi - j0) * ol); q += kRT) {
     const int jj = ol == 2 ? q >> 1 : q;
     const int l = q - jj * ol;
-    const int i = jj >> lc, t = jj & (int)(chain - 1);
-    hb[jj * hs + l] = so[((t << lp) + i) * 2 + l];
+    const int i = jj >> lc, p = jj & (int)(chain - 1);
+    const uint64_t *v = so + 2 * (((int64_t)p << lp) + i);
+    const uint64_t lo = v[0] | (v[1] << M), hi = v[1] >> (64 - M);
+    uint64_t w = l == 0 ? lo : hi;
+    if (kb >= 0) {
+      uint64_t borrow = 0;
+      const uint64_t l0 = sub_k(lo, kb, 0, borrow);
+      w = l == 0 ? l0 : sub_k(hi, kb, 1, borrow);
+    }
+    h[(R.kbase + R.kstride * (j0 + jj)) * ol + l] = w;
   }
 }
 
-// 64 <= M <= 127
+// 64 <= M <= 127, one thread per chain, digits read from global memory
 template <class Src>
 __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
   int64_t local;
   const RecoverArgs &a = src.locate(blockIdx.x, local);
   uint64_t *h = a.h;
-  const int ol = a.ol;
+  const int ol = a.ol, kb = a.kb;
   int *status = a.status;
   int64_t gid = local * 128 + threadIdx.x;
   int r;
   if (!chain_index(a, gid, r)) return;
   const RecoverRun &R = a.run[r];
   const int M = a.M;
-  const int64_t n = R.n;
-  const int64_t s = gid * a.chain;
-  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
+  const int64_t n = R.n, nwords = a.nwords;
+  const ChainLane L = chain_lane(a, R, gid);
+  auto DU = [&](int64_t t) { return load_d2(L.A, nwords, L.offA + (L.pA + t) * (int64_t)M, M); };
+  auto DW = [&](int64_t t) { return load_d2(L.B, nwords, L.offB + (L.pB - t) * (int64_t)M, M); };
   const D2 zero = {0ull, 0ull};
   D2 a_prev, a_cur;
   uint64_t delta;
-  if (s == 0) {
+  if (!L.seeded) {
     a_prev = zero;
-    a_cur = load_d2(R.Vf, a.nwords, R.off_f, M);
+    a_cur = DU(0);
     delta = 0;
   } else {
     uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
-    seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
-    seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
+    seed_value(a, L.vprev, s0);
+    seed_value(a, L.vcur, s1);
     a_prev = load_d2(s0, kAccSeedWords, 0, M);
     const D2 b_prev = load_d2(s0, kAccSeedWords, M, M);
     a_cur = load_d2(s1, kAccSeedWords, 0, M);
-    const D2 us = load_d2(R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
+    const D2 us = DU(0);
     const D2 dprev = sub_d2(sub_d2(us, b_prev, 0, M), a_cur, 0, M);
     if (dprev.hi != 0 || dprev.lo > 1) atomicExch(status, 2);
     delta = carry_d2(b_prev, a_cur, dprev.lo & 1ull, M);
   }
-  D2 w_cur = load_d2(R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
-  for (int64_t j = s; j < e; j++) {
-    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
-    if (j <= n - 2) {
-      const D2 w_next = load_d2(R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+  D2 w_cur = DW(0);
+  const int64_t last = n - 1 - L.pA;
+  for (int64_t t = 0; t < L.len; t++) {
+    uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, t)) * ol;
+    if (t != last) {
+      const D2 w_next = DW(t + 1);
       const uint64_t eps = gt_d2(a_cur, w_next) ? 1ull : 0ull;
       const D2 beta = sub_d2(sub_d2(w_cur, a_prev, 0, M), zero, eps, M);
-      const D2 u_next = load_d2(R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      const D2 u_next = DU(t + 1);
       const D2 a_next = sub_d2(sub_d2(u_next, beta, 0, M), zero, delta, M);
       const uint64_t dnext = carry_d2(beta, a_next, delta, M);
-      write_h2(out, ol, a_cur, beta, M);
+      write_h2(out, ol, a_cur, beta, M, kb);
       a_prev = a_cur;
       a_cur = a_next;
       delta = dnext;
       w_cur = w_next;
     } else {
-      write_h2(out, ol, a_cur, sub_d2(w_cur, a_prev, 0, M), M);
+      write_h2(out, ol, a_cur, sub_d2(w_cur, a_prev, 0, M), M, kb);
     }
   }
 }
 
+// out limbs of alpha + 2^M beta - K, alpha, beta < 2^M (any M)
+__device__ void write_coeff(uint64_t *out, int ol, const Dig &al, const Dig &be, int M, int kb) {
+  const int W = (M + 31) / 32;
+  uint64_t borrow = 0;
+  for (int l = 0; l < ol; l++) {
+    uint64_t v = 0;
+    for (int half = 0; half < 2; half++) {
+      const int64_t p0 = 64 * (int64_t)l + 32 * half;  // bit position of this 32-bit chunk
+      uint64_t chunk = 0;
+      if (p0 < M) chunk |= al.w[(int)(p0 >> 5)];  // alpha's bits above M are zero
+      // from beta: bits [p0 - M, p0 - M + 32)
+      const int64_t q = p0 - M;
+      if (q + 32 > 0 && q < (int64_t)32 * W) {
+        const int64_t wi = q >= 0 ? (q >> 5) : -1;
+        const int sh = (int)(q & 31);
+        const uint64_t lo = (wi >= 0 && wi < W) ? be.w[wi] : 0u;
+        const uint64_t hi = (wi + 1 >= 0 && wi + 1 < W) ? be.w[wi + 1] : 0u;
+        const uint64_t pair = lo | (hi << 32);
+        uint32_t part;
+        if (q >= 0)
+          part = (uint32_t)(pair >> sh);
+        else
+          part = (uint32_t)(((uint64_t)be.w[0]) << (int)(-q));  // -q < 32
+        chunk |= part;
+      }
+      v |= (chunk & 0xffffffffull) << (32 * half);
+    }
+    out[l] = sub_k(v, kb, l, borrow);
+  }
+}
+
+// any M (digits of W 32-bit words), one thread per chain
 template <class Src>
 __global__ void __launch_bounds__(64) recover_wide(Src src) {
   int64_t local;
   const RecoverArgs &a = src.locate(blockIdx.x, local);
   uint64_t *h = a.h;
-  const int ol = a.ol;
+  const int ol = a.ol, kb = a.kb;
   int *status = a.status;
   int64_t gid = local * 64 + threadIdx.x;
-  int r = 0;
-  while (r < a.nruns && gid >= a.run[r].nchains) {
-    gid -= a.run[r].nchains;
-    r++;
-  }
-  if (r >= a.nruns) return;
+  int r;
+  if (!chain_index(a, gid, r)) return;
   const RecoverRun &R = a.run[r];
   const int M = a.M;
   const int W = (M + 31) / 32;
-  const int64_t n = R.n;
-  const int64_t s = gid * a.chain;
-  const int64_t e = (s + a.chain < n) ? s + a.chain : n;
-  Dig a_prev, a_cur, delta_d, w_cur, w_next, u_next, beta, a_next, zero;
+  const int64_t n = R.n, nwords = a.nwords;
+  const ChainLane L = chain_lane(a, R, gid);
+  Dig a_prev, a_cur, w_cur, w_next, u_next, beta, a_next, zero;
   for (int i = 0; i < W; i++) zero.w[i] = 0;
   uint32_t delta;
-  if (s == 0) {
+  if (!L.seeded) {
     a_prev = zero;
-    dig_load(a_cur, R.Vf, a.nwords, R.off_f, M);
+    dig_load(a_cur, L.A, nwords, L.offA + L.pA * (int64_t)M, M);
     delta = 0;
   } else {
     Dig b_prev, us, dp;
-    if (R.seed_acc != nullptr) {
+    if (a.seed_acc != nullptr) {
       uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
-      seed_value(R, R.seed_base + 2 * (gid - 1), a.seed_words, s0);
-      seed_value(R, R.seed_base + 2 * (gid - 1) + 1, a.seed_words, s1);
+      seed_value(a, L.vprev, s0);
+      seed_value(a, L.vcur, s1);
       dig_load_local(a_prev, s0, kAccSeedWords, 0, M);
       dig_load_local(b_prev, s0, kAccSeedWords, M, M);
       dig_load_local(a_cur, s1, kAccSeedWords, 0, M);
     } else {
-      const uint32_t *sd = R.seeds + (R.seed_base + 2 * (gid - 1)) * a.seed_words;
-      dig_load_local(a_prev, sd, a.seed_words, 0, M);
-      dig_load_local(b_prev, sd, a.seed_words, M, M);
-      dig_load_local(a_cur, sd + a.seed_words, a.seed_words, 0, M);
+      const uint32_t *sp = a.seeds + L.vprev * a.seed_words;
+      const uint32_t *sc = a.seeds + L.vcur * a.seed_words;
+      dig_load_local(a_prev, sp, a.seed_words, 0, M);
+      dig_load_local(b_prev, sp, a.seed_words, M, M);
+      dig_load_local(a_cur, sc, a.seed_words, 0, M);
     }
-    dig_load(us, R.Vf, a.nwords, R.off_f + s * (int64_t)M, M);
+    dig_load(us, L.A, nwords, L.offA + L.pA * (int64_t)M, M);
     Dig t1;
     dig_sub(t1, us, b_prev, 0, M);
     dig_sub(dp, t1, a_cur, 0, M);
@@ -1085,31 +694,33 @@ __global__ void __launch_bounds__(64) recover_wide(Src src) {
     if (!ok) atomicExch(status, 2);
     delta = dig_add_carry(b_prev, a_cur, dp.w[0] & 1u, M);
   }
-  (void)delta_d;
-  dig_load(w_cur, R.Vr, a.nwords, R.off_r + (n - s) * (int64_t)M, M);
-  for (int64_t j = s; j < e; j++) {
-    uint64_t *out = h + (R.kbase + R.kstride * j) * ol;
-    if (j <= n - 2) {
-      dig_load(w_next, R.Vr, a.nwords, R.off_r + (n - j - 1) * (int64_t)M, M);
+  dig_load(w_cur, L.B, nwords, L.offB + L.pB * (int64_t)M, M);
+  const int64_t last = n - 1 - L.pA;
+  for (int64_t t = 0; t < L.len; t++) {
+    uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, t)) * ol;
+    if (t != last) {
+      dig_load(w_next, L.B, nwords, L.offB + (L.pB - t - 1) * (int64_t)M, M);
       const uint32_t eps = dig_gt(a_cur, w_next, W) ? 1u : 0u;
       dig_sub(beta, w_cur, a_prev, eps, M);
-      dig_load(u_next, R.Vf, a.nwords, R.off_f + (j + 1) * (int64_t)M, M);
+      dig_load(u_next, L.A, nwords, L.offA + (L.pA + t + 1) * (int64_t)M, M);
       dig_sub(a_next, u_next, beta, delta, M);
       const uint32_t dnext = dig_add_carry(beta, a_next, delta, M);
-      write_coeff(out, ol, a_cur, beta, M);
+      write_coeff(out, ol, a_cur, beta, M, kb);
       a_prev = a_cur;
       a_cur = a_next;
       delta = dnext;
       w_cur = w_next;
     } else {
       dig_sub(beta, w_cur, a_prev, 0, M);
-      write_coeff(out, ol, a_cur, beta, M);
+      write_coeff(out, ol, a_cur, beta, M, kb);
     }
   }
 }
 
-int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, int64_t nwords,
-                      int M, int64_t chain, int seed_words, int *status, RecoverArgs &a,
+int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int nruns,
+                      int64_t nwords, int M, int64_t chain, int C,
+                      const unsigned long long *seed_acc, int64_t seed_slices,
+                      const uint32_t *seeds, int seed_words, int *status, RecoverArgs &a,
                       int64_t &blocks) {
   a = RecoverArgs{};
   int64_t total = 0;
@@ -1121,10 +732,15 @@ int make_recover_args(uint64_t *h, int ol, const RecoverRun *runs, int nruns, in
   a.nwords = nwords;
   a.M = M;
   a.chain = chain;
-  a.seed_words = seed_words;
   a.h = h;
   a.ol = ol;
+  a.kb = kb;
   a.status = status;
+  a.C = C;
+  a.seed_acc = seed_acc;
+  a.seed_slices = seed_slices;
+  a.seeds = seeds;
+  a.seed_words = seed_words;
   if ((M + 31) / 32 > kMaxDigitWordsM) return -1;
   if (M <= 63) {  // staged: CTAs of cpc chains that do not straddle runs
     // fewer chains per CTA (down to 8) until there are two CTAs per SM: the
@@ -1180,15 +796,9 @@ static cudaError_t launch_recover_class(int cls, int64_t blocks, const Src &src,
   return cudaGetLastError();
 }
 
-cudaError_t launch_recover(uint64_t *h, int ol, const RecoverRun *runs, int nruns,
-                           int64_t nwords, int M, int64_t chain, int seed_words, int *status,
-                           cudaStream_t s) {
-  RecoverArgs a;
-  int64_t blocks;
-  if (make_recover_args(h, ol, runs, nruns, nwords, M, chain, seed_words, status, a, blocks) != 0)
-    return cudaErrorInvalidValue;
+cudaError_t launch_recover(const RecoverArgs &a, int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  return launch_recover_class(recover_class(M), blocks, One<RecoverArgs>{a}, a.smem, s);
+  return launch_recover_class(recover_class(a.M), blocks, One<RecoverArgs>{a}, a.smem, s);
 }
 
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
