@@ -20,7 +20,9 @@ gives the phase times and the dominant kernel's duration for the roofline.
 copy) with pinned buffers.
 
 `--impl reference` times the CPU oracle (plain schoolbook, all host cores) on
-the same workload instead.
+the same workload instead.  `--case V,L,B,SIGNED[,ENGINE[,REPS]]` runs one
+product shape REPS times through ks_mul and prints its plan (no timing; a
+fixed launch sequence for profilers).
 """
 from __future__ import annotations
 
@@ -45,10 +47,11 @@ WORKLOAD = {"workload": "zx_product_16384_s48", "len_f": 16384, "len_g": 16384,
             "coeff_bits": 48, "is_signed": True, "seed_f": 20071229, "seed_g": 20071230}
 METRIC = "Z[x] products/s and output Gbit/s, KS4 vs KS1, bit-exact, 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one tc_kernel launch on this workload's KS4
-# product, from the ncu capture summarised in
-# profiles/tc_kernel_zx_product_16384_s48_ks4.md (re-taken whenever the kernel changes)
-TC_KERNEL_DRAM_BYTES = 6001408
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_kernel
+# launch on this workload's KS4 product, from an ncu capture of the current
+# kernel (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k
+# regex:tc_kernel`); None until the kernel has been captured since it last changed
+TC_KERNEL_DRAM_BYTES = None
 # 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC
 IMAD_PER_SM_CLK = 64
 SMS = 152
@@ -60,7 +63,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default=None,
+                    help="V,L,B,SIGNED[,ENGINE[,REPS]]: run one product shape, no timing")
     return ap.parse_args()
+
+
+def run_case(spec: str) -> int:
+    """One product shape REPS times through ks_mul (a fixed launch sequence for
+    profilers); prints the plan the library ran."""
+    import torch
+    import paper_0712_4046_gb300 as ks
+    parts = [int(x) for x in spec.split(",")]
+    v, L, b, sg = parts[:4]
+    engine = parts[4] if len(parts) > 4 else 0
+    reps = parts[5] if len(parts) > 5 else 3
+    f = ks_inputs.random_poly(L, b, bool(sg), WORKLOAD["seed_f"])
+    g = ks_inputs.random_poly(L, b, bool(sg), WORKLOAD["seed_g"])
+    tf = torch.from_numpy(f.view(np.int64)).cuda()
+    tg = torch.from_numpy(g.view(np.int64)).cuda()
+    for _ in range(reps):
+        ks.mul(tf, tg, b, bool(sg), v, engine)
+    torch.cuda.synchronize()
+    ks.status_sync()
+    print(json.dumps(ks.plan_info(L, L, b, bool(sg), v, engine)))
+    return 0
 
 
 def output_bits(lf, lg, b):
@@ -252,10 +278,13 @@ def main_ours(args):
     hbm_gbs, sm_max_mhz, peak_kind = peaks()
 
     results = {}
-    # (label, variant, engine): the library's choice for every variant, plus the
-    # INT32-pipe schoolbook engine for KS1 and KS4 (the plain GPU baseline)
-    runs = [("KS1", 1, 0), ("KS2", 2, 0), ("KS3", 3, 0), ("KS4", 4, 0),
-            ("KS1_int32", 1, ks.ENGINE_SCHOOLBOOK), ("KS4_int32", 4, ks.ENGINE_SCHOOLBOOK)]
+    outputs = {}  # each variant's product, checked against the oracle in the CPU leg
+    # (label, variant, engine): the library's choice for every variant, KS1 on the
+    # tensor cores (the same engine as KS4's), and the INT32-pipe schoolbook engine
+    # for KS1 and KS4 (the plain GPU baseline)
+    runs = [("KS1", 1, 0), ("KS1_tc", 1, ks.ENGINE_TC), ("KS2", 2, 0), ("KS3", 3, 0),
+            ("KS4", 4, 0), ("KS1_int32", 1, ks.ENGINE_SCHOOLBOOK),
+            ("KS4_int32", 4, ks.ENGINE_SCHOOLBOOK)]
     ws = {}
 
     def timed(fn, steps):
@@ -292,12 +321,15 @@ def main_ours(args):
             total_ms = timed(step, args.steps)
             launches = (ks.launch_count() - launches0) // (args.steps + args.warmup)
             # (2) the same product through a one-product plan replayed as a CUDA graph
+            h.zero_()
             plan = ks.Plan([dict(h=h, f=tf, g=tg, coeff_bits=b, is_signed=sg, variant=variant,
                                  engine=engine)])
             plan.capture(stream)
             graph_ms = timed(lambda: plan.execute(stream), args.steps)
+            plan.status()
             graph_launches = plan.launches()
             plan.close()
+            outputs[label] = h.cpu().numpy().view(np.uint64).copy()
             # (3) a short profiled pass for the per-phase times (events between phases)
             ks.profile_collect()
             ks.profile_enable(True)
@@ -311,6 +343,10 @@ def main_ours(args):
                               "graph_ms_per_step": graph_ms / args.steps,
                               "launches": launches, "graph_launches": graph_launches,
                               "phases": phases, "variant": variant, "engine": engine}
+        # ---- KS1-KS4 across the moderate-size regime (Sec. 4's experiment)
+        curve, curve_out = run_curve(ks, dev, stream, flush, args.steps, args.warmup, world)
+        # ---- 64 products in (Z/pZ)[x], p = 2^61 - 1, L = 2^16 (the Sec. 4 application)
+        modp, modp_out = run_modp(ks, dev, stream, flush, args.warmup, world)
         # ---- batched workload: 4096 uneven products, one plan per dispatch mode
         batched = run_batched(ks, dev, stream, flush, args.steps, args.warmup, world)
         # ---- HBM-bound phases (pack, normalize, unpack) where the arrays exceed L2
@@ -331,11 +367,11 @@ def main_ours(args):
     for _ in range(args.steps):
         ks.ks_mul_host(hh, fh, gh, b, sg, 4, 0, stream)
     e2e_s = barrier_max(time.perf_counter() - t0, world, dev)
+    outputs["KS4_host"] = hh.copy()
 
     # ---- roofline of the dominant kernel of KS4: the tensor-core product
-    # (the largest share of the serialised ncu launch list; the seeds and the
-    # signed prefix run concurrently on a helper stream, so their event spans
-    # overlap the product's and are not a kernel's own duration)
+    # (the largest share of the serialised ncu launch list; the seeds run
+    # concurrently on a helper stream, so their event spans overlap others)
     r4 = results["KS4"]
     info = ks.plan_info(lf, lg, b, sg, 4, ks.ENGINE_AUTO)
     ph = {k: v for k, v in r4["phases"].items() if v[1] > 0}
@@ -344,15 +380,13 @@ def main_ours(args):
     roof = roofline_for(dom, dom_ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind)
     if info["engine"] == ks.ENGINE_TC:
         roof["traffic"] = TC_KERNEL_DRAM_BYTES
-        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+                                  if TC_KERNEL_DRAM_BYTES else "not captured for this kernel")
         roof["kernel"] = "tc_kernel"
 
-    cpu = None
+    cpu, exact = None, None
     if rank == 0 and world == 1:
-        times, cores = run_oracle(f, g, 30, 1, budget_s=15.0)
-        v = len(times) / sum(times)
-        cpu = {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle",
-               "sample": "%d full products of the workload, all host threads" % len(times)}
+        cpu, exact = cpu_leg(f, g, outputs, curve_out, modp_out)
 
     if rank != 0:
         return 0
@@ -371,6 +405,7 @@ def main_ours(args):
                        "output_gbit_per_s": pps * obits / 1e9,
                        "phases_ms": {k: round(x[0] / max(1, x[1]), 5)
                                      for k, x in r["phases"].items() if x[1] > 0}}
+    best_ks1 = min(results[k]["graph_ms_per_step"] for k in ("KS1", "KS1_tc", "KS1_int32"))
     line = {
         "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms4,
@@ -381,7 +416,9 @@ def main_ours(args):
                        l2="flushed between steps (256 MiB write)",
                        parallelism="replicas" if world > 1 else "single"),
         "output_gbit_per_s": value * obits / 1e9,
-        "ks4_over_ks1": results["KS1"]["graph_ms_per_step"] / ms4,
+        "bit_exact": exact,
+        "ks4_over_ks1": best_ks1 / ms4,
+        "ks4_over_ks1_same_engine": results["KS1_tc"]["graph_ms_per_step"] / ms4,
         "ks4_over_int32_ks1": results["KS1_int32"]["graph_ms_per_step"] / ms4,
         "ks_mul_products_per_s": world * 1000.0 / r4["ms_per_step"],
         "variants": variants,
@@ -392,12 +429,137 @@ def main_ours(args):
                 "h2d_bytes_per_step": int(f.nbytes + g.nbytes),
                 "d2h_bytes_per_step": int(lh * ol * 8)},
         "cpu_baseline": cpu,
+        "ks4_over_ks1_curve": curve,
+        "modp_batch": modp,
         "batched": batched,
         "hbm_phases": hbm_phases,
         "bivariate": bivariate,
     }
     print(json.dumps(line))
     return 0
+
+
+def cpu_leg(f, g, outputs, curve_out, modp_out):
+    """The CPU oracle timed on the host cores over full products of the
+    workload (bounded), and the bit-exactness of every product the GPU arm
+    computed: each variant's output on the workload, the curve's shapes and one
+    product of the (Z/pZ)[x] batch."""
+    import oracle
+    w = WORKLOAD
+    times, cores = run_oracle(f, g, 30, 1, budget_s=15.0)
+    v = len(times) / sum(times)
+    cpu = {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle",
+           "sample": "%d full products of the workload, all host threads" % len(times)}
+    want = oracle.mul(f, g, w["coeff_bits"], w["is_signed"], threads=cores)
+    exact = {k: bool(np.array_equal(o, want)) for k, o in outputs.items()}
+    for key, (fc, gc, bc, hs) in curve_out.items():
+        wc = oracle.mul(fc, gc, bc, False, threads=cores)
+        exact["curve_" + key] = all(bool(np.array_equal(x, wc)) for x in hs)
+    if modp_out is not None:
+        fm, gm, p, hm = modp_out
+        exact["modp_product0"] = bool(np.array_equal(hm, oracle.mul_mod(fm, gm, p, threads=cores)))
+    exact["all"] = all(exact.values())
+    return cpu, exact
+
+
+CURVE = {"lens": [128, 512, 1024, 2048, 4096, 8192], "bits": [4, 48], "seed": 4046}
+
+
+def run_curve(ks, dev, stream, flush, steps, warmup, world):
+    """KS1-KS4 at degree {128 .. 8192} x {4, 48}-bit unsigned coefficients (the
+    sizes and moduli of Sec. 4's experiments), each through a one-product plan
+    replayed as a CUDA graph, L2 flushed between steps.  KS1 is timed on every
+    engine and its best is the reference; KS2-KS4 use the library's engine."""
+    import torch
+    out, keep = {"config": dict(CURVE, l2="flushed between steps", api="ks_plan graph replay")}, {}
+    cfgs = [("KS1", 1, 0), ("KS1_tc", 1, ks.ENGINE_TC), ("KS1_ntt", 1, ks.ENGINE_NTT),
+            ("KS2", 2, 0), ("KS3", 3, 0), ("KS4", 4, 0), ("KS4_tc", 4, ks.ENGINE_TC)]
+    for b in CURVE["bits"]:
+        for L in CURVE["lens"]:
+            f = ks_inputs.random_poly(L, b, False, CURVE["seed"] + L + b)
+            g = ks_inputs.random_poly(L, b, False, CURVE["seed"] + L + b + 1)
+            tf = torch.from_numpy(f.view(np.int64)).to(dev)
+            tg = torch.from_numpy(g.view(np.int64)).to(dev)
+            h = torch.empty((2 * L - 1, ks.out_limbs(L, L, b, False)), dtype=torch.int64,
+                            device=dev)
+            row, hs = {}, []
+            for label, v, e in cfgs:
+                try:
+                    plan = ks.Plan([dict(h=h, f=tf, g=tg, coeff_bits=b, is_signed=False,
+                                         variant=v, engine=e)])
+                except ks.KSError:
+                    continue  # engine not available at this size
+                plan.capture(stream)
+                for _ in range(max(warmup, 3)):
+                    plan.execute(stream)
+                torch.cuda.synchronize()
+                evs = [(torch.cuda.Event(enable_timing=True),
+                        torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+                for i in range(steps):
+                    flush.zero_()
+                    evs[i][0].record(stream)
+                    plan.execute(stream)
+                    evs[i][1].record(stream)
+                torch.cuda.synchronize()
+                plan.status()
+                us = 1000.0 * barrier_max(sum(a.elapsed_time(z) for a, z in evs), world,
+                                          dev) / steps
+                row[label] = {"us": round(us, 2), "engine": plan.choice(0)[1]}
+                plan.close()
+                hs.append(h.cpu().numpy().view(np.uint64).copy())
+            ks1 = min(row[k]["us"] for k in ("KS1", "KS1_tc", "KS1_ntt") if k in row)
+            ks4 = min(row[k]["us"] for k in ("KS4", "KS4_tc") if k in row)
+            row["ks4_over_best_ks1"] = round(ks1 / ks4, 3)
+            row["ks2_over_best_ks1"] = round(ks1 / row["KS2"]["us"], 3)
+            key = "L%d_b%d" % (L, b)
+            out[key] = row
+            keep[key] = (f, g, b, hs)
+    return out, keep
+
+
+MODP = {"workload": "modp_64x2pow16_p61", "n": 64, "len": 1 << 16, "p": (1 << 61) - 1,
+        "seed": 5}
+
+
+def run_modp(ks, dev, stream, flush, warmup, world, steps=3):
+    """64 products in (Z/pZ)[x], p = 2^61 - 1, L = 2^16, uniform residues: one
+    ks_mul_mod call per product (the library's variant and engine), a step is
+    the whole batch, L2 flushed before each step."""
+    import torch
+    n, L, p = MODP["n"], MODP["len"], MODP["p"]
+    fs, gs, hs = [], [], []
+    for i in range(n):
+        fs.append(torch.from_numpy(ks_inputs.random_residues(L, p, MODP["seed"] + 2 * i)
+                                   .view(np.int64)).to(dev).reshape(L, 1))
+        gs.append(torch.from_numpy(ks_inputs.random_residues(L, p, MODP["seed"] + 2 * i + 1)
+                                   .view(np.int64)).to(dev).reshape(L, 1))
+        hs.append(torch.empty((2 * L - 1, 1), dtype=torch.int64, device=dev))
+
+    def step():
+        for i in range(n):
+            ks.ks_mul_mod(hs[i], fs[i], gs[i], p, 0, stream)
+    for _ in range(max(1, warmup)):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ks.status_sync(stream)
+    ms = barrier_max(sum(a.elapsed_time(z) for a, z in evs), world, dev) / steps
+    info = ks.plan_info(L, L, 61, False)
+    res = {"config": dict(MODP, api="ks_mul_mod per product", l2="flushed before each step"),
+           "products_per_s": world * n * 1000.0 / ms, "ms_per_batch": ms,
+           "variant": info["variant"], "engine": info["engine"]}
+    keep = (fs[0].cpu().numpy().view(np.uint64).reshape(-1),
+            gs[0].cpu().numpy().view(np.uint64).reshape(-1), p,
+            hs[0].cpu().numpy().view(np.uint64).reshape(-1, 1))
+    del fs, gs, hs
+    return res, keep
 
 
 BIV_WORKLOAD = {"workload": "biv_mod_p61_256x256", "lx": 256, "ly": 256, "p": (1 << 61) - 1,
@@ -443,16 +605,42 @@ HBM_WORKLOAD = {"workload": "zx_product_2pow20_u256", "len_f": 1 << 20, "len_g":
                 "coeff_bits": 256, "is_signed": False, "seed_f": 55, "seed_g": 56}
 
 
-def phase_bytes(phase, info, lf, lg):
-    """Algorithmic bytes of one launch of a memory-bound phase: every input
-    element read once, every output element written once."""
+def op_bits(info, lf, lg, b):
+    """Bit lengths of the evaluated operands of one sub-product (the
+    Propositions of Sec. 3.1-3.4: N (L - 1) + b)."""
+    N = info["N"]
+    return N * (lf - 1) + b, N * (lg - 1) + b
+
+
+def phase_bytes(phase, info, lf, lg, b):
+    """Algorithmic bytes of one memory-bound phase (every input read once, every
+    output written once, in the most compact form the step has): pack reads the
+    coefficients and writes the packed operands (N (L - 1) + b bits each);
+    normalization reads the sub-products and writes the normalized values (each
+    the size of a product of the operands); unpack reads the normalized values
+    and writes the coefficients."""
+    nprod, nnorm, ol, il = info["nprod"], info["nnorm"], info["out_limbs"], info["in_limbs"]
+    fa, fb = op_bits(info, lf, lg, b)
+    prod_bytes = (fa + fb + 7) // 8
+    if phase == "pack":
+        return (lf + lg) * il * 8 + nprod * ((fa + 7) // 8 + (fb + 7) // 8)
+    if phase == "normalize":
+        return (nprod + nnorm) * prod_bytes
+    if phase == "unpack":
+        return nnorm * prod_bytes + (lf + lg - 1) * ol * 8
+    return None
+
+
+def engine_bytes(phase, info, lf, lg):
+    """Bytes the library's kernels move in that phase (its own storage formats:
+    16-bit digits held in int32, int64 column sums), for comparison."""
     nprod, nA, nB, ncols = info["nprod"], info["nA"], info["nB"], info["ncols"]
     nw, nnorm, ol, il = info["nwords"], info["nnorm"], info["out_limbs"], info["in_limbs"]
-    if phase == "pack":  # coefficients in, int32 digits out
+    if phase == "pack":
         return (lf + lg) * il * 8 + nprod * (nA + nB) * 4
-    if phase == "normalize":  # column sums in (each once), 32-bit words out
+    if phase == "normalize":
         return nprod * ncols * 8 + nnorm * nw * 4
-    if phase == "unpack":  # words in, coefficients out
+    if phase == "unpack":
         return nnorm * nw * 4 + (lf + lg - 1) * ol * 8
     return None
 
@@ -494,11 +682,13 @@ def run_hbm_phases(ks, dev, stream, flush, hbm_gbs, peak_kind, reps=3):
             if cnt == 0:
                 continue
             ms = tot / cnt
-            byts = phase_bytes(name, info, lf, lg)
+            byts = phase_bytes(name, info, lf, lg, b)
             r = {"ms": ms}
             if byts is not None:
                 gbs = byts / (ms / 1000.0) / 1e9
-                r.update({"bytes": int(byts), "achieved_gbs": gbs, "frac": gbs / hbm_gbs})
+                eb = engine_bytes(name, info, lf, lg)
+                r.update({"bytes": int(byts), "achieved_gbs": gbs, "frac": gbs / hbm_gbs,
+                          "engine_bytes": int(eb), "engine_over_algorithmic": eb / byts})
             res[name] = r
         out["variants"][label] = res
     del tf, tg, h
@@ -568,34 +758,29 @@ def run_batched(ks, dev, stream, flush, steps, warmup, world):
 
 
 def roofline_for(phase, ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind):
-    """Algorithmic work of one launch of the dominant phase over its event time."""
-    nprod, nA, nB, ncols = info["nprod"], info["nA"], info["nB"], info["ncols"]
-    nw, nnorm, ol, il = info["nwords"], info["nnorm"], info["out_limbs"], info["in_limbs"]
+    """Algorithmic work of one launch of the dominant phase over its event time.
+    For the products: k ceil(opbits_f / 8) ceil(opbits_g / 8) 8-bit-digit
+    multiply-adds (2 flops each) over the k sub-products, the Propositions'
+    operand lengths; the engine's own digit work (7-bit digits on the tensor
+    cores, 16-bit on the INT32 pipe) over that is `engine_overhead`."""
+    nprod, nA, nB = info["nprod"], info["nA"], info["nB"]
     sec = ms / 1000.0
+    fa, fb = op_bits(info, lf, lg, b)
+    alg = 2.0 * nprod * ((fa + 7) // 8) * ((fb + 7) // 8)
     if phase == "product" and info["engine"] == 3:
-        flops = 2.0 * nprod * nA * nB  # one multiply-add per pair of 7-bit digits
-        peak = BF16_TFLOPS
-        ach = flops / sec / 1e12
-        return {"bound": "tensor", "phase": phase, "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_kind": PEAK_KIND + " dense bf16 (fp16 runs at the bf16 rate)"}
+        ach = alg / sec / 1e12
+        return {"bound": "tensor", "phase": phase, "achieved": ach, "peak": BF16_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / BF16_TFLOPS, "traffic": None,
+                "algorithmic_flops": alg, "engine_overhead": 2.0 * nprod * nA * nB / alg,
+                "peak_kind": PEAK_KIND + " dense bf16 burst (fp16 runs at the bf16 rate)"}
     if phase == "product" and info["engine"] == 1:
-        ops = 2.0 * nprod * nA * nB  # one multiply-add per digit pair
         peak = SMS * IMAD_PER_SM_CLK * 2 * sm_max_mhz * 1e6 / 1e12
-        ach = ops / sec / 1e12
+        ach = alg / sec / 1e12
         return {"bound": "alu", "phase": phase, "achieved": ach, "peak": peak,
                 "unit": "TOP/s", "frac": ach / peak, "traffic": None,
+                "algorithmic_flops": alg, "engine_overhead": 2.0 * nprod * nA * nB / alg,
                 "peak_kind": "derived: 152 SMs x 64 IMAD/clk x 2 ops x max SM clock"}
-    if phase == "pack":
-        byts = (lf + lg) * il * 8 + nprod * (nA + nB) * 4
-    elif phase == "normalize":
-        byts = nprod * ncols * 8 + nnorm * nw * 4
-    elif phase in ("unpack", "recover"):
-        byts = nnorm * nw * 4 + (lf + lg - 1) * ol * 8
-    elif phase == "signed_fix":
-        byts = (lf + lg) * ol * 8 * 2 + (lf + lg - 1) * ol * 8 * 2
-    else:
-        byts = nprod * ncols * 8
+    byts = phase_bytes(phase, info, lf, lg, b)
     ach = byts / sec / 1e9
     return {"bound": "hbm", "phase": phase, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
             "frac": ach / hbm_gbs, "traffic": None, "peak_kind": peak_kind}
@@ -603,6 +788,8 @@ def roofline_for(phase, ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind)
 
 def main():
     args = parse()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return reference_main(args)
     return main_ours(args)

@@ -340,6 +340,19 @@ long long ks_launch_count(void);
 void ks_debug_fail_allocs(int n);
 
 /*
+ * Test hook for the device-side failure path (no counterpart in the paper):
+ * with on != 0, later launches of the tensor-core product kernel wait, before
+ * their first operand copy, on a barrier that nothing completes, and every
+ * wait of that kernel is bounded by wait_ns (> 0; else the default of one
+ * second).  The wait runs out while no copy or MMA is in flight; the kernel
+ * records the timeout in the status word, releases its tensor memory and
+ * returns, and ks_status_sync / ks_plan_status report KS_ETIMEOUT.  on = 0
+ * restores the normal kernel (wait_ns <= 0: the default bound).  Plans keep the
+ * setting in force when they were created or captured.
+ */
+void ks_debug_tc_stall(int on, int64_t wait_ns);
+
+/*
  * The plan ks_mul_ex would run, as int64 fields (n of them are written):
  * 0 variant, 1 engine, 2 N, 3 digit bits d, 4 sub-products, 5 digits of each
  * f-side operand, 6 digits of each g-side operand, 7 column sums per

@@ -59,6 +59,7 @@ _sig("ks_plan_choice", _ci, _vp, _i64, ctypes.POINTER(_ci), ctypes.POINTER(_ci))
 _sig("ks_plan_destroy", None, _vp)
 _sig("ks_plan_status", _ci, _vp)
 _sig("ks_debug_fail_allocs", None, _ci)
+_sig("ks_debug_tc_stall", None, _ci, _i64)
 
 DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
 
@@ -366,6 +367,12 @@ def debug_fail_allocs(n: int) -> None:
     """Host-side fault injection: the library's next n device allocations fail
     (the calls return KS_ENOMEM); 0 clears it."""
     lib.ks_debug_fail_allocs(int(n))
+
+
+def debug_tc_stall(on: bool, wait_ns: int = 0) -> None:
+    """Test hook: the tensor-core kernel gives up on a barrier nothing completes
+    (every wait bounded by wait_ns), so the call reports KS_ETIMEOUT."""
+    lib.ks_debug_tc_stall(int(on), int(wait_ns))
 
 
 def launch_count() -> int:

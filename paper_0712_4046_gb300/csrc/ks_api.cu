@@ -116,8 +116,13 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.kb = is_signed ? 2 * b - 2 + p.e : -1;
   p.in_limbs = (b + 63) / 64;
   p.out_limbs = (2 * b + p.e + p.is_signed + 63) / 64;
-  p.d = engine == KS_ENGINE_TC ? 7 : 16;
-  p.dn = engine == KS_ENGINE_TC ? 28 : p.d;
+  p.d = engine == KS_ENGINE_TC ? 8 : 16;
+  p.dn = engine == KS_ENGINE_TC ? 32 : p.d;
+  // the tensor cores' exact chunks allow at most eight coefficient fields per
+  // 8-bit window: tiny coefficients at tiny N take a larger N (any N above the
+  // Propositions' is valid for every variant)
+  if (engine == KS_ENGINE_TC)
+    while ((b + p.d - 2) / p.N + 1 > 8) p.N++;
   p.nprod = variant == KS_1 ? 1 : (variant == KS_4 ? 4 : 2);
   p.nnorm = p.nprod;
   const int64_t bitsF = (int64_t)p.N * (lf - 1) + b;
@@ -133,7 +138,7 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     tc_geometry(p.nA, p.nB, p.tg);
     p.ncols = p.tg.ncols;
     if (p.tg.T > ((int64_t)1 << 20)) return KS_ERANGE;
-    // exact fp32 chunks need |recoded digit| <= 72: at most eight fields per 7-bit window
+    // exact fp32 chunks need |recoded digit| <= 136: at most eight fields per 8-bit window
     if ((b + p.d - 2) / p.N + 1 > 8) return KS_ENOTSUP;
   }
   // a multiple of four: every normalized combination starts 16-byte aligned
@@ -197,6 +202,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.off_seedacc = off;  // narrow seeds: six words per (value, slice), each written once
   if (b <= 64 && p.nseeds > 0)
     off = align256(off + (size_t)p.nseeds * seed_slices(lf, lg, p.C) * 6 * 8);
+  p.off_planes = off;   // narrow seeds: the coefficients' balanced 8-bit digit planes
+  if (b <= 64 && p.nseeds > 0) off = align256(off + (size_t)seed_planes_bytes(lf, lg, seed_digits(b, b, p.is_signed)));
   p.off_flags = off;
   p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
   off = align256(p.off_flags + (size_t)p.flag_bytes);
@@ -218,13 +225,13 @@ static int choose_heuristic(int64_t lf, int64_t lg, int b, int *variant, int *en
   if (v == KS_AUTO) v = (lh >= 64) ? KS_4 : KS_1;
   int eng = *engine;
   if (eng == KS_ENGINE_AUTO) {
-    // 7-bit digit products below the cutoff run on the tensor cores, larger
+    // 8-bit digit products below the cutoff run on the tensor cores, larger
     // ones through the transform (quasi-linear)
     const int e = ceil_log2(lf < lg ? lf : lg);
     const int N = variant_N(v, b, e);
-    const double dA = ((double)N * (double)(lf - 1) + b) / 7.0;
-    const double dB = ((double)N * (double)(lg - 1) + b) / 7.0;
-    eng = (dA * dB <= 2.0e10) ? KS_ENGINE_TC : KS_ENGINE_NTT;
+    const double dA = ((double)N * (double)(lf - 1) + b) / 8.0;
+    const double dB = ((double)N * (double)(lg - 1) + b) / 8.0;
+    eng = (dA * dB <= 1.5e10) ? KS_ENGINE_TC : KS_ENGINE_NTT;
   }
   *variant = v;
   *engine = eng;
@@ -441,7 +448,8 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   if (recon) {
     plan_runs(p, words, runs);
     if (make_seed_plan(f, p.lf, p.b, g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl, p.C,
-                       seed_acc, seeds, p.seed_words, sp) != 0)
+                       seed_acc, seeds, p.seed_words,
+                       reinterpret_cast<__half *>(ws + p.off_planes), sp) != 0)
       return KS_ERANGE;
   }
   Fork fk{};

@@ -95,10 +95,12 @@ struct ks_plan {
   ks::List<ks::TcPackArgs> tcpack;
   ks::List<ks::SchoolArgs> school;
   ks::List<ks::TcArgs> tc;
-  ks::List<ks::NormArgs> norm[2];   // digit width 16 and 28 (tensor cores): tile pass
+  ks::List<ks::NormArgs> norm[2];   // digit width 16 and 32 (tensor cores): tile pass
   ks::List<ks::NormArgs> normc[2];  // the same descriptors, carry-pass block counts
   ks::List<ks::UnpackArgs> unpack;
   ks::List<ks::SeedArgs> seeds[ks::kSeedKinds];  // per kernel kind (kSeedKindList)
+  ks::List<ks::SeedArgs> planes;                  // the narrow seeds' digit planes
+  int seed_smem[ks::kSeedKinds] = {0};            // per kind: the largest CTA's shared memory
   ks::List<ks::RecoverArgs> recover[3];
   int recover_smem = 0;  // class 1: the largest staged-digit buffer of the batch
   std::vector<ks::NttJob> ntt;
@@ -151,14 +153,17 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     KS_TRY(cudaEventRecord(P->ev_fork, s));
     KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
   }
+  if (P->planes.n())
+    KS_TRY(launch_seed_planes(P->planes.d, P->planes.dprefix, P->planes.n(), P->planes.blocks(),
+                              side));
   for (int i = 0; i < kSeedKinds; i++)
     if (P->seeds[i].n())
       KS_TRY(launch_seeds_batch(kSeedKindList[i], P->seeds[i].d, P->seeds[i].dprefix,
-                                P->seeds[i].n(), P->seeds[i].blocks(), side));
+                                P->seeds[i].n(), P->seeds[i].blocks(), P->seed_smem[i], side));
   if (fork) KS_TRY(cudaEventRecord(P->ev_join, side));
   for (int c = 0; c < 2; c++)
     if (P->norm[c].n())
-      KS_TRY(launch_normalize_batch(c == 0 ? 16 : 28, P->norm[c].d, P->norm[c].dprefix,
+      KS_TRY(launch_normalize_batch(c == 0 ? 16 : 32, P->norm[c].d, P->norm[c].dprefix,
                                     P->normc[c].dprefix, P->norm[c].n(), P->norm[c].blocks(),
                                     P->normc[c].blocks(), s));
   if (P->unpack.n())
@@ -230,8 +235,8 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   plan_norm_jobs(p, cols, words, flags, jobs);
   NormArgs na;
   if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
-  P->norm[p.dn == 28 ? 1 : 0].add(na, norm_blocks(na));
-  P->normc[p.dn == 28 ? 1 : 0].add(na, norm_carry_blocks(na));
+  P->norm[p.dn == 32 ? 1 : 0].add(na, norm_blocks(na));
+  P->normc[p.dn == 32 ? 1 : 0].add(na, norm_carry_blocks(na));
   const uint32_t *V0 = words, *V1 = words + p.nwords;
   const int ol = p.out_limbs;
   if (p.variant == KS_1 || p.variant == KS_2) {
@@ -245,12 +250,17 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws + p.off_seedacc);
     SeedPlan sp;
     if (make_seed_plan(q.f, p.lf, p.b, q.g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl,
-                       p.C, acc, seeds, p.seed_words, sp) != 0)
+                       p.C, acc, seeds, p.seed_words,
+                       reinterpret_cast<__half *>(ws + p.off_planes), sp) != 0)
       return KS_ERANGE;
     if (sp.kind != 0) {
       const int i = seed_kind_index(sp.kind);
       if (i < 0) return KS_ERANGE;
       P->seeds[i].add(sp.a, sp.blocks);
+      if (sp.narrow()) {
+        P->planes.add(sp.a, planes_blocks(sp.a));
+        if (sp.a.smem > P->seed_smem[i]) P->seed_smem[i] = sp.a.smem;
+      }
     }
     RecoverArgs ra;
     int64_t blocks;
@@ -347,6 +357,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
               P->normc[1].bytes() + P->unpack.bytes() +
               0;
   for (int i = 0; i < kSeedKinds; i++) db += P->seeds[i].bytes();
+  db += P->planes.bytes();
   for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
   P->desc_bytes = db;
   if (alloc_device(reinterpret_cast<void **>(&P->desc), db) != cudaSuccess ||
@@ -367,6 +378,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   }
   P->unpack.place(h, d);
   for (int i = 0; i < kSeedKinds; i++) P->seeds[i].place(h, d);
+  P->planes.place(h, d);
   for (int c = 0; c < 3; c++) P->recover[c].place(h, d);
   if (cudaMemcpy(P->desc, P->hdesc, db, cudaMemcpyHostToDevice) != cudaSuccess) {
     ks_plan_destroy(P);

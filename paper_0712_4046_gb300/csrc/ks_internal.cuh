@@ -26,7 +26,7 @@ struct TcGeom {
   int64_t T = 0;      // output tiles of 128 block columns
   int64_t nE = 0;     // rows of the A window array (8 fp16 digits each, zero padded)
   int64_t rows = 0;   // rows per B plane, zero padding included
-  int64_t ncols = 0;  // output column sums of four 7-bit digits (28-bit digits)
+  int64_t ncols = 0;  // output column sums of four 8-bit digits (32-bit digits)
 };
 
 struct Plan {
@@ -58,7 +58,7 @@ struct Plan {
   // workspace layout (byte offsets from the base)
   size_t off_digits = 0, off_cols = 0, off_flags = 0, off_words = 0;
   int64_t flag_bytes = 0;  // the normalization's per-tile transfer functions
-  size_t off_seeds = 0, off_seedacc = 0, off_hp = 0, off_ntt = 0;
+  size_t off_seeds = 0, off_seedacc = 0, off_planes = 0, off_hp = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
 };
@@ -216,7 +216,7 @@ int64_t norm_blocks(const NormArgs &a);        // CTAs of the tile pass
 int64_t norm_carry_blocks(const NormArgs &a);  // CTAs of the carry pass
 // bytes of a product's flag region (the tiles' transfer functions)
 int64_t norm_flag_bytes(int njobs, int64_t ntiles);
-// the two launches for a whole batch, per digit width d (16 or 28)
+// the two launches for a whole batch, per digit width d (16 or 32)
 cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix_tiles,
                                    const int64_t *prefix_carry, int n, int64_t tile_blocks,
                                    int64_t carry_blocks, cudaStream_t s);
@@ -298,7 +298,12 @@ struct SeedArgs {
   int kb;                // K = 2^kb is added (sgn), else kb < 0
   int64_t k00, kstep, ncl;
   int C;
-  int64_t slices, tslice;   // narrow path: items per cluster, indices t per item
+  int64_t slices;           // narrow path: windows of the t' axis (partials per value)
+  int G;                    // narrow path: clusters per CTA (1, 2 or 4)
+  int smem;                 // narrow path: dynamic shared memory of a CTA
+  int P;                    // narrow path: balanced 8-bit digits per coefficient (2 .. 9)
+  int64_t Z;                // narrow path: origin of the reversed g planes (Z = k00 mod 8)
+  __half *planes;           // narrow path: the digit planes (fp16)
   // narrow path: per (value, slice) six 32-bit words of the slice's partial
   // (value v, slice s at acc + (v slices + s) 6)
   unsigned long long *acc;
@@ -306,23 +311,32 @@ struct SeedArgs {
   int seed_words;
 };
 struct SeedPlan {
-  // 0 none; 1-6 narrow (both operands <= 64 bits; by path and cluster size);
-  // 100 + words: wide
+  // 0 none; 10 P + C narrow (both operands <= 64 bits; P digits per
+  // coefficient, clusters of C values); 100 + words: wide
   int kind = 0;
   SeedArgs a;
   int64_t blocks = 0, nvalues = 0;
   bool narrow() const { return kind >= 1 && kind < 100; }
 };
-// items per seed cluster of the narrow path (slices of its t range)
+// partials per seed value of the narrow path (windows of the t' axis)
 int64_t seed_slices(int64_t lf, int64_t lg, int C);
 int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int64_t lg, int bg,
                    int sgn, int kb, int64_t k00, int64_t kstep, int64_t ncl, int C,
-                   unsigned long long *acc, uint32_t *seeds, int seed_words, SeedPlan &sp);
+                   unsigned long long *acc, uint32_t *seeds, int seed_words, __half *planes,
+                   SeedPlan &sp);
+// narrow seeds: digits per coefficient (-1: too wide), bytes of the digit
+// planes, blocks of their kernel
+int seed_digits(int bf, int bg, int sgn);
+int64_t seed_planes_bytes(int64_t lf, int64_t lg, int P);
+int64_t planes_blocks(const SeedArgs &a);
+cudaError_t launch_seed_planes(const SeedArgs *d, const int64_t *prefix, int n, int64_t blocks,
+                               cudaStream_t s);
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s);
+// smem: the largest dynamic shared memory of the batch's CTAs (narrow kinds)
 cudaError_t launch_seeds_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
-                               int64_t blocks, cudaStream_t s);
+                               int64_t blocks, int smem, cudaStream_t s);
 int seed_kind_index(int kind);  // 0 .. kSeedKinds - 1, or -1
-constexpr int kSeedKinds = 12;  // six narrow kinds, then wide classes of 2 .. 64 words
+constexpr int kSeedKinds = 16;  // ten narrow kinds, then wide classes of 2 .. 64 words
 extern const int kSeedKindList[kSeedKinds];
 
 struct RecoverArgs {
@@ -409,6 +423,10 @@ struct PhaseTimer {
 };
 
 // ---------------------------------------------------------------- device helpers
+// Status words hold the first failure a kernel recorded (0 = none): 1 a
+// bounded wait gave up, 2 a reconstruction carry out of range, 3 an internal
+// range check.  Writers use atomicCAS(status, 0, code), so a later failure
+// that follows from the first (garbage in, range checks out) does not hide it.
 // bits [pos, pos + 64) of a little-endian word array; words >= n read as 0.
 __device__ __forceinline__ uint64_t get_bits64(const uint32_t *w, int64_t n, int64_t pos) {
   int64_t i = pos >> 5;

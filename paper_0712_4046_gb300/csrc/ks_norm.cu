@@ -58,8 +58,8 @@ struct Geo<16> {
   static constexpr int WPT = 4, CPT = 8, BACK = 6;
 };
 template <>
-struct Geo<28> {
-  static constexpr int WPT = 7, CPT = 8, BACK = 3;
+struct Geo<32> {
+  static constexpr int WPT = 8, CPT = 8, BACK = 3;  // column -3's top slice is word -1's
 };
 // staged columns of a tile: 128 CPT + BACK, one padding slot per 8 (banks)
 constexpr int kStage = (kThreads * 8 + 8) + (kThreads * 8 + 8) / 8 + 8;
@@ -346,7 +346,7 @@ constexpr int tile_words() { return kThreads * Geo<D>::WPT; }
 
 }  // namespace
 
-int norm_tile_words(int d) { return d == 28 ? tile_words<28>() : tile_words<16>(); }
+int norm_tile_words(int d) { return d == 32 ? tile_words<32>() : tile_words<16>(); }
 
 int64_t norm_tiles_for(int64_t nwords, int d) {
   const int tw = norm_tile_words(d);
@@ -356,7 +356,7 @@ int64_t norm_tiles_for(int64_t nwords, int d) {
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
                    NormArgs &a) {
   if (njobs < 1 || njobs > 4) return -1;
-  if (d != 16 && d != 28) return -1;
+  if (d != 16 && d != 32) return -1;
   if (ntiles * norm_tile_words(d) < nwords || (nwords & 3) != 0) return -1;
   a = NormArgs{};
   for (int i = 0; i < njobs; i++) a.job[i] = jobs[i];
@@ -388,9 +388,9 @@ cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwor
   if (make_norm_args(jobs, njobs, d, nwords, ntiles, a) != 0) return cudaErrorInvalidValue;
   const One<NormArgs> one{a};
   const unsigned g1 = (unsigned)norm_blocks(a), g2 = (unsigned)norm_carry_blocks(a);
-  if (d == 28) {
-    norm_tiles<28, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
-    norm_carry<28, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
+  if (d == 32) {
+    norm_tiles<32, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
+    norm_carry<32, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
   } else {
     norm_tiles<16, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
     norm_carry<16, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
@@ -404,9 +404,9 @@ cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *pre
                                    int64_t carry_blocks, cudaStream_t s) {
   if (n == 0 || tile_blocks == 0) return cudaSuccess;
   const Many<NormArgs> t{da, prefix_tiles, n}, c{da, prefix_carry, n};
-  if (d == 28) {
-    norm_tiles<28, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
-    norm_carry<28, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
+  if (d == 32) {
+    norm_tiles<32, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
+    norm_carry<32, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
   } else {
     norm_tiles<16, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
     norm_carry<16, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);

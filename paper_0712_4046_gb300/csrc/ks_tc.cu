@@ -1,19 +1,19 @@
 // Tensor-core engine: exact column sums C_k = sum_i A_i B_(k-i) of signed
-// 7-bit digit strings on the 5th-generation tensor cores (tcgen05.mma,
+// 8-bit digit strings on the 5th-generation tensor cores (tcgen05.mma,
 // kind::f16, fp16 operands, fp32 accumulation in tensor memory).
 //
 // Digits and exactness.  Each evaluation digit D_j (a signed sum of at most
-// eight 7-bit bit slices, Sec. 3) is recoded into the balanced form
-//   D'_j = D_j - 128 c_j + c_(j-1),   c_j = floor((D_j + 64) / 128),
+// P <= 8 bit slices of 8 bits, Sec. 3) is recoded into the balanced form
+//   D'_j = D_j - 256 c_j + c_(j-1),   c_j = floor((D_j + 128) / 256),
 // which keeps the value of the digit string (one more top digit holds the
-// last carry), needs no carry chain, and gives |D'_j| <= 72.  An accumulation
-// chunk of ks <= 16 block offsets adds at most 16 * 128 products per output
-// digit, so every partial sum stays below 2048 * 72^2 = 10,616,832 < 2^24 and
-// fp32 holds it exactly.  After each chunk the accumulator is read out of
-// tensor memory, converted to int32 (exact) and added to per-thread integer
-// sums; after a work item the sums of four neighbouring digits are merged
-// into one 28-bit-digit column sum and added to global memory with a 64-bit
-// atomic.
+// last carry), needs no carry chain, and gives |D'_j| <= 128 + P <= 136
+// (fp16 holds it exactly).  An accumulation chunk of ks <= 7 block offsets
+// adds at most 7 * 128 products per output digit, so every partial sum stays
+// below 896 * 136^2 = 16,572,416 < 2^24 and fp32 holds it exactly.  After
+// each chunk the accumulator is read out of tensor memory, converted to int32
+// (exact) and added to per-thread integer sums; after a work item the sums of
+// four neighbouring digits are merged into one 32-bit-digit column sum and
+// added to global memory with a bulk reduction.
 //
 // Blocking (a product of digit strings is a Toeplitz matrix-vector product):
 // write output digit k = 128 p + q.  For a block offset delta,
@@ -56,6 +56,8 @@
 // returns.
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -64,8 +66,8 @@ namespace ks {
 namespace {
 constexpr int kTM = 128;                   // MMA M: digits per output block column
 constexpr int kNT = 128;                   // MMA N (largest): block columns per tile
-constexpr int kKS = 16;                    // largest number of delta steps per chunk
-constexpr int kStages = 2;
+constexpr int kKS = 7;                     // largest number of delta steps per chunk
+constexpr int kStages = 3;
 constexpr int kCoreA = 16 * kKS + 15;      // A strip core matrices per chunk
 constexpr int kBRows = kNT + kKS - 1;      // B rows per plane per chunk
 constexpr int kStageA = kCoreA * 128;
@@ -80,13 +82,13 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kNumAcc = 4;
 constexpr int kTmemCols = kNT * kNumAcc;
-constexpr int kMaxItemChunks = 128;        // int32 sums: 128 * 10,616,832 < 2^31
+constexpr int kMaxItemChunks = 128;        // int32 sums: 128 * 16,572,416 < 2^31
 constexpr int kPackSeg = 2048;             // A window rows / reversed B digits per pack CTA
 constexpr int kPackStageWords = 2048;       // coefficient words a pack CTA stages (16 KB)
 // instruction descriptor, kind::f16: D = f32 (bits 4-5 = 1), A = B = f16
 // (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t kIdescM = (1u << 4) | ((uint32_t)(kTM >> 4) << 24);
-constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint64_t kWaitNs = 1000000000ull;  // default bound of every wait (1 s)
 static_assert(kSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -120,19 +122,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait (limit ns of %globaltimer) for the phase with the given
+// parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit) return false;
   return true;
 }
 // all eight epilogue warps meet (bounded); false on timeout
-__device__ __forceinline__ bool epi_sync(uint64_t *bar, uint32_t &ph, int lane) {
+__device__ __forceinline__ bool epi_sync(uint64_t *bar, uint32_t &ph, int lane, uint64_t limit) {
   __syncwarp();
   if (lane == 0) mbar_arrive(bar);
-  const bool ok = mbar_wait(bar, ph);
+  const bool ok = mbar_wait(bar, ph, limit);
   ph ^= 1;
   return __all_sync(0xffffffffu, ok);
 }
@@ -222,14 +225,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }  // namespace
 
 // ------------------------------------------------------------------ pack
-__device__ __forceinline__ int32_t carry7(int32_t d) { return (d + 64) >> 7; }
+__device__ __forceinline__ int32_t carry8(int32_t d) { return (d + 128) >> 8; }
 // balanced recoding of digit d whose lower neighbour is prev
-__device__ __forceinline__ int32_t recode7(int32_t d, int32_t prev) {
-  return d - (carry7(d) << 7) + carry7(prev);
+__device__ __forceinline__ int32_t recode8(int32_t d, int32_t prev) {
+  return d - (carry8(d) << 8) + carry8(prev);
 }
 
 // One CTA writes kPackSeg rows of an A window array or 16 storage rows of the
-// 16 B planes of one sub-product: first the plain 7-bit digits of the segment
+// 16 B planes of one sub-product: first the plain 8-bit digits of the segment
 // (one more for the recoding carry) into shared memory, then the recoded
 // fp16 digits in the operand layout, 16 bytes per thread, coalesced.
 template <class Src>
@@ -257,20 +260,20 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     // digits x0 - 1 + i, i < kPackSeg + 8: runs of eight per thread (digits
     // at negative positions come out as zero)
     int64_t t_lo, t_hi, src0;
-    field_range<7>(op, x0 - 1, x0 + kPackSeg + 6, a.N, a.ninv, a.b, t_lo, t_hi);
+    field_range<8>(op, x0 - 1, x0 + kPackSeg + 6, a.N, a.ninv, a.b, t_lo, t_hi);
     const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
     __syncthreads();
     for (int i0 = 8 * tid; i0 < kPackSeg + 8; i0 += 8 * 256) {
       int32_t v[8];
       if (staged)
-        digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
       else
-        digit_run<7, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
+        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
 #pragma unroll
       for (int m = 0; m < 8; m++) raw[i0 + m] = v[m];
     }
     __syncthreads();
-    for (int i = tid; i < kPackSeg + 7; i += 256) dig[i] = __int2half_rn(recode7(raw[i + 1], raw[i]));
+    for (int i = tid; i < kPackSeg + 7; i += 256) dig[i] = __int2half_rn(recode8(raw[i + 1], raw[i]));
     __syncthreads();
     __half *E = a.E[q];
     for (int i = tid; i < kPackSeg; i += 256) {
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     // reversed digits j = top - (128 rho0 + m), m <= kPackSeg: runs of eight
     // consecutive j per thread, zero outside [0, top]
     int64_t t_lo, t_hi, src0;
-    field_range<7>(op, top - 128 * rho0 - kPackSeg - 7, top - 128 * rho0, a.N, a.ninv, a.b, t_lo,
+    field_range<8>(op, top - 128 * rho0 - kPackSeg - 7, top - 128 * rho0, a.N, a.ninv, a.b, t_lo,
                    t_hi);
     const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
     __syncthreads();
@@ -301,9 +304,9 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
       const int64_t jhi = top - (128 * rho0 + m0);  // j of m0; j of m0 + 7 is jhi - 7
       int32_t v[8];
       if (staged)
-        digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
       else
-        digit_run<7, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
+        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const int64_t j = jhi - u;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
       }
     }
     __syncthreads();
-    for (int m = tid; m < kPackSeg; m += 256) dig[m] = __int2half_rn(recode7(raw[m], raw[m + 1]));
+    for (int m = tid; m < kPackSeg; m += 256) dig[m] = __int2half_rn(recode8(raw[m], raw[m + 1]));
     __syncthreads();
     const int t1 = tid >> 4, u = tid & 15;
     const int64_t s = s0 + u;
@@ -421,8 +424,12 @@ __device__ __forceinline__ void slot_load(TcSlot &v, const TcSlot *src) {
 }
 }  // namespace
 
+// wait_ns bounds every wait of the kernel; stall (a test hook) makes the copy
+// warp wait, before its first copy, on a barrier that nothing completes, so the
+// kernel's waits run out while no copy or MMA is in flight.
 template <class Src>
-__global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total) {
+__global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total, uint64_t wait_ns,
+                                                          int stall) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_full[kStages];
   __shared__ __align__(8) uint64_t bar_empty[kStages];
@@ -432,6 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
   __shared__ __align__(8) uint64_t bar_iempty[kItemSlots];
   __shared__ __align__(8) uint64_t bar_drain;
   __shared__ __align__(8) uint64_t bar_epi;
+  __shared__ __align__(8) uint64_t bar_never;  // the stall hook's: nothing arrives on it
   __shared__ TcSlot slots[kItemSlots];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh, bad_range_sh;
@@ -465,6 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
     }
     mbar_init(&bar_drain, 1);
     mbar_init(&bar_epi, kEpiWarps);
+    mbar_init(&bar_never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
     bad_range_sh = 0;
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
           tc_decode(src, s, s_end, it, next);
         else
           it.done = 1;
-        if (!mbar_wait(&bar_iempty[islot], iphase ^ 1) || *abort_v) {
+        if (!mbar_wait(&bar_iempty[islot], iphase ^ 1, wait_ns) || *abort_v) {
           aborted = true;
           break;
         }
@@ -507,7 +516,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
         s = next;
         if (status_sh == nullptr) status_sh = it.status;
         for (int c = it.c0; c < it.c1; c++) {
-          if (!mbar_wait(&bar_empty[stage], phase ^ 1) || *abort_v) {
+          if (!mbar_wait(&bar_empty[stage], phase ^ 1, wait_ns) || *abort_v) {
+            aborted = true;
+            break;
+          }
+          if (stall && !mbar_wait(&bar_never, 0, wait_ns)) {  // the test hook: gives up
             aborted = true;
             break;
           }
@@ -542,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       if (aborted) {
         *abort_v = 1;
         for (int s = 0; s < kStages; s++)  // copies still in flight land before exit
-          if (armed & (1u << s)) mbar_wait(&bar_full[s], (armed_par >> s) & 1);
+          if (armed & (1u << s)) mbar_wait(&bar_full[s], (armed_par >> s) & 1, wait_ns);
       }
     }
   } else if (warp == 1) {
@@ -556,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
     const uint32_t lane_u = (uint32_t)lane;
     const uint64_t zdesc = sdesc(smem_u32(smem + kStages * kStage), 128u, 128u);
     for (;;) {
-      const bool iok = mbar_wait(&bar_ifull[islot], iphase);
+      const bool iok = mbar_wait(&bar_ifull[islot], iphase, wait_ns);
       if (__any_sync(0xffffffffu, !iok || *abort_v)) {
         aborted = true;
         break;
@@ -571,7 +584,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       }
       if (it.done) break;
       for (int c = it.c0; c < it.c1; c++) {
-        const bool ok = mbar_wait(&bar_full[stage], phase) && mbar_wait(&bar_tempty[acc], aphase ^ 1);
+        const bool ok = mbar_wait(&bar_full[stage], phase, wait_ns) &&
+                        mbar_wait(&bar_tempty[acc], aphase ^ 1, wait_ns);
         if (__any_sync(0xffffffffu, !ok || *abort_v)) {
           aborted = true;
           break;
@@ -621,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       if (lane == 0) *abort_v = 1;
       if (issued) {  // every MMA issued so far completes before the memory is released
         mma_commit_lane0(&bar_drain, lane_u);
-        mbar_wait(&bar_drain, 0);
+        mbar_wait(&bar_drain, 0, wait_ns);
       }
     }
   } else {
@@ -634,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
     uint32_t aphase = 0, iphase = 0, ephase = 0;
     bool aborted = false;
     for (;;) {
-      const bool iok = mbar_wait(&bar_ifull[islot], iphase);
+      const bool iok = mbar_wait(&bar_ifull[islot], iphase, wait_ns);
       if (__any_sync(0xffffffffu, !iok || *abort_v)) {
         aborted = true;
         break;
@@ -652,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
 #pragma unroll
       for (int i = 0; i < 64; i++) sum[i] = 0;
       for (int c = it.c0; c < it.c1; c++) {
-        const bool ok = mbar_wait(&bar_tfull[acc], aphase);
+        const bool ok = mbar_wait(&bar_tfull[acc], aphase, wait_ns);
         if (__any_sync(0xffffffffu, !ok || *abort_v)) {
           aborted = true;
           break;
@@ -678,8 +692,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
         }
       }
       if (aborted) break;
-      // Four neighbouring digits (lanes 4g .. 4g + 3, weights 128^w) form one
-      // 28-bit-digit column sum.  A two-step butterfly over each group of
+      // Four neighbouring digits (lanes 4g .. 4g + 3, weights 256^w) form one
+      // 32-bit-digit column sum.  A two-step butterfly over each group of
       // four block columns gives lane 4g + u the whole sum of column i + u:
       // step 1 (lanes u, u ^ 1) pairs the columns i + (u & 1) and
       // i + 2 + (u & 1), step 2 (lanes u, u ^ 2) completes column i + u.
@@ -687,13 +701,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
       // are contiguous in C: they are staged in shared memory and added with
       // one bulk reduction.
       if (epi_leader) bulk_wait_read_all();  // the previous tile's reduction has read the staging
-      if (!epi_sync(&bar_epi, ephase, lane)) {
+      if (!epi_sync(&bar_epi, ephase, lane, wait_ns)) {
         aborted = true;
         break;
       }
       {
         const bool odd = (u & 1) != 0, up = (u & 2) != 0;
-        const long long w_me = 1ll << (7 * u), w_x1 = 1ll << (7 * (u ^ 1));
+        const long long w_me = 1ll << (8 * u), w_x1 = 1ll << (8 * (u ^ 1));
         long long *srow = staging + 8 * quad + (lane >> 2);
 #pragma unroll
         for (int i = 0; i < 64; i += 4) {
@@ -708,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (!epi_sync(&bar_epi, ephase, lane)) {
+      if (!epi_sync(&bar_epi, ephase, lane, wait_ns)) {
         aborted = true;
         break;
       }
@@ -730,8 +744,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total)
   __syncthreads();
   tc_fence_after();
   if (tid == 0 && status_sh) {
-    if (*abort_v) atomicExch(status_sh, 1);
-    if (bad_range_sh) atomicExch(status_sh, 3);
+    if (*abort_v) atomicCAS(status_sh, 0, 1);
+    if (bad_range_sh) atomicCAS(status_sh, 0, 3);
   }
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
@@ -822,6 +836,10 @@ static cudaError_t tc_attr(int *sms) {
 
 int64_t tc_work(const TcGeom &g) { return tc_offset_prefix(g.dmax, g.R, g.T); }
 
+// the wait bound and the stall hook of the kernel (a test hook; see ks.h)
+static std::atomic<int> g_tc_stall{0};
+static std::atomic<unsigned long long> g_tc_wait_ns{kWaitNs};
+
 void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
                   TcArgs &a) {
   a = TcArgs{};
@@ -855,7 +873,9 @@ cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base, int64_t *
   const int64_t work = a.work_prefix[nprod];
   if (work <= 0) return cudaSuccess;
   const int64_t grid = work < sms ? work : sms;
-  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, work);
+  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, work,
+                                                                  g_tc_wait_ns.load(),
+                                                                  g_tc_stall.load());
   note_launches(1);
   return cudaGetLastError();
 }
@@ -867,9 +887,15 @@ cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64
   cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
   const int64_t grid = work < sms ? work : sms;
-  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(Many<TcArgs>{d, prefix, n}, work);
+  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(
+      Many<TcArgs>{d, prefix, n}, work, g_tc_wait_ns.load(), g_tc_stall.load());
   note_launches(1);
   return cudaGetLastError();
 }
 
 }  // namespace ks
+
+extern "C" void ks_debug_tc_stall(int on, int64_t wait_ns) {
+  ks::g_tc_stall.store(on ? 1 : 0);
+  ks::g_tc_wait_ns.store(wait_ns > 0 ? (unsigned long long)wait_ns : ks::kWaitNs);
+}

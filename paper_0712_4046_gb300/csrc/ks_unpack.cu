@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
                      ~(int64_t)3;
   const int64_t capw = staged_words(chain, M, cpc), capd = staged_digits(chain, cpc);
   if (nu > capw || nw > capw || ub0 < 0 || wb0 < 0 || (chain & (chain - 1)) != 0 || ol > 2) {
-    if (tid == 0) atomicExch(status, 3);  // not for a plan from make_recover_args
+    if (tid == 0) atomicCAS(status, 0, 3);  // not for a plan from make_recover_args
     return;
   }
   uint32_t *su = stg, *sw = stg + capw;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
   }
   __syncthreads();
   if (!__syncthreads_and(stage_wait(&bar))) {
-    if (tid == 0) atomicExch(status, 1);
+    if (tid == 0) atomicCAS(status, 0, 1);
     stage_wait(&bar);  // once more (bounded) for the copies in flight before leaving
     return;
   }
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
       a_cur = load_d1(s1, kAccSeedWords, 0, M);
       const uint64_t us = du[ln];
       const uint64_t dprev = (us - b_prev - a_cur) & mask;
-      if (dprev > 1) atomicExch(status, 2);
+      if (dprev > 1) atomicCAS(status, 0, 2);
       delta = (b_prev + a_cur + dprev - us) >> M;
     }
     uint64_t w_cur = dw[ln];
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
     a_cur = load_d2(s1, kAccSeedWords, 0, M);
     const D2 us = DU(0);
     const D2 dprev = sub_d2(sub_d2(us, b_prev, 0, M), a_cur, 0, M);
-    if (dprev.hi != 0 || dprev.lo > 1) atomicExch(status, 2);
+    if (dprev.hi != 0 || dprev.lo > 1) atomicCAS(status, 0, 2);
     delta = carry_d2(b_prev, a_cur, dprev.lo & 1ull, M);
   }
   D2 w_cur = DW(0);
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(64) recover_wide(Src src) {
     dig_sub(dp, t1, a_cur, 0, M);
     bool ok = dp.w[0] <= 1;
     for (int i = 1; i < W; i++) ok = ok && dp.w[i] == 0;
-    if (!ok) atomicExch(status, 2);
+    if (!ok) atomicCAS(status, 0, 2);
     delta = dig_add_carry(b_prev, a_cur, dp.w[0] & 1u, M);
   }
   dig_load(w_cur, L.B, nwords, L.offB + L.pB * (int64_t)M, M);

@@ -80,3 +80,38 @@ def test_workspace_is_host_computable(ks):
         assert n > 0 and n % 256 == 0
     v, e = ks.choose(16384, 16384, 48, True)
     assert v in (1, 2, 3, 4) and e in (1, 2, 3)
+
+
+def test_binding_refuses_wrong_layouts_before_any_device_call():
+    # shapes, dtypes and devices are checked before a pointer reaches the C ABI
+    import torch
+
+    import paper_0712_4046_gb300 as ks
+    lf, lg, b = 5, 4, 70  # two limbs per coefficient
+    ol = ks.out_limbs(lf, lg, b, True)
+    f = torch.zeros((lf, 2), dtype=torch.int64)
+    g = torch.zeros((lg, 2), dtype=torch.int64)
+    h = torch.zeros((lf + lg - 1, ol), dtype=torch.int64)
+    bad = [
+        (h, torch.zeros((lf, 1), dtype=torch.int64), g, "shape"),          # one limb short
+        (h, f, torch.zeros((lg, 2), dtype=torch.int32), "dtype"),          # 4-byte elements
+        (torch.zeros((lf + lg, ol), dtype=torch.int64), f, g, "shape"),   # h one row long
+        (torch.zeros((lf + lg - 1, ol + 1), dtype=torch.int64), f, g, "shape"),
+        (h, torch.zeros((2, lf), dtype=torch.int64).t(), g, "contiguous"),  # transposed
+        (h, torch.zeros((lf, 2, 1), dtype=torch.int64), g, "2-d"),
+        (h, torch.zeros((lf, 4), dtype=torch.int64)[:, ::2], g, "contiguous"),
+    ]
+    for hh, ff, gg, what in bad:
+        with pytest.raises(ValueError, match=what):
+            ks.ks_mul(hh, ff, gg, b, True, ks.KS_4)
+    # correct layouts on the host: refused for the device, still before the ABI
+    with pytest.raises(ValueError, match="CUDA"):
+        ks.ks_mul(h, f, g, b, True, ks.KS_4)
+    with pytest.raises(ValueError, match="CUDA"):
+        ks.ks_mul_static(h, f, g, b, True, ks.KS_4)
+    with pytest.raises(ValueError, match="shape"):
+        ks.ks_mul_bits(h, f, 70, torch.zeros((lg, 2), dtype=torch.int64), 64, True)
+    with pytest.raises(ValueError, match="shape"):
+        ks.ks_mul_mod(torch.zeros((lf + lg - 1, 2), dtype=torch.int64),
+                      torch.zeros((lf, 1), dtype=torch.int64),
+                      torch.zeros((lg, 1), dtype=torch.int64), 97)
