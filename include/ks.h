@@ -332,6 +332,18 @@ const char *ks_last_cuda_error(void);
 long long ks_launch_count(void);
 
 /*
+ * Launch overlap (no counterpart in the paper).  With enabled != 0 the
+ * library launches its kernels with programmatic dependent launch: a kernel
+ * may be scheduled while the previous kernel of its stream is still running
+ * and waits on the device, before touching memory, until that kernel has
+ * finished.  enabled = 0 (the default) launches every kernel after the
+ * previous one has finished.  Results are identical either way.  Calls and
+ * plans captured afterwards use the setting; plans captured earlier keep
+ * theirs.
+ */
+void ks_set_pdl(int enabled);
+
+/*
  * Host-side fault injection for tests (no counterpart in the paper): the next
  * n device allocations the library makes (cached workspaces, plans) fail as
  * if the device were out of memory, so the calls return KS_ENOMEM.  No device

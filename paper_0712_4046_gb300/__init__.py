@@ -60,6 +60,7 @@ _sig("ks_plan_destroy", None, _vp)
 _sig("ks_plan_status", _ci, _vp)
 _sig("ks_debug_fail_allocs", None, _ci)
 _sig("ks_debug_tc_stall", None, _ci, _i64)
+_sig("ks_set_pdl", None, _ci)
 
 DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
 
@@ -361,6 +362,14 @@ def mul(f, g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO, stream
                          dtype=torch.int64, device=f.device)
         ks_mul_ex(h, f, g, coeff_bits, is_signed, variant, engine, ws, stream)
     return h
+
+
+def set_pdl(enabled: bool) -> None:
+    """Launch overlap: enabled, every kernel may be scheduled while the previous
+    kernel of its stream runs and waits for it on the device (programmatic
+    dependent launch); off (the default), kernels start after the previous one
+    ends.  Results are identical either way."""
+    lib.ks_set_pdl(1 if enabled else 0)
 
 
 def debug_fail_allocs(n: int) -> None:

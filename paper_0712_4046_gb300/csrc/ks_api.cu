@@ -28,6 +28,9 @@ static int cuda_fail(cudaError_t e) {
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static std::atomic<int> g_pdl{0};
+bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed) != 0; }
+
 struct PhaseRecord {
   int phase;
   cudaEvent_t a, b;
@@ -199,9 +202,9 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
                              (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3)) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
-  p.off_seedacc = off;  // narrow seeds: six words per (value, slice), each written once
+  p.off_seedacc = off;  // narrow seeds: six column sums per value
   if (b <= 64 && p.nseeds > 0)
-    off = align256(off + (size_t)p.nseeds * seed_slices(lf, lg, p.C) * 6 * 8);
+    off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_planes = off;   // narrow seeds: the coefficients' balanced 8-bit digit planes
   if (b <= 64 && p.nseeds > 0) off = align256(off + (size_t)seed_planes_bytes(lf, lg, seed_digits(b, b, p.is_signed)));
   p.off_flags = off;
@@ -458,6 +461,16 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     if (rc != KS_OK) return rc;
   }
   const cudaStream_t side = fk.side != nullptr ? fk.side : s;
+  // the seeds read only f and g, on the helper stream: the digit planes from
+  // the start, beside the packing
+  if (recon && sp.narrow()) {
+    if (side != s) {
+      KS_CUDA(cudaEventRecord(fk.fork, s));
+      KS_CUDA(cudaStreamWaitEvent(side, fk.fork, 0));
+    }
+    PhaseTimer t(side, PH_SEEDS);
+    KS_CUDA(launch_seed_planes_one(sp, side));
+  }
 
   // sub-product p: (reversed, sigma)
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
@@ -505,9 +518,9 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     }
   }
 
-  // the exact seeds read only f and g: on the helper stream, forked after the
-  // products (the persistent product kernels want every SM, and share their
-  // SMs' shared-memory bandwidth with no one), overlapping the normalization
+  // the seed contraction: on the helper stream, forked after the products (the
+  // persistent product kernels want every SM, and share their SMs'
+  // shared-memory bandwidth with no one), overlapping the normalization
   if (recon && sp.kind != 0) {
     if (side != s) {
       KS_CUDA(cudaEventRecord(fk.fork, s));
@@ -542,7 +555,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     RecoverArgs ra;
     int64_t blocks = 0;
     if (make_recover_args(h, ol, p.kb, runs, p.nruns, p.nwords, p.M, p.chain, p.C,
-                          sp.narrow() ? seed_acc : nullptr, sp.a.slices, seeds, p.seed_words,
+                          sp.narrow() ? seed_acc : nullptr, seeds, p.seed_words,
                           status, ra, blocks) != 0)
       return KS_ERANGE;
     PhaseTimer t(s, PH_RECOVER);
@@ -927,6 +940,8 @@ const char *ks_strerror(int status) {
 const char *ks_last_cuda_error(void) { return g_cuda_err; }
 
 void ks_debug_fail_allocs(int n) { g_fail_allocs.store(n < 0 ? 0 : n); }
+
+void ks_set_pdl(int enabled) { g_pdl.store(enabled ? 1 : 0); }
 
 long long ks_launch_count(void) { return g_launches.load(); }
 

@@ -37,6 +37,7 @@ struct ZeroArgs {
 
 template <class Src>
 __global__ void __launch_bounds__(256) zero_kernel(Src src) {
+  pdl_enter();
   int64_t local;
   const ZeroArgs &a = src.locate(blockIdx.x, local);
   const int64_t i = local * 256 + threadIdx.x;
@@ -127,8 +128,22 @@ namespace {
   } while (0)
 
 cudaError_t issue(ks_plan *P, cudaStream_t s) {
+  // the seeds read only the inputs, on the helper stream: the digit planes
+  // from the start (beside the packing), the seed contraction after the
+  // products (which want every SM); joined before the reconstruction
+  bool any_seeds = false;
+  for (int i = 0; i < kSeedKinds; i++) any_seeds = any_seeds || P->seeds[i].n() > 0;
+  const bool fork = P->side != nullptr && any_seeds;
+  cudaStream_t side = fork ? P->side : s;
+  if (fork) {
+    KS_TRY(cudaEventRecord(P->ev_fork, s));
+    KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
+  }
+  if (P->planes.n())
+    KS_TRY(launch_seed_planes(P->planes.d, P->planes.dprefix, P->planes.n(), P->planes.blocks(),
+                              side));
   if (P->zero.n()) {
-    zero_kernel<Many<ZeroArgs>><<<(unsigned)P->zero.blocks(), 256, 0, s>>>(
+    (void)launch_k(zero_kernel<Many<ZeroArgs>>, dim3((unsigned)P->zero.blocks()), dim3(256), 0, s, 
         Many<ZeroArgs>{P->zero.d, P->zero.dprefix, P->zero.n()});
     note_launches(1);
     KS_TRY(cudaGetLastError());
@@ -143,19 +158,10 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
                                    P->school.blocks(), s));
   if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, s));
   for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
-  // the seeds read only the inputs: on the helper stream, forked after the
-  // products, joined before the reconstruction
-  bool any_seeds = false;
-  for (int i = 0; i < kSeedKinds; i++) any_seeds = any_seeds || P->seeds[i].n() > 0;
-  const bool fork = P->side != nullptr && any_seeds;
-  cudaStream_t side = fork ? P->side : s;
   if (fork) {
     KS_TRY(cudaEventRecord(P->ev_fork, s));
     KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
   }
-  if (P->planes.n())
-    KS_TRY(launch_seed_planes(P->planes.d, P->planes.dprefix, P->planes.n(), P->planes.blocks(),
-                              side));
   for (int i = 0; i < kSeedKinds; i++)
     if (P->seeds[i].n())
       KS_TRY(launch_seeds_batch(kSeedKindList[i], P->seeds[i].d, P->seeds[i].dprefix,
@@ -265,7 +271,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     RecoverArgs ra;
     int64_t blocks;
     if (make_recover_args(q.h, ol, p.kb, runs, p.nruns, p.nwords, p.M, p.chain, p.C,
-                          sp.narrow() ? acc : nullptr, sp.a.slices, seeds, p.seed_words, status,
+                          sp.narrow() ? acc : nullptr, seeds, p.seed_words, status,
                           ra, blocks) != 0)
       return KS_ERANGE;
     P->recover[recover_class(p.M) - 1].add(ra, blocks);

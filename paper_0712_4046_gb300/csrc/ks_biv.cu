@@ -38,6 +38,7 @@ __device__ __forceinline__ uint64_t half_p(uint64_t a, uint64_t p) {
 // s_i f_(pi(i))[m - i N] mod p, with pi the identity or the reversal of the
 // rows and s_i = -1 for odd i at a negated point.
 __global__ void __launch_bounds__(256) biv_eval(const __grid_constant__ BivEvalArgs a) {
+  pdl_enter();
   const BivEval &e = a.e[blockIdx.y];
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < e.len;
        m += (int64_t)gridDim.x * blockDim.x) {
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(256) biv_eval(const __grid_constant__ BivEvalA
 // KS_1 / KS_2: h[k][j] = P1[k N + j] (KS_1), or (P1 + (-1)^k P2)[k N + j] / 2
 // (KS_2: the even rows from the sum, the odd ones from the difference).
 __global__ void __launch_bounds__(256) biv_readoff(BivReadArgs a) {
+  pdl_enter();
   const int64_t hx = 2 * a.lx - 1, total = (2 * a.ly - 1) * hx;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -89,6 +91,7 @@ __device__ __forceinline__ uint64_t comb(const BivSeq &q, int64_t m, uint64_t p)
 // Thread j carries c_(k-1)[j] and c_(k-1)[M + j] from block to block; block
 // k is row row0 + rstep k of h.
 __global__ void __launch_bounds__(128) biv_recover(BivRecoverArgs a) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.M) return;
   const int64_t hx = 2 * a.lx - 1;
@@ -115,20 +118,20 @@ unsigned grid1(int64_t n, int threads) {
 
 cudaError_t launch_biv_eval(const BivEvalArgs &a, int64_t maxlen, cudaStream_t s) {
   if (a.n < 1 || a.n > kMaxBivEvals) return cudaErrorInvalidValue;
-  biv_eval<<<dim3(grid1(maxlen, 256), (unsigned)a.n), 256, 0, s>>>(a);
+  (void)launch_k(biv_eval, dim3(dim3(grid1(maxlen, 256), (unsigned)a.n)), dim3(256), 0, s, a);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_biv_readoff(const BivReadArgs &a, cudaStream_t s) {
-  biv_readoff<<<grid1((2 * a.ly - 1) * (2 * a.lx - 1), 256), 256, 0, s>>>(a);
+  (void)launch_k(biv_readoff, dim3(grid1((2 * a.ly - 1) * (2 * a.lx - 1), 256)), dim3(256), 0, s, a);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_biv_recover(const BivRecoverArgs &a, cudaStream_t s) {
   if (a.n < 1) return cudaSuccess;
-  biv_recover<<<(unsigned)((a.M + 127) / 128), 128, 0, s>>>(a);
+  (void)launch_k(biv_recover, dim3((unsigned)((a.M + 127) / 128)), dim3(128), 0, s, a);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -304,8 +304,8 @@ struct SeedArgs {
   int P;                    // narrow path: balanced 8-bit digits per coefficient (2 .. 9)
   int64_t Z;                // narrow path: origin of the reversed g planes (Z = k00 mod 8)
   __half *planes;           // narrow path: the digit planes (fp16)
-  // narrow path: per (value, slice) six 32-bit words of the slice's partial
-  // (value v, slice s at acc + (v slices + s) 6)
+  // narrow path: per value six 64-bit column sums of its 32-bit words (value
+  // v at acc + 6 v), zeroed by the digit-plane kernel
   unsigned long long *acc;
   uint32_t *seeds;          // wide path: seed_words words per value
   int seed_words;
@@ -318,7 +318,7 @@ struct SeedPlan {
   int64_t blocks = 0, nvalues = 0;
   bool narrow() const { return kind >= 1 && kind < 100; }
 };
-// partials per seed value of the narrow path (windows of the t' axis)
+// windows of the t' axis of the narrow seed kernel
 int64_t seed_slices(int64_t lf, int64_t lg, int C);
 int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int64_t lg, int bg,
                    int sgn, int kb, int64_t k00, int64_t kstep, int64_t ncl, int C,
@@ -331,6 +331,9 @@ int64_t seed_planes_bytes(int64_t lf, int64_t lg, int P);
 int64_t planes_blocks(const SeedArgs &a);
 cudaError_t launch_seed_planes(const SeedArgs *d, const int64_t *prefix, int n, int64_t blocks,
                                cudaStream_t s);
+// the digit planes of a narrow seed plan (before launch_seed_plan, same or
+// earlier stream order), then the seed values themselves
+cudaError_t launch_seed_planes_one(const SeedPlan &sp, cudaStream_t s);
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s);
 // smem: the largest dynamic shared memory of the batch's CTAs (narrow kinds)
 cudaError_t launch_seeds_batch(int kind, const SeedArgs *d, const int64_t *prefix, int n,
@@ -351,8 +354,7 @@ struct RecoverArgs {
   int *status;
   // the exact seed values: value index (pair C + slot)
   int C;
-  const unsigned long long *seed_acc;  // narrow seeds: six words per (value, slice)
-  int64_t seed_slices;
+  const unsigned long long *seed_acc;  // narrow seeds: six column sums per value
   const uint32_t *seeds;               // wide seeds: seed_words words per value
   int seed_words;
   int64_t rblocks[2];  // M <= 63: CTAs of cpc chains per run
@@ -361,9 +363,8 @@ struct RecoverArgs {
 };
 int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int nruns,
                       int64_t nwords, int M, int64_t chain, int C,
-                      const unsigned long long *seed_acc, int64_t seed_slices,
-                      const uint32_t *seeds, int seed_words, int *status, RecoverArgs &a,
-                      int64_t &blocks);
+                      const unsigned long long *seed_acc, const uint32_t *seeds,
+                      int seed_words, int *status, RecoverArgs &a, int64_t &blocks);
 int recover_class(int M);
 cudaError_t launch_recover(const RecoverArgs &a, int64_t blocks, cudaStream_t s);
 // smem: the largest RecoverArgs::smem of the batch (class 1)
@@ -407,6 +408,37 @@ cudaError_t launch_biv_recover(const BivRecoverArgs &a, cudaStream_t s);
 // (Z/pZ)[x]: out_k = h'_k mod p.
 cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh,
                               uint64_t p, cudaStream_t s);
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch (ks_set_pdl; off by default).  With it on, the
+// library's kernels are launched with the programmatic stream-serialization
+// attribute: a kernel may be scheduled while the kernel before it in the
+// stream is still running, so its launch latency hides behind that kernel's
+// tail.  Every such kernel calls pdl_enter() before
+// its first global memory access: it waits until the previous kernel has
+// finished and its writes are visible (both read-after-write and
+// write-after-read hazards stay covered), then lets the next kernel start
+// launching.  For a kernel launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+bool pdl_enabled();  // ks_set_pdl
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // ---------------------------------------------------------------- accounting
 // Kernel launches issued by the library (host counter), and optional per-phase

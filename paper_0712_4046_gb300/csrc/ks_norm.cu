@@ -53,16 +53,18 @@ constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
 // word or the word before it (their slices span three words).
 template <int D>
 struct Geo;
+// Two words per thread keep a thread's dependent chain short and give a
+// product four times the CTAs of eight words per thread.
 template <>
 struct Geo<16> {
-  static constexpr int WPT = 4, CPT = 8, BACK = 6;
+  static constexpr int WPT = 2, CPT = 4, BACK = 6;
 };
 template <>
 struct Geo<32> {
-  static constexpr int WPT = 8, CPT = 8, BACK = 3;  // column -3's top slice is word -1's
+  static constexpr int WPT = 2, CPT = 2, BACK = 3;  // column -3's top slice is word -1's
 };
 // staged columns of a tile: 128 CPT + BACK, one padding slot per 8 (banks)
-constexpr int kStage = (kThreads * 8 + 8) + (kThreads * 8 + 8) / 8 + 8;
+constexpr int kStage = (kThreads * 4 + 8) + (kThreads * 4 + 8) / 8 + 8;
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 
 // carry-transfer function: 2 bits per input carry c in {-1,0,1}, value c'+1
@@ -129,6 +131,7 @@ __device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + G
 
 template <int D, class Src>
 __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
+  pdl_enter();
   constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
   constexpr int NX = BACK + CPT;
   constexpr int TW = kThreads * WPT;  // words per tile
@@ -258,10 +261,9 @@ __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
       o[w] = (uint32_t)v;
       c = (int)(v >> 32);
     }
-    if (WPT == 4) {
-      // nwords is a multiple of four: the four words are all inside or all outside
-      if (j0 < a.nwords)
-        *reinterpret_cast<uint4 *>(J.out + j0) = make_uint4(o[0], o[1], o[2], o[3 % WPT]);
+    if (WPT == 2) {
+      // nwords is a multiple of four: the two words are both inside or both outside
+      if (j0 < a.nwords) *reinterpret_cast<uint2 *>(J.out + j0) = make_uint2(o[0], o[1 % WPT]);
     } else {
 #pragma unroll
       for (int w = 0; w < WPT; w++)
@@ -299,6 +301,7 @@ __device__ __forceinline__ uint32_t block_compose(uint32_t f, uint32_t &excl, ui
 // stored words (tile t's words were written as if its carry in were 0).
 template <int D, class Src>
 __global__ void __launch_bounds__(kCarryThreads) norm_carry(Src src) {
+  pdl_enter();
   constexpr int TW = kThreads * Geo<D>::WPT;
   __shared__ uint32_t s_warp[kCarryThreads / 32];
   int64_t bid;
@@ -389,11 +392,11 @@ cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwor
   const One<NormArgs> one{a};
   const unsigned g1 = (unsigned)norm_blocks(a), g2 = (unsigned)norm_carry_blocks(a);
   if (d == 32) {
-    norm_tiles<32, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
-    norm_carry<32, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
+    (void)launch_k(norm_tiles<32, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+    (void)launch_k(norm_carry<32, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
   } else {
-    norm_tiles<16, One<NormArgs>><<<g1, kThreads, 0, s>>>(one);
-    norm_carry<16, One<NormArgs>><<<g2, kCarryThreads, 0, s>>>(one);
+    (void)launch_k(norm_tiles<16, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+    (void)launch_k(norm_carry<16, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
   }
   note_launches(2);
   return cudaGetLastError();
@@ -405,11 +408,11 @@ cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *pre
   if (n == 0 || tile_blocks == 0) return cudaSuccess;
   const Many<NormArgs> t{da, prefix_tiles, n}, c{da, prefix_carry, n};
   if (d == 32) {
-    norm_tiles<32, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
-    norm_carry<32, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
+    (void)launch_k(norm_tiles<32, Many<NormArgs>>, dim3((unsigned)tile_blocks), dim3(kThreads), 0, s, t);
+    (void)launch_k(norm_carry<32, Many<NormArgs>>, dim3((unsigned)carry_blocks), dim3(kCarryThreads), 0, s, c);
   } else {
-    norm_tiles<16, Many<NormArgs>><<<(unsigned)tile_blocks, kThreads, 0, s>>>(t);
-    norm_carry<16, Many<NormArgs>><<<(unsigned)carry_blocks, kCarryThreads, 0, s>>>(c);
+    (void)launch_k(norm_tiles<16, Many<NormArgs>>, dim3((unsigned)tile_blocks), dim3(kThreads), 0, s, t);
+    (void)launch_k(norm_carry<16, Many<NormArgs>>, dim3((unsigned)carry_blocks), dim3(kCarryThreads), 0, s, c);
   }
   note_launches(2);
   return cudaGetLastError();

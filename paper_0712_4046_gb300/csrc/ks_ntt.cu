@@ -95,6 +95,7 @@ __device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
 
 template <bool kForward>
 __global__ void __launch_bounds__(kPassThreads) ntt_pass(NttArgs g) {
+  pdl_enter();
   __shared__ uint32_t S[kTile + kTile / 32];
   const int a = blockIdx.y * g.astride + g.aoff;
   const int r = prime_of(a);
@@ -252,6 +253,7 @@ struct LoadArgs {
 };
 
 __global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs g) {
+  pdl_enter();
   const int64_t n = (int64_t)1 << g.L;
   const int64_t total = n * 4 * g.nprod;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -273,6 +275,7 @@ __global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs
 
 __global__ void __launch_bounds__(256) ntt_pointwise(uint32_t *data, int L, int nprod, PrimeC p0,
                                                      PrimeC p1, int square) {
+  pdl_enter();
   const int64_t n = (int64_t)1 << L;
   const int64_t total = n * 2 * nprod;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -298,6 +301,7 @@ struct CrtArgs {
 };
 
 __global__ void __launch_bounds__(256) ntt_crt(const __grid_constant__ CrtArgs g) {
+  pdl_enter();
   const int64_t n = (int64_t)1 << g.L;
   const uint64_t P = (uint64_t)g.pc[0].p * g.pc[1].p;
   const int q = blockIdx.y;  // product
@@ -439,7 +443,7 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   int64_t tot = n * 4 * nprod;
   int64_t blocks = (tot + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  ntt_load<<<(unsigned)blocks, 256, 0, s>>>(la);
+  (void)launch_k(ntt_load, dim3((unsigned)blocks), dim3(256), 0, s, la);
 
   int s0[8], kk[8];
   const int np = plan_passes(log_n, s0, kk);
@@ -456,13 +460,12 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
     const int64_t F = n >> (s0[i] + kk[i]);
     const int64_t Wc = F < (kTile >> kk[i]) ? F : (kTile >> kk[i]);
     const int64_t ctas = ((int64_t)1 << s0[i]) * (F / Wc);
-    ntt_pass<true><<<dim3((unsigned)ctas, (unsigned)((square ? 2 : 4) * nprod)), kPassThreads, 0,
-                     s>>>(g);
+    (void)launch_k(ntt_pass<true>, dim3(dim3((unsigned)ctas, (unsigned)((square ? 2 : 4) * nprod))), dim3(kPassThreads), 0, s, g);
   }
   tot = n * 2 * nprod;
   blocks = (tot + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  ntt_pointwise<<<(unsigned)blocks, 256, 0, s>>>(data, log_n, nprod, pc0, pc1, square);
+  (void)launch_k(ntt_pointwise, dim3((unsigned)blocks), dim3(256), 0, s, data, log_n, nprod, pc0, pc1, square);
   for (int i = np - 1; i >= 0; i--) {  // inverse: the product arrays (side 0)
     g.s0 = s0[i];
     g.k = kk[i];
@@ -471,7 +474,7 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
     const int64_t F = n >> (s0[i] + kk[i]);
     const int64_t Wc = F < (kTile >> kk[i]) ? F : (kTile >> kk[i]);
     const int64_t ctas = ((int64_t)1 << s0[i]) * (F / Wc);
-    ntt_pass<false><<<dim3((unsigned)ctas, (unsigned)(2 * nprod)), kPassThreads, 0, s>>>(g);
+    (void)launch_k(ntt_pass<false>, dim3(dim3((unsigned)ctas, (unsigned)(2 * nprod))), dim3(kPassThreads), 0, s, g);
   }
   CrtArgs c{};
   c.data = data;
@@ -492,7 +495,7 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   c.M = to_mont(p1inv, kP[1]);
   blocks = (c.ncols + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ntt_crt<<<dim3((unsigned)blocks, (unsigned)nprod), 256, 0, s>>>(c);
+  (void)launch_k(ntt_crt, dim3(dim3((unsigned)blocks, (unsigned)nprod)), dim3(256), 0, s, c);
   note_launches(3 + 2 * np);
   return cudaGetLastError();
 }

@@ -53,6 +53,7 @@ __host__ __device__ __forceinline__ int64_t op_ctas(const PackArgs &a, const Pac
 //    Digits between fields cost nothing but their store.
 template <class Src>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
+  pdl_enter();
   __shared__ __align__(16) uint64_t raw[kStageWords + kFieldDigits / 2];
   int64_t local;
   const PackArgs &a = src.locate(blockIdx.x, local);
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
 // extended with its sign (signed) or with zeros: the same integers, wider.
 __global__ void __launch_bounds__(256) widen_kernel(uint64_t *out, const uint64_t *in, int64_t len,
                                                     int il, int ol, int is_signed) {
+  pdl_enter();
   const int64_t total = len * ol;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -161,7 +163,7 @@ cudaError_t launch_widen(uint64_t *out, const uint64_t *in, int64_t len, int il,
   int64_t blocks = (len * ol + 255) / 256;
   if (blocks < 1) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  widen_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, in, len, il, ol, is_signed);
+  (void)launch_k(widen_kernel, dim3((unsigned)blocks), dim3(256), 0, s, out, in, len, il, ol, is_signed);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -210,7 +212,7 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
   if (a.d != 16) return cudaErrorInvalidValue;  // the int32-digit engines use 16-bit digits
   const int64_t blocks = pack_blocks(a);
   if (blocks == 0) return cudaSuccess;
-  pack_kernel<One<PackArgs>><<<(unsigned)blocks, kPackThreads, 0, s>>>(One<PackArgs>{a});
+  (void)launch_k(pack_kernel<One<PackArgs>>, dim3((unsigned)blocks), dim3(kPackThreads), 0, s, One<PackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -218,7 +220,7 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
 cudaError_t launch_pack_batch(const PackArgs *d, const int64_t *prefix, int n, int64_t blocks,
                               cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  pack_kernel<Many<PackArgs>><<<(unsigned)blocks, kPackThreads, 0, s>>>(
+  (void)launch_k(pack_kernel<Many<PackArgs>>, dim3((unsigned)blocks), dim3(kPackThreads), 0, s, 
       Many<PackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();

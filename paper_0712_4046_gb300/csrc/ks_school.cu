@@ -31,6 +31,7 @@ constexpr int kTI = 1024;           // i-chunk per CTA
 
 template <class Src>
 __global__ void __launch_bounds__(kThreads) schoolbook_kernel(Src src) {
+  pdl_enter();
   __shared__ __align__(16) int32_t sA[kTI];
   __shared__ __align__(16) int32_t sB[kTK + kTI];
   __shared__ long long sHi[kThreads][7];
@@ -125,7 +126,7 @@ cudaError_t launch_schoolbook(const Product *prods, int nprod, cudaStream_t s) {
   const int64_t blocks = a.block_prefix[nprod];
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  schoolbook_kernel<One<SchoolArgs>><<<(unsigned)blocks, kThreads, 0, s>>>(One<SchoolArgs>{a});
+  (void)launch_k(schoolbook_kernel<One<SchoolArgs>>, dim3((unsigned)blocks), dim3(kThreads), 0, s, One<SchoolArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -134,8 +135,8 @@ cudaError_t launch_schoolbook_batch(const SchoolArgs *d, const int64_t *prefix, 
                                     int64_t blocks, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  schoolbook_kernel<Many<SchoolArgs>>
-      <<<(unsigned)blocks, kThreads, 0, s>>>(Many<SchoolArgs>{d, prefix, n});
+  (void)launch_k(schoolbook_kernel<Many<SchoolArgs>>, dim3((unsigned)blocks), dim3(kThreads), 0, s,
+                 Many<SchoolArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }

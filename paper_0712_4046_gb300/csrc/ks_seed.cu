@@ -20,14 +20,15 @@
 // (mod 8) (every cluster start k0 is k00 mod 8).  Inside a block of 64
 // indices t' a lane's eight 32-bit fragment words are 16 consecutive indices;
 // the same permutation of t' on both sides leaves the sum unchanged.
-// A warp runs mma.sync m16n8k16 (fp16 in, fp32 accumulate) over 512 indices
-// t': every partial sum is an integer of magnitude at most 512 * 128^2 = 2^23,
-// which fp32 holds exactly.  Each thread's entries belong to the values
-// r' + r'' of its row parity; it weights them by 256^(p+q) into 192-bit two's
-// complement partials, and the CTA (four warps, 2048 t') adds its lanes'
-// partials as 32-bit-word column sums and stores them (slice 0 adds K) in a
-// slot of its own; the reconstruction adds the slices' words and carries them
-// into the value mod 2^192 (exact: the values are non-negative and below 2^192).
+// A CTA takes a group of consecutive clusters over one window of 1024
+// indices t', staged in shared memory; its warps run mma.sync m16n8k16 (fp16
+// in, fp32 accumulate) over at most 512 indices t' each: every partial sum is
+// an integer of magnitude at most 512 * 128^2 = 2^23, which fp32 holds
+// exactly.  The entries are added along the digit diagonals p + q, carried
+// into a 192-bit two's complement partial per value and window, and its six
+// 32-bit words are added to the value's six 64-bit column sums (window 0
+// adds K); the reconstruction carries them into the value mod 2^192 (exact:
+// the values are non-negative and below 2^192).
 //
 // Wide operands: one CTA per value; a thread multiplies the magnitudes of its
 // terms word by word (NW 32-bit words, a compile-time size) and keeps signed
@@ -105,7 +106,8 @@ __device__ __forceinline__ void write_zeros(int P, __half *out, int64_t stride) 
   for (int p = 0; p < P; p++) out[p * stride] = __int2half_rn(0);
 }
 
-// Digit planes, a thread per column:
+// Digit planes, a thread per column (and the zeroing of the seed values'
+// column sums, which the seed kernel then accumulates):
 //   f copy c (c = 0, 1), plane p at planes + (c P + p) fs: column x holds
 //     digit p of f_(x - kPad + 2c);
 //   g copy c, plane q at planes + 2 P fs + (c P + q) gs: column y holds digit q
@@ -113,11 +115,13 @@ __device__ __forceinline__ void write_zeros(int P, __half *out, int64_t stride) 
 // zero outside the polynomials.  One launch covers a batch (any P).
 template <class Src>
 __global__ void __launch_bounds__(256) seed_planes(Src src) {
+  pdl_enter();
   int64_t local;
   const SeedArgs &a = src.locate(blockIdx.x, local);
   const int P = a.P;
   const int64_t fs = plane_stride(a.lf), gs = plane_stride(a.lg);
   const int64_t i = local * 256 + threadIdx.x;
+  if (i < a.ncl * a.C * 6) a.acc[i] = 0ull;
   if (i < fs) {
     for (int c = 0; c < 2; c++) {
       const int64_t t = i - kPad + 2 * c;
@@ -283,13 +287,9 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
   cluster_range(a, j0 + gact - 1, k0l, tlol, thil);
   const bool any = tlo0 <= T + kWin - 1 && thil >= T && tlo0 <= thil;
   const int wpc = kSeedWarps / G;  // warps per cluster
-  if (!any) {  // block-uniform: zero partials (and K in window 0)
-    for (int i = tid; i < gact * C * 6; i += kSeedWarps * 32) {
-      const int ci = i / (C * 6), rv = (i / 6) % C, wd = i % 6;
-      const unsigned long long k =
-          (w == 0 && a.kb >= 0 && (a.kb >> 5) == wd) ? 1ull << (a.kb & 31) : 0ull;
-      a.acc[(((j0 + ci) * C + rv) * a.slices + w) * 6 + wd] = k;
-    }
+  if (!any) {  // block-uniform: nothing to add but K (window 0)
+    if (w == 0 && a.kb >= 0 && tid < gact * C)
+      atomicAdd(&a.acc[(j0 * C + tid) * 6 + (a.kb >> 5)], 1ull << (a.kb & 31));
     return;
   }
   for (int i = tid; i < 4 * C * ND; i += kSeedWarps * 32) (&dsum[0][0][0])[i] = 0;
@@ -429,13 +429,13 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
       shl192((int64_t)dsum[cc][rv][k], 8 * k, v0, v1, v2);
       add3(v, v0, v1, v2);
     }
-    unsigned long long *o = a.acc + (((j0 + cc) * C + rv) * a.slices + w) * 6;
+    unsigned long long *o = a.acc + ((j0 + cc) * C + rv) * 6;
 #pragma unroll
     for (int wd = 0; wd < 6; wd++) {
       const uint64_t wv = wd < 2 ? v.w0 : wd < 4 ? v.w1 : v.w2;
       unsigned long long x = (uint32_t)(wv >> (32 * (wd & 1)));
       if (w == 0 && a.kb >= 0 && (a.kb >> 5) == wd) x += 1ull << (a.kb & 31);
-      o[wd] = x;
+      if (x) atomicAdd(&o[wd], x);
     }
   }
 }
@@ -444,6 +444,7 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
 // holds the staged digits.
 template <int P, int C, class Src>
 __global__ void __launch_bounds__(kSeedWarps * 32, 2) seed_mma(Src src) {
+  pdl_enter();
   extern __shared__ __align__(16) __half seed_sm[];
   int64_t local;
   const SeedArgs &a = src.locate(blockIdx.x, local);
@@ -485,6 +486,7 @@ __device__ __forceinline__ bool mag_words(const uint64_t *c, int il, int b, int 
 
 template <int NW, class Src>
 __global__ void __launch_bounds__(kWT) seed_wide(Src src) {
+  pdl_enter();
   __shared__ unsigned long long colsum[kMaxSeedWords];
   int64_t vid;
   const SeedArgs &a = src.locate(blockIdx.x, vid);
@@ -555,7 +557,7 @@ cudaError_t launch_mma(int64_t blocks, int smem, const Src &src, cudaStream_t s)
     if (e != cudaSuccess) return e;
     done[dev] = true;
   }
-  seed_mma<P, C, Src><<<(unsigned)blocks, kSeedWarps * 32, smem, s>>>(src);
+  (void)launch_k(seed_mma<P, C, Src>, dim3((unsigned)blocks), dim3(kSeedWarps * 32), smem, s, src);
   return cudaSuccess;
 }
 
@@ -573,12 +575,12 @@ cudaError_t launch_kind(int kind, int64_t blocks, int smem, const Src &src, cuda
     case 84: return launch_mma<8, 4>(blocks, smem, src, s);
     case 92: return launch_mma<9, 2>(blocks, smem, src, s);
     case 94: return launch_mma<9, 4>(blocks, smem, src, s);
-    case 102: seed_wide<2, Src><<<grid, kWT, 0, s>>>(src); break;
-    case 104: seed_wide<4, Src><<<grid, kWT, 0, s>>>(src); break;
-    case 108: seed_wide<8, Src><<<grid, kWT, 0, s>>>(src); break;
-    case 116: seed_wide<16, Src><<<grid, kWT, 0, s>>>(src); break;
-    case 132: seed_wide<32, Src><<<grid, kWT, 0, s>>>(src); break;
-    case 164: seed_wide<64, Src><<<grid, kWT, 0, s>>>(src); break;
+    case 102: (void)launch_k(seed_wide<2, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
+    case 104: (void)launch_k(seed_wide<4, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
+    case 108: (void)launch_k(seed_wide<8, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
+    case 116: (void)launch_k(seed_wide<16, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
+    case 132: (void)launch_k(seed_wide<32, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
+    case 164: (void)launch_k(seed_wide<64, Src>, dim3(grid), dim3(kWT), 0, s, src); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaSuccess;
@@ -587,7 +589,9 @@ cudaError_t launch_kind(int kind, int64_t blocks, int smem, const Src &src, cuda
 }  // namespace
 
 int64_t planes_blocks(const SeedArgs &a) {
-  return (plane_stride(a.lf) + plane_stride(a.lg) + 255) / 256;
+  int64_t n = plane_stride(a.lf) + plane_stride(a.lg);
+  if (a.ncl * a.C * 6 > n) n = a.ncl * a.C * 6;
+  return (n + 255) / 256;
 }
 int64_t seed_planes_bytes(int64_t lf, int64_t lg, int P) { return planes_halves(lf, lg, P) * 2; }
 
@@ -613,7 +617,7 @@ int64_t seed_slices(int64_t lf, int64_t lg, int C) {
 cudaError_t launch_seed_planes(const SeedArgs *d, const int64_t *prefix, int n, int64_t blocks,
                                cudaStream_t s) {
   if (n == 0 || blocks == 0) return cudaSuccess;
-  seed_planes<Many<SeedArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<SeedArgs>{d, prefix, n});
+  (void)launch_k(seed_planes<Many<SeedArgs>>, dim3((unsigned)blocks), dim3(256), 0, s, Many<SeedArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -696,14 +700,16 @@ int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int
   return 0;
 }
 
+cudaError_t launch_seed_planes_one(const SeedPlan &sp, cudaStream_t s) {
+  if (!sp.narrow() || sp.blocks == 0) return cudaSuccess;
+  (void)launch_k(seed_planes<One<SeedArgs>>, dim3((unsigned)planes_blocks(sp.a)), dim3(256), 0, s,
+                 One<SeedArgs>{sp.a});
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seed_plan(const SeedPlan &sp, cudaStream_t s) {
   if (sp.kind == 0 || sp.blocks == 0) return cudaSuccess;
-  if (sp.narrow()) {
-    seed_planes<One<SeedArgs>><<<(unsigned)planes_blocks(sp.a), 256, 0, s>>>(One<SeedArgs>{sp.a});
-    note_launches(1);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   const cudaError_t e = launch_kind(sp.kind, sp.blocks, sp.narrow() ? sp.a.smem : 0,
                                     One<SeedArgs>{sp.a}, s);
   if (e != cudaSuccess) return e;

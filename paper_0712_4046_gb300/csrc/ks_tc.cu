@@ -237,6 +237,7 @@ __device__ __forceinline__ int32_t recode8(int32_t d, int32_t prev) {
 // fp16 digits in the operand layout, 16 bytes per thread, coalesced.
 template <class Src>
 __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
+  pdl_enter();
   __shared__ int32_t raw[kPackSeg + 8];
   __shared__ __align__(16) __half dig[kPackSeg + 8];
   __shared__ uint64_t cf[kPackStageWords];  // the segment's coefficients, when they fit
@@ -483,6 +484,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total,
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the setup above touched only shared and tensor memory: it overlaps the
+  // previous kernel of the stream
+  pdl_enter();
   const uint32_t tmem = tmem_sh;
 
   if (warp == 0) {
@@ -798,7 +802,7 @@ cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char 
   TcPackArgs a;
   int64_t blocks;
   make_tc_pack_args(pa, g, nprod, base, a, blocks, zero, nzero);
-  tc_pack_kernel<One<TcPackArgs>><<<(unsigned)blocks, 256, 0, s>>>(One<TcPackArgs>{a});
+  (void)launch_k(tc_pack_kernel<One<TcPackArgs>>, dim3((unsigned)blocks), dim3(256), 0, s, One<TcPackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -806,7 +810,7 @@ cudaError_t launch_tc_pack(const PackArgs &pa, const TcGeom &g, int nprod, char 
 cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int n,
                                  int64_t blocks, cudaStream_t s) {
   if (n == 0 || blocks == 0) return cudaSuccess;
-  tc_pack_kernel<Many<TcPackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<TcPackArgs>{d, prefix, n});
+  (void)launch_k(tc_pack_kernel<Many<TcPackArgs>>, dim3((unsigned)blocks), dim3(256), 0, s, Many<TcPackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -873,7 +877,7 @@ cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base, int64_t *
   const int64_t work = a.work_prefix[nprod];
   if (work <= 0) return cudaSuccess;
   const int64_t grid = work < sms ? work : sms;
-  tc_kernel<One<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(One<TcArgs>{a}, work,
+  (void)launch_k(tc_kernel<One<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s, One<TcArgs>{a}, work,
                                                                   g_tc_wait_ns.load(),
                                                                   g_tc_stall.load());
   note_launches(1);
@@ -887,7 +891,7 @@ cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64
   cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
   const int64_t grid = work < sms ? work : sms;
-  tc_kernel<Many<TcArgs>><<<(unsigned)grid, kThreads, kSmem, s>>>(
+  (void)launch_k(tc_kernel<Many<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s, 
       Many<TcArgs>{d, prefix, n}, work, g_tc_wait_ns.load(), g_tc_stall.load());
   note_launches(1);
   return cudaGetLastError();

@@ -16,6 +16,7 @@ namespace ks {
 constexpr int kUnpackPer = 4;
 template <class Src>
 __global__ void __launch_bounds__(256) unpack_kernel(Src src) {
+  pdl_enter();
   int64_t local;
   const UnpackArgs &a = src.locate(blockIdx.x, local);
   const int64_t total = a.lh * a.ol;
@@ -71,7 +72,7 @@ int64_t unpack_blocks(const UnpackArgs &a) {
 }
 
 cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s) {
-  unpack_kernel<One<UnpackArgs>><<<(unsigned)unpack_blocks(a), 256, 0, s>>>(One<UnpackArgs>{a});
+  (void)launch_k(unpack_kernel<One<UnpackArgs>>, dim3((unsigned)unpack_blocks(a)), dim3(256), 0, s, One<UnpackArgs>{a});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -79,7 +80,7 @@ cudaError_t launch_unpack(const UnpackArgs &a, cudaStream_t s) {
 cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int n,
                                 int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  unpack_kernel<Many<UnpackArgs>><<<(unsigned)blocks, 256, 0, s>>>(Many<UnpackArgs>{d, prefix, n});
+  (void)launch_k(unpack_kernel<Many<UnpackArgs>>, dim3((unsigned)blocks), dim3(256), 0, s, Many<UnpackArgs>{d, prefix, n});
   note_launches(1);
   return cudaGetLastError();
 }
@@ -183,17 +184,16 @@ __device__ __forceinline__ D2 load_d2(const uint32_t *V, int64_t nwords, int64_t
   r.hi = get_bits64(V, nwords, pos + 64) & hi_mask(M);
   return r;
 }
-// Seed value v as kAccSeedWords 32-bit words: the narrow seed kernel's slice
-// partials added as six 64-bit column sums and carried (mod 2^192: the top
-// words are zero), or the wide seed kernel's words.
+// Seed value v as kAccSeedWords 32-bit words: the narrow seed kernel's six
+// 64-bit column sums carried (mod 2^192: the top words are zero), or the wide
+// seed kernel's words.
 __device__ __forceinline__ void seed_value(const RecoverArgs &a, int64_t v,
                                            uint32_t (&out)[kAccSeedWords]) {
   if (a.seed_acc != nullptr) {
-    const unsigned long long *acc = a.seed_acc + v * a.seed_slices * 6;
-    unsigned long long col[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t sl = 0; sl < a.seed_slices; sl++)
+    const unsigned long long *acc = a.seed_acc + v * 6;
+    unsigned long long col[6];
 #pragma unroll
-      for (int w = 0; w < 6; w++) col[w] += acc[sl * 6 + w];
+    for (int w = 0; w < 6; w++) col[w] = acc[w];
     unsigned long long carry = 0;
 #pragma unroll
     for (int w = 0; w < kAccSeedWords; w++) {
@@ -385,6 +385,7 @@ __host__ __device__ __forceinline__ int64_t staged_bytes(int64_t chain, int M, i
 
 template <class Src>
 __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
+  pdl_enter();
   extern __shared__ __align__(16) uint32_t stg[];
   __shared__ __align__(8) uint64_t bar;
   int64_t local;
@@ -560,6 +561,7 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
 // 64 <= M <= 127, one thread per chain, digits read from global memory
 template <class Src>
 __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
+  pdl_enter();
   int64_t local;
   const RecoverArgs &a = src.locate(blockIdx.x, local);
   uint64_t *h = a.h;
@@ -649,6 +651,7 @@ __device__ void write_coeff(uint64_t *out, int ol, const Dig &al, const Dig &be,
 // any M (digits of W 32-bit words), one thread per chain
 template <class Src>
 __global__ void __launch_bounds__(64) recover_wide(Src src) {
+  pdl_enter();
   int64_t local;
   const RecoverArgs &a = src.locate(blockIdx.x, local);
   uint64_t *h = a.h;
@@ -719,9 +722,8 @@ __global__ void __launch_bounds__(64) recover_wide(Src src) {
 
 int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int nruns,
                       int64_t nwords, int M, int64_t chain, int C,
-                      const unsigned long long *seed_acc, int64_t seed_slices,
-                      const uint32_t *seeds, int seed_words, int *status, RecoverArgs &a,
-                      int64_t &blocks) {
+                      const unsigned long long *seed_acc, const uint32_t *seeds,
+                      int seed_words, int *status, RecoverArgs &a, int64_t &blocks) {
   a = RecoverArgs{};
   int64_t total = 0;
   for (int r = 0; r < nruns; r++) {
@@ -738,7 +740,6 @@ int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int n
   a.status = status;
   a.C = C;
   a.seed_acc = seed_acc;
-  a.seed_slices = seed_slices;
   a.seeds = seeds;
   a.seed_words = seed_words;
   if ((M + 31) / 32 > kMaxDigitWordsM) return -1;
@@ -787,11 +788,11 @@ static cudaError_t launch_recover_class(int cls, int64_t blocks, const Src &src,
   if (cls == 1) {
     const cudaError_t e = staged_attr<Src>(smem);
     if (e != cudaSuccess) return e;
-    recover_staged1<Src><<<(unsigned)blocks, kRT, smem, s>>>(src);
+    (void)launch_k(recover_staged1<Src>, dim3((unsigned)blocks), dim3(kRT), smem, s, src);
   } else if (cls == 2)
-    recover_kernel2<Src><<<(unsigned)blocks, 128, 0, s>>>(src);
+    (void)launch_k(recover_kernel2<Src>, dim3((unsigned)blocks), dim3(128), 0, s, src);
   else
-    recover_wide<Src><<<(unsigned)blocks, 64, 0, s>>>(src);
+    (void)launch_k(recover_wide<Src>, dim3((unsigned)blocks), dim3(64), 0, s, src);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -820,6 +821,7 @@ __device__ __forceinline__ uint64_t mod_128(uint64_t hi, uint64_t lo, uint64_t p
 
 __global__ void __launch_bounds__(256) reduce_mod_kernel(uint64_t *out, const uint64_t *h, int ol,
                                                          int64_t lh, uint64_t p) {
+  pdl_enter();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < lh;
        k += (int64_t)gridDim.x * blockDim.x) {
     uint64_t r = 0;
@@ -830,7 +832,7 @@ __global__ void __launch_bounds__(256) reduce_mod_kernel(uint64_t *out, const ui
 
 cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh, uint64_t p,
                               cudaStream_t s) {
-  reduce_mod_kernel<<<grid_for(lh, 256), 256, 0, s>>>(out, h, ol, lh, p);
+  (void)launch_k(reduce_mod_kernel, dim3(grid_for(lh, 256)), dim3(256), 0, s, out, h, ol, lh, p);
   note_launches(1);
   return cudaGetLastError();
 }
