@@ -452,7 +452,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     plan_runs(p, words, runs);
     if (make_seed_plan(f, p.lf, p.b, g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl, p.C,
                        seed_acc, seeds, p.seed_words,
-                       reinterpret_cast<__half *>(ws + p.off_planes), sp) != 0)
+                       reinterpret_cast<__half *>(ws + p.off_planes), status, sp) != 0)
       return KS_ERANGE;
   }
   Fork fk{};

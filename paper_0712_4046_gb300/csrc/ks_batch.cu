@@ -217,9 +217,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   if (p.engine == KS_ENGINE_TC) {
     TcPackArgs ta;
     int64_t blocks;
-    make_tc_pack_args(pa, p.tg, p.nprod, ws + p.off_digits, ta, blocks);
+    // the packing kernel also zeroes the column sums the products accumulate into
+    make_tc_pack_args(pa, p.tg, p.nprod, ws + p.off_digits, ta, blocks, cols, nzero);
     P->tcpack.add(ta, blocks);
-    P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
   } else {
     P->pack.add(pa, pack_blocks(pa));
     if (p.engine == KS_ENGINE_SCHOOLBOOK) {
@@ -257,7 +257,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     SeedPlan sp;
     if (make_seed_plan(q.f, p.lf, p.b, q.g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl,
                        p.C, acc, seeds, p.seed_words,
-                       reinterpret_cast<__half *>(ws + p.off_planes), sp) != 0)
+                       reinterpret_cast<__half *>(ws + p.off_planes), status, sp) != 0)
       return KS_ERANGE;
     if (sp.kind != 0) {
       const int i = seed_kind_index(sp.kind);

@@ -309,6 +309,7 @@ struct SeedArgs {
   unsigned long long *acc;
   uint32_t *seeds;          // wide path: seed_words words per value
   int seed_words;
+  int *status;              // the product's status word (a bounded wait that gave up: 1)
 };
 struct SeedPlan {
   // 0 none; 10 P + C narrow (both operands <= 64 bits; P digits per
@@ -323,7 +324,7 @@ int64_t seed_slices(int64_t lf, int64_t lg, int C);
 int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int64_t lg, int bg,
                    int sgn, int kb, int64_t k00, int64_t kstep, int64_t ncl, int C,
                    unsigned long long *acc, uint32_t *seeds, int seed_words, __half *planes,
-                   SeedPlan &sp);
+                   int *status, SeedPlan &sp);
 // narrow seeds: digits per coefficient (-1: too wide), bytes of the digit
 // planes, blocks of their kernel
 int seed_digits(int bf, int bg, int sgn);
@@ -408,6 +409,49 @@ cudaError_t launch_biv_recover(const BivRecoverArgs &a, cudaStream_t s);
 // (Z/pZ)[x]: out_k = h'_k mod p.
 cudaError_t launch_reduce_mod(uint64_t *out, const uint64_t *h, int ol, int64_t lh,
                               uint64_t p, cudaStream_t s);
+
+// ---------------------------------------------------------------- bulk copies
+// Bulk copies into shared memory: one thread issues them on an mbarrier, all
+// threads wait (bounded: about one second of %globaltimer).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void stage_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes,
+                                           uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// wait for phase 0 of the barrier, about one second at most; false on timeout
+__device__ __forceinline__ bool stage_wait(uint64_t *bar) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar))
+        : "memory");
+    if (ok) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
 
 // ---------------------------------------------------------------- launches
 // Programmatic dependent launch (ks_set_pdl; off by default).  With it on, the

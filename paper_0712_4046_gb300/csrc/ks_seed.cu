@@ -197,13 +197,6 @@ __host__ __device__ __forceinline__ int64_t seed_smem(int P, int C, int G, int64
   return 2 * (2 * ca + (C / 2) * cb);
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool in) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
-               "r"(in ? 16 : 0)
-               : "memory");
-}
-
 // the operand fragments of one block of 64 indices t'
 template <int MT, int NT>
 struct Frag {
@@ -271,13 +264,13 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
   constexpr int NB = C / 2;              // f copies in use: shifts r'' = 0 (and 2)
   constexpr int MT = (2 * P + 15) / 16;  // m16 tiles: A rows m = 2 q + r'
   constexpr int NT = (NB * P + 7) / 8;   // n8 tiles: B columns n = NB p + c
-  constexpr int NA = MT * NT <= 2 ? 4 : (MT * NT <= 4 ? 2 : 1);  // accumulator sets
+  constexpr int NA = MT * NT <= 2 ? 2 : 1;  // accumulator sets
   constexpr int ND = 2 * P - 1;          // digit diagonals s = p + q
   __shared__ int dsum[4][C][ND];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane >> 2, tig = lane & 3;
   const int G = a.G;
-  const int64_t gi = local / a.slices, w = local - gi * a.slices;
+  const int64_t gi = (int)local / (int)a.slices, w = local - gi * a.slices;
   const int64_t j0 = gi * G;
   const int gact = (int)(a.ncl - j0 < G ? a.ncl - j0 : G);
   const int64_t T = -8 + w * kWin;
@@ -295,11 +288,13 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
   for (int i = tid; i < 4 * C * ND; i += kSeedWarps * 32) (&dsum[0][0][0])[i] = 0;
   // staging: A rows (c, q) at sm + c ca + q lys, column i <-> g plane column
   // ybase + i; B rows (c, p) at smB + c cb + p bs, column i <-> f plane
-  // column kPad + T + i; 16-byte chunks outside a plane are zero-filled.
+  // column kPad + T + i.  One thread copies the part of every row inside its
+  // plane with a bulk copy (all boundaries are multiples of 8 halves: 16-byte
+  // aligned); the rest of a row (past a plane's ends) is zero-filled.
   // Row strides are 64 bytes (mod 128) and a copy starts 64 bytes (mod 128)
   // after the same row of the other copy: the eight lanes of a 16-byte read
   // phase (rows (0, k), (1, k)) fall in opposite halves of the banks.
-  const int64_t fs = plane_stride(a.lf), gs = plane_stride(a.lg);
+  const int fs = (int)plane_stride(a.lf), gs = (int)plane_stride(a.lg);
   const int ly = kWin + (int)a.kstep * (gact - 1), lys = ly + kRowPad;
   constexpr int bs = kWin + kRowPad;
   const int ca = P * lys + (P % 2 == 0 ? kRowPad : 0);
@@ -307,26 +302,48 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
   const int64_t ybase = kPad + a.Z - k0l + T;  // k0l: the group's last cluster start
   __half *smB = sm + 2 * ca;
   {
+    __shared__ __align__(8) uint64_t sbar;
+    // the in-plane columns [ya, yb) of the A rows, [xa, xb) of the B rows
+    const int64_t ya = ybase < 0 ? 0 : ybase, yb = ybase + ly < gs ? ybase + ly : gs;
+    const int64_t xs = kPad + T, xa = xs < 0 ? 0 : xs, xb = xs + kWin < fs ? xs + kWin : fs;
+    const int na = yb > ya ? (int)(yb - ya) : 0, nbx = xb > xa ? (int)(xb - xa) : 0;
     const __half *fpl = a.planes, *gpl = a.planes + 2 * (int64_t)P * fs;
-    for (int row = 0; row < 2 * P; row++) {
-      __half *dst = sm + (row / P) * ca + (row % P) * lys;
-      for (int col = 8 * tid; col < ly; col += 8 * kSeedWarps * 32) {
-        const int64_t y = ybase + col;
-        const bool in = y >= 0 && y < gs;
-        cp_async16(dst + col, gpl + row * gs + (in ? y : 0), in);
+    if (tid == 0) {
+      stage_init(&sbar);
+      stage_expect(&sbar, (uint32_t)(2 * (2 * P * na + NB * P * nbx)));
+      if (na > 0)
+        for (int row = 0; row < 2 * P; row++)
+          stage_copy(sm + (row / P) * ca + (row % P) * lys + (ya - ybase),
+                     gpl + (int64_t)row * gs + ya, 2u * na, &sbar);
+      if (nbx > 0)
+        for (int row = 0; row < NB * P; row++)
+          stage_copy(smB + (row / P) * cb + (row % P) * bs + (xa - xs),
+                     fpl + (int64_t)row * fs + xa, 2u * nbx, &sbar);
+    }
+    // zeros where a row reaches past its plane (block-uniform conditions)
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+    if (na < ly) {
+      const int lo = (int)(ya - ybase), hi = lo + na;  // in-plane columns of a row
+      for (int i = tid; i < 2 * P * (ly / 8); i += kSeedWarps * 32) {
+        const int row = i / (ly / 8), col = 8 * (i - row * (ly / 8));
+        if (col < lo || col >= hi)
+          *reinterpret_cast<uint4 *>(sm + (row / P) * ca + (row % P) * lys + col) = z4;
       }
     }
-    for (int row = 0; row < NB * P; row++) {
-      __half *dst = smB + (row / P) * cb + (row % P) * bs;
-      for (int col = 8 * tid; col < kWin; col += 8 * kSeedWarps * 32) {
-        const int64_t x = kPad + T + col;
-        const bool in = x >= 0 && x < fs;
-        cp_async16(dst + col, fpl + row * fs + (in ? x : 0), in);
+    if (nbx < kWin) {
+      const int lo = (int)(xa - xs), hi = lo + nbx;
+      for (int i = tid; i < NB * P * (kWin / 8); i += kSeedWarps * 32) {
+        const int row = i / (kWin / 8), col = 8 * (i - row * (kWin / 8));
+        if (col < lo || col >= hi)
+          *reinterpret_cast<uint4 *>(smB + (row / P) * cb + (row % P) * bs + col) = z4;
       }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    __syncthreads();  // the barrier's initialization, the zeros
+    if (!__syncthreads_and(stage_wait(&sbar))) {
+      if (tid == 0) atomicCAS(a.status, 0, 1);
+      stage_wait(&sbar);  // once more (bounded) for the copies in flight before leaving
+      return;
+    }
   }
   const int ci = warp / wpc, part_i = warp - ci * wpc;
   if (ci < gact) {
@@ -443,7 +460,7 @@ __device__ __forceinline__ void seed_mma_body(const SeedArgs &a, int64_t local, 
 // One CTA per item (group, window) of every product; dynamic shared memory
 // holds the staged digits.
 template <int P, int C, class Src>
-__global__ void __launch_bounds__(kSeedWarps * 32, 2) seed_mma(Src src) {
+__global__ void __launch_bounds__(kSeedWarps * 32, P >= 9 ? 1 : 3) seed_mma(Src src) {
   pdl_enter();
   extern __shared__ __align__(16) __half seed_sm[];
   int64_t local;
@@ -634,7 +651,7 @@ int seed_kind_index(int kind) {
 int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int64_t lg, int bg,
                    int sgn, int kb, int64_t k00, int64_t kstep, int64_t ncl, int C,
                    unsigned long long *acc, uint32_t *seeds, int seed_words, __half *planes,
-                   SeedPlan &sp) {
+                   int *status, SeedPlan &sp) {
   sp = SeedPlan{};
   sp.nvalues = ncl * C;
   if (sp.nvalues == 0) return 0;
@@ -669,6 +686,7 @@ int make_seed_plan(const uint64_t *f, int64_t lf, int bf, const uint64_t *g, int
   a.acc = acc;
   a.seeds = seeds;
   a.seed_words = seed_words;
+  a.status = status;
   if (narrow) {
     // the g copies' origin Z = k00 (mod 8) keeps every fragment read aligned,
     // which needs every cluster start k0 = k00 (mod 8); the staged rows keep

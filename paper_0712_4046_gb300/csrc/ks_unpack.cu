@@ -301,47 +301,6 @@ __device__ __forceinline__ int64_t lane_coeff(const ChainLane &L, int64_t t) {
   return L.up ? L.s + t : L.s - 1 - t;
 }
 
-// ---- bulk copies into shared memory (one thread issues, all wait, bounded)
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void stage_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes,
-                                           uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-// wait for phase 0 of the barrier, about one second at most; false on timeout
-__device__ __forceinline__ bool stage_wait(uint64_t *bar) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar))
-        : "memory");
-    if (ok) return true;
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 1000000000ull) return false;
-  }
-}
-
 // M <= 63, digits staged in shared memory.  A CTA of 128 threads runs cpc
 // consecutive chains of one run (cpc <= 32, cpc * chain <= 2048), which
 // cover the coefficients [j0, jhi) without gaps:
