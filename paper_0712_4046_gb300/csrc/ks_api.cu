@@ -174,8 +174,12 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
       p.run_n[1] = p.lh / 2;
     }
     const int64_t nmax = p.run_n[0];
-    p.chain = p.M <= 127 ? (nmax + 4095) / 4096 : (nmax + 511) / 512;
-    const int64_t minchain = 64;
+    // chains: long enough that the seeds (one exact dot product per chain
+    // start) stay a small share, short enough for parallelism; a step of a
+    // digit wider than 63 bits costs several times more, so those take shorter
+    // chains (at least 32: the narrow seed kernel wants cluster starts 64 apart)
+    p.chain = p.M <= 63 ? (nmax + 4095) / 4096 : (nmax + 255) / 256;
+    const int64_t minchain = p.M <= 63 ? 64 : 32;
     if (p.chain < minchain) p.chain = minchain;
     int64_t c2 = 1;  // a power of two (the staged reconstruction indexes by shifts)
     while (c2 < p.chain) c2 <<= 1;

@@ -102,8 +102,8 @@ struct ks_plan {
   ks::List<ks::SeedArgs> seeds[ks::kSeedKinds];  // per kernel kind (kSeedKindList)
   ks::List<ks::SeedArgs> planes;                  // the narrow seeds' digit planes
   int seed_smem[ks::kSeedKinds] = {0};            // per kind: the largest CTA's shared memory
-  ks::List<ks::RecoverArgs> recover[3];
-  int recover_smem = 0;  // class 1: the largest staged-digit buffer of the batch
+  ks::List<ks::RecoverArgs> recover[ks::kRecoverClasses];
+  int recover_smem[ks::kRecoverClasses] = {0};  // per class: the largest staged-digit buffer
   std::vector<ks::NttJob> ntt;
   int64_t tc_work = 0;
   long long launches = 0;
@@ -176,10 +176,10 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     KS_TRY(launch_unpack_batch(P->unpack.d, P->unpack.dprefix, P->unpack.n(),
                                P->unpack.blocks(), s));
   if (fork) KS_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
-  for (int c = 0; c < 3; c++)
+  for (int c = 0; c < kRecoverClasses; c++)
     if (P->recover[c].n())
       KS_TRY(launch_recover_batch(c + 1, P->recover[c].d, P->recover[c].dprefix,
-                                  P->recover[c].n(), P->recover[c].blocks(), P->recover_smem, s));
+                                  P->recover[c].n(), P->recover[c].blocks(), P->recover_smem[c], s));
   return cudaSuccess;
 }
 }  // namespace
@@ -274,8 +274,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
                           sp.narrow() ? acc : nullptr, seeds, p.seed_words, status,
                           ra, blocks) != 0)
       return KS_ERANGE;
-    P->recover[recover_class(p.M) - 1].add(ra, blocks);
-    if (ra.smem > P->recover_smem) P->recover_smem = ra.smem;
+    const int rc = recover_class(p.M, p.chain) - 1;
+    P->recover[rc].add(ra, blocks);
+    if (ra.smem > P->recover_smem[rc]) P->recover_smem[rc] = ra.smem;
   }
   return KS_OK;
 }
@@ -364,7 +365,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
               0;
   for (int i = 0; i < kSeedKinds; i++) db += P->seeds[i].bytes();
   db += P->planes.bytes();
-  for (int c = 0; c < 3; c++) db += P->recover[c].bytes();
+  for (int c = 0; c < kRecoverClasses; c++) db += P->recover[c].bytes();
   P->desc_bytes = db;
   if (alloc_device(reinterpret_cast<void **>(&P->desc), db) != cudaSuccess ||
       cudaMallocHost(&P->hdesc, db) != cudaSuccess) {
@@ -385,7 +386,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->unpack.place(h, d);
   for (int i = 0; i < kSeedKinds; i++) P->seeds[i].place(h, d);
   P->planes.place(h, d);
-  for (int c = 0; c < 3; c++) P->recover[c].place(h, d);
+  for (int c = 0; c < kRecoverClasses; c++) P->recover[c].place(h, d);
   if (cudaMemcpy(P->desc, P->hdesc, db, cudaMemcpyHostToDevice) != cudaSuccess) {
     ks_plan_destroy(P);
     return KS_ECUDA;

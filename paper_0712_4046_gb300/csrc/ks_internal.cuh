@@ -366,7 +366,10 @@ int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int n
                       int64_t nwords, int M, int64_t chain, int C,
                       const unsigned long long *seed_acc, const uint32_t *seeds,
                       int seed_words, int *status, RecoverArgs &a, int64_t &blocks);
-int recover_class(int M);
+// 1 .. kRecoverClasses: the kernel that reconstructs digits of M bits on
+// chains of the given length
+int recover_class(int M, int64_t chain);
+constexpr int kRecoverClasses = 6;
 cudaError_t launch_recover(const RecoverArgs &a, int64_t blocks, cudaStream_t s);
 // smem: the largest RecoverArgs::smem of the batch (class 1)
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,

@@ -544,9 +544,15 @@ __global__ void __launch_bounds__(kWT) seed_wide(Src src) {
       for (int w = 0; w < 2 * NW; w++) loc[w] += pr[w];
     }
   }
+  // the CTA's column sums: a shuffle tree in every warp, then one add per warp
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int w = 0; w < 2 * NW; w++)
-    if (w < seed_words && loc[w]) atomicAdd(&colsum[w], (unsigned long long)loc[w]);
+  for (int w = 0; w < 2 * NW; w++) {
+    long long v = loc[w];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0 && w < seed_words && v) atomicAdd(&colsum[w], (unsigned long long)v);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t *out = a.seeds + vid * seed_words;

@@ -107,64 +107,6 @@ cudaError_t launch_unpack_batch(const UnpackArgs *d, const int64_t *prefix, int 
 // subtracts.
 namespace {
 
-// digit arithmetic on W 32-bit words, values in [0, 2^M)
-struct Dig {
-  uint32_t w[kMaxDigitWordsM];
-};
-
-__device__ __forceinline__ void dig_load(Dig &x, const uint32_t *V, int64_t nwords, int64_t pos,
-                                         int M) {
-  const int W = (M + 31) / 32;
-  for (int i = 0; i < W; i += 2) {
-    const uint64_t v = get_bits64(V, nwords, pos + 32 * (int64_t)i);
-    x.w[i] = (uint32_t)v;
-    if (i + 1 < W) x.w[i + 1] = (uint32_t)(v >> 32);
-  }
-  const int top = M - 32 * (W - 1);
-  if (top < 32) x.w[W - 1] &= (1u << top) - 1u;
-}
-__device__ __forceinline__ void dig_load_local(Dig &x, const uint32_t *src, int nsrc, int pos,
-                                               int M) {
-  const int W = (M + 31) / 32;
-  for (int i = 0; i < W; i += 2) {
-    const uint64_t v = get_bits64(src, nsrc, pos + 32 * (int64_t)i);
-    x.w[i] = (uint32_t)v;
-    if (i + 1 < W) x.w[i + 1] = (uint32_t)(v >> 32);
-  }
-  const int top = M - 32 * (W - 1);
-  if (top < 32) x.w[W - 1] &= (1u << top) - 1u;
-}
-__device__ __forceinline__ bool dig_gt(const Dig &a, const Dig &b, int W) {
-  for (int i = W - 1; i >= 0; i--)
-    if (a.w[i] != b.w[i]) return a.w[i] > b.w[i];
-  return false;
-}
-// r = (a - b - c) mod 2^M
-__device__ __forceinline__ void dig_sub(Dig &r, const Dig &a, const Dig &b, uint32_t c, int M) {
-  const int W = (M + 31) / 32;
-  int64_t borrow = c;
-  for (int i = 0; i < W; i++) {
-    const int64_t t = (int64_t)a.w[i] - b.w[i] - borrow;
-    r.w[i] = (uint32_t)t;
-    borrow = t < 0 ? 1 : 0;
-  }
-  const int top = M - 32 * (W - 1);
-  if (top < 32) r.w[W - 1] &= (1u << top) - 1u;
-}
-// floor((a + b + c) / 2^M) for a, b < 2^M, c in {0, 1}
-__device__ __forceinline__ uint32_t dig_add_carry(const Dig &a, const Dig &b, uint32_t c, int M) {
-  const int W = (M + 31) / 32;
-  uint64_t carry = c;
-  uint32_t topw = 0;
-  for (int i = 0; i < W; i++) {
-    const uint64_t t = (uint64_t)a.w[i] + b.w[i] + carry;
-    topw = (uint32_t)t;
-    carry = t >> 32;
-  }
-  const int top = M - 32 * (W - 1);
-  if (top == 32) return (uint32_t)carry;
-  return (topw >> top) & 1u;
-}
 }  // namespace
 
 // Digits of at most 63 bits live in one 64-bit register; digits of 64..127
@@ -251,7 +193,9 @@ __device__ __forceinline__ void write_h2(uint64_t *out, int ol, D2 a, D2 be, int
   s[2] |= (r ? (be.lo >> (64 - r)) : 0ull) | (be.hi << r);
   s[3] |= r ? (be.hi >> (64 - r)) : 0ull;
   uint64_t borrow = 0;
-  for (int l = 0; l < ol; l++) out[l] = sub_k(l < 5 ? s[l] : 0ull, kb, l, borrow);
+#pragma unroll
+  for (int l = 0; l < 5; l++)  // ol <= 5 here (2M + 2 bits): s stays in registers
+    if (l < ol) out[l] = sub_k(s[l], kb, l, borrow);
 }
 
 __device__ __forceinline__ bool chain_index(const RecoverArgs &a, int64_t &gid, int &r) {
@@ -517,7 +461,176 @@ __global__ void __launch_bounds__(kRT) recover_staged1(Src src) {
   }
 }
 
-// 64 <= M <= 127, one thread per chain, digits read from global memory
+// 64 <= M <= 127, digits staged in shared memory: the scheme of the kernel
+// above with two-limb digits (D2).  A CTA of 128 threads runs cpc <= 16
+// consecutive chains of one run: one bulk copy of the word ranges holding
+// the CTA's u_j and w_j, all threads extract each chain's digits, warp 0
+// (a lane per chain) runs the recurrence from shared memory and stages
+// (alpha, beta) per coefficient, and all threads write the coefficients.
+constexpr int kRC2max = 16;
+__host__ __device__ __forceinline__ int64_t staged2_bytes(int64_t chain, int M, int cpc) {
+  // two word ranges, four digit arrays (u, w: lo, hi), (alpha, beta) per coefficient
+  return 2 * staged_words(chain, M, cpc) * 4 + 4 * staged_digits(chain, cpc) * 8 +
+         cpc * chain * 4 * 8;
+}
+template <class Src>
+__global__ void __launch_bounds__(kRT) recover_staged2(Src src) {
+  pdl_enter();
+  extern __shared__ __align__(16) uint32_t stg[];
+  __shared__ __align__(8) uint64_t bar;
+  int64_t local;
+  const RecoverArgs &a = src.locate(blockIdx.x, local);
+  int r = 0;
+  while (r + 1 < a.nruns && local >= a.rblocks[r]) {
+    local -= a.rblocks[r];
+    r++;
+  }
+  const RecoverRun &R = a.run[r];
+  int *status = a.status;
+  const int M = a.M, ol = a.ol, kb = a.kb;
+  const uint64_t hmask = (1ull << (M - 64)) - 1ull;  // 64 <= M <= 127
+  const int64_t n = R.n, chain = a.chain, nwords = a.nwords;
+  const int cpc = a.cpc;
+  const int tid = threadIdx.x;
+  const int64_t c0 = local * cpc;
+  const int64_t c1 = c0 + cpc < R.nchains ? c0 + cpc : R.nchains;
+  const int64_t j0 = c0 * chain;
+  const int64_t jhi = c1 * chain < n ? c1 * chain : n;
+  const int64_t ub0 = ((R.off_f + j0 * (int64_t)M) >> 5) & ~(int64_t)3;
+  const int64_t nu = ((((R.off_f + (jhi + 1) * (int64_t)M) >> 5) + 5 - ub0) + 3) & ~(int64_t)3;
+  const int64_t wb0 = ((R.off_r + (n - jhi) * (int64_t)M) >> 5) & ~(int64_t)3;
+  const int64_t nw = ((((R.off_r + (n - j0 + 1) * (int64_t)M) >> 5) + 5 - wb0) + 3) &
+                     ~(int64_t)3;
+  const int64_t capw = staged_words(chain, M, cpc), capd = staged_digits(chain, cpc);
+  if (nu > capw || nw > capw || ub0 < 0 || wb0 < 0 || (chain & (chain - 1)) != 0 || ol > 5 ||
+      M < 64 || M > 127) {
+    if (tid == 0) atomicCAS(status, 0, 3);  // not for a plan from make_recover_args
+    return;
+  }
+  uint32_t *su = stg, *sw = stg + capw;
+  uint64_t *dul = reinterpret_cast<uint64_t *>(stg + 2 * capw);
+  uint64_t *duh = dul + capd, *dwl = duh + capd, *dwh = dwl + capd;
+  uint64_t *so = dwh + capd;  // so(position p, lane i): alpha lo, hi, beta lo, hi
+  const int64_t cu = ub0 + nu <= nwords ? nu : (nwords > ub0 ? nwords - ub0 : 0);
+  const int64_t cw = wb0 + nw <= nwords ? nw : (nwords > wb0 ? nwords - wb0 : 0);
+  for (int64_t i = cu + tid; i < nu; i += kRT) su[i] = 0u;
+  for (int64_t i = cw + tid; i < nw; i += kRT) sw[i] = 0u;
+  if (tid == 0) {
+    stage_init(&bar);
+    stage_expect(&bar, (uint32_t)((cu + cw) * 4));
+    if (cu > 0) stage_copy(su, R.Vf + ub0, (uint32_t)(cu * 4), &bar);
+    if (cw > 0) stage_copy(sw, R.Vr + wb0, (uint32_t)(cw * 4), &bar);
+  }
+  const int64_t c_me = c0 + tid;
+  const bool chain_lane_me = tid < 32 && c_me < c1;
+  uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
+  ChainLane Lm;
+  if (chain_lane_me) {
+    Lm = chain_lane(a, R, c_me);
+    if (Lm.seeded) {
+      seed_value(a, Lm.vprev, s0);
+      seed_value(a, Lm.vcur, s1);
+    }
+  }
+  __syncthreads();
+  if (!__syncthreads_and(stage_wait(&bar))) {
+    if (tid == 0) atomicCAS(status, 0, 1);
+    stage_wait(&bar);  // once more (bounded) for the copies in flight before leaving
+    return;
+  }
+  // each chain's digits, [step t][chain i] (chain and cpc are powers of two)
+  const int lc = __ffsll((long long)chain) - 1, lp = __ffs(cpc) - 1;
+  const int64_t pu = R.off_f - ub0 * 32, pw = R.off_r - wb0 * 32;
+  for (int q = tid; q < (int)capd; q += kRT) {
+    const int t = q >> lp, i = q & (cpc - 1);
+    const int64_t c = c0 + i;
+    uint64_t xl = 0, xh = 0, yl = 0, yh = 0;
+    if (c < c1) {
+      bool up, seeded;
+      int64_t s_, len;
+      chain_geom(n, chain, c, up, s_, len, seeded);
+      if (t <= len) {
+        const int64_t j = up ? s_ + t : s_ - t;
+        const int64_t bu = pu + j * (int64_t)M, bw = pw + (n - j) * (int64_t)M;
+        const uint64_t ul = sbits64(su, nu, bu), uh = sbits64(su, nu, bu + 64) & hmask;
+        const uint64_t wl = sbits64(sw, nw, bw), wh = sbits64(sw, nw, bw + 64) & hmask;
+        xl = up ? ul : wl;
+        xh = up ? uh : wh;
+        yl = up ? wl : ul;
+        yh = up ? wh : uh;
+      }
+    }
+    dul[q] = xl;
+    duh[q] = xh;
+    dwl[q] = yl;
+    dwh[q] = yh;
+  }
+  __syncthreads();
+  // the chains (warp 0)
+  if (chain_lane_me) {
+    const int ln = tid;
+    const ChainLane &L = Lm;
+    const D2 zero = {0ull, 0ull};
+    D2 a_prev, a_cur;
+    uint64_t delta;
+    if (!L.seeded) {
+      a_prev = zero;
+      a_cur = D2{dul[ln], duh[ln]};
+      delta = 0;
+    } else {
+      a_prev = load_d2(s0, kAccSeedWords, 0, M);
+      const D2 b_prev = load_d2(s0, kAccSeedWords, M, M);
+      a_cur = load_d2(s1, kAccSeedWords, 0, M);
+      const D2 us = D2{dul[ln], duh[ln]};
+      const D2 dprev = sub_d2(sub_d2(us, b_prev, 0, M), a_cur, 0, M);
+      if (dprev.hi != 0 || dprev.lo > 1) atomicCAS(status, 0, 2);
+      delta = carry_d2(b_prev, a_cur, dprev.lo & 1ull, M);
+    }
+    D2 w_cur = D2{dwl[ln], dwh[ln]};
+    const int len = (int)L.len;
+    const int64_t last = n - 1 - L.pA;
+    const int steps = last == len - 1 ? len - 1 : len;
+    const int pstride = 4 * cpc;  // so words between consecutive positions
+    uint64_t *po = so + 4 * ln + (L.up ? 0 : (int64_t)(len - 1) * pstride);
+    const int pdir = L.up ? pstride : -pstride;
+    for (int t = 0; t < steps; t++) {
+      const int q = (t + 1) * cpc + ln;
+      const D2 u_next = D2{dul[q], duh[q]}, w_next = D2{dwl[q], dwh[q]};
+      const uint64_t eps = gt_d2(a_cur, w_next) ? 1ull : 0ull;
+      const D2 beta = sub_d2(sub_d2(w_cur, a_prev, 0, M), zero, eps, M);
+      const D2 a_next = sub_d2(sub_d2(u_next, beta, 0, M), zero, delta, M);
+      const uint64_t dnext = carry_d2(beta, a_next, delta, M);
+      po[0] = a_cur.lo;
+      po[1] = a_cur.hi;
+      po[2] = beta.lo;
+      po[3] = beta.hi;
+      po += pdir;
+      a_prev = a_cur;
+      a_cur = a_next;
+      delta = dnext;
+      w_cur = w_next;
+    }
+    if (steps < len) {
+      const D2 beta = sub_d2(w_cur, a_prev, 0, M);
+      po[0] = a_cur.lo;
+      po[1] = a_cur.hi;
+      po[2] = beta.lo;
+      po[3] = beta.hi;
+    }
+  }
+  __syncthreads();
+  // coefficients alpha + 2^M beta out, minus K: a thread per coefficient
+  uint64_t *h = a.h;
+  for (int jj = tid; jj < (int)(jhi - j0); jj += kRT) {
+    const int i = jj >> lc, p = jj & (int)(chain - 1);
+    const uint64_t *v = so + 4 * (((int64_t)p << lp) + i);
+    write_h2(h + (R.kbase + R.kstride * (j0 + jj)) * ol, ol, D2{v[0], v[1]}, D2{v[2], v[3]}, M,
+             kb);
+  }
+}
+
+// 64 <= M <= 127 with chains too long to stage: one thread per chain, the
+// digits read from global memory, eight steps' worth at a time
 template <class Src>
 __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
   pdl_enter();
@@ -556,126 +669,280 @@ __global__ void __launch_bounds__(128) recover_kernel2(Src src) {
   }
   D2 w_cur = DW(0);
   const int64_t last = n - 1 - L.pA;
-  for (int64_t t = 0; t < L.len; t++) {
-    uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, t)) * ol;
-    if (t != last) {
-      const D2 w_next = DW(t + 1);
-      const uint64_t eps = gt_d2(a_cur, w_next) ? 1ull : 0ull;
-      const D2 beta = sub_d2(sub_d2(w_cur, a_prev, 0, M), zero, eps, M);
-      const D2 u_next = DU(t + 1);
-      const D2 a_next = sub_d2(sub_d2(u_next, beta, 0, M), zero, delta, M);
-      const uint64_t dnext = carry_d2(beta, a_next, delta, M);
-      write_h2(out, ol, a_cur, beta, M, kb);
-      a_prev = a_cur;
-      a_cur = a_next;
-      delta = dnext;
-      w_cur = w_next;
-    } else {
-      write_h2(out, ol, a_cur, sub_d2(w_cur, a_prev, 0, M), M, kb);
-    }
-  }
-}
-
-// out limbs of alpha + 2^M beta - K, alpha, beta < 2^M (any M)
-__device__ void write_coeff(uint64_t *out, int ol, const Dig &al, const Dig &be, int M, int kb) {
-  const int W = (M + 31) / 32;
-  uint64_t borrow = 0;
-  for (int l = 0; l < ol; l++) {
-    uint64_t v = 0;
-    for (int half = 0; half < 2; half++) {
-      const int64_t p0 = 64 * (int64_t)l + 32 * half;  // bit position of this 32-bit chunk
-      uint64_t chunk = 0;
-      if (p0 < M) chunk |= al.w[(int)(p0 >> 5)];  // alpha's bits above M are zero
-      // from beta: bits [p0 - M, p0 - M + 32)
-      const int64_t q = p0 - M;
-      if (q + 32 > 0 && q < (int64_t)32 * W) {
-        const int64_t wi = q >= 0 ? (q >> 5) : -1;
-        const int sh = (int)(q & 31);
-        const uint64_t lo = (wi >= 0 && wi < W) ? be.w[wi] : 0u;
-        const uint64_t hi = (wi + 1 >= 0 && wi + 1 < W) ? be.w[wi + 1] : 0u;
-        const uint64_t pair = lo | (hi << 32);
-        uint32_t part;
-        if (q >= 0)
-          part = (uint32_t)(pair >> sh);
-        else
-          part = (uint32_t)(((uint64_t)be.w[0]) << (int)(-q));  // -q < 32
-        chunk |= part;
+  // the digits of eight steps are loaded together, ahead of their steps
+  constexpr int kAhead2 = 8;
+  for (int64_t t0 = 0; t0 < L.len; t0 += kAhead2) {
+    D2 un[kAhead2], wn[kAhead2];
+#pragma unroll
+    for (int q = 0; q < kAhead2; q++) {
+      const int64_t t = t0 + q;
+      if (t < L.len && t != last) {
+        wn[q] = DW(t + 1);
+        un[q] = DU(t + 1);
       }
-      v |= (chunk & 0xffffffffull) << (32 * half);
     }
-    out[l] = sub_k(v, kb, l, borrow);
+#pragma unroll
+    for (int q = 0; q < kAhead2; q++) {
+      const int64_t t = t0 + q;
+      if (t >= L.len) break;
+      uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, t)) * ol;
+      if (t != last) {
+        const D2 w_next = wn[q];
+        const uint64_t eps = gt_d2(a_cur, w_next) ? 1ull : 0ull;
+        const D2 beta = sub_d2(sub_d2(w_cur, a_prev, 0, M), zero, eps, M);
+        const D2 a_next = sub_d2(sub_d2(un[q], beta, 0, M), zero, delta, M);
+        const uint64_t dnext = carry_d2(beta, a_next, delta, M);
+        write_h2(out, ol, a_cur, beta, M, kb);
+        a_prev = a_cur;
+        a_cur = a_next;
+        delta = dnext;
+        w_cur = w_next;
+      } else {
+        write_h2(out, ol, a_cur, sub_d2(w_cur, a_prev, 0, M), M, kb);
+      }
+    }
   }
 }
 
-// any M (digits of W 32-bit words), one thread per chain
-template <class Src>
-__global__ void __launch_bounds__(64) recover_wide(Src src) {
+// ---- wide digits (M >= 128): one warp per chain
+// A digit of W = ceil(M / 32) words is spread over the warp: lane l holds
+// words l, l + 32, l + 64 (row k = word / 32; KR rows, a compile-time count).
+// Each multiword subtraction is a carry-lookahead over the warp: lane i
+// generates a borrow (x_i < y_i) or propagates one (x_i = y_i); with G, P the
+// ballots of those and A = G | P, the sum G + A + b_in carries exactly where a
+// borrow runs, so bit i of (G + A + b_in) ^ A ^ G is the borrow into word i
+// and bit 32 the borrow out of the row (the next row's borrow in).
+// (at most 3 rows: W <= 96, M <= 3072)
+constexpr int kWarpChains = 4;  // chains (warps) per CTA
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int KR>
+struct WD {
+  uint32_t w[KR];
+};
+// bits [pos, pos + 32) of a word array, words outside [0, n) read as zero
+__device__ __forceinline__ uint32_t bits32(const uint32_t *V, int64_t n, int64_t pos) {
+  const int64_t wi = pos >> 5;
+  const int sh = (int)(pos & 31);
+  const uint32_t lo = (wi >= 0 && wi < n) ? __ldg(V + wi) : 0u;
+  const uint32_t hi = (wi + 1 >= 0 && wi + 1 < n) ? __ldg(V + wi + 1) : 0u;
+  return sh ? (lo >> sh) | (hi << (32 - sh)) : lo;
+}
+// the M-bit digit at bit pos of V, this lane's words
+template <int KR>
+__device__ __forceinline__ void wd_load(WD<KR> &x, const uint32_t *V, int64_t n, int64_t pos,
+                                        int W, uint32_t topmask, int lane) {
+#pragma unroll
+  for (int k = 0; k < KR; k++) {
+    const int i = lane + 32 * k;
+    uint32_t v = i < W ? bits32(V, n, pos + 32 * i) : 0u;
+    x.w[k] = i == W - 1 ? v & topmask : v;
+  }
+}
+// d = (x - y - bin) mod 2^M; returns the borrow out (x, y < 2^M: the borrow
+// out of the top row is the borrow out of bit M)
+template <int KR>
+__device__ __forceinline__ uint32_t wd_sub(WD<KR> &d, const WD<KR> &x, const WD<KR> &y,
+                                           uint32_t bin, int W, uint32_t topmask, int lane) {
+  uint32_t b = bin;
+#pragma unroll
+  for (int k = 0; k < KR; k++) {
+    const int i = lane + 32 * k;
+    const bool valid = i < W;
+    const uint32_t xv = x.w[k], yv = y.w[k];
+    const uint32_t G = __ballot_sync(kFull, valid && xv < yv);
+    const uint32_t P = __ballot_sync(kFull, !valid || xv == yv);
+    const uint64_t A = G | P;
+    const uint64_t S = (uint64_t)G + A + b;
+    const uint32_t v = xv - yv - (((uint32_t)(S ^ A ^ G) >> lane) & 1u);
+    d.w[k] = !valid ? 0u : (i == W - 1 ? v & topmask : v);
+    b = (uint32_t)(S >> 32) & 1u;
+  }
+  return b;
+}
+// the borrow out of x - y (x < y), without the difference
+template <int KR>
+__device__ __forceinline__ uint32_t wd_less(const WD<KR> &x, const WD<KR> &y, int W, int lane) {
+  uint32_t b = 0;
+#pragma unroll
+  for (int k = 0; k < KR; k++) {
+    const int i = lane + 32 * k;
+    const bool valid = i < W;
+    const uint32_t G = __ballot_sync(kFull, valid && x.w[k] < y.w[k]);
+    const uint32_t P = __ballot_sync(kFull, !valid || x.w[k] == y.w[k]);
+    const uint64_t A = G | P;
+    b = (uint32_t)(((uint64_t)G + A + b) >> 32) & 1u;
+  }
+  return b;
+}
+// bits [bit, bit + M) of seed value v, this lane's words
+template <int KR>
+__device__ __forceinline__ void wd_seed(WD<KR> &x, const RecoverArgs &a, int64_t v, int bit,
+                                        int W, uint32_t topmask, int lane) {
+  if (a.seed_acc != nullptr) {
+    uint32_t s[kAccSeedWords];
+    seed_value(a, v, s);
+#pragma unroll
+    for (int k = 0; k < KR; k++) {
+      const int i = lane + 32 * k;
+      uint32_t r = 0;
+      if (i < W) {
+        const int pos = bit + 32 * i, wi = pos >> 5, sh = pos & 31;
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int j = 0; j < kAccSeedWords; j++) {
+          lo = j == wi ? s[j] : lo;
+          hi = j == wi + 1 ? s[j] : hi;
+        }
+        r = sh ? (lo >> sh) | (hi << (32 - sh)) : lo;
+        if (i == W - 1) r &= topmask;
+      }
+      x.w[k] = r;
+    }
+  } else {
+    wd_load(x, a.seeds + v * a.seed_words, a.seed_words, bit, W, topmask, lane);
+  }
+}
+// out limbs (ol of them) of alpha + 2^M beta - K for the steps q < nq of a
+// group, from their words in this warp's shared memory (al, be: 32 KR words
+// per step); step q's limbs at out + q cstep
+template <int KR>
+__device__ __forceinline__ void wd_write_group(uint64_t *out, int64_t cstep, int nq, int ol,
+                                               const uint32_t *al, const uint32_t *be, int M,
+                                               int W, int kb, int lane) {
+  const int ow = 2 * ol;  // 32-bit output words
+  for (int q = 0; q < nq; q++) {
+    const uint32_t *A = al + q * 32 * KR, *B = be + q * 32 * KR;
+    uint32_t *o = reinterpret_cast<uint32_t *>(out + q * cstep);
+    // the value's words, then - K (a one-bit subtrahend) by the same lookahead
+    uint32_t b = 0;
+    for (int k = 0; 32 * k < ow; k++) {
+      const int i = lane + 32 * k;
+      uint32_t v = 0;
+      if (i < ow) {
+        if (i < W) v = A[i];
+        const int qb = 32 * i - M;  // beta's bits [qb, qb + 32)
+        if (qb > -32) {
+          const int wi = qb >= 0 ? qb >> 5 : -1, sh = qb & 31;
+          const uint32_t lo = (wi >= 0 && wi < W) ? B[wi] : 0u;
+          const uint32_t hi = (wi + 1 >= 0 && wi + 1 < W) ? B[wi + 1] : 0u;
+          v |= qb >= 0 ? (sh ? (lo >> sh) | (hi << (32 - sh)) : lo) : (hi << (32 - sh));
+        }
+      }
+      if (kb >= 0) {
+        const uint32_t kv = (i == (kb >> 5)) ? 1u << (kb & 31) : 0u;
+        const bool valid = i < ow;
+        const uint32_t G = __ballot_sync(kFull, valid && v < kv);
+        const uint32_t P = __ballot_sync(kFull, !valid || v == kv);
+        const uint64_t Aa = G | P;
+        const uint64_t S = (uint64_t)G + Aa + b;
+        v = v - kv - (((uint32_t)(S ^ Aa ^ G) >> lane) & 1u);
+        b = (uint32_t)(S >> 32) & 1u;
+      }
+      if (i < ow) o[i] = v;
+    }
+  }
+}
+
+// M >= 128: a warp per chain, digits of KR rows of 32 words.  The digits of a
+// group of kAhead steps are loaded together, ahead of their steps; the steps
+// keep only the recurrence (and their alpha, beta words in shared memory), and
+// the group's coefficients are written after it.
+template <int KR, class Src>
+__global__ void __launch_bounds__(32 * kWarpChains) recover_warp(Src src) {
   pdl_enter();
+  constexpr int kAhead = KR == 1 ? 8 : 4;
+  __shared__ uint32_t wbuf[kWarpChains][2 * kAhead * 32 * KR];
   int64_t local;
   const RecoverArgs &a = src.locate(blockIdx.x, local);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   uint64_t *h = a.h;
   const int ol = a.ol, kb = a.kb;
   int *status = a.status;
-  int64_t gid = local * 64 + threadIdx.x;
+  int64_t gid = local * kWarpChains + wq;
   int r;
-  if (!chain_index(a, gid, r)) return;
+  if (!chain_index(a, gid, r)) return;  // warp-uniform
   const RecoverRun &R = a.run[r];
   const int M = a.M;
-  const int W = (M + 31) / 32;
+  const int W = (M + 31) >> 5;
+  const uint32_t topmask = (M & 31) ? (1u << (M & 31)) - 1u : 0xffffffffu;
   const int64_t n = R.n, nwords = a.nwords;
   const ChainLane L = chain_lane(a, R, gid);
-  Dig a_prev, a_cur, w_cur, w_next, u_next, beta, a_next, zero;
-  for (int i = 0; i < W; i++) zero.w[i] = 0;
+  uint32_t *sal = wbuf[wq], *sbe = wbuf[wq] + kAhead * 32 * KR;
+  WD<KR> a_prev, a_cur, w_cur, beta, a_next;
   uint32_t delta;
   if (!L.seeded) {
-    a_prev = zero;
-    dig_load(a_cur, L.A, nwords, L.offA + L.pA * (int64_t)M, M);
+#pragma unroll
+    for (int k = 0; k < KR; k++) a_prev.w[k] = 0;
+    wd_load(a_cur, L.A, nwords, L.offA + L.pA * (int64_t)M, W, topmask, lane);
     delta = 0;
   } else {
-    Dig b_prev, us, dp;
-    if (a.seed_acc != nullptr) {
-      uint32_t s0[kAccSeedWords], s1[kAccSeedWords];
-      seed_value(a, L.vprev, s0);
-      seed_value(a, L.vcur, s1);
-      dig_load_local(a_prev, s0, kAccSeedWords, 0, M);
-      dig_load_local(b_prev, s0, kAccSeedWords, M, M);
-      dig_load_local(a_cur, s1, kAccSeedWords, 0, M);
-    } else {
-      const uint32_t *sp = a.seeds + L.vprev * a.seed_words;
-      const uint32_t *sc = a.seeds + L.vcur * a.seed_words;
-      dig_load_local(a_prev, sp, a.seed_words, 0, M);
-      dig_load_local(b_prev, sp, a.seed_words, M, M);
-      dig_load_local(a_cur, sc, a.seed_words, 0, M);
+    WD<KR> b_prev, us, t1, dp;
+    wd_seed(a_prev, a, L.vprev, 0, W, topmask, lane);
+    wd_seed(b_prev, a, L.vprev, M, W, topmask, lane);
+    wd_seed(a_cur, a, L.vcur, 0, W, topmask, lane);
+    wd_load(us, L.A, nwords, L.offA + L.pA * (int64_t)M, W, topmask, lane);
+    // delta_(s-1) = u_s - beta_(s-1) - alpha_s (mod X) is 0 or 1, and the
+    // two borrows of that difference add up to delta_s
+    const uint32_t b1 = wd_sub(t1, us, b_prev, 0, W, topmask, lane);
+    const uint32_t b2 = wd_sub(dp, t1, a_cur, 0, W, topmask, lane);
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < KR; k++) ok = ok && (dp.w[k] == 0 || (k == 0 && lane == 0 && dp.w[0] == 1));
+    if (!__all_sync(kFull, ok) || b1 + b2 > 1) {
+      if (lane == 0) atomicCAS(status, 0, 2);
     }
-    dig_load(us, L.A, nwords, L.offA + L.pA * (int64_t)M, M);
-    Dig t1;
-    dig_sub(t1, us, b_prev, 0, M);
-    dig_sub(dp, t1, a_cur, 0, M);
-    bool ok = dp.w[0] <= 1;
-    for (int i = 1; i < W; i++) ok = ok && dp.w[i] == 0;
-    if (!ok) atomicCAS(status, 0, 2);
-    delta = dig_add_carry(b_prev, a_cur, dp.w[0] & 1u, M);
+    delta = b1 + b2;
   }
-  dig_load(w_cur, L.B, nwords, L.offB + L.pB * (int64_t)M, M);
+  wd_load(w_cur, L.B, nwords, L.offB + L.pB * (int64_t)M, W, topmask, lane);
   const int64_t last = n - 1 - L.pA;
-  for (int64_t t = 0; t < L.len; t++) {
-    uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, t)) * ol;
-    if (t != last) {
-      dig_load(w_next, L.B, nwords, L.offB + (L.pB - t - 1) * (int64_t)M, M);
-      const uint32_t eps = dig_gt(a_cur, w_next, W) ? 1u : 0u;
-      dig_sub(beta, w_cur, a_prev, eps, M);
-      dig_load(u_next, L.A, nwords, L.offA + (L.pA + t + 1) * (int64_t)M, M);
-      dig_sub(a_next, u_next, beta, delta, M);
-      const uint32_t dnext = dig_add_carry(beta, a_next, delta, M);
-      write_coeff(out, ol, a_cur, beta, M, kb);
-      a_prev = a_cur;
-      a_cur = a_next;
-      delta = dnext;
-      w_cur = w_next;
-    } else {
-      dig_sub(beta, w_cur, a_prev, 0, M);
-      write_coeff(out, ol, a_cur, beta, M, kb);
+  // bit positions of step t's next digits: DU(t + 1), DW(t + 1)
+  int64_t pu = L.offA + (L.pA + 1) * (int64_t)M, pw = L.offB + (L.pB - 1) * (int64_t)M;
+  const int64_t cstep = (L.up ? 1 : -1) * R.kstride * ol;  // output limbs between steps
+  uint64_t *out = h + (R.kbase + R.kstride * lane_coeff(L, 0)) * ol;
+  for (int64_t t0 = 0; t0 < L.len; t0 += kAhead) {
+    WD<KR> un[kAhead], wn[kAhead];  // DU, DW of steps t0 + 1 .. t0 + kAhead
+#pragma unroll
+    for (int q = 0; q < kAhead; q++) {
+      if (t0 + q < L.len && t0 + q != last) {
+        wd_load(wn[q], L.B, nwords, pw - (int64_t)q * M, W, topmask, lane);
+        wd_load(un[q], L.A, nwords, pu + (int64_t)q * M, W, topmask, lane);
+      }
     }
+    pu += (int64_t)kAhead * M;
+    pw -= (int64_t)kAhead * M;
+    int nq = 0;
+#pragma unroll
+    for (int q = 0; q < kAhead; q++) {
+      const int64_t t = t0 + q;
+      if (t >= L.len) break;
+      if (t != last) {
+        const uint32_t eps = wd_less(wn[q], a_cur, W, lane);  // alpha_j > w_(j+1)
+        wd_sub(beta, w_cur, a_prev, eps, W, topmask, lane);
+        const uint32_t dnext = wd_sub(a_next, un[q], beta, delta, W, topmask, lane);
+#pragma unroll
+        for (int k = 0; k < KR; k++) {
+          sal[q * 32 * KR + lane + 32 * k] = a_cur.w[k];
+          sbe[q * 32 * KR + lane + 32 * k] = beta.w[k];
+        }
+        a_prev = a_cur;
+        a_cur = a_next;
+        delta = dnext;
+        w_cur = wn[q];
+      } else {
+        wd_sub(beta, w_cur, a_prev, 0, W, topmask, lane);
+#pragma unroll
+        for (int k = 0; k < KR; k++) {
+          sal[q * 32 * KR + lane + 32 * k] = a_cur.w[k];
+          sbe[q * 32 * KR + lane + 32 * k] = beta.w[k];
+        }
+      }
+      nq = q + 1;
+    }
+    __syncwarp();
+    wd_write_group<KR>(out, cstep, nq, ol, sal, sbe, M, W, kb, lane);
+    __syncwarp();
+    out += kAhead * cstep;
   }
 }
 
@@ -718,14 +985,41 @@ int make_recover_args(uint64_t *h, int ol, int kb, const RecoverRun *runs, int n
     a.smem = (int)bytes;
     return 0;
   }
-  const int per = M <= 127 ? 128 : 64;
-  blocks = (total + per - 1) / per;
+  if (M <= 127 && staged2_bytes(chain, M, 1) <= 200 * 1024) {
+    // staged, two-limb digits: the same division into CTAs
+    int cpc = recover_cpc(chain);
+    if (cpc > kRC2max) cpc = kRC2max;
+    while (cpc > 8 && (total + cpc - 1) / cpc < 2 * 152) cpc >>= 1;
+    a.cpc = cpc;
+    blocks = 0;
+    for (int r = 0; r < nruns; r++) {
+      a.rblocks[r] = (runs[r].nchains + cpc - 1) / cpc;
+      blocks += a.rblocks[r];
+    }
+    const int64_t bytes = staged2_bytes(chain, M, cpc);
+    if (bytes > 200 * 1024 || ol > 5) return -1;
+    a.smem = (int)bytes;
+    return 0;
+  }
+  if (M <= 127) {  // chains too long to stage: a thread per chain
+    blocks = (total + 127) / 128;
+    return 0;
+  }
+  blocks = (total + kWarpChains - 1) / kWarpChains;  // a warp per chain
   return 0;
 }
 
-int recover_class(int M) { return M <= 63 ? 1 : (M <= 127 ? 2 : 3); }
+// 1: M <= 63 (staged), 2: M <= 127 (staged, two limbs), 3-5: wider, by rows
+// of 32 words (1-3), 6: M <= 127 with chains too long to stage
+int recover_class(int M, int64_t chain) {
+  if (M <= 63) return 1;
+  if (M <= 127) return staged2_bytes(chain, M, 1) <= 200 * 1024 ? 2 : 6;
+  return 2 + (((M + 31) / 32 + 31) / 32);
+}
 
-template <class Src>
+// the staged kernels' shared memory may pass the default 48 KB: opt in
+// (once per device and kernel, to the largest size asked so far)
+template <class Src, int D>
 static cudaError_t staged_attr(int smem) {
   static int done[64] = {0};
   int dev = 0;
@@ -733,8 +1027,8 @@ static cudaError_t staged_attr(int smem) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (smem > 48 * 1024 && smem > done[dev]) {
-    e = cudaFuncSetAttribute(recover_staged1<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
+    e = cudaFuncSetAttribute(D == 1 ? recover_staged1<Src> : recover_staged2<Src>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     done[dev] = smem;
   }
@@ -745,20 +1039,29 @@ template <class Src>
 static cudaError_t launch_recover_class(int cls, int64_t blocks, const Src &src, int smem,
                                         cudaStream_t s) {
   if (cls == 1) {
-    const cudaError_t e = staged_attr<Src>(smem);
+    const cudaError_t e = staged_attr<Src, 1>(smem);
     if (e != cudaSuccess) return e;
     (void)launch_k(recover_staged1<Src>, dim3((unsigned)blocks), dim3(kRT), smem, s, src);
-  } else if (cls == 2)
-    (void)launch_k(recover_kernel2<Src>, dim3((unsigned)blocks), dim3(128), 0, s, src);
+  } else if (cls == 2) {
+    const cudaError_t e = staged_attr<Src, 2>(smem);
+    if (e != cudaSuccess) return e;
+    (void)launch_k(recover_staged2<Src>, dim3((unsigned)blocks), dim3(kRT), smem, s, src);
+  }
+  else if (cls == 3)
+    (void)launch_k(recover_warp<1, Src>, dim3((unsigned)blocks), dim3(32 * kWarpChains), 0, s, src);
+  else if (cls == 4)
+    (void)launch_k(recover_warp<2, Src>, dim3((unsigned)blocks), dim3(32 * kWarpChains), 0, s, src);
+  else if (cls == 5)
+    (void)launch_k(recover_warp<3, Src>, dim3((unsigned)blocks), dim3(32 * kWarpChains), 0, s, src);
   else
-    (void)launch_k(recover_wide<Src>, dim3((unsigned)blocks), dim3(64), 0, s, src);
+    (void)launch_k(recover_kernel2<Src>, dim3((unsigned)blocks), dim3(128), 0, s, src);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_recover(const RecoverArgs &a, int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  return launch_recover_class(recover_class(a.M), blocks, One<RecoverArgs>{a}, a.smem, s);
+  return launch_recover_class(recover_class(a.M, a.chain), blocks, One<RecoverArgs>{a}, a.smem, s);
 }
 
 cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *prefix, int n,
