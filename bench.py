@@ -49,9 +49,11 @@ METRIC = "Z[x] products/s and output Gbit/s, KS4 vs KS1, bit-exact, 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_kernel
 # launch on this workload's KS4 product, from an ncu capture of the current
-# kernel (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k
-# regex:tc_kernel`); None until the kernel has been captured since it last changed
-TC_KERNEL_DRAM_BYTES = None
+# kernel (the tc_kernel summary under profiles/: 5.21 MB read, no DRAM
+# writes); set to None whenever the kernel changes until it is captured again
+TC_KERNEL_DRAM_BYTES = 5.21e6
+TC_KERNEL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                            "profiles/tc_kernel_zx_product_16384_s48_ks4.md")
 # 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC
 IMAD_PER_SM_CLK = 64
 SMS = 152
@@ -380,8 +382,8 @@ def main_ours(args):
     roof = roofline_for(dom, dom_ms, info, lf, lg, b, sg, hbm_gbs, sm_max_mhz, peak_kind)
     if info["engine"] == ks.ENGINE_TC:
         roof["traffic"] = TC_KERNEL_DRAM_BYTES
-        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
-                                  if TC_KERNEL_DRAM_BYTES else "not captured for this kernel")
+        roof["traffic_source"] = (TC_KERNEL_TRAFFIC_SOURCE if TC_KERNEL_DRAM_BYTES
+                                  else "not captured for this kernel")
         roof["kernel"] = "tc_kernel"
 
     cpu, exact = None, None
