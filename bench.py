@@ -582,7 +582,7 @@ def run_bivariate(ks, dev, stream, flush, steps, warmup):
     h = torch.empty((2 * ly - 1, 2 * lx - 1), dtype=torch.int64, device=dev)
     out = {"config": dict(w, l2="flushed before each product (256 MiB write)")}
     ref = None
-    for label, variant in (("KS1", 1), ("KS2", 2), ("KS3", 3), ("KS4", 4)):
+    for label, variant in (("KS1", 1), ("KS2", 2), ("KS3", 3), ("KS4", 4), ("KS_C", 5)):
         for _ in range(max(1, warmup)):
             ks.ks_mul_bivariate_mod(h, tf, tg, p, variant, stream)
         torch.cuda.synchronize()

@@ -52,8 +52,10 @@ extern "C" {
 
 typedef void *ks_stream_t; /* a cudaStream_t */
 
-/* Variant selector (Sec. 3.1-3.4).  KS_AUTO lets the library choose. */
-enum { KS_AUTO = 0, KS_1 = 1, KS_2 = 2, KS_3 = 3, KS_4 = 4 };
+/* Variant selector (Sec. 3.1-3.4).  KS_AUTO lets the library choose.  KS_C,
+ * the complex evaluation points of Sec. 2.5, exists for ks_mul_bivariate_mod
+ * only. */
+enum { KS_AUTO = 0, KS_1 = 1, KS_2 = 2, KS_3 = 3, KS_4 = 4, KS_C = 5 };
 
 /* Engine for the independent big-integer sub-products. */
 enum {
@@ -165,10 +167,18 @@ int ks_mul_bits(uint64_t *h, const uint64_t *f, int64_t len_f, int bits_f,
  *   KS_3  y = x^N and x^-N, N = lx, two products of length lx ly (Sec. 2.2)
  *   KS_4  y = +-x^N, +-x^-N, N = ceil(lx / 2), four products of length
  *         N (ly - 1) + lx (Sec. 2.4; p odd)
+ *   KS_C  y = x^M, -x^M and i x^M, M = ceil(lx / 2), in R[i] = R[t]/(t^2 + 1)
+ *         (Sec. 2.5; p odd): f(x, i x^M) = F_re + i F_im, and the complex
+ *         product by three real ones (F_re G_re, F_im G_im,
+ *         (F_re + F_im)(G_re + G_im)): five products of length M (ly - 1) + lx.
+ *         With A_r the part of h(x, x^M) whose rows k are r mod 4,
+ *         h(x, +-x^M) = A0 +- A1 + A2 +- A3, Re = A0 - A2, Im = A1 - A3, and
+ *         every A_r is a quarter of a sum of those; its rows lie 4M >= 2 lx - 1
+ *         apart, so they are read off.
  *   KS_AUTO  KS_2 for odd p, else KS_1.
  * Each univariate product runs through ks_mul_mod (whose own substitution
  * is chosen as for KS_AUTO).  Workspace is cached per (device, stream).
- * KS_EINVAL for bad arguments (KS_2 / KS_4 with even p); KS_ERANGE beyond
+ * KS_EINVAL for bad arguments (KS_2 / KS_4 / KS_C with even p); KS_ERANGE beyond
  * lx, ly <= 2^26 and lx ly <= 2^28.  Asynchronous on `stream`.
  */
 int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx,

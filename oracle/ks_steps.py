@@ -410,3 +410,72 @@ def recover_chains(fwd: int, rev: int, n: int, X: int, m: int, exact: list[int])
             for t, v in enumerate(vals):
                 out[s - 1 - t] = v
     return out
+
+
+# ---------------------------------------------------------------- Sec. 2.5
+def _pmul(a: list[int], b: list[int], p: int) -> list[int]:
+    """a b in (Z/pZ)[x] by the plain convolution."""
+    out = [0] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] = (out[i + j] + x * y) % p
+    return out
+
+
+def biv_complex_points(f: list[list[int]], g: list[list[int]], p: int) -> dict:
+    """h = f g in (Z/pZ)[x, y] (f[i][j]: the coefficient of x^j y^i) by the
+    complex evaluation points of Sec. 2.5, p odd.
+
+    M = ceil(lx / 2); S = R[i] with i^2 = -1 (pairs re + i im, so any odd p).
+    The three points y = x^M, -x^M, i x^M give H1 = h(x, x^M), H2 = h(x, -x^M)
+    (two products in R[x]) and h(x, i x^M) = F G with F = f(x, i x^M) =
+    F_re + i F_im: a complex product, done with three products in R[x]
+    (F_re G_re, F_im G_im, (F_re + F_im)(G_re + G_im)) -- five in all.
+
+    The reading of "appropriate linear combinations": with A_r the sum of the
+    terms h_k(x) x^(kM) whose rows k are r (mod 4),
+      H1 = A0 + A1 + A2 + A3,  H2 = A0 - A1 + A2 - A3,
+      Re h(x, i x^M) = A0 - A2,  Im h(x, i x^M) = A1 - A3,
+    so A0 = (H1 + H2 + 2 Re) / 4, A2 = (H1 + H2 - 2 Re) / 4,
+       A1 = (H1 - H2 + 2 Im) / 4, A3 = (H1 - H2 - 2 Im) / 4,
+    and, as h_k has length 2 lx - 1 <= 4M - 1, the rows of one A_r do not
+    overlap: h_k is read off A_(k mod 4) at x^(kM).  Returns h and the
+    intermediates."""
+    if p % 2 == 0:
+        raise ValueError("Sec. 2.5's combinations halve: p must be odd")
+    ly, lx = len(f), len(f[0])
+    M = (lx + 1) // 2
+    LF = M * (ly - 1) + lx
+
+    def ev(a, sign_of_row, rows):
+        out = [0] * LF
+        for r in rows:
+            s = sign_of_row(r)
+            for j, c in enumerate(a[r]):
+                out[r * M + j] = (out[r * M + j] + s * c) % p
+        return out
+
+    allr = range(ly)
+    # f(x, +-x^M), and f(x, i x^M) = F_re + i F_im (i^r = (-1)^(r/2) or i (-1)^((r-1)/2))
+    Fp = ev(f, lambda r: 1, allr)
+    Fm = ev(f, lambda r: -1 if r % 2 else 1, allr)
+    Fre = ev(f, lambda r: -1 if (r // 2) % 2 else 1, range(0, ly, 2))
+    Fim = ev(f, lambda r: -1 if (r // 2) % 2 else 1, range(1, ly, 2))
+    Gp = ev(g, lambda r: 1, allr)
+    Gm = ev(g, lambda r: -1 if r % 2 else 1, allr)
+    Gre = ev(g, lambda r: -1 if (r // 2) % 2 else 1, range(0, ly, 2))
+    Gim = ev(g, lambda r: -1 if (r // 2) % 2 else 1, range(1, ly, 2))
+    H1, H2 = _pmul(Fp, Gp, p), _pmul(Fm, Gm, p)
+    P3, P4 = _pmul(Fre, Gre, p), _pmul(Fim, Gim, p)
+    P5 = _pmul([(x + y) % p for x, y in zip(Fre, Fim)], [(x + y) % p for x, y in zip(Gre, Gim)], p)
+    Re = [(x - y) % p for x, y in zip(P3, P4)]
+    Im = [(z - x - y) % p for x, y, z in zip(P3, P4, P5)]
+    inv4 = pow(4, -1, p)
+    A = [[(x + y + 2 * r) * inv4 % p for x, y, r in zip(H1, H2, Re)],
+         [(x - y + 2 * m) * inv4 % p for x, y, m in zip(H1, H2, Im)],
+         [(x + y - 2 * r) * inv4 % p for x, y, r in zip(H1, H2, Re)],
+         [(x - y - 2 * m) * inv4 % p for x, y, m in zip(H1, H2, Im)]]
+    hx = 2 * lx - 1
+    h = [[A[k % 4][k * M + j] for j in range(hx)] for k in range(2 * ly - 1)]
+    return {"h": h, "M": M, "H1": H1, "H2": H2, "Re": Re, "Im": Im, "A": A,
+            "products": 5}

@@ -21,6 +21,7 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 
 KS_AUTO, KS_1, KS_2, KS_3, KS_4 = 0, 1, 2, 3, 4
+KS_C = 5  # complex evaluation points (Sec. 2.5), ks_mul_bivariate_mod only
 ENGINE_AUTO, ENGINE_SCHOOLBOOK, ENGINE_NTT, ENGINE_TC = 0, 1, 2, 3
 KS_OK, KS_EINVAL, KS_ERANGE, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 

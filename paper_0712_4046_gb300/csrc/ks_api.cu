@@ -812,8 +812,9 @@ int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int6
                          int64_t ly, uint64_t p_mod, int variant, ks_stream_t stream) {
   if (!h || !f || !g || lx < 1 || ly < 1 || p_mod < 2 || p_mod >= (1ull << 63)) return KS_EINVAL;
   if (variant == KS_AUTO) variant = (p_mod & 1) ? KS_2 : KS_1;
-  if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
-  if ((variant == KS_2 || variant == KS_4) && (p_mod & 1) == 0) return KS_EINVAL;  // halving
+  if (variant < KS_1 || variant > KS_C) return KS_EINVAL;
+  if ((variant == KS_2 || variant == KS_4 || variant == KS_C) && (p_mod & 1) == 0)
+    return KS_EINVAL;  // halving
   if (lx > ((int64_t)1 << 26) || ly > ((int64_t)1 << 26) || lx * ly > ((int64_t)1 << 28))
     return KS_ERANGE;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -824,6 +825,7 @@ int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int6
     case KS_1: N = 2 * lx - 1; LF = (ly - 1) * N + lx; nprod = 1; break;
     case KS_2:
     case KS_3: N = lx; LF = lx * ly; nprod = 2; break;
+    case KS_C: N = (lx + 1) / 2; LF = N * (ly - 1) + lx; nprod = 5; break;
     default: N = (lx + 1) / 2; LF = N * (ly - 1) + lx; nprod = 4; break;
   }
   const int64_t LP = 2 * LF - 1;
@@ -832,19 +834,22 @@ int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int6
   int rc = cached_buffer(3, s, (size_t)(2 * nprod) * ebytes + (size_t)nprod * pbytes, &buf);
   if (rc != KS_OK) return rc;
   char *base = static_cast<char *>(buf);
-  uint64_t *E[8], *P[4];
+  uint64_t *E[kMaxBivEvals], *P[5];
   for (int i = 0; i < 2 * nprod; i++) E[i] = reinterpret_cast<uint64_t *>(base + i * ebytes);
   for (int q = 0; q < nprod; q++)
     P[q] = reinterpret_cast<uint64_t *>(base + 2 * nprod * ebytes + q * pbytes);
-  // product q multiplies E[2q] (from f) by E[2q + 1] (from g): (reversed, alternating)
-  static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
-  static const int kAlt[5][4] = {{0}, {0}, {0, 1}, {0, 0}, {0, 1, 0, 1}};
+  // product q multiplies E[2q] (from f) by E[2q + 1] (from g): (reversed,
+  // alternating, part of the complex point)
+  static const int kRev[6][5] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}, {0, 0, 0, 0, 0}};
+  static const int kAlt[6][5] = {{0}, {0}, {0, 1}, {0, 0}, {0, 1, 0, 1}, {0, 1, 0, 0, 0}};
+  static const int kPart[6][5] = {{0}, {0}, {0, 0}, {0, 0}, {0, 0, 0, 0}, {0, 0, 1, 2, 3}};
   BivEvalArgs ea{};
   ea.n = 2 * nprod;
   for (int q = 0; q < nprod; q++)
     for (int side = 0; side < 2; side++)
       ea.e[2 * q + side] = BivEval{side ? g : f, E[2 * q + side], lx, ly, N, LF,
-                                   kRev[variant][q], kAlt[variant][q], p_mod};
+                                   kRev[variant][q], kAlt[variant][q], p_mod,
+                                   kPart[variant][q]};
   KS_CUDA(launch_biv_eval(ea, LF, s));
   for (int q = 0; q < nprod; q++) {
     rc = ks_mul_mod(P[q], E[2 * q], LF, E[2 * q + 1], LF, p_mod, KS_AUTO, stream);
@@ -857,6 +862,17 @@ int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int6
     case KS_2:
       KS_CUDA(launch_biv_readoff(BivReadArgs{h, P[0], P[1], lx, ly, N, p_mod}, s));
       break;
+    case KS_C: {
+      BivComplexArgs ca{};
+      ca.h = h;
+      for (int q = 0; q < 5; q++) ca.P[q] = P[q];
+      ca.lx = lx;
+      ca.ly = ly;
+      ca.M = N;
+      ca.p = p_mod;
+      KS_CUDA(launch_biv_readoff_complex(ca, s));
+      break;
+    }
     case KS_3:
       KS_CUDA(launch_biv_recover(BivRecoverArgs{h, BivSeq{P[0], nullptr, 1, 0, LP},
                                                 BivSeq{P[1], nullptr, 1, 0, LP}, 2 * ly - 1, lx,

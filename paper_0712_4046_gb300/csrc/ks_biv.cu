@@ -14,6 +14,9 @@
 //   KS_4  Sec. 2.4: all four points, N = ceil(lx / 2); the rows of f overlap
 //         already in the evaluations; the even and the odd h_k are recovered
 //         as in KS_3 at spacing 2N.
+//   KS_C  Sec. 2.5: y = x^M, -x^M, i x^M, M = ceil(lx / 2), in R[i]; the
+//         complex product as three real ones; the rows k = r (mod 4) are read
+//         off a quarter of a combination of the five products.
 //
 // All arithmetic is on residues in [0, p), p < 2^63 (no overflow in a + b);
 // halving (KS_2, KS_4) needs p odd.
@@ -48,9 +51,11 @@ __global__ void __launch_bounds__(256) biv_eval(const __grid_constant__ BivEvalA
     const int64_t i_lo = lo > 0 ? (lo + e.N - 1) / e.N : 0;
     uint64_t acc = 0;
     for (int64_t i = i_lo; i <= i_hi; i++) {
+      if ((e.part == 1 && (i & 1)) || (e.part == 2 && !(i & 1))) continue;
       const int64_t row = e.reversed ? e.ly - 1 - i : i;
       const uint64_t v = e.f[row * e.lx + (m - i * e.N)];
-      acc = (e.alternate && (i & 1)) ? sub_p(acc, v, e.p) : add_p(acc, v, e.p);
+      const bool neg = e.part ? ((i >> 1) & 1) != 0 : (e.alternate && (i & 1));
+      acc = neg ? sub_p(acc, v, e.p) : add_p(acc, v, e.p);
     }
     e.out[m] = acc;
   }
@@ -71,6 +76,34 @@ __global__ void __launch_bounds__(256) biv_readoff(BivReadArgs a) {
       v = half_p((k & 1) ? sub_p(v, w, a.p) : add_p(v, w, a.p), a.p);
     }
     a.h[idx] = v;
+  }
+}
+
+// KS_C (Sec. 2.5): at q = k M + j, with s = P1 + P2, d = P1 - P2 (the points
+// +-x^M), Re = P3 - P4, Im = P5 - P3 - P4 (the point i x^M):
+//   h[k][j] = (s + 2 Re) / 4, (d + 2 Im) / 4, (s - 2 Re) / 4, (d - 2 Im) / 4
+// for k = 0, 1, 2, 3 (mod 4).
+__global__ void __launch_bounds__(256) biv_readoff_complex(BivComplexArgs a) {
+  pdl_enter();
+  const uint64_t p = a.p;
+  const int64_t hx = 2 * a.lx - 1, total = (2 * a.ly - 1) * hx;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx / hx, j = idx - k * hx;
+    const int64_t q = k * a.M + j;
+    const uint64_t p1 = a.P[0][q], p2 = a.P[1][q], p3 = a.P[2][q], p4 = a.P[3][q],
+                   p5 = a.P[4][q];
+    uint64_t v, w;
+    if (k & 1) {
+      v = sub_p(p1, p2, p);                                // d
+      w = sub_p(sub_p(p5, p3, p), p4, p);                  // Im
+    } else {
+      v = add_p(p1, p2, p);                                // s
+      w = sub_p(p3, p4, p);                                // Re
+    }
+    const uint64_t w2 = add_p(w, w, p);
+    const uint64_t t = (k & 2) ? sub_p(v, w2, p) : add_p(v, w2, p);
+    a.h[idx] = half_p(half_p(t, p), p);
   }
 }
 
@@ -125,6 +158,13 @@ cudaError_t launch_biv_eval(const BivEvalArgs &a, int64_t maxlen, cudaStream_t s
 
 cudaError_t launch_biv_readoff(const BivReadArgs &a, cudaStream_t s) {
   (void)launch_k(biv_readoff, dim3(grid1((2 * a.ly - 1) * (2 * a.lx - 1), 256)), dim3(256), 0, s, a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_biv_readoff_complex(const BivComplexArgs &a, cudaStream_t s) {
+  (void)launch_k(biv_readoff_complex, dim3(grid1((2 * a.ly - 1) * (2 * a.lx - 1), 256)),
+                 dim3(256), 0, s, a);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -376,13 +376,17 @@ cudaError_t launch_recover_batch(int cls, const RecoverArgs *d, const int64_t *p
                                  int64_t blocks, int smem, cudaStream_t s);
 
 // (Z/pZ)[x, y] by the substitutions of Sec. 2 (ks_biv.cu).
-constexpr int kMaxBivEvals = 8;
-struct BivEval {  // one evaluation of f or g at +-x^N or +-x^-N
+constexpr int kMaxBivEvals = 10;
+struct BivEval {  // one evaluation of f or g at +-x^N or +-x^-N, or a part at i x^N
   const uint64_t *f;
   uint64_t *out;
   int64_t lx, ly, N, len;
   int reversed, alternate;
   uint64_t p;
+  // 0: every row (sign -1 for odd rows if alternate); complex point y = i x^N:
+  // 1 the real part (even rows i, sign (-1)^(i/2)), 2 the imaginary part (odd
+  // rows, sign (-1)^((i-1)/2)), 3 their sum (every row, sign (-1)^floor(i/2))
+  int part;
 };
 struct BivEvalArgs {
   BivEval e[kMaxBivEvals];
@@ -407,6 +411,13 @@ struct BivRecoverArgs {  // KS_3 / KS_4 reciprocal recovery of n blocks
 };
 cudaError_t launch_biv_eval(const BivEvalArgs &a, int64_t maxlen, cudaStream_t s);
 cudaError_t launch_biv_readoff(const BivReadArgs &a, cudaStream_t s);
+struct BivComplexArgs {  // KS_C read-off (Sec. 2.5) from the five products
+  uint64_t *h;
+  const uint64_t *P[5];
+  int64_t lx, ly, M;
+  uint64_t p;
+};
+cudaError_t launch_biv_readoff_complex(const BivComplexArgs &a, cudaStream_t s);
 cudaError_t launch_biv_recover(const BivRecoverArgs &a, cudaStream_t s);
 
 // (Z/pZ)[x]: out_k = h'_k mod p.

@@ -1,6 +1,7 @@
 """(Z/pZ)[x, y] products by the polynomial-ring substitutions of Sec. 2
-(KS_1 standard, KS_2 negated, KS_3 reciprocal, KS_4 four-point), through
-the C ABI, exact against the bivariate oracle."""
+(KS_1 standard, KS_2 negated, KS_3 reciprocal, KS_4 four-point, KS_C the
+complex points of Sec. 2.5), through the C ABI, exact against the bivariate
+oracle."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ from tests._gpu import to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 P61 = (1 << 61) - 1
-VARIANTS = [0, 1, 2, 3, 4]
+VARIANTS = [0, 1, 2, 3, 4, 5]
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +37,7 @@ def biv_gpu(ks, f, g, p, variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("p", [3, 65537, 2147483647, P61])
+@pytest.mark.parametrize("p", [3, 5, 65537, 998244353, 2147483647, P61])
 def test_bivariate_exact(ks, variant, p):
     for lx, ly in ((1, 1), (1, 7), (6, 1), (2, 2), (3, 4), (5, 5), (17, 9), (40, 33), (64, 3)):
         f, g = rand_biv(lx, ly, p, 11 * lx + ly), rand_biv(lx, ly, p, 11 * lx + ly + 5)
@@ -87,7 +88,7 @@ def test_bivariate_errors(ks):
     import torch
     f = to_dev(np.zeros((3, 4), dtype=np.uint64))
     h = torch.zeros((5, 7), dtype=torch.int64, device="cuda")
-    for variant in (2, 4):  # halving needs an odd modulus
+    for variant in (2, 4, 5):  # halving needs an odd modulus
         with pytest.raises(ks.KSError):
             ks.ks_mul_bivariate_mod(h, f, f, 1 << 20, variant)
     for variant in (1, 3, 0):  # the other variants take any modulus

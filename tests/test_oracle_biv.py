@@ -101,3 +101,63 @@ def test_rejects_bad_inputs():
     f[0][0] = 7
     with pytest.raises(ValueError):
         oracle.mul_biv_mod(f, f, 7)
+
+
+# ---- the complex evaluation points of Sec. 2.5 (step model)
+from oracle import ks_steps  # noqa: E402
+
+
+@pytest.mark.parametrize("p", [3, 5, 13, 65537, 998244353, P61])
+def test_complex_points_equal_the_plain_product(p):
+    # p = 1 (mod 4) and p = 3 (mod 4): R[i] = R[t]/(t^2 + 1) either way
+    rng = np.random.default_rng(p % 1000)
+    for lx, ly in ((1, 1), (1, 5), (4, 1), (2, 2), (3, 4), (5, 5), (8, 7), (9, 6)):
+        f = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+        g = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+        run = ks_steps.biv_complex_points(f, g, p)
+        assert run["h"] == pyref.biv_mul_mod(f, g, p), (p, lx, ly)
+        assert run["products"] == 5
+
+
+def test_complex_points_combinations():
+    # H1 = A0 + A1 + A2 + A3, H2 = A0 - A1 + A2 - A3, Re = A0 - A2, Im = A1 - A3,
+    # each A_r holding the rows k = r (mod 4) at x^(kM) without overlap
+    p, lx, ly = 65537, 7, 9
+    rng = np.random.default_rng(5)
+    f = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+    g = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+    run = ks_steps.biv_complex_points(f, g, p)
+    A, M, h = run["A"], run["M"], pyref.biv_mul_mod(f, g, p)
+    n = len(run["H1"])
+    for r in range(4):
+        want = [0] * n
+        for k in range(r, 2 * ly - 1, 4):
+            for j, c in enumerate(h[k]):
+                assert want[k * M + j] == 0 or c == 0  # no two rows of A_r meet
+                want[k * M + j] = (want[k * M + j] + c) % p
+        assert A[r][:n] == want
+    assert run["H1"] == [(a + b + c + d) % p for a, b, c, d in zip(*A)]
+    assert run["H2"] == [(a - b + c - d) % p for a, b, c, d in zip(*A)]
+    assert run["Re"] == [(a - c) % p for a, _, c, _ in zip(*A)]
+    assert run["Im"] == [(b - d) % p for _, b, _, d in zip(*A)]
+
+
+def test_complex_points_planted_slips_fail():
+    # a combination without the factor 2 on Re, or with Im's sign flipped,
+    # does not give the product
+    p, lx, ly = 998244353, 5, 6
+    rng = np.random.default_rng(6)
+    f = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+    g = [[int(x) for x in rng.integers(0, p, lx)] for _ in range(ly)]
+    run = ks_steps.biv_complex_points(f, g, p)
+    want, M, inv4 = pyref.biv_mul_mod(f, g, p), run["M"], pow(4, -1, p)
+    H1, H2, Re, Im = run["H1"], run["H2"], run["Re"], run["Im"]
+    slip0 = [(a + b + r) * inv4 % p for a, b, r in zip(H1, H2, Re)]
+    assert [slip0[0 * M + j] for j in range(2 * lx - 1)] != want[0]
+    slip1 = [(a - b - 2 * m) * inv4 % p for a, b, m in zip(H1, H2, Im)]
+    assert [slip1[1 * M + j] for j in range(2 * lx - 1)] != want[1]
+
+
+def test_complex_points_need_an_odd_modulus():
+    with pytest.raises(ValueError):
+        ks_steps.biv_complex_points([[1, 2]], [[3, 4]], 1 << 20)
