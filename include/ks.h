@@ -86,6 +86,14 @@ typedef enum {
  */
 int ks_out_limbs(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed);
 
+/*
+ * Limbs per output coefficient for bits_f-bit coefficients in f and
+ * bits_g-bit ones in g: ceil((bits_f + bits_g + e + is_signed) / 64), since
+ * |h_i| <= L 2^bits_f 2^bits_g (the same inequality with bits_f + bits_g in
+ * place of 2b).  ks_out_limbs(.., b, ..) is ks_out_limbs_bits(.., b, b, ..).
+ */
+int ks_out_limbs_bits(int64_t len_f, int64_t len_g, int bits_f, int bits_g, int is_signed);
+
 /* Evaluation exponent N the given variant uses (Sec. 3.1-3.4); < 0 on error. */
 int ks_eval_bits(int64_t len_f, int64_t len_g, int coeff_bits, int variant);
 
@@ -108,7 +116,12 @@ int64_t ks_workspace_bytes(int64_t len_f, int64_t len_g, int coeff_bits,
  * call per (device, stream),
  * forked from and joined back into `stream` with events; as seen from
  * `stream` the call is ordered like any other work on it, and it can be
- * captured into a CUDA graph (the helper stream becomes a parallel branch).
+ * captured into a CUDA graph (the helper stream becomes a parallel branch)
+ * once a call of the same size has run outside the capture.  The first call
+ * on each device (of any entry point) also loads the transform engine's
+ * twiddle tables with blocking copies; a transform product whose first use
+ * on a device is inside a capture returns KS_ECUDA and leaves the capture
+ * intact.
  */
 int ks_mul(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
            int64_t len_g, int coeff_bits, int is_signed, int variant,
@@ -144,14 +157,17 @@ int ks_mul_mod(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
 
 /*
  * h = f * g for coefficients of different sizes: f has bits_f-bit
- * coefficients (in_limbs ceil(bits_f / 64)), g has bits_g-bit ones (signed
- * or unsigned as for ks_mul, both the same).  The narrower operand is taken
- * as a B-bit one, B = max(bits_f, bits_g) (re-encoded with ceil(B / 64)
- * limbs, sign- or zero-extended, when its limb count differs), and the
- * product is ks_mul's with coeff_bits = B: exact, with the evaluation
- * exponents of B-bit operands (not the smaller ones b_f + b_g allows).  h has
- * ks_out_limbs(len_f, len_g, B, is_signed) limbs per coefficient.  The
- * re-encoded copy lives in a cache kept per (device, stream).  Asynchronous.
+ * coefficients (ceil(bits_f / 64) limbs each), g has bits_g-bit ones
+ * (ceil(bits_g / 64) limbs; signed or unsigned as for ks_mul, both the same).
+ * Every size bound of Sec. 3.1-3.4 holds with bits_f + bits_g in place of
+ * 2b, so the evaluation exponents are N = bits_f + bits_g + e (KS_1),
+ * ceil((bits_f + bits_g + e) / 2) (KS_2, KS_3; signed KS_3 at most 2 below
+ * that sum: 2) and ceil((bits_f + bits_g + e) / 4) (KS_4); each operand is
+ * packed from its own limbs with its own field width, and signed results are
+ * read shifted by K = 2^(bits_f + bits_g - 2 + e).  h has
+ * ks_out_limbs_bits(len_f, len_g, bits_f, bits_g, is_signed) limbs per
+ * coefficient.  KS_AUTO chooses as ks_mul does for ceil((bits_f + bits_g) / 2)
+ * bits.  Workspace is cached per (device, stream).  Asynchronous.
  */
 int ks_mul_bits(uint64_t *h, const uint64_t *f, int64_t len_f, int bits_f,
                 const uint64_t *g, int64_t len_g, int bits_g, int is_signed,
@@ -204,8 +220,9 @@ int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int6
  * ks_mul; the call makes no cudaMalloc, cudaFree or other allocating call.
  *
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture begins.  All calls, from any thread or stream,
+ * (cudaGetSymbolAddress, with that device current) and loads the transform
+ * engine's tables (blocking copies); make that first call before any stream
+ * capture begins.  All calls, from any thread or stream,
  * share the one array and it keeps the last call's contents; the parts that
  * must start at zero are cleared on `stream` by every call.  Calls that
  * overlap on the GPU race on the array: order them (one stream, or events).
@@ -215,13 +232,18 @@ int ks_mul_static(uint64_t *h, const uint64_t *f, int64_t len_f,
                   const uint64_t *g, int64_t len_g, int coeff_bits,
                   int is_signed, int variant, ks_stream_t stream);
 
-/* One product of a batch (device pointers, layout as for ks_mul). */
+/*
+ * One product of a batch (device pointers, layout as for ks_mul).
+ * coeff_bits_g = 0: g has coeff_bits-bit coefficients like f; otherwise g's
+ * size, and the product is ks_mul_bits's (h with ks_out_limbs_bits limbs).
+ */
 typedef struct {
   uint64_t *h;
   const uint64_t *f;
   const uint64_t *g;
   int64_t len_f, len_g;
   int32_t coeff_bits, is_signed, variant, engine;
+  int32_t coeff_bits_g;
 } ks_problem;
 
 /*
@@ -387,6 +409,10 @@ void ks_debug_tc_stall(int on, int64_t wait_ns);
  */
 int ks_plan_info(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
                  int variant, int engine, int64_t *info, int n);
+/* The plan ks_mul_bits (or a batch problem with coeff_bits_g) would run, as
+ * ks_plan_info's fields; field 14 is the larger operand's limb count. */
+int ks_plan_info_bits(int64_t len_f, int64_t len_g, int bits_f, int bits_g, int is_signed,
+                      int variant, int engine, int64_t *info, int n);
 void ks_profile_enable(int on);
 int ks_profile_collect(double *ms, long long *count, int n);
 const char *ks_phase_name(int phase);

@@ -31,7 +31,8 @@ _i64, _ci, _vp, _u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_u
 class KSProblem(ctypes.Structure):
     _fields_ = [("h", _vp), ("f", _vp), ("g", _vp), ("len_f", _i64), ("len_g", _i64),
                 ("coeff_bits", ctypes.c_int32), ("is_signed", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("engine", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("coeff_bits_g", ctypes.c_int32)]
 
 
 def _sig(name, res, *args):
@@ -42,6 +43,7 @@ def _sig(name, res, *args):
 
 
 _sig("ks_out_limbs", _ci, _i64, _i64, _ci, _ci)
+_sig("ks_out_limbs_bits", _ci, _i64, _i64, _ci, _ci, _ci)
 _sig("ks_eval_bits", _ci, _i64, _i64, _ci, _ci)
 _sig("ks_workspace_bytes", _i64, _i64, _i64, _ci, _ci, _ci, _ci)
 _sig("ks_mul", _ci, _vp, _vp, _i64, _vp, _i64, _ci, _ci, _ci, _vp)
@@ -89,6 +91,7 @@ _sig("ks_profile_collect", _ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(
      _ci)
 _sig("ks_phase_name", ctypes.c_char_p, _ci)
 _sig("ks_plan_info", _ci, _i64, _i64, _ci, _ci, _ci, _ci, ctypes.POINTER(_i64), _ci)
+_sig("ks_plan_info_bits", _ci, _i64, _i64, _ci, _ci, _ci, _ci, _ci, ctypes.POINTER(_i64), _ci)
 
 PLAN_FIELDS = ("variant", "engine", "N", "d", "nprod", "nA", "nB", "ncols", "nwords", "nnorm",
                "M", "chain", "nseeds", "out_limbs", "in_limbs", "workspace_bytes", "ntt_log",
@@ -171,7 +174,7 @@ def _check_product(h, f, g, bits_f, bits_g, is_signed) -> None:
         raise ValueError("coefficient bits must be >= 1")
     _check_poly(f, None, _limbs(bits_f), "f")
     _check_poly(g, None, _limbs(bits_g), "g")
-    ol = out_limbs(f.shape[0], g.shape[0], max(bits_f, bits_g), is_signed)
+    ol = out_limbs_bits(f.shape[0], g.shape[0], bits_f, bits_g, is_signed)
     _check_poly(h, f.shape[0] + g.shape[0] - 1, ol, "h")
     _check_device(h, f, g)
 
@@ -180,6 +183,14 @@ def out_limbs(len_f: int, len_g: int, coeff_bits: int, is_signed: bool) -> int:
     r = lib.ks_out_limbs(len_f, len_g, coeff_bits, int(is_signed))
     if r < 0:
         raise KSError(r, "ks_out_limbs")
+    return r
+
+
+def out_limbs_bits(len_f: int, len_g: int, bits_f: int, bits_g: int, is_signed: bool) -> int:
+    """Output limbs for bits_f-bit coefficients in f and bits_g-bit ones in g."""
+    r = lib.ks_out_limbs_bits(len_f, len_g, bits_f, bits_g, int(is_signed))
+    if r < 0:
+        raise KSError(r, "ks_out_limbs_bits")
     return r
 
 
@@ -260,7 +271,8 @@ def ks_mul_mod(h, f, g, p, variant=KS_AUTO, stream=None):
 
 def ks_mul_bits(h, f, bits_f, g, bits_g, is_signed, variant=KS_AUTO, stream=None):
     """h = f g with bits_f-bit coefficients in f and bits_g-bit ones in g (device
-    tensors of shape (L, ceil(bits / 64))); h has out_limbs(.., max(bits), ..) limbs."""
+    tensors of shape (L, ceil(bits / 64))); h has out_limbs_bits(..) limbs (N from
+    bits_f + bits_g)."""
     _check_product(h, f, g, bits_f, bits_g, is_signed)
     _check(lib.ks_mul_bits(_dptr(h), _dptr(f), f.shape[0], bits_f, _dptr(g), g.shape[0], bits_g,
                            int(is_signed), variant, _stream_ptr(stream)), "ks_mul_bits")
@@ -286,11 +298,13 @@ def ks_mul_bivariate_mod(h, f, g, p, variant=KS_AUTO, stream=None):
 def _problems(problems):
     arr = (KSProblem * len(problems))()
     for i, q in enumerate(problems):
-        _check_product(q["h"], q["f"], q["g"], q["coeff_bits"], q["coeff_bits"], q["is_signed"])
+        bg = q.get("coeff_bits_g", 0)
+        _check_product(q["h"], q["f"], q["g"], q["coeff_bits"], bg or q["coeff_bits"],
+                       q["is_signed"])
         arr[i] = KSProblem(_dptr(q["h"]).value, _dptr(q["f"]).value, _dptr(q["g"]).value,
                            q["f"].shape[0], q["g"].shape[0], q["coeff_bits"],
                            int(q["is_signed"]), q.get("variant", KS_AUTO),
-                           q.get("engine", ENGINE_AUTO))
+                           q.get("engine", ENGINE_AUTO), bg)
     return arr
 
 
@@ -406,11 +420,14 @@ def profile_collect() -> dict:
     return {lib.ks_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES)}
 
 
-def plan_info(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO) -> dict:
-    """The plan the library would run for this problem (sizes of every stage)."""
+def plan_info(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO,
+              bits_g=None) -> dict:
+    """The plan the library would run for this problem (sizes of every stage);
+    bits_g: g's coefficient bits when they differ from f's (coeff_bits)."""
     arr = (_i64 * len(PLAN_FIELDS))()
-    _check(lib.ks_plan_info(len_f, len_g, coeff_bits, int(is_signed), variant, engine, arr,
-                            len(PLAN_FIELDS)), "ks_plan_info")
+    bg = coeff_bits if bits_g is None else bits_g
+    _check(lib.ks_plan_info_bits(len_f, len_g, coeff_bits, bg, int(is_signed), variant, engine,
+                                 arr, len(PLAN_FIELDS)), "ks_plan_info_bits")
     return dict(zip(PLAN_FIELDS, [int(x) for x in arr]))
 
 

@@ -67,6 +67,9 @@ int *status_ptr() {
   if (ptrs[dev] == nullptr) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    // the transform's tables too, while no capture can be under way on a
+    // first call (a first call inside a capture would break it in either case)
+    if (ntt_init_tables() != 0) return nullptr;
     ptrs[dev] = static_cast<int *>(p);
   }
   return ptrs[dev];
@@ -78,29 +81,39 @@ int ceil_log2(int64_t n) {
   return e;
 }
 
-int variant_N(int variant, int b, int e) {
+// The coefficients of h lie below min(Lf, Lg) 2^(bf + bg) <= 2^(s + e),
+// s = bf + bg, which Sec. 3.1-3.4 bound by 2^(2b + e) for equal sizes: s takes
+// the place of 2b.
+int variant_N_sum(int variant, int s, int e) {
   switch (variant) {
-    case KS_1: return 2 * b + e;             // Sec. 3.1
+    case KS_1: return s + e;                 // Sec. 3.1
     case KS_2:                               // Sec. 3.3
-    case KS_3: return b + (e + 1) / 2;       // Sec. 3.2
-    case KS_4: return (2 * b + e + 3) / 4;   // Sec. 3.4
+    case KS_3: return (s + e + 1) / 2;       // Sec. 3.2
+    case KS_4: return (s + e + 3) / 4;       // Sec. 3.4
     default: return -1;
   }
 }
 
+int variant_N(int variant, int b, int e) { return variant_N_sum(variant, 2 * b, e); }
+
 // N for signed inputs (the offset reading): every coefficient is read shifted
-// into [0, 2^(2b-1+e)], one bit below the unsigned bound, so the
-// Propositions' N holds, except for the reciprocal variant at 2b + e = 2,
+// into [0, 2^(s-1+e)], one bit below the unsigned bound, so the
+// Propositions' N holds, except for the reciprocal variant at s + e = 2,
 // where X (X - 1) = 2 does not exceed the shifted top 2: there N = 2.
-int signed_N(int variant, int b, int e) {
-  const int N = variant_N(variant, b, e);
-  return (variant == KS_3 && 2 * b + e <= 2) ? 2 : N;
+int signed_N_sum(int variant, int s, int e) {
+  const int N = variant_N_sum(variant, s, e);
+  return (variant == KS_3 && s + e <= 2) ? 2 : N;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine) {
-  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS) return KS_EINVAL;
+int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant, int engine,
+              int bg) {
+  if (bg == 0) bg = b;
+  if (lf < 1 || lg < 1 || b < 1 || b > KS_MAX_COEFF_BITS || bg < 1 || bg > KS_MAX_COEFF_BITS)
+    return KS_EINVAL;
+  const int bf = b, s = bf + bg;  // s takes the place of 2b
+  if (bg > b) b = bg;             // the larger size, for the per-digit bounds
   if (variant < KS_1 || variant > KS_4) return KS_EINVAL;
   if (engine != KS_ENGINE_SCHOOLBOOK && engine != KS_ENGINE_TC && engine != KS_ENGINE_NTT)
     return KS_ENOTSUP;
@@ -112,13 +125,17 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   p.lg = lg;
   p.lh = lf + lg - 1;
   p.b = b;
+  p.bf = bf;
+  p.bg = bg;
   p.is_signed = is_signed ? 1 : 0;
   p.e = ceil_log2(lf < lg ? lf : lg);
-  p.N = is_signed ? signed_N(variant, b, p.e) : variant_N(variant, b, p.e);
-  // signed: every coefficient is read shifted by K = 2^(2b-2+e) >= |h_k|
-  p.kb = is_signed ? 2 * b - 2 + p.e : -1;
+  p.N = is_signed ? signed_N_sum(variant, s, p.e) : variant_N_sum(variant, s, p.e);
+  // signed: every coefficient is read shifted by K = 2^(bf+bg-2+e) >= |h_k|
+  p.kb = is_signed ? s - 2 + p.e : -1;
   p.in_limbs = (b + 63) / 64;
-  p.out_limbs = (2 * b + p.e + p.is_signed + 63) / 64;
+  p.ilf = (bf + 63) / 64;
+  p.ilg = (bg + 63) / 64;
+  p.out_limbs = (s + p.e + p.is_signed + 63) / 64;
   p.d = engine == KS_ENGINE_TC ? 8 : 16;
   p.dn = engine == KS_ENGINE_TC ? 32 : p.d;
   // the tensor cores' exact chunks allow at most eight coefficient fields per
@@ -128,8 +145,8 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     while ((b + p.d - 2) / p.N + 1 > 8) p.N++;
   p.nprod = variant == KS_1 ? 1 : (variant == KS_4 ? 4 : 2);
   p.nnorm = p.nprod;
-  const int64_t bitsF = (int64_t)p.N * (lf - 1) + b;
-  const int64_t bitsG = (int64_t)p.N * (lg - 1) + b;
+  const int64_t bitsF = (int64_t)p.N * (lf - 1) + bf;
+  const int64_t bitsG = (int64_t)p.N * (lg - 1) + bg;
   p.nA = (bitsF + p.d - 1) / p.d;
   p.nB = (bitsG + p.d - 1) / p.d;
   p.ncols = p.nA + p.nB - 1;
@@ -147,10 +164,11 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   // a multiple of four: every normalized combination starts 16-byte aligned
   p.nwords = ((p.dn * p.ncols + 95) / 32 + 1 + 3) & ~(int64_t)3;
   p.ntiles = norm_tiles_for(p.nwords, p.dn);
-  // digit magnitude: at most `pieces` fields meet a d-bit window
-  const int64_t pieces = (b + p.d - 2) / p.N + 1;
-  const double dmax = (double)pieces * (double)((1 << p.d) - 1);
-  const double colmax = dmax * dmax * (double)(p.nA < p.nB ? p.nA : p.nB);
+  // digit magnitude: at most `pieces` fields of an operand meet a d-bit window
+  const int64_t pieces_f = (bf + p.d - 2) / p.N + 1, pieces_g = (bg + p.d - 2) / p.N + 1;
+  const double dunit = (double)((1 << p.d) - 1);
+  const double colmax = (double)pieces_f * dunit * (double)pieces_g * dunit *
+                        (double)(p.nA < p.nB ? p.nA : p.nB);
   if (colmax * 2.0 >= 9.2e18) return KS_ERANGE;
   if (engine == KS_ENGINE_SCHOOLBOOK && (double)p.nA * (double)p.nB > 1.5e11) return KS_ENOTSUP;
   // the contraction engines are quadratic: beyond ~0.1 s of work the transform is the engine
@@ -184,7 +202,7 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
     int64_t c2 = 1;  // a power of two (the staged reconstruction indexes by shifts)
     while (c2 < p.chain) c2 <<= 1;
     p.chain = c2;
-    p.seed_words = (2 * b + p.e + 1 + 31) / 32 + 1;
+    p.seed_words = (s + p.e + 1 + 31) / 32 + 1;
     for (int r = 0; r < p.nruns; r++) p.nchains[r] = (p.run_n[r] + p.chain - 1) / p.chain;
     // one seed cluster per pair position s = chain (2j + 1) of the longer run:
     // (h_(s-1), h_s) for Sec. 3.2, (h_(2s-2), h_(2s-1), h_(2s), h_(2s+1)) for
@@ -210,7 +228,7 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
   if (b <= 64 && p.nseeds > 0)
     off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_planes = off;   // narrow seeds: the coefficients' balanced 8-bit digit planes
-  if (b <= 64 && p.nseeds > 0) off = align256(off + (size_t)seed_planes_bytes(lf, lg, seed_digits(b, b, p.is_signed)));
+  if (b <= 64 && p.nseeds > 0) off = align256(off + (size_t)seed_planes_bytes(lf, lg, seed_digits(bf, bg, p.is_signed)));
   p.off_flags = off;
   p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
   off = align256(p.off_flags + (size_t)p.flag_bytes);
@@ -302,7 +320,7 @@ bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *en
   if (!mlp_installed()) return false;
   std::vector<float> x(n * KS_MLP_IN), y(n * KS_MLP_OUT);
   for (int64_t i = 0; i < n; i++)
-    mlp_features(probs[i].len_f, probs[i].len_g, probs[i].coeff_bits, probs[i].is_signed, n,
+    mlp_features(probs[i].len_f, probs[i].len_g, problem_bits(probs[i]), probs[i].is_signed, n,
                  &x[i * KS_MLP_IN]);
   if (mlp_predict_host(x.data(), n, y.data()) != KS_OK) return false;
   static const int kEng[3] = {KS_ENGINE_SCHOOLBOOK, KS_ENGINE_NTT, KS_ENGINE_TC};
@@ -322,7 +340,7 @@ bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *en
       }
     for (int a = 0; a < KS_MLP_OUT; a++) {
       const int v = order[a] / 3 + 1, e = kEng[order[a] % 3];
-      if (feasible(q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e)) {
+      if (feasible(q.len_f, q.len_g, problem_bits(q), q.is_signed, v, e)) {
         variants[i] = v;
         engines[i] = e;
         break;
@@ -454,7 +472,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   SeedPlan sp;
   if (recon) {
     plan_runs(p, words, runs);
-    if (make_seed_plan(f, p.lf, p.b, g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl, p.C,
+    if (make_seed_plan(f, p.lf, p.bf, g, p.lg, p.bg, p.is_signed, p.kb, p.k00, p.kstep, p.ncl, p.C,
                        seed_acc, seeds, p.seed_words,
                        reinterpret_cast<__half *>(ws + p.off_planes), status, sp) != 0)
       return KS_ERANGE;
@@ -491,13 +509,15 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
     // operands padded to multiples of four digits: every one 16-byte aligned
     int32_t *A = dig + (int64_t)q * (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3));
     int32_t *B = A + ((p.nA + 3) & ~(int64_t)3);
-    pa.op[2 * q] = PackOp{f, p.lf, kRev[p.variant][q], kSig[p.variant][q], A, p.nA};
-    pa.op[2 * q + 1] = PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB};
+    pa.op[2 * q] = PackOp{f, p.lf, kRev[p.variant][q], kSig[p.variant][q], A, p.nA, p.bf, p.ilf};
+    pa.op[2 * q + 1] =
+        PackOp{g, p.lg, kRev[p.variant][q], kSig[p.variant][q], B, p.nB, p.bg, p.ilg};
     prods[q] = Product{A, p.nA, B, p.nB, cols + (int64_t)q * p.ncols};
   }
-  // squaring (f = g, equal lengths): the int32-digit engines pack every
+  // squaring (f = g, equal lengths and sizes): the int32-digit engines pack every
   // evaluation once and multiply its digits by themselves
-  if (f == g && p.lf == p.lg && p.engine != KS_ENGINE_TC) squaring_pack(pa, prods, p.nprod);
+  if (f == g && p.lf == p.lg && p.bf == p.bg && p.engine != KS_ENGINE_TC)
+    squaring_pack(pa, prods, p.nprod);
   pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     {
@@ -626,13 +646,29 @@ static bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
 }
 
 static int check_args(uint64_t *h, const uint64_t *f, int64_t lf, const uint64_t *g, int64_t lg,
-                      int b, int ol) {
+                      int b, int ol, int bg = 0) {
   if (!h || !f || !g) return KS_EINVAL;
-  const int il = (b + 63) / 64;
+  const int ilf = (b + 63) / 64, ilg = ((bg ? bg : b) + 63) / 64;
   const size_t hb = (size_t)(lf + lg - 1) * ol * 8;
-  if (overlaps(h, hb, f, (size_t)lf * il * 8) || overlaps(h, hb, g, (size_t)lg * il * 8))
+  if (overlaps(h, hb, f, (size_t)lf * ilf * 8) || overlaps(h, hb, g, (size_t)lg * ilg * 8))
     return KS_EINVAL;
   return KS_OK;
+}
+
+// The plan of a product with bf-bit coefficients in f and bg-bit ones in g.
+// KS_AUTO and KS_ENGINE_AUTO are chosen as for equal sizes of the same sum
+// (ceil((bf + bg) / 2) bits each: the exponents N depend on bf + bg only); an
+// engine chosen so that the unequal sizes exceed its limits gives way to the
+// transform.
+static int plan_bits(Plan &p, int64_t lf, int64_t lg, int bf, int bg, int is_signed, int variant,
+                     int engine) {
+  const bool auto_engine = engine == KS_ENGINE_AUTO;
+  int rc = choose(lf, lg, (bf + bg + 1) / 2, is_signed, &variant, &engine);
+  if (rc != KS_OK) return rc;
+  rc = make_plan(p, lf, lg, bf, is_signed, variant, engine, bg);
+  if (rc != KS_OK && auto_engine && engine != KS_ENGINE_NTT)
+    rc = make_plan(p, lf, lg, bf, is_signed, variant, KS_ENGINE_NTT, bg);
+  return rc;
 }
 
 // ------------------------------------------------------- no-allocation scratch
@@ -668,9 +704,15 @@ extern "C" {
 int ks_version(void) { return 100; }
 
 int ks_out_limbs(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed) {
-  if (len_f < 1 || len_g < 1 || coeff_bits < 1 || coeff_bits > KS_MAX_COEFF_BITS) return KS_EINVAL;
+  return ks_out_limbs_bits(len_f, len_g, coeff_bits, coeff_bits, is_signed);
+}
+
+int ks_out_limbs_bits(int64_t len_f, int64_t len_g, int bits_f, int bits_g, int is_signed) {
+  if (len_f < 1 || len_g < 1 || bits_f < 1 || bits_f > KS_MAX_COEFF_BITS || bits_g < 1 ||
+      bits_g > KS_MAX_COEFF_BITS)
+    return KS_EINVAL;
   const int e = ceil_log2(len_f < len_g ? len_f : len_g);
-  return (2 * coeff_bits + e + (is_signed ? 1 : 0) + 63) / 64;
+  return (bits_f + bits_g + e + (is_signed ? 1 : 0) + 63) / 64;
 }
 
 int ks_eval_bits(int64_t len_f, int64_t len_g, int coeff_bits, int variant) {
@@ -792,20 +834,15 @@ int ks_mul_bits(uint64_t *h, const uint64_t *f, int64_t len_f, int bits_f, const
   if (bits_f < 1 || bits_g < 1 || bits_f > KS_MAX_COEFF_BITS || bits_g > KS_MAX_COEFF_BITS ||
       len_f < 1 || len_g < 1 || !h || !f || !g)
     return KS_EINVAL;
-  const int B = bits_f > bits_g ? bits_f : bits_g;
-  const int il = (B + 63) / 64, ilf = (bits_f + 63) / 64, ilg = (bits_g + 63) / 64;
-  if (ilf == il && ilg == il)  // same limb layout: a bits_g-bit value is a B-bit value
-    return ks_mul(h, f, len_f, g, len_g, B, is_signed, variant, stream);
-  // re-encode the narrower operand with il limbs
-  const bool wf = ilf < il;
-  const int64_t len = wf ? len_f : len_g;
-  void *buf = nullptr;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int rc = cached_buffer(4, s, (size_t)len * il * 8, &buf);
+  Plan p;
+  int rc = plan_bits(p, len_f, len_g, bits_f, bits_g, is_signed, variant, KS_ENGINE_AUTO);
   if (rc != KS_OK) return rc;
-  uint64_t *w = static_cast<uint64_t *>(buf);
-  KS_CUDA(launch_widen(w, wf ? f : g, len, wf ? ilf : ilg, il, is_signed, s));
-  return ks_mul(h, wf ? w : f, len_f, wf ? g : w, len_g, B, is_signed, variant, stream);
+  rc = check_args(h, f, len_f, g, len_g, bits_f, p.out_limbs, bits_g);
+  if (rc != KS_OK) return rc;
+  void *ws = nullptr;
+  rc = cached_buffer(0, static_cast<cudaStream_t>(stream), p.total, &ws);
+  if (rc != KS_OK) return rc;
+  return run_plan(p, h, f, g, static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
 }
 
 int ks_mul_bivariate_mod(uint64_t *h, const uint64_t *f, const uint64_t *g, int64_t lx,
@@ -967,11 +1004,15 @@ long long ks_launch_count(void) { return g_launches.load(); }
 
 int ks_plan_info(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed, int variant,
                  int engine, int64_t *info, int n) {
+  return ks_plan_info_bits(len_f, len_g, coeff_bits, coeff_bits, is_signed, variant, engine, info,
+                           n);
+}
+
+int ks_plan_info_bits(int64_t len_f, int64_t len_g, int bits_f, int bits_g, int is_signed,
+                      int variant, int engine, int64_t *info, int n) {
   if (info == nullptr || n < 1) return KS_EINVAL;
-  int rc = choose(len_f, len_g, coeff_bits, is_signed, &variant, &engine);
-  if (rc != KS_OK) return rc;
   Plan p;
-  rc = make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, engine);
+  const int rc = plan_bits(p, len_f, len_g, bits_f, bits_g, is_signed, variant, engine);
   if (rc != KS_OK) return rc;
   const int64_t v[] = {p.variant, p.engine, p.N, p.d, p.nprod, p.nA, p.nB, p.ncols, p.nwords,
                        p.nnorm, p.M, p.chain, p.nseeds, p.out_limbs, p.in_limbs,

@@ -206,13 +206,16 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     // operands padded to multiples of four digits: every one 16-byte aligned
     int32_t *A = dig + (int64_t)k * (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3));
     int32_t *B = A + ((p.nA + 3) & ~(int64_t)3);
-    pa.op[2 * k] = PackOp{q.f, p.lf, kRev[p.variant][k], kSig[p.variant][k], A, p.nA};
-    pa.op[2 * k + 1] = PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB};
+    pa.op[2 * k] =
+        PackOp{q.f, p.lf, kRev[p.variant][k], kSig[p.variant][k], A, p.nA, p.bf, p.ilf};
+    pa.op[2 * k + 1] =
+        PackOp{q.g, p.lg, kRev[p.variant][k], kSig[p.variant][k], B, p.nB, p.bg, p.ilg};
     prods[k] = Product{A, p.nA, B, p.nB, cols + (int64_t)k * p.ncols};
   }
-  // squaring (f = g, equal lengths): the int32-digit engines pack every
+  // squaring (f = g, equal lengths and sizes): the int32-digit engines pack every
   // evaluation once and multiply its digits by themselves
-  if (q.f == q.g && p.lf == p.lg && p.engine != KS_ENGINE_TC) squaring_pack(pa, prods, p.nprod);
+  if (q.f == q.g && p.lf == p.lg && p.bf == p.bg && p.engine != KS_ENGINE_TC)
+    squaring_pack(pa, prods, p.nprod);
   pack_finish(pa);
   if (p.engine == KS_ENGINE_TC) {
     TcPackArgs ta;
@@ -255,7 +258,7 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
     plan_runs(p, words, runs);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws + p.off_seedacc);
     SeedPlan sp;
-    if (make_seed_plan(q.f, p.lf, p.b, q.g, p.lg, p.b, p.is_signed, p.kb, p.k00, p.kstep, p.ncl,
+    if (make_seed_plan(q.f, p.lf, p.bf, q.g, p.lg, p.bg, p.is_signed, p.kb, p.k00, p.kstep, p.ncl,
                        p.C, acc, seeds, p.seed_words,
                        reinterpret_cast<__half *>(ws + p.off_planes), status, sp) != 0)
       return KS_ERANGE;
@@ -292,7 +295,8 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   *out = nullptr;
   ks_plan *P = new (std::nothrow) ks_plan();
   if (P == nullptr) return KS_ENOMEM;
-  if (cudaGetDevice(&P->device) != cudaSuccess) {
+  // the transform's tables are loaded here, before any capture of the plan
+  if (cudaGetDevice(&P->device) != cudaSuccess || ntt_init_tables() != 0) {
     delete P;
     return KS_ECUDA;
   }
@@ -312,8 +316,16 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       return KS_EINVAL;
     }
     int v = learned ? mv[i] : q.variant, e = learned ? me[i] : q.engine;
-    int rc = choose_mode(q.len_f, q.len_g, q.coeff_bits, q.is_signed, dispatch_mode, &v, &e);
-    if (rc == KS_OK) rc = make_plan(P->plans[i], q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e);
+    const int bg = problem_bits_g(q);
+    int rc = q.coeff_bits_g < 0 ? KS_EINVAL : KS_OK;
+    if (rc == KS_OK)
+      rc = choose_mode(q.len_f, q.len_g, problem_bits(q), q.is_signed, dispatch_mode, &v, &e);
+    if (rc == KS_OK)
+      rc = make_plan(P->plans[i], q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, e, bg);
+    // unequal sizes: an engine chosen for the equal size may exceed its limits
+    if (rc != KS_OK && bg != q.coeff_bits && q.engine == KS_ENGINE_AUTO && e != KS_ENGINE_NTT)
+      rc = make_plan(P->plans[i], q.len_f, q.len_g, q.coeff_bits, q.is_signed, v, KS_ENGINE_NTT,
+                     bg);
     if (rc != KS_OK) {
       delete P;
       return rc;

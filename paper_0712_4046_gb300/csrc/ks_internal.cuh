@@ -33,6 +33,9 @@ struct Plan {
   int variant = 0, engine = 0;
   int64_t lf = 0, lg = 0, lh = 0;
   int b = 0, e = 0, N = 0, is_signed = 0, in_limbs = 0, out_limbs = 0;
+  // coefficient bits and limbs of f and of g (b, in_limbs: the larger ones);
+  // bf + bg takes the place of 2b in every size bound
+  int bf = 0, bg = 0, ilf = 0, ilg = 0;
   int d = 16;           // digit bits of the sub-product operands
   int dn = 16;          // digit bits of the column sums fed to the normalization
   TcGeom tg;
@@ -64,12 +67,21 @@ struct Plan {
 };
 
 int ceil_log2(int64_t n);
+// N of a variant for coefficient sizes adding up to s = bf + bg (2b for equal ones)
+int variant_N_sum(int variant, int s, int e);
 int variant_N(int variant, int b, int e);
-// Fills `p` (layout included) for an explicit variant and engine; KS_OK or error.
+// Fills `p` (layout included) for an explicit variant and engine; KS_OK or
+// error.  f has b-bit coefficients, g bg-bit ones (bg = 0: b bits as well).
 int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant,
-              int engine);
+              int engine, int bg = 0);
 int choose(int64_t lf, int64_t lg, int b, int is_signed, int *variant, int *engine);
-int signed_N(int variant, int b, int e);
+// g's coefficient bits of a batch problem, and the equal size the dispatch
+// sees for it (ceil((bf + bg) / 2): the exponents N depend on bf + bg only)
+inline int problem_bits_g(const ks_problem &q) {
+  return q.coeff_bits_g != 0 ? q.coeff_bits_g : q.coeff_bits;
+}
+inline int problem_bits(const ks_problem &q) { return (q.coeff_bits + problem_bits_g(q) + 1) / 2; }
+int signed_N_sum(int variant, int s, int e);
 
 // ---------------------------------------------------------------- kernels
 struct PackOp {
@@ -79,22 +91,20 @@ struct PackOp {
   int sigma;     // +1: f(X); -1: f(-X) (odd coefficients negated)
   int32_t *out;
   int64_t ndig;
+  int b = 0;       // coefficient bits of this operand
+  int il = 0;      // 64-bit limbs per coefficient
   int narrow = 0;  // every bit position of this evaluation is below 2^31
 };
 
 struct PackArgs {
   PackOp op[kMaxOperands];
   int nops;
-  int N, b, d, in_limbs, flip;
+  int N, b, d, in_limbs, flip;  // b, in_limbs: the largest over the operands
   uint64_t ninv = 0;  // floor(2^64 / N) + 1: floor(x / N) = umulhi(x, ninv), x < 2^31
   int fields = 0;     // > 0: coefficient fields per CTA of the field-centric path (N >= b)
 };
 // Fills ninv and the per-operand narrow flags (after the operands are set).
 void pack_finish(PackArgs &a);
-
-// Coefficients of il limbs re-encoded with ol >= il limbs (sign- or zero-extended).
-cudaError_t launch_widen(uint64_t *out, const uint64_t *in, int64_t len, int il, int ol,
-                         int is_signed, cudaStream_t s);
 
 struct Product;
 // Squaring: keeps only the f-side operand of each sub-product (2 q) and makes
@@ -180,6 +190,9 @@ cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64
                             cudaStream_t s);
 
 // NTT engine: column sums of each product by a two-prime transform + CRT.
+// Loads the transform's twiddle tables on the current device (once; 0 on
+// success).  Every entry point calls it on its first call per device.
+int ntt_init_tables();
 size_t ntt_workspace_bytes(int log_n, int nprod);
 cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d,
                                 void *scratch, cudaStream_t s);

@@ -338,13 +338,21 @@ uint32_t inv_mod_2_32(uint32_t p) {  // Newton iteration for p^-1 mod 2^32 (p od
 PrimeC prime_c(int r) { return PrimeC{kP[r], inv_mod_2_32(kP[r])}; }
 uint32_t to_mont(uint64_t x, uint32_t p) { return (uint32_t)(((unsigned __int128)x << 32) % p); }
 
-int init_tables() {
+// The twiddle tables of the current device, loaded once per device by
+// blocking copies.  Those copies cannot run inside a stream capture: a first
+// use on a capturing stream returns -2 and leaves the capture intact (every
+// entry point loads the tables on its first call per device, so a call made
+// before the capture is enough).
+int init_tables(cudaStream_t s) {
   static std::mutex mu;
   static bool done[64] = {false};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s != nullptr && cudaStreamIsCapturing(s, &cs) != cudaSuccess) return -1;
+  if (cs != cudaStreamCaptureStatusNone) return -2;
   static uint32_t host[2][2][kT1 + kT2];
   static bool host_ready = false;
   if (!host_ready) {
@@ -411,6 +419,8 @@ int plan_passes(int L, int *s0, int *kk) {
 }
 }  // namespace
 
+int ntt_init_tables() { return init_tables(nullptr); }
+
 size_t ntt_workspace_bytes(int log_n, int nprod) {
   return ((size_t)4 * nprod << log_n) * sizeof(uint32_t);
 }
@@ -420,7 +430,9 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   (void)d;
   if (log_n > kMaxLog || nprod < 1 || nprod > 4) return cudaErrorInvalidValue;
   if (log_n < 1) log_n = 1;
-  if (init_tables() != 0) return cudaErrorInitializationError;
+  const int tr = init_tables(s);
+  if (tr == -2) return cudaErrorStreamCaptureUnsupported;
+  if (tr != 0) return cudaErrorInitializationError;
   const int64_t n = (int64_t)1 << log_n;
   uint32_t *data = static_cast<uint32_t *>(scratch);
   const PrimeC pc0 = prime_c(0), pc1 = prime_c(1);

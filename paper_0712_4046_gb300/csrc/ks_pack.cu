@@ -78,11 +78,11 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
     // every field that meets digit D0: the earlier ones only with their tails
     // (more than one when N < 16)
     int64_t src0;
-    const int64_t e0 = 16 * D0 - a.b;
+    const int64_t e0 = 16 * D0 - op.b;
     const int64_t t_lo = e0 < 0 ? 0 : e0 / N + 1;
-    const bool staged = stage_coeffs(op, t_lo, c1 - 1, a.in_limbs, cf, kStageWords, src0);
+    const bool staged = stage_coeffs(op, t_lo, c1 - 1, op.il, cf, kStageWords, src0);
     __syncthreads();
-    const int b = a.b, il = a.in_limbs, flip = a.flip;
+    const int b = op.b, il = op.il, flip = a.flip;
     const int64_t t = t_lo + tid;  // this thread's field
     if (t < c1) {
       const int64_t pos = t * N;
@@ -120,16 +120,16 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
   const int64_t jc = local * kCtaDigits;
   // the coefficients this CTA's digits read, staged once (coalesced)
   int64_t t_lo, t_hi, src0;
-  field_range<16>(op, jc, jc + kCtaDigits - 1, a.N, a.ninv, a.b, t_lo, t_hi);
-  const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kStageWords, src0);
+  field_range<16>(op, jc, jc + kCtaDigits - 1, a.N, a.ninv, op.b, t_lo, t_hi);
+  const bool staged = stage_coeffs(op, t_lo, t_hi, op.il, cf, kStageWords, src0);
   __syncthreads();
   int32_t v[kRun];
   // two call sites, so that the staged one reads shared memory as such
   if (staged)
-    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v,
+    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, op.b, op.il, a.flip, v,
                         cf, src0);
   else
-    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
+    digit_run<16, kRun>(op, jc + (int64_t)kRun * tid, a.N, a.ninv, op.b, op.il, a.flip, v);
 #pragma unroll
   for (int m = 0; m < kRun; m++) st[pad8(kRun * tid + m)] = v[m];
   __syncthreads();
@@ -137,35 +137,6 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(Src src) {
     const int64_t j = jc + i;
     if (j < op.ndig) op.out[j] = st[pad8(i)];
   }
-}
-
-// out (len x ol limbs) = in (len x il limbs, il <= ol), each coefficient
-// extended with its sign (signed) or with zeros: the same integers, wider.
-__global__ void __launch_bounds__(256) widen_kernel(uint64_t *out, const uint64_t *in, int64_t len,
-                                                    int il, int ol, int is_signed) {
-  pdl_enter();
-  const int64_t total = len * ol;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / ol;
-    const int l = (int)(idx - i * ol);
-    uint64_t v;
-    if (l < il)
-      v = in[i * il + l];
-    else
-      v = (is_signed && (in[i * il + il - 1] >> 63)) ? ~0ull : 0ull;
-    out[idx] = v;
-  }
-}
-
-cudaError_t launch_widen(uint64_t *out, const uint64_t *in, int64_t len, int il, int ol,
-                         int is_signed, cudaStream_t s) {
-  int64_t blocks = (len * ol + 255) / 256;
-  if (blocks < 1) blocks = 1;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  (void)launch_k(widen_kernel, dim3((unsigned)blocks), dim3(256), 0, s, out, in, len, il, ol, is_signed);
-  note_launches(1);
-  return cudaGetLastError();
 }
 
 void squaring_pack(PackArgs &a, Product *prods, int nprod) {

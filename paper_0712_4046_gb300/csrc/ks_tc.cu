@@ -261,15 +261,15 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     // digits x0 - 1 + i, i < kPackSeg + 8: runs of eight per thread (digits
     // at negative positions come out as zero)
     int64_t t_lo, t_hi, src0;
-    field_range<8>(op, x0 - 1, x0 + kPackSeg + 6, a.N, a.ninv, a.b, t_lo, t_hi);
-    const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
+    field_range<8>(op, x0 - 1, x0 + kPackSeg + 6, a.N, a.ninv, op.b, t_lo, t_hi);
+    const bool staged = stage_coeffs(op, t_lo, t_hi, op.il, cf, kPackStageWords, src0);
     __syncthreads();
     for (int i0 = 8 * tid; i0 < kPackSeg + 8; i0 += 8 * 256) {
       int32_t v[8];
       if (staged)
-        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, op.b, op.il, a.flip, v, cf, src0);
       else
-        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
+        digit_run<8, 8>(op, x0 - 1 + i0, a.N, a.ninv, op.b, op.il, a.flip, v);
 #pragma unroll
       for (int m = 0; m < 8; m++) raw[i0 + m] = v[m];
     }
@@ -297,17 +297,17 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(Src src) {
     // reversed digits j = top - (128 rho0 + m), m <= kPackSeg: runs of eight
     // consecutive j per thread, zero outside [0, top]
     int64_t t_lo, t_hi, src0;
-    field_range<8>(op, top - 128 * rho0 - kPackSeg - 7, top - 128 * rho0, a.N, a.ninv, a.b, t_lo,
+    field_range<8>(op, top - 128 * rho0 - kPackSeg - 7, top - 128 * rho0, a.N, a.ninv, op.b, t_lo,
                    t_hi);
-    const bool staged = stage_coeffs(op, t_lo, t_hi, a.in_limbs, cf, kPackStageWords, src0);
+    const bool staged = stage_coeffs(op, t_lo, t_hi, op.il, cf, kPackStageWords, src0);
     __syncthreads();
     for (int m0 = 8 * tid; m0 < kPackSeg + 1; m0 += 8 * 256) {
       const int64_t jhi = top - (128 * rho0 + m0);  // j of m0; j of m0 + 7 is jhi - 7
       int32_t v[8];
       if (staged)
-        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v, cf, src0);
+        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, op.b, op.il, a.flip, v, cf, src0);
       else
-        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, a.b, a.in_limbs, a.flip, v);
+        digit_run<8, 8>(op, jhi - 7, a.N, a.ninv, op.b, op.il, a.flip, v);
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const int64_t j = jhi - u;

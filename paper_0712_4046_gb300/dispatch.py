@@ -46,11 +46,12 @@ def features(lf, lg, b, signed, batch):
 
 
 def default_grid():
-    """Config-3 sweep (equal lengths x bits, unsigned and signed), uneven
-    lengths, and batch sizes for the batched executor."""
+    """Config-3 sweep (equal lengths x bits, unsigned and signed; b = 4 is the
+    small-modulus regime of Sec. 4, where packing dominates), uneven lengths,
+    and batch sizes for the batched executor."""
     shapes = []
     for L in (16, 64, 256, 1024, 4096, 16384, 65536, 262144):
-        for b in (8, 64, 256, 1024):
+        for b in (4, 8, 64, 256, 1024):
             for s in (0, 1):
                 if L >= 65536 and b >= 256 and s:
                     continue

@@ -60,6 +60,35 @@ def test_eval_bits_follow_the_paper(ks):
     assert ks.eval_bits(5, 1000, 10, 1) == 2 * 10 + 3
 
 
+def test_unequal_sizes_plan_with_bf_plus_bg(ks):
+    # Sec. 3.1-3.4 with bf + bg in place of 2b: the plan's N is the step model's
+    # (pinned there against the plain product and its tightness), and it is below
+    # the equal-size N at max(bf, bg) whenever the sizes differ
+    from oracle import ks_steps as S
+    shapes = [(300, 200, 48, 16), (100, 150, 130, 20), (1, 700, 5, 200), (500, 1, 3, 1),
+              (16384, 16384, 4, 60), (1024, 4096, 1, 64), (2000, 3000, 4, 4), (64, 64, 64, 65)]
+    for lf, lg, bf, bg in shapes:
+        e = S.ceil_log(min(lf, lg), 2)
+        for sg in (False, True):
+            for v in (1, 2, 3, 4):
+                info = ks.plan_info(lf, lg, bf, sg, v, ks.ENGINE_NTT, bits_g=bg)
+                want = S.signed_N(v, bf, bg, e) if sg else S.variant_N_bits(v, bf, bg, e)
+                assert info["N"] == want, (lf, lg, bf, bg, sg, v)
+                ol = (bf + bg + e + int(sg) + 63) // 64
+                assert info["out_limbs"] == ks.out_limbs_bits(lf, lg, bf, bg, sg) == ol
+                assert info["in_limbs"] == (max(bf, bg) + 63) // 64
+                if bf != bg and v == 1:
+                    eq = ks.plan_info(lf, lg, max(bf, bg), sg, v, ks.ENGINE_NTT)
+                    assert info["N"] < eq["N"]
+            # equal sizes: the same plan as ks_plan_info
+            assert ks.plan_info(lf, lg, bf, sg, 4, ks.ENGINE_NTT, bits_g=bf) == \
+                ks.plan_info(lf, lg, bf, sg, 4, ks.ENGINE_NTT)
+    with pytest.raises(ks.KSError):
+        ks.out_limbs_bits(5, 5, 8, 0, False)
+    with pytest.raises(ks.KSError):
+        ks.plan_info(5, 5, 8, False, 1, ks.ENGINE_NTT, bits_g=2049)
+
+
 def test_out_limbs_and_errors(ks):
     assert ks.out_limbs(1024, 1024, 64, False) == 3     # 138 bits
     assert ks.out_limbs(16384, 16384, 48, True) == 2    # 111 bits
