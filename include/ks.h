@@ -313,7 +313,10 @@ void ks_plan_destroy(ks_plan *plan);
  * The cost model is an MLP 5 -> 32 -> 32 -> 12 (ReLU) whose output
  * 3 (variant - 1) + e (e = 0 schoolbook, 1 NTT, 2 tensor cores) predicts
  * log2 of the time per product in microseconds from the features
- * (log2 len_f / 20, log2 len_g / 20, log2 bits / 11, signed, log2 batch / 12).
+ * (log2 len_f / 20, log2 len_g / 20, log2 bits / 11, signed, min(log2 W, 26) / 26),
+ * W the operand bits of the whole batch, sum of (len_f + len_g) bits over its
+ * products (a batch beyond 2^26 bits fills the GPU, and a product's cost is
+ * then its share of the work rather than its latency).
  * Parameters: KS_MLP_PARAMS floats, W1 [32x5], b1, W2 [32x32], b2, W3 [12x32],
  * b3.  ks_mlp_train: full-batch Adam on the GPU (the library's forward,
  * backward and update kernels), masked mean squared error; params updated in

@@ -311,7 +311,7 @@ int choose_mode(int64_t lf, int64_t lg, int b, int is_signed, int mode, int *var
 
 bool mlp_installed();
 int mlp_predict_host(const float *x, int64_t n, float *y);
-void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, int64_t batch, float *x);
+void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, double batch_bits, float *x);
 
 // Learned dispatch for a batch: one GPU inference over every product whose
 // variant and engine are both left to the library; the cheapest feasible
@@ -319,9 +319,12 @@ void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, int64_t batch, f
 bool mlp_choose_batch(const ks_problem *probs, int64_t n, int *variants, int *engines) {
   if (!mlp_installed()) return false;
   std::vector<float> x(n * KS_MLP_IN), y(n * KS_MLP_OUT);
+  double batch_bits = 0.0;  // operand bits of the whole batch
   for (int64_t i = 0; i < n; i++)
-    mlp_features(probs[i].len_f, probs[i].len_g, problem_bits(probs[i]), probs[i].is_signed, n,
-                 &x[i * KS_MLP_IN]);
+    batch_bits += (double)(probs[i].len_f + probs[i].len_g) * problem_bits(probs[i]);
+  for (int64_t i = 0; i < n; i++)
+    mlp_features(probs[i].len_f, probs[i].len_g, problem_bits(probs[i]), probs[i].is_signed,
+                 batch_bits, &x[i * KS_MLP_IN]);
   if (mlp_predict_host(x.data(), n, y.data()) != KS_OK) return false;
   static const int kEng[3] = {KS_ENGINE_SCHOOLBOOK, KS_ENGINE_NTT, KS_ENGINE_TC};
   for (int64_t i = 0; i < n; i++) {

@@ -73,10 +73,14 @@ struct List {
   }
 };
 
-struct NttJob {
-  Product prods[4];
-  int nprod, log_n, d;
-  char *scratch;
+// Transform sub-products of one length (and all squarings or none): one
+// launch sequence for all of them, their arrays side by side in one scratch.
+struct NttGroup {
+  int log_n = 0, square = 0;
+  std::vector<Product> prods;
+  int64_t max_ncols = 0;
+  int64_t first = 0;       // index of the first descriptor in the plan's list
+  char *scratch = nullptr;
 };
 }  // namespace
 
@@ -104,7 +108,10 @@ struct ks_plan {
   int seed_smem[ks::kSeedKinds] = {0};            // per kind: the largest CTA's shared memory
   ks::List<ks::RecoverArgs> recover[ks::kRecoverClasses];
   int recover_smem[ks::kRecoverClasses] = {0};  // per class: the largest staged-digit buffer
-  std::vector<ks::NttJob> ntt;
+  std::vector<ks::NttGroup> ntt;
+  ks::List<ks::Product> nttd;  // the groups' descriptors, side by side
+  char *ntt_scratch = nullptr;
+  size_t ntt_bytes = 0;
   int64_t tc_work = 0;
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
@@ -157,7 +164,9 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
     KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
                                    P->school.blocks(), s));
   if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, s));
-  for (auto &j : P->ntt) KS_TRY(launch_ntt_products(j.prods, j.nprod, j.log_n, j.d, j.scratch, s));
+  for (auto &g : P->ntt)
+    KS_TRY(launch_ntt_batch(P->nttd.d + g.first, (int)g.prods.size(), g.max_ncols, g.square,
+                            g.log_n, g.scratch, s));
   if (fork) {
     KS_TRY(cudaEventRecord(P->ev_fork, s));
     KS_TRY(cudaStreamWaitEvent(side, P->ev_fork, 0));
@@ -231,13 +240,23 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
       P->school.add(sa, sa.block_prefix[p.nprod]);
       P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
     } else {
-      NttJob j{};
-      for (int k = 0; k < p.nprod; k++) j.prods[k] = prods[k];
-      j.nprod = p.nprod;
-      j.log_n = p.ntt_log;
-      j.d = p.d;
-      j.scratch = ws + p.off_ntt;
-      P->ntt.push_back(j);
+      // into the last group of this length and kind that has room
+      const int square = (prods[0].A == prods[0].B) ? 1 : 0;
+      NttGroup *g = nullptr;
+      for (auto it = P->ntt.rbegin(); it != P->ntt.rend(); ++it)
+        if (it->log_n == p.ntt_log && it->square == square &&
+            (int64_t)it->prods.size() + p.nprod <= kMaxNttBatch) {
+          g = &*it;
+          break;
+        }
+      if (g == nullptr) {
+        P->ntt.emplace_back();
+        g = &P->ntt.back();
+        g->log_n = p.ntt_log;
+        g->square = square;
+      }
+      for (int k = 0; k < p.nprod; k++) g->prods.push_back(prods[k]);
+      if (p.ncols > g->max_ncols) g->max_ncols = p.ncols;
     }
   }
   NormJob jobs[4];
@@ -331,7 +350,9 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
       return rc;
     }
     offs[i] = total;
-    total += align256(P->plans[i].total);
+    // a transform product's scratch lives with its group's (below)
+    const Plan &pi = P->plans[i];
+    total += align256(pi.engine == KS_ENGINE_NTT ? pi.off_ntt : pi.total);
   }
   if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -370,6 +391,25 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     }
   }
   P->tc_work = P->tc.blocks();
+  // the transform groups: one scratch allocation, descriptors in the list
+  size_t &ntt_bytes = P->ntt_bytes;
+  for (auto &g : P->ntt) {
+    g.first = P->nttd.n();
+    for (const Product &x : g.prods) P->nttd.add(x, 0);
+    ntt_bytes += align256(ntt_workspace_bytes(g.log_n, (int)g.prods.size()));
+  }
+  if (ntt_bytes > 0) {
+    if (alloc_device(reinterpret_cast<void **>(&P->ntt_scratch), ntt_bytes) != cudaSuccess) {
+      P->ntt_scratch = nullptr;
+      ks_plan_destroy(P);
+      return KS_ENOMEM;
+    }
+    char *at = P->ntt_scratch;
+    for (auto &g : P->ntt) {
+      g.scratch = at;
+      at += align256(ntt_workspace_bytes(g.log_n, (int)g.prods.size()));
+    }
+  }
   // descriptor arrays: one device allocation, filled from a pinned host copy
   size_t db = P->zero.bytes() + P->pack.bytes() + P->tcpack.bytes() + P->school.bytes() +
               P->tc.bytes() + P->norm[0].bytes() + P->norm[1].bytes() + P->normc[0].bytes() +
@@ -377,6 +417,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
               0;
   for (int i = 0; i < kSeedKinds; i++) db += P->seeds[i].bytes();
   db += P->planes.bytes();
+  db += P->nttd.bytes();
   for (int c = 0; c < kRecoverClasses; c++) db += P->recover[c].bytes();
   P->desc_bytes = db;
   if (alloc_device(reinterpret_cast<void **>(&P->desc), db) != cudaSuccess ||
@@ -398,6 +439,7 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
   P->unpack.place(h, d);
   for (int i = 0; i < kSeedKinds; i++) P->seeds[i].place(h, d);
   P->planes.place(h, d);
+  P->nttd.place(h, d);
   for (int c = 0; c < kRecoverClasses; c++) P->recover[c].place(h, d);
   if (cudaMemcpy(P->desc, P->hdesc, db, cudaMemcpyHostToDevice) != cudaSuccess) {
     ks_plan_destroy(P);
@@ -479,7 +521,7 @@ int ks_plan_status(ks_plan *P) {
 long long ks_plan_launches(const ks_plan *P) { return P ? P->launches : -1; }
 
 int64_t ks_plan_workspace_bytes(const ks_plan *P) {
-  return P ? (int64_t)(P->ws_bytes + P->desc_bytes) : -1;
+  return P ? (int64_t)(P->ws_bytes + P->ntt_bytes + P->desc_bytes) : -1;
 }
 
 int ks_plan_choice(const ks_plan *P, int64_t i, int *variant, int *engine) {
@@ -497,6 +539,7 @@ void ks_plan_destroy(ks_plan *P) {
   cudaDeviceSynchronize();
   if (P->graph) cudaGraphExecDestroy(P->graph);
   if (P->ws) cudaFree(P->ws);
+  if (P->ntt_scratch) cudaFree(P->ntt_scratch);
   if (P->desc) cudaFree(P->desc);
   if (P->hdesc) cudaFreeHost(P->hdesc);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);

@@ -196,6 +196,12 @@ int ntt_init_tables();
 size_t ntt_workspace_bytes(int log_n, int nprod);
 cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d,
                                 void *scratch, cudaStream_t s);
+// Sub-products of one transform length 2^log_n from a DEVICE array of
+// descriptors (all squarings or none; at most kMaxNttBatch), their transform
+// arrays at scratch (ntt_workspace_bytes(log_n, nprod)): one launch sequence.
+constexpr int kMaxNttBatch = 4096;
+cudaError_t launch_ntt_batch(const Product *dprods, int nprod, int64_t max_ncols, int square,
+                             int log_n, void *scratch, cudaStream_t s);
 
 struct NormJob {
   const int64_t *c1;

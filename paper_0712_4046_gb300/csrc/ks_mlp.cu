@@ -24,6 +24,7 @@ namespace ks {
 namespace {
 constexpr int IN = KS_MLP_IN, H = KS_MLP_HIDDEN, OUT = KS_MLP_OUT;
 constexpr int64_t NPARAM = (int64_t)H * IN + H + H * H + H + (int64_t)OUT * H + OUT;
+constexpr double kBatchBitsSat = 26.0;  // log2 of the operand bits that fill the GPU
 struct Layout {
   int64_t w1 = 0, b1 = w1 + H * IN, w2 = b1 + H, b2 = w2 + H * H, w3 = b2 + H,
           b3 = w3 + OUT * H;
@@ -184,12 +185,17 @@ struct TableEntry {
 std::vector<TableEntry> g_table;
 }  // namespace
 
-void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, int64_t batch, float *x) {
+// Features of one product: its lengths and size, its sign, and the operand
+// bits of the whole batch it runs in (sum of (Lf + Lg) b over the batch),
+// log-scaled and saturating at 2^26: beyond that the batch fills the GPU and
+// a product's cost is its share of the work, not its latency.
+void mlp_features(int64_t lf, int64_t lg, int b, int is_signed, double batch_bits, float *x) {
   x[0] = (float)(log2((double)lf) / 20.0);
   x[1] = (float)(log2((double)lg) / 20.0);
   x[2] = (float)(log2((double)b) / 11.0);
   x[3] = is_signed ? 1.f : 0.f;
-  x[4] = (float)(log2((double)(batch < 1 ? 1 : batch)) / 12.0);
+  const double w = log2(batch_bits < 1.0 ? 1.0 : batch_bits);
+  x[4] = (float)((w < kBatchBitsSat ? w : kBatchBitsSat) / kBatchBitsSat);
 }
 
 bool mlp_installed() {

@@ -241,10 +241,22 @@ __global__ void __launch_bounds__(kPassThreads) ntt_pass(NttArgs g) {
   }
 }
 
+// The sub-products of one launch: up to four in the kernel's parameters (a
+// direct call), or a device array of any number (a plan's batch of equal
+// transform lengths).
+using NttProd = Product;
+struct InlineProds {
+  NttProd p[4];
+  __device__ __forceinline__ const NttProd &get(int q) const { return p[q]; }
+};
+struct DeviceProds {
+  const NttProd *p;
+  __device__ __forceinline__ const NttProd &get(int q) const { return p[q]; }
+};
+
+template <class Prods>
 struct LoadArgs {
-  const int32_t *A[4];
-  const int32_t *B[4];
-  int64_t nA, nB;
+  Prods prods;
   uint32_t *data;
   int L;
   int nprod;
@@ -252,7 +264,8 @@ struct LoadArgs {
   PrimeC pc[2];
 };
 
-__global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs g) {
+template <class Prods>
+__global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs<Prods> g) {
   pdl_enter();
   const int64_t n = (int64_t)1 << g.L;
   const int64_t total = n * 4 * g.nprod;
@@ -263,11 +276,12 @@ __global__ void __launch_bounds__(256) ntt_load(const __grid_constant__ LoadArgs
     const int q = a >> 2, r = (a >> 1) & 1, side = a & 1;
     if (g.square && side == 1) continue;
     const uint32_t p = g.pc[r].p;
+    const NttProd &pq = g.prods.get(q);
     int32_t d = 0;
     if (side == 0) {
-      if (i < g.nA) d = g.A[q][i];
+      if (i < pq.nA) d = pq.A[i];
     } else {
-      if (i < g.nB) d = g.B[q][i];
+      if (i < pq.nB) d = pq.B[i];
     }
     g.data[idx] = d >= 0 ? (uint32_t)d : (uint32_t)((int64_t)d + p);
   }
@@ -289,23 +303,27 @@ __global__ void __launch_bounds__(256) ntt_pointwise(uint32_t *data, int L, int 
   }
 }
 
+template <class Prods>
 struct CrtArgs {
+  Prods prods;
   const uint32_t *data;
   int L;
   int nprod;
-  int64_t *C[4];
-  int64_t ncols;
   PrimeC pc[2];
   uint32_t K[2];      // n^-1 R^2 mod p (Montgomery scale after the inverse transform)
   uint32_t M;         // p1^-1 R mod p2
 };
 
-__global__ void __launch_bounds__(256) ntt_crt(const __grid_constant__ CrtArgs g) {
+template <class Prods>
+__global__ void __launch_bounds__(256) ntt_crt(const __grid_constant__ CrtArgs<Prods> g) {
   pdl_enter();
   const int64_t n = (int64_t)1 << g.L;
   const uint64_t P = (uint64_t)g.pc[0].p * g.pc[1].p;
   const int q = blockIdx.y;  // product
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.ncols;
+  const NttProd &pq = g.prods.get(q);
+  const int64_t ncols = pq.nA + pq.nB - 1;
+  int64_t *C = pq.C;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ncols;
        k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t z1 = g.data[(int64_t)(4 * q + 0) * n + k];
     const uint32_t z2 = g.data[(int64_t)(4 * q + 2) * n + k];
@@ -315,7 +333,7 @@ __global__ void __launch_bounds__(256) ntt_crt(const __grid_constant__ CrtArgs g
     const uint32_t t = mont_mul(d, g.M, g.pc[1].p, g.pc[1].pinv);
     const uint64_t x = (uint64_t)c1 + (uint64_t)g.pc[0].p * t;  // in [0, P)
     const int64_t v = x > P / 2 ? (int64_t)(x - P) : (int64_t)x;
-    g.C[q][k] = v;
+    C[k] = v;
   }
 }
 
@@ -425,11 +443,12 @@ size_t ntt_workspace_bytes(int log_n, int nprod) {
   return ((size_t)4 * nprod << log_n) * sizeof(uint32_t);
 }
 
-cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d, void *scratch,
-                                cudaStream_t s) {
-  (void)d;
-  if (log_n > kMaxLog || nprod < 1 || nprod > 4) return cudaErrorInvalidValue;
-  if (log_n < 1) log_n = 1;
+namespace {
+// The transform products of one launch sequence: nprod sub-products of one
+// transform length 2^log_n (all squarings or none), their arrays at scratch.
+template <class Prods>
+cudaError_t launch_ntt_core(const Prods &prods, int nprod, int64_t max_ncols, int square,
+                            int log_n, void *scratch, cudaStream_t s) {
   const int tr = init_tables(s);
   if (tr == -2) return cudaErrorStreamCaptureUnsupported;
   if (tr != 0) return cudaErrorInitializationError;
@@ -437,15 +456,8 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   uint32_t *data = static_cast<uint32_t *>(scratch);
   const PrimeC pc0 = prime_c(0), pc1 = prime_c(1);
 
-  LoadArgs la{};
-  for (int q = 0; q < nprod; q++) {
-    la.A[q] = prods[q].A;
-    la.B[q] = prods[q].B;
-  }
-  la.nA = prods[0].nA;
-  la.nB = prods[0].nB;
-  // squaring: both operands are the same digits
-  const int square = (prods[0].A == prods[0].B && prods[0].nA == prods[0].nB) ? 1 : 0;
+  LoadArgs<Prods> la{};
+  la.prods = prods;
   la.square = square;
   la.data = data;
   la.L = log_n;
@@ -455,7 +467,7 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   int64_t tot = n * 4 * nprod;
   int64_t blocks = (tot + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  (void)launch_k(ntt_load, dim3((unsigned)blocks), dim3(256), 0, s, la);
+  (void)launch_k(ntt_load<Prods>, dim3((unsigned)blocks), dim3(256), 0, s, la);
 
   int s0[8], kk[8];
   const int np = plan_passes(log_n, s0, kk);
@@ -472,12 +484,14 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
     const int64_t F = n >> (s0[i] + kk[i]);
     const int64_t Wc = F < (kTile >> kk[i]) ? F : (kTile >> kk[i]);
     const int64_t ctas = ((int64_t)1 << s0[i]) * (F / Wc);
-    (void)launch_k(ntt_pass<true>, dim3(dim3((unsigned)ctas, (unsigned)((square ? 2 : 4) * nprod))), dim3(kPassThreads), 0, s, g);
+    (void)launch_k(ntt_pass<true>, dim3((unsigned)ctas, (unsigned)((square ? 2 : 4) * nprod)),
+                   dim3(kPassThreads), 0, s, g);
   }
   tot = n * 2 * nprod;
   blocks = (tot + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  (void)launch_k(ntt_pointwise, dim3((unsigned)blocks), dim3(256), 0, s, data, log_n, nprod, pc0, pc1, square);
+  (void)launch_k(ntt_pointwise, dim3((unsigned)blocks), dim3(256), 0, s, data, log_n, nprod, pc0,
+                 pc1, square);
   for (int i = np - 1; i >= 0; i--) {  // inverse: the product arrays (side 0)
     g.s0 = s0[i];
     g.k = kk[i];
@@ -486,14 +500,14 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
     const int64_t F = n >> (s0[i] + kk[i]);
     const int64_t Wc = F < (kTile >> kk[i]) ? F : (kTile >> kk[i]);
     const int64_t ctas = ((int64_t)1 << s0[i]) * (F / Wc);
-    (void)launch_k(ntt_pass<false>, dim3(dim3((unsigned)ctas, (unsigned)(2 * nprod))), dim3(kPassThreads), 0, s, g);
+    (void)launch_k(ntt_pass<false>, dim3((unsigned)ctas, (unsigned)(2 * nprod)),
+                   dim3(kPassThreads), 0, s, g);
   }
-  CrtArgs c{};
+  CrtArgs<Prods> c{};
+  c.prods = prods;
   c.data = data;
   c.L = log_n;
   c.nprod = nprod;
-  for (int q = 0; q < nprod; q++) c.C[q] = prods[q].C;
-  c.ncols = prods[0].nA + prods[0].nB - 1;
   c.pc[0] = pc0;
   c.pc[1] = pc1;
   for (int r = 0; r < 2; r++) {
@@ -505,11 +519,32 @@ cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int 
   }
   const uint64_t p1inv = powmod(kP[0] % kP[1], kP[1] - 2, kP[1]);
   c.M = to_mont(p1inv, kP[1]);
-  blocks = (c.ncols + 255) / 256;
+  blocks = (max_ncols + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  (void)launch_k(ntt_crt, dim3(dim3((unsigned)blocks, (unsigned)nprod)), dim3(256), 0, s, c);
+  if (blocks < 1) blocks = 1;
+  (void)launch_k(ntt_crt<Prods>, dim3((unsigned)blocks, (unsigned)nprod), dim3(256), 0, s, c);
   note_launches(3 + 2 * np);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_ntt_products(const Product *prods, int nprod, int log_n, int d, void *scratch,
+                                cudaStream_t s) {
+  (void)d;
+  if (log_n > kMaxLog || nprod < 1 || nprod > 4) return cudaErrorInvalidValue;
+  if (log_n < 1) log_n = 1;
+  InlineProds ip{};
+  for (int q = 0; q < nprod; q++) ip.p[q] = prods[q];
+  // squaring: both operands are the same digits
+  const int square = (prods[0].A == prods[0].B && prods[0].nA == prods[0].nB) ? 1 : 0;
+  return launch_ntt_core(ip, nprod, prods[0].nA + prods[0].nB - 1, square, log_n, scratch, s);
+}
+
+cudaError_t launch_ntt_batch(const Product *dprods, int nprod, int64_t max_ncols, int square,
+                             int log_n, void *scratch, cudaStream_t s) {
+  if (log_n > kMaxLog || nprod < 1 || nprod > kMaxNttBatch) return cudaErrorInvalidValue;
+  if (log_n < 1) log_n = 1;
+  return launch_ntt_core(DeviceProds{dprods}, nprod, max_ncols, square, log_n, scratch, s);
 }
 
 }  // namespace ks

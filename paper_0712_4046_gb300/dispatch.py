@@ -40,9 +40,25 @@ def output_index(variant: int, engine: int) -> int:
     return 3 * (variant - 1) + ENGINE_INDEX[engine]
 
 
+BATCH_BITS_SAT = 26.0  # log2 of the batch operand bits beyond which the GPU is full
+
+
 def features(lf, lg, b, signed, batch):
+    """The library's features of a product in a batch of `batch` equal ones:
+    lengths, size, sign and the batch's operand bits W = batch (lf + lg) b,
+    log-scaled and saturating at 2^26."""
+    w = math.log2(max(1.0, float(batch) * (lf + lg) * b))
     return [math.log2(lf) / 20.0, math.log2(lg) / 20.0, math.log2(b) / 11.0,
-            1.0 if signed else 0.0, math.log2(max(1, batch)) / 12.0]
+            1.0 if signed else 0.0, min(w, BATCH_BITS_SAT) / BATCH_BITS_SAT]
+
+
+def saturating_batch(lf, lg, b, cap=4096):
+    """The smallest power-of-two batch of equal products whose operand bits reach
+    2^26 (the saturated regime), at most `cap`."""
+    B = 1
+    while B < cap and B * (lf + lg) * b < (1 << int(BATCH_BITS_SAT)):
+        B *= 2
+    return B
 
 
 def default_grid():
@@ -66,6 +82,14 @@ def default_grid():
     for L, b, s in ((64, 16, 0), (256, 48, 1), (1024, 64, 0), (512, 256, 1)):
         for batch in (1024, 4096):
             shapes.append((L, L, b, s, batch))
+    # saturated batches over the uneven-batch range (lengths 8 .. 8192, bits
+    # 4 .. 512): what a product costs inside a batch that fills the GPU
+    pairs = [(L, L) for L in (8, 32, 128, 512, 2048, 8192)]
+    pairs += [(8, 2048), (64, 8192), (512, 32), (2048, 128), (8192, 1024)]
+    for lf, lg in pairs:
+        for b in (4, 16, 64, 256, 512):
+            for s in (0, 1):
+                shapes.append((lf, lg, b, s, saturating_batch(lf, lg, b)))
     return shapes
 
 

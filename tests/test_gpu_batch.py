@@ -115,3 +115,40 @@ def test_plan_dispatch_ks1(ks):
     assert all(plan.choice(i)[0] == 1 for i in range(len(probs)))
     _check(ks, probs, host)
     plan.close()
+
+
+def test_plan_batches_transform_products(ks):
+    # transform-engine products of a few lengths (several per length, squarings among
+    # them, all four variants): one launch sequence per transform length and kind,
+    # not one per product, and every result exact
+    import torch
+    probs, host = [], []
+    for i in range(48):
+        L = [200, 700, 1500, 3000][i % 4]
+        lf, lg, b, sg = L + (i % 7), L - (i % 5), [16, 64, 130][i % 3], bool(i & 1)
+        f, g = random_case(lf, lg, b, sg, 4400 + i)
+        square = i % 8 == 0
+        if square:
+            g, lg = f, lf
+        ol = ks.out_limbs(lf, lg, b, sg)
+        df = to_dev(f)
+        h = torch.full((lf + lg - 1, ol), -1, dtype=torch.int64, device="cuda")
+        probs.append(dict(h=h, f=df, g=df if square else to_dev(g), coeff_bits=b, is_signed=sg,
+                          variant=1 + i % 4, engine=ks.ENGINE_NTT))
+        host.append((f, g))
+    plan = ks.Plan(probs)
+    plan.execute()
+    plan.status()
+    _check(ks, probs, host)
+    few = plan.launches()
+    plan.close()
+    # the same products one per plan launch their transforms separately
+    single = 0
+    for q in probs[:8]:
+        p1 = ks.Plan([q])
+        p1.execute()
+        p1.status()
+        single += p1.launches()
+        p1.close()
+    _check(ks, probs[:8], host[:8])
+    assert few < 0.5 * single * len(probs) / 8, (few, single)

@@ -85,7 +85,8 @@ def test_learned_dispatch_gains_over_the_method_without_it(ks):
     """On timings the library measured (the committed tuning run), a model
     trained by the GPU kernels on 3/4 of the shapes picks, on the held-out
     quarter, configurations closer to the measured best than the library
-    without it: its built-in heuristic, and fixed KS1 with the library's engine."""
+    without it (its built-in heuristic, and fixed KS1 with the library's
+    engine) and than the autotuned table."""
     from paper_0712_4046_gb300 import dispatch
     body = dispatch.load_state()
     assert body is not None, "the committed dispatch state is missing or corrupt"
@@ -99,6 +100,11 @@ def test_learned_dispatch_gains_over_the_method_without_it(ks):
         r_ks1 = dispatch.regret(test_set, dispatch.library_choices(test_set, variant=1))
     finally:
         dispatch.install()
+    # and closer than the exhaustive table built from the same training shapes
+    # (nearest measured shape, one product at a time)
+    table = dispatch.choose_table(dispatch.build_table(train_set))
+    r_table = dispatch.regret(test_set, [table(d) for d in test_set])
     assert r_mlp < r_heuristic, (r_mlp, r_heuristic)
     assert r_mlp < r_ks1, (r_mlp, r_ks1)
+    assert r_mlp <= r_table, (r_mlp, r_table)
     assert r_mlp < 0.25, r_mlp
