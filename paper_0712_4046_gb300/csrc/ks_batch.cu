@@ -113,6 +113,7 @@ struct ks_plan {
   char *ntt_scratch = nullptr;
   size_t ntt_bytes = 0;
   int64_t tc_work = 0;
+  ks::TcSplit tc_split;  // the tensor-core work over the CTAs (made at creation)
   long long launches = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -163,7 +164,8 @@ cudaError_t issue(ks_plan *P, cudaStream_t s) {
   if (P->school.n())
     KS_TRY(launch_schoolbook_batch(P->school.d, P->school.dprefix, P->school.n(),
                                    P->school.blocks(), s));
-  if (P->tc.n()) KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, s));
+  if (P->tc.n())
+    KS_TRY(launch_tc_batch(P->tc.d, P->tc.dprefix, P->tc.n(), P->tc_work, P->tc_split, s));
   for (auto &g : P->ntt)
     KS_TRY(launch_ntt_batch(P->nttd.d + g.first, (int)g.prods.size(), g.max_ncols, g.square,
                             g.log_n, g.scratch, s));
@@ -391,6 +393,9 @@ int ks_plan_create(ks_plan **out, const ks_problem *probs, int64_t n, int dispat
     }
   }
   P->tc_work = P->tc.blocks();
+  if (P->tc.n() > 0)
+    tc_make_split(P->tc.v.data(), P->tc.prefix.data(), P->tc.n(), tc_grid(P->tc_work),
+                  P->tc_split);
   // the transform groups: one scratch allocation, descriptors in the list
   size_t &ntt_bytes = P->ntt_bytes;
   for (auto &g : P->ntt) {

@@ -185,9 +185,29 @@ cudaError_t launch_tc_pack_batch(const TcPackArgs *d, const int64_t *prefix, int
 int64_t tc_work(const TcGeom &g);  // block offsets over the output tiles of one sub-product
 void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int *status,
                   TcArgs &a);
-// the prefix (in chunks) over the descriptors splits evenly over one CTA per SM
-cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t chunks,
-                            cudaStream_t s);
+// The split of the tensor-core work (block offsets of all output tiles, in
+// order) over the persistent CTAs, made on the host: CTA b takes positions
+// [at[b], at[b + 1]), and its first work item lies in tile `tile[b]` of
+// sub-product q[b] of descriptor desc[b].  A share that crosses into another
+// tile pays for a second item (its own drain and reduction), so crossings
+// are charged kTcSwitchCost offsets and the split equalises that cost; a
+// split point that falls inside a charge snaps to the tile's start.  n = 0:
+// the kernel splits the offsets evenly itself.
+constexpr int kTcMaxCtas = 160;
+constexpr int64_t kTcSwitchCost = 8;
+struct TcSplit {
+  int n = 0;
+  int64_t at[kTcMaxCtas + 1];
+  int32_t desc[kTcMaxCtas];
+  int32_t q[kTcMaxCtas];
+  int32_t tile[kTcMaxCtas];  // tiles per sub-product are at most 2^20
+};
+// args: n descriptors (host copies) whose work starts at prefix[i]; grid CTAs
+void tc_make_split(const TcArgs *args, const int64_t *prefix, int n, int grid, TcSplit &sp);
+int tc_grid(int64_t work);  // CTAs of a launch over `work` offsets (one per SM at most)
+// the prefix (in offsets) over the descriptors is split as `split` says
+cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t work,
+                            const TcSplit &split, cudaStream_t s);
 
 // NTT engine: column sums of each product by a two-prime transform + CRT.
 // Loads the transform's twiddle tables on the current device (once; 0 on

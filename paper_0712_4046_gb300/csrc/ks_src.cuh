@@ -27,6 +27,11 @@ struct One {
     idx = 0;
     return d;
   }
+  // the descriptor of a known index (no search)
+  __device__ __forceinline__ const T &at(int, int64_t bid, int64_t &local) const {
+    local = bid;
+    return d;
+  }
 };
 
 template <class T>
@@ -50,6 +55,11 @@ struct Many {
     const T &r = locate(bid, local);
     idx = (int)(&r - d);
     return r;
+  }
+  // the descriptor of a known index (no search)
+  __device__ __forceinline__ const T &at(int idx, int64_t bid, int64_t &local) const {
+    local = bid - prefix[idx];
+    return d[idx];
   }
 };
 

@@ -57,6 +57,7 @@
 #include <cuda_fp16.h>
 
 #include <atomic>
+#include <vector>
 
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
@@ -367,19 +368,24 @@ struct __align__(16) TcSlot {
 };
 constexpr int kItemSlots = 4;
 
-// The CTAs split the offsets of all tiles evenly.  tc_decode gives the item
-// that starts at offset position s: that offset and the ones after it in the
-// same tile, up to position s_end and at most kMaxItemChunks chunks of kKS
-// offsets; `next` is the position after the item.  Requires s < s_end.
+// tc_decode gives the item that starts at offset position s: that offset and
+// the ones after it in the same tile, up to position s_end and at most
+// kMaxItemChunks chunks of kKS offsets; `next` is the position after the item.
+// Requires s < s_end.  hdesc >= 0: the item lies in tile htile of sub-product
+// hq of descriptor hdesc (the host's split says so for a CTA's first item),
+// which saves the searches and their dependent loads.
 template <class Src>
-__device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it, int64_t &next) {
+__device__ void tc_decode(const Src &src, int64_t s, int64_t s_end, TcSlot &it, int64_t &next,
+                          int hdesc = -1, int hq = 0, int64_t htile = 0) {
   int64_t local;
-  const TcArgs &a = src.locate(s, local);
-  int q = 0;
-  while (q + 1 < a.nprod && local >= a.work_prefix[q + 1]) q++;
+  const TcArgs &a = hdesc >= 0 ? src.at(hdesc, s, local) : src.locate(s, local);
+  int q = hq;
+  if (hdesc < 0)
+    while (q + 1 < a.nprod && local >= a.work_prefix[q + 1]) q++;
   const TcProduct &P = a.p[q];
   const int64_t L = local - a.work_prefix[q];
-  int64_t tlo = 0, thi = P.T - 1;  // last tile whose prefix is <= L
+  int64_t tlo = htile, thi = P.T - 1;  // last tile whose prefix is <= L
+  if (hdesc >= 0) thi = tlo;
   while (tlo < thi) {
     const int64_t mid = (tlo + thi + 1) >> 1;
     if (tc_offset_prefix(P.dmax, P.R, mid) <= L)
@@ -429,8 +435,9 @@ __device__ __forceinline__ void slot_load(TcSlot &v, const TcSlot *src) {
 // warp wait, before its first copy, on a barrier that nothing completes, so the
 // kernel's waits run out while no copy or MMA is in flight.
 template <class Src>
-__global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total, uint64_t wait_ns,
-                                                          int stall) {
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(Src src, int64_t total, uint64_t wait_ns, int stall,
+              const __grid_constant__ TcSplit split) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_full[kStages];
   __shared__ __align__(8) uint64_t bar_empty[kStages];
@@ -448,18 +455,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   volatile int *abort_v = &abort_sh;
 
+  // this CTA's share of the offsets: the host's split, else an even one
+  const bool hsplit = split.n == (int)gridDim.x;
+  const int64_t s_beg = hsplit ? split.at[blockIdx.x] : total * blockIdx.x / gridDim.x;
+  const int64_t s_end = hsplit ? split.at[blockIdx.x + 1] : total * (blockIdx.x + 1) / gridDim.x;
+  // the producer decodes its first item (descriptor loads) while the other
+  // warps set up shared and tensor memory
+  TcSlot first_it;
+  int64_t first_next = s_end;
+  if (tid == 0 && s_beg < s_end) {
+    if (hsplit)
+      tc_decode(src, s_beg, s_end, first_it, first_next, split.desc[blockIdx.x],
+                split.q[blockIdx.x], split.tile[blockIdx.x]);
+    else
+      tc_decode(src, s_beg, s_end, first_it, first_next);
+  }
   // the B planes and the zero strip start as zeros: B rows a chunk does not
   // copy stay finite (the clearing MMA multiplies them by zero)
-  for (int st = 0; st < kStages; st++)
-    for (int i = tid; i < kStageB / 16; i += kThreads)
-      reinterpret_cast<uint4 *>(smem + st * kStage + kStageA)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int i = tid; i < kZeroA / 16; i += kThreads)
-    reinterpret_cast<uint4 *>(smem + kStages * kStage)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (warp == 0) {
+  if (warp > 0) {
+    for (int st = 0; st < kStages; st++)
+      for (int i = tid - 32; i < kStageB / 16; i += kThreads - 32)
+        reinterpret_cast<uint4 *>(smem + st * kStage + kStageA)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid - 32; i < kZeroA / 16; i += kThreads - 32)
+      reinterpret_cast<uint4 *>(smem + kStages * kStage)[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 1) {  // allocates (and at the end releases) the tensor memory
     tmem_alloc(&tmem_sh, kTmemCols);
     tmem_relinquish();
   }
-  if (tid == 0) {
+  if (tid == 64) {
     for (int s = 0; s < kStages; s++) {
       mbar_init(&bar_full[s], 1);
       mbar_init(&bar_empty[s], 1);
@@ -484,8 +508,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total,
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // the setup above touched only shared and tensor memory: it overlaps the
-  // previous kernel of the stream
+  // the setup above touched only shared and tensor memory and read the
+  // host-written descriptors: it overlaps the previous kernel of the stream
   pdl_enter();
   const uint32_t tmem = tmem_sh;
 
@@ -495,17 +519,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total,
       int stage = 0, islot = 0;
       uint32_t phase = 0, iphase = 0, armed = 0, armed_par = 0;
       bool aborted = false;
-      // this CTA's even share of the offsets
-      const int64_t s_beg = total * blockIdx.x / gridDim.x;
-      const int64_t s_end = total * (blockIdx.x + 1) / gridDim.x;
       for (int64_t s = s_beg;;) {
         TcSlot it;
         int64_t next = s_end;
         const bool have = s < s_end;
-        if (have)
+        if (have && s == s_beg) {
+          it = first_it;
+          next = first_next;
+        } else if (have) {
           tc_decode(src, s, s_end, it, next);
-        else
+        } else {
           it.done = 1;
+        }
         if (!mbar_wait(&bar_iempty[islot], iphase ^ 1, wait_ns) || *abort_v) {
           aborted = true;
           break;
@@ -751,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(Src src, int64_t total,
     if (*abort_v) atomicCAS(status_sh, 0, 1);
     if (bad_range_sh) atomicCAS(status_sh, 0, 3);
   }
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ host
@@ -840,6 +865,67 @@ static cudaError_t tc_attr(int *sms) {
 
 int64_t tc_work(const TcGeom &g) { return tc_offset_prefix(g.dmax, g.R, g.T); }
 
+int tc_grid(int64_t work) {
+  int sms = 0;
+  if (tc_attr(&sms) != cudaSuccess) return 0;
+  return (int)(work < sms ? work : sms);
+}
+
+// Virtual positions: tile j (in order over all descriptors and sub-products)
+// covers [b_j + c j, b_(j+1) + c j) with c = kTcSwitchCost, and the charge
+// [b_j + c (j - 1), b_j + c j) before it maps to its start b_j.  Equal shares
+// of the virtual length charge every share that runs into a next tile.
+void tc_make_split(const TcArgs *args, const int64_t *prefix, int n, int grid, TcSplit &sp) {
+  sp.n = 0;
+  if (grid < 1 || grid > kTcMaxCtas || n < 1) return;
+  struct Tile {
+    int64_t b;
+    int32_t desc, q, t;
+  };
+  std::vector<Tile> tiles;
+  for (int i = 0; i < n; i++)
+    for (int q = 0; q < args[i].nprod; q++) {
+      const TcProduct &P = args[i].p[q];
+      if ((int64_t)tiles.size() + P.T > (1 << 22)) return;  // too many to walk: even split
+      for (int64_t t = 0; t < P.T; t++) {
+        const int64_t b = prefix[i] + args[i].work_prefix[q] + tc_offset_prefix(P.dmax, P.R, t);
+        if (b < prefix[i] + args[i].work_prefix[q + 1]) tiles.push_back(Tile{b, i, q, (int32_t)t});
+      }
+    }
+  const int64_t total = prefix[n];
+  if (tiles.empty() || total <= 0) return;
+  const int64_t nt = (int64_t)tiles.size();
+  const double V = (double)total + (double)kTcSwitchCost * (double)(nt - 1);
+  size_t j = 0;  // tile of the current split point
+  sp.at[0] = 0;
+  for (int k = 1; k < grid; k++) {
+    const double tau = V * k / grid;
+    // the last tile whose virtual start is <= tau
+    while (j + 1 < tiles.size() &&
+           (double)tiles[j + 1].b + (double)kTcSwitchCost * (double)(j + 1) <= tau)
+      j++;
+    int64_t x;
+    if (j + 1 < tiles.size() && tau >= (double)tiles[j + 1].b + (double)kTcSwitchCost * (double)j)
+      x = tiles[j + 1].b;  // inside the charge before tile j + 1: snap to its start
+    else
+      x = (int64_t)(tau - (double)kTcSwitchCost * (double)j);
+    if (x < sp.at[k - 1]) x = sp.at[k - 1];
+    if (x > total) x = total;
+    sp.at[k] = x;
+  }
+  sp.at[grid] = total;
+  // each share's first tile
+  size_t u = 0;
+  for (int k = 0; k < grid; k++) {
+    const int64_t s0 = sp.at[k] < total ? sp.at[k] : total - 1;
+    while (u + 1 < tiles.size() && tiles[u + 1].b <= s0) u++;
+    sp.desc[k] = tiles[u].desc;
+    sp.q[k] = tiles[u].q;
+    sp.tile[k] = tiles[u].t;
+  }
+  sp.n = grid;
+}
+
 // the wait bound and the stall hook of the kernel (a test hook; see ks.h)
 static std::atomic<int> g_tc_stall{0};
 static std::atomic<unsigned long long> g_tc_wait_ns{kWaitNs};
@@ -877,22 +963,24 @@ cudaError_t launch_tc_products(const TcGeom &g, int nprod, char *base, int64_t *
   const int64_t work = a.work_prefix[nprod];
   if (work <= 0) return cudaSuccess;
   const int64_t grid = work < sms ? work : sms;
-  (void)launch_k(tc_kernel<One<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s, One<TcArgs>{a}, work,
-                                                                  g_tc_wait_ns.load(),
-                                                                  g_tc_stall.load());
+  const int64_t prefix[2] = {0, work};
+  TcSplit split;
+  tc_make_split(&a, prefix, 1, (int)grid, split);
+  (void)launch_k(tc_kernel<One<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s,
+                 One<TcArgs>{a}, work, g_tc_wait_ns.load(), g_tc_stall.load(), split);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64_t work,
-                            cudaStream_t s) {
+                            const TcSplit &split, cudaStream_t s) {
   if (n == 0 || work == 0) return cudaSuccess;
   int sms = 0;
   cudaError_t e = tc_attr(&sms);
   if (e != cudaSuccess) return e;
   const int64_t grid = work < sms ? work : sms;
-  (void)launch_k(tc_kernel<Many<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s, 
-      Many<TcArgs>{d, prefix, n}, work, g_tc_wait_ns.load(), g_tc_stall.load());
+  (void)launch_k(tc_kernel<Many<TcArgs>>, dim3((unsigned)grid), dim3(kThreads), kSmem, s,
+                 Many<TcArgs>{d, prefix, n}, work, g_tc_wait_ns.load(), g_tc_stall.load(), split);
   note_launches(1);
   return cudaGetLastError();
 }
