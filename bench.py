@@ -51,7 +51,7 @@ L2_FLUSH_BYTES = 256 << 20
 # launch on this workload's KS4 product, from an ncu capture of the current
 # kernel (the tc_kernel summary under profiles/: 5.21 MB read, no DRAM
 # writes); set to None whenever the kernel changes until it is captured again
-TC_KERNEL_DRAM_BYTES = 5.21e6
+TC_KERNEL_DRAM_BYTES = 5.22e6
 TC_KERNEL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
                             "profiles/tc_kernel_zx_product_16384_s48_ks4.md")
 # 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC

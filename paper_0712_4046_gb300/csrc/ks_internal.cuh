@@ -190,11 +190,12 @@ void make_tc_args(const TcGeom &g, int nprod, char *base, int64_t *const *C, int
 // [at[b], at[b + 1]), and its first work item lies in tile `tile[b]` of
 // sub-product q[b] of descriptor desc[b].  A share that crosses into another
 // tile pays for a second item (its own drain and reduction), so crossings
-// are charged kTcSwitchCost offsets and the split equalises that cost; a
-// split point that falls inside a charge snaps to the tile's start.  n = 0:
-// the kernel splits the offsets evenly itself.
+// are charged kTcSwitchCost offsets (measured: a second item costs about as
+// much as two offsets once its descriptor is decoded ahead) and the split
+// equalises that cost; a split point that falls inside a charge snaps to the
+// tile's start.  n = 0: the kernel splits the offsets evenly itself.
 constexpr int kTcMaxCtas = 160;
-constexpr int64_t kTcSwitchCost = 8;
+constexpr int64_t kTcSwitchCost = 2;
 struct TcSplit {
   int n = 0;
   int64_t at[kTcMaxCtas + 1];

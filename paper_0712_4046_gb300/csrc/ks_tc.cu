@@ -622,11 +622,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + stage * kStage), b0 = a0 + kStageA;
         const uint32_t dt = tmem + (uint32_t)(acc * kNT);
-        mma_f16_lane0(dt, zdesc, sdesc(b0, (uint32_t)kPlaneB, 128u),
-                      kIdescM | ((uint32_t)(kNT >> 3) << 17), 0u, lane_u);
         const int64_t d0 = it.dlo + (int64_t)c * kKS;
         // block columns n' of offset delta: [P0 + 128 - delta - R, P0 + 128 - delta) clipped
         const int64_t top = it.P0 + kNT - d0;
+        // when the chunk's first offset covers every block column, its first
+        // MMA overwrites the accumulator; otherwise an MMA of the zero strip
+        // clears it first
+        const bool full0 = top - it.R <= 0 && top >= kNT;
+        if (!full0)
+          mma_f16_lane0(dt, zdesc, sdesc(b0, (uint32_t)kPlaneB, 128u),
+                        kIdescM | ((uint32_t)(kNT >> 3) << 17), 0u, lane_u);
         int jmax = kKS;
         if (d0 + jmax - 1 > it.dhi) jmax = (int)(it.dhi - d0 + 1);
         for (int j = 0; j < jmax; j++) {
@@ -644,7 +649,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < 8; k++)
             mma_f16_lane0(dt + lo16, ad + (uint64_t)(16 * k), bd + (uint64_t)((2 * k * kPlaneB) >> 4),
-                          idesc, 1u, lane_u);
+                          idesc, (j == 0 && k == 0 && full0) ? 0u : 1u, lane_u);
         }
         mma_commit_lane0(&bar_empty[stage], lane_u);
         mma_commit_lane0(&bar_tfull[acc], lane_u);
