@@ -140,7 +140,12 @@ int ks_mul_ex(uint64_t *h, const uint64_t *f, int64_t len_f, const uint64_t *g,
 /*
  * As ks_mul but with HOST buffers: copies f and g to the device, multiplies,
  * copies h back, and returns when h is complete (synchronous).  Device
- * buffers are cached per (device, stream).
+ * buffers are cached per (device, stream).  On a stream other than the legacy
+ * default streams, the product's launches are captured into a CUDA graph on
+ * the first call of a problem (size, variant, engine) and replayed by the
+ * following calls of the same problem on that stream; another problem, a
+ * change of ks_set_pdl or ks_release_cache captures afresh.  Returns the
+ * device status word's error (as ks_status_sync would) with the result.
  */
 int ks_mul_host(uint64_t *h, const uint64_t *f, int64_t len_f,
                 const uint64_t *g, int64_t len_g, int coeff_bits,

@@ -67,6 +67,8 @@ struct Plan {
 };
 
 int ceil_log2(int64_t n);
+// Retires the graphs a host-buffer call captured (a setting they bake in changed).
+void bump_epoch();
 // N of a variant for coefficient sizes adding up to s = bf + bg (2b for equal ones)
 int variant_N_sum(int variant, int s, int e);
 int variant_N(int variant, int b, int e);

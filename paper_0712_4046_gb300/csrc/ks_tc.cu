@@ -995,4 +995,5 @@ cudaError_t launch_tc_batch(const TcArgs *d, const int64_t *prefix, int n, int64
 extern "C" void ks_debug_tc_stall(int on, int64_t wait_ns) {
   ks::g_tc_stall.store(on ? 1 : 0);
   ks::g_tc_wait_ns.store(wait_ns > 0 ? (unsigned long long)wait_ns : ks::kWaitNs);
+  ks::bump_epoch();
 }
