@@ -13,7 +13,7 @@
 // each chunk the accumulator is read out of tensor memory, converted to int32
 // (exact) and added to per-thread integer sums; after a work item the sums of
 // four neighbouring digits are merged into one 32-bit-digit column sum and
-// added to global memory with a bulk reduction.
+// added to global memory with 64-bit reductions.
 //
 // Blocking (a product of digit strings is a Toeplitz matrix-vector product):
 // write output digit k = 128 p + q.  For a block offset delta,
@@ -76,8 +76,7 @@ constexpr int kPlaneB = kBRows * 16;
 constexpr int kStageB = 16 * kPlaneB;
 constexpr int kStage = kStageA + kStageB;
 constexpr int kZeroA = 17 * 128;           // all-zero strip of the clearing MMA
-constexpr int kStaging = 128 * 32 * 8;     // column sums of one output tile (int64)
-constexpr int kSmem = kStages * kStage + kZeroA + kStaging;
+constexpr int kSmem = kStages * kStage + kZeroA;
 constexpr int kPadB = 16;                  // zero rows on each side of the B planes
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -131,14 +130,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
   while (!mbar_try_wait(bar, parity))
     if (globaltimer() - t0 > limit) return false;
   return true;
-}
-// all eight epilogue warps meet (bounded); false on timeout
-__device__ __forceinline__ bool epi_sync(uint64_t *bar, uint32_t &ph, int lane, uint64_t limit) {
-  __syncwarp();
-  if (lane == 0) mbar_arrive(bar);
-  const bool ok = mbar_wait(bar, ph, limit);
-  ph ^= 1;
-  return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile(
@@ -202,21 +193,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // bulk reduction (add, u64) of `bytes` from shared to global memory, bulk async-group
-__device__ __forceinline__ void bulk_reduce_add_u64(void *dst, const void *src, uint32_t bytes) {
-  asm volatile(
-      "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(dst),
-      "r"(smem_u32(src)), "r"(bytes)
-      : "memory");
-}
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
 // shared memory matrix descriptor, no swizzle: start, leading (K) and stride
 // (M/N) byte offsets between 8x16-byte core matrices, version bits 46-48 = 1
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -446,7 +422,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t bar_ifull[kItemSlots];
   __shared__ __align__(8) uint64_t bar_iempty[kItemSlots];
   __shared__ __align__(8) uint64_t bar_drain;
-  __shared__ __align__(8) uint64_t bar_epi;
   __shared__ __align__(8) uint64_t bar_never;  // the stall hook's: nothing arrives on it
   __shared__ TcSlot slots[kItemSlots];
   __shared__ uint32_t tmem_sh;
@@ -497,7 +472,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&bar_iempty[s], 1 + kEpiWarps);
     }
     mbar_init(&bar_drain, 1);
-    mbar_init(&bar_epi, kEpiWarps);
     mbar_init(&bar_never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
@@ -676,10 +650,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: tensor memory -> integer sums -> column atomics
     const int quad = warp & 3, half = (warp - 2) >> 2;
     const int u = lane & 3;
-    const bool epi_leader = warp == 2 && lane == 0;
-    long long *staging = reinterpret_cast<long long *>(smem + kStages * kStage + kZeroA);
     int acc = 0, islot = 0;
-    uint32_t aphase = 0, iphase = 0, ephase = 0;
+    uint32_t aphase = 0, iphase = 0;
     bool aborted = false;
     for (;;) {
       const bool iok = mbar_wait(&bar_ifull[islot], iphase, wait_ns);
@@ -732,17 +704,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       // step 1 (lanes u, u ^ 1) pairs the columns i + (u & 1) and
       // i + 2 + (u & 1), step 2 (lanes u, u ^ 2) completes column i + u.
       // The tile's 4096 column sums (block column p = P0 + row, 32 per row)
-      // are contiguous in C: they are staged in shared memory and added with
-      // one bulk reduction.
-      if (epi_leader) bulk_wait_read_all();  // the previous tile's reduction has read the staging
-      if (!epi_sync(&bar_epi, ephase, lane, wait_ns)) {
-        aborted = true;
-        break;
-      }
+      // are contiguous in C; every thread adds its 16 with reductions that
+      // return nothing (a warp's 32 touch four 64-byte runs), so no warp
+      // waits for another and no staging buffer is needed.
       {
         const bool odd = (u & 1) != 0, up = (u & 2) != 0;
         const long long w_me = 1ll << (8 * u), w_x1 = 1ll << (8 * (u ^ 1));
-        long long *srow = staging + 8 * quad + (lane >> 2);
+        const int64_t k0 = 32 * it.P0;
+        const int64_t n = it.ncols - k0 < 4096 ? it.ncols - k0 : 4096;
+        unsigned long long *cb = reinterpret_cast<unsigned long long *>(it.C + k0);
+        const int col = 8 * quad + (lane >> 2);
 #pragma unroll
         for (int i = 0; i < 64; i += 4) {
           const int32_t m01 = odd ? sum[i + 1] : sum[i];
@@ -752,26 +723,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const long long p01 = (long long)m01 * w_me + (long long)r01 * w_x1;
           const long long p23 = (long long)m23 * w_me + (long long)r23 * w_x1;
           const long long v = (up ? p23 : p01) + __shfl_xor_sync(0xffffffffu, up ? p01 : p23, 2);
-          srow[(kNT - 1 - half * 64 - i - u) * 32] = v;
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (!epi_sync(&bar_epi, ephase, lane, wait_ns)) {
-        aborted = true;
-        break;
-      }
-      if (epi_leader) {
-        const int64_t k0 = 32 * it.P0;
-        int64_t n = it.ncols - k0;
-        if (n > 4096) n = 4096;
-        if (n > 0) {
-          bulk_reduce_add_u64(it.C + k0, staging, (uint32_t)n * 8u);
-          bulk_commit();
+          const int idx = (kNT - 1 - half * 64 - i - u) * 32 + col;
+          if (v != 0 && idx < n) atomicAdd(cb + idx, (unsigned long long)v);
         }
       }
     }
     if (aborted) *abort_v = 1;
-    if (epi_leader) bulk_wait_all();  // every reduction has landed before the CTA exits
   }
 
   tc_fence_before();
