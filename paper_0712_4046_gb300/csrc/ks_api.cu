@@ -226,14 +226,17 @@ int make_plan(Plan &p, int64_t lf, int64_t lg, int b, int is_signed, int variant
                              (((p.nA + 3) & ~(int64_t)3) + ((p.nB + 3) & ~(int64_t)3)) * 4);
   p.off_cols = off;
   off = align256(off + (size_t)p.nprod * p.ncols * 8);
+  // the normalization's tile flags right after the column sums: one range
+  // that the product's first kernel clears
+  p.off_flags = off;
+  p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
+  off = align256(p.off_flags + (size_t)p.flag_bytes);
+  p.zero_words = (int64_t)((p.off_flags + (size_t)p.flag_bytes - p.off_cols + 7) / 8);
   p.off_seedacc = off;  // narrow seeds: six column sums per value
   if (b <= 64 && p.nseeds > 0)
     off = align256(off + (size_t)p.nseeds * 6 * 8);
   p.off_planes = off;   // narrow seeds: the coefficients' balanced 8-bit digit planes
   if (b <= 64 && p.nseeds > 0) off = align256(off + (size_t)seed_planes_bytes(lf, lg, seed_digits(bf, bg, p.is_signed)));
-  p.off_flags = off;
-  p.flag_bytes = norm_flag_bytes(p.nnorm, p.ntiles);
-  off = align256(p.off_flags + (size_t)p.flag_bytes);
   p.off_words = off;
   off = align256(off + (size_t)p.nnorm * p.nwords * 4);
   p.off_seeds = off;
@@ -470,7 +473,8 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
   unsigned long long *seed_acc = reinterpret_cast<unsigned long long *>(ws + p.off_seedacc);
-  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
+  // the column sums accumulate from zero; the tile flags start clear
+  const int64_t nzero = p.zero_words;
 
   const bool recon = p.variant == KS_3 || p.variant == KS_4;
   RecoverRun runs[2];
@@ -543,6 +547,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
       KS_CUDA(cudaMemsetAsync(cols, 0, (size_t)nzero * 8, s));
       KS_CUDA(launch_schoolbook(prods, p.nprod, s));
     } else {
+      KS_CUDA(cudaMemsetAsync(flags, 0, (size_t)p.flag_bytes, s));
       KS_CUDA(launch_ntt_products(prods, p.nprod, p.ntt_log, p.d, ws + p.off_ntt, s));
     }
   }
@@ -567,7 +572,7 @@ static int run_plan(const Plan &p, uint64_t *h, const uint64_t *f, const uint64_
   plan_norm_jobs(p, cols, words, flags, jobs);
   {
     PhaseTimer t(s, PH_NORMALIZE);
-    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, s));
+    KS_CUDA(launch_normalize(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, status, s));
   }
   const uint32_t *V0 = words, *V1 = words + p.nwords;
   const int ol = p.out_limbs;

@@ -201,7 +201,8 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   int64_t *cols = reinterpret_cast<int64_t *>(ws + p.off_cols);
   uint32_t *words = reinterpret_cast<uint32_t *>(ws + p.off_words);
   uint32_t *flags = reinterpret_cast<uint32_t *>(ws + p.off_flags);
-  const int64_t nzero = (int64_t)p.nprod * p.ncols;  // the column sums accumulate from zero
+  // the column sums accumulate from zero; the tile flags start clear
+  const int64_t nzero = p.zero_words;
   uint32_t *seeds = reinterpret_cast<uint32_t *>(ws + p.off_seeds);
   static const int kRev[5][4] = {{0}, {0}, {0, 0}, {0, 1}, {0, 0, 1, 1}};
   static const int kSig[5][4] = {{1}, {1}, {1, -1}, {1, 1}, {1, -1, 1, -1}};
@@ -242,6 +243,9 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
       P->school.add(sa, sa.block_prefix[p.nprod]);
       P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(cols), nzero}, (nzero + 255) / 256);
     } else {
+      // the transform writes every column sum; only the tile flags need clearing
+      P->zero.add(ZeroArgs{reinterpret_cast<uint64_t *>(flags), (p.flag_bytes + 7) / 8},
+                  (p.flag_bytes / 8 + 255) / 256);
       // into the last group of this length and kind that has room
       const int square = (prods[0].A == prods[0].B) ? 1 : 0;
       NttGroup *g = nullptr;
@@ -264,7 +268,8 @@ static int add_product(ks_plan *P, const Plan &p, const ks_problem &q, char *ws,
   NormJob jobs[4];
   plan_norm_jobs(p, cols, words, flags, jobs);
   NormArgs na;
-  if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, na) != 0) return KS_EINVAL;
+  if (make_norm_args(jobs, p.nnorm, p.dn, p.nwords, p.ntiles, status, na) != 0)
+    return KS_EINVAL;
   P->norm[p.dn == 32 ? 1 : 0].add(na, norm_blocks(na));
   P->normc[p.dn == 32 ? 1 : 0].add(na, norm_carry_blocks(na));
   const uint32_t *V0 = words, *V1 = words + p.nwords;

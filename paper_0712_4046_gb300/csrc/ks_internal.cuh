@@ -61,6 +61,7 @@ struct Plan {
   // workspace layout (byte offsets from the base)
   size_t off_digits = 0, off_cols = 0, off_flags = 0, off_words = 0;
   int64_t flag_bytes = 0;  // the normalization's per-tile transfer functions
+  int64_t zero_words = 0;  // 64-bit words cleared before a product: column sums, flags
   size_t off_seeds = 0, off_seedacc = 0, off_planes = 0, off_hp = 0, off_ntt = 0;
   size_t total = 0;
   int64_t ntiles = 0;   // scan tiles per normalized combination
@@ -233,16 +234,19 @@ struct NormJob {
   int64_t n2;
   int sigma;          // value = sum (c1_k + sigma c2_k) 2^(d k) + sum_i 2^(pstart + i pstride)
   uint32_t *out;
-  uint32_t *flags;    // one transfer function per scan tile (written by the tile pass)
+  uint32_t *flags;    // one flag word per scan tile; the jobs' arrays lie back to back
+                      // from job 0's, and a tile counter follows the last (clear
+                      // before the launch)
   // the shift of signed coefficients: one bit per coefficient read from this
   // value (K U(Y) with K = 2^kb); pcount = 0 for none
   int64_t pstart = 0, pstride = 1, pcount = 0;
 };
 
-// Normalizes up to 4 column-sum combinations into two's complement words
-// (two launches: the tiles, then the carries between them).
+// Normalizes up to 4 column-sum combinations into two's complement words:
+// one launch while the tiles fit in about one wave (a tile takes its carry
+// from its predecessors' flags), else a tile pass and a carry pass.
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, cudaStream_t s);
+                             int64_t ntiles, int *status, cudaStream_t s);
 
 struct NormArgs {
   NormJob job[4];
@@ -251,14 +255,16 @@ struct NormArgs {
   int d;
   int64_t nwords;
   int64_t ntiles;
+  int *status;        // a wait that gave up records 1 here
 };
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
-                   NormArgs &a);
+                   int *status, NormArgs &a);
 int64_t norm_blocks(const NormArgs &a);        // CTAs of the tile pass
-int64_t norm_carry_blocks(const NormArgs &a);  // CTAs of the carry pass
-// bytes of a product's flag region (the tiles' transfer functions)
+int64_t norm_carry_blocks(const NormArgs &a);  // CTAs of the carry pass (two-pass form)
+// bytes of a product's flag region (the tiles' flags and the tile counter)
 int64_t norm_flag_bytes(int njobs, int64_t ntiles);
-// the two launches for a whole batch, per digit width d (16 or 32)
+// the launches for a whole batch, per digit width d (16 or 32): one (single
+// pass) or two (tile pass, carry pass), by the number of tile CTAs
 cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *prefix_tiles,
                                    const int64_t *prefix_carry, int n, int64_t tile_blocks,
                                    int64_t carry_blocks, cudaStream_t s);

@@ -18,25 +18,34 @@
 //     carry values.  Functions compose associatively, so the carries are a
 //     parallel prefix: warp shuffles, then the block, then across tiles.
 //
-// Two launches, neither of which waits on another CTA:
+// Tiles.  Every CTA of norm_tiles takes one tile of words (one or both of a +- pair
+// of combinations: same c1, c2, opposite sigma, so those columns are read
+// once).  It stages the columns the tile needs in shared memory (one
+// coalesced read of the column sums; a thread's words are exactly its
+// columns' bit span, so all slicing offsets are compile-time constants of the
+// digit width), forms s_j, and composes the tile's transfer function.  Usually
+// every thread's function is constant (a word that absorbs any incoming
+// carry), and then a thread's carry in is simply its predecessor's carry out.
 //
-//  * norm_tiles: every CTA takes one tile of words (one or both of a +- pair
-//    of combinations: same c1, c2, opposite sigma, so those columns are read
-//    once).  It stages the columns the tile needs in shared memory (one
-//    coalesced read of the column sums; a thread's words are exactly its
-//    columns' bit span, so all slicing offsets are compile-time constants of
-//    the digit width), forms s_j, resolves the carries inside the tile as if
-//    the carry into the tile were 0, writes the words, and records the tile's
-//    transfer function.  Usually every thread's function is constant (a word
-//    that absorbs any incoming carry), and then a thread's carry in is simply
-//    its predecessor's carry out.
-//  * norm_carry: the carry into each tile is the composition of the earlier
-//    tiles' functions applied to 0.  A CTA covers 256 tiles: it composes the
-//    functions of the tiles before its range, 256 at a time backwards until
-//    the composition is constant (block-wide ordered reductions), scans its
-//    own 256, and each thread adds its tile's carry in to the stored words --
-//    an exact increment or decrement of the tile's value, which stops at the
-//    first word that absorbs it.
+// The carry into a tile comes from the tiles before it.  While the tiles of a
+// launch fit in about one wave of CTAs, by a single-pass scan
+// with look-back (the decoupled look-back of Merrill and Garland's single-pass
+// prefix scan): the tile publishes its function in its flag word, then composes
+// the predecessors' published functions, newest first, until the composition
+// is constant or a predecessor has already published its carry out -- almost
+// always after the previous tile alone, since its function is constant -- and
+// publishes its own carry out.  Tiles are handed to CTAs by a counter in the
+// order the CTAs start, so every predecessor a tile waits for is running or
+// done; each wait is bounded (1 s, then status 1).  The flags and the counter
+// must be clear before the launch (the product's first kernel clears them).
+//
+// Larger launches (tens of thousands of tiles, where those waits add up) take
+// two: norm_tiles writes each tile's words with carry 0 and records its
+// function, and norm_carry, one CTA per 256 tiles, composes the functions of
+// the earlier tiles (walking back 256 at a time until the composition is
+// constant, usually one step), scans its own 256, and adds each tile's carry
+// in to its stored words -- an exact increment or decrement of the tile's
+// value, which stops at the first word that absorbs it.
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -45,7 +54,17 @@ namespace ks {
 namespace {
 constexpr int kThreads = 128;
 constexpr int kCarryThreads = 256;  // tiles per CTA of norm_carry
+// launches of at most this many tile CTAs (about one wave at 16 per SM) take
+// the single pass; larger ones the tile pass and the carry pass, whose tiles
+// never wait (with tens of thousands of tiles, the look-back costs more than
+// the second launch)
+constexpr int64_t kSinglePassCtas = 2048;
 constexpr uint32_t kIdentity = 0u | (1u << 2) | (2u << 4);
+// a tile's flag: its two functions (bits 0-5, 8-13), then whether they are
+// the tile's own (kFlagAgg) or the constant carry out of it (kFlagPrefix)
+constexpr uint32_t kFnMask = 63u | (63u << 8);
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 1u << 31;
+constexpr uint64_t kFlagWaitNs = 1000000000ull;  // bound of a wait for a predecessor (1 s)
 
 // Per digit width D: every thread takes WPT words = 32 WPT bits = CPT columns
 // exactly (32 WPT = D CPT), so each column sits at a compile-time bit offset
@@ -77,6 +96,21 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f) {
 #pragma unroll
   for (int c = -1; c <= 1; c++) h |= (uint32_t)(apply_fn(g, apply_fn(f, c)) + 1) << (2 * (c + 1));
   return h;
+}
+__device__ __forceinline__ bool is_const(uint32_t f) {  // monotone: f(-1) = f(1)
+  return apply_fn(f, -1) == apply_fn(f, 1);
+}
+__device__ __forceinline__ uint32_t const_fn(int v) {
+  const uint32_t e = (uint32_t)(v + 1);
+  return e | (e << 2) | (e << 4);
+}
+// flags are read past the L1 (another CTA writes them) and written whole
+__device__ __forceinline__ uint32_t flag_load(const uint32_t *p) { return __ldcv(p); }
+__device__ __forceinline__ void flag_store(uint32_t *p, uint32_t v) { atomicExch(p, v); }
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 // two functions side by side (bits 0-5 and 8-13), composed lane-wise
 __device__ __forceinline__ uint32_t compose2(uint32_t g, uint32_t f) {
@@ -129,7 +163,7 @@ __device__ __forceinline__ void thread_words(const int64_t (&x)[Geo<D>::BACK + G
   for (int w = 0; w < WPT; w++) s[w] = (int64_t)(uint32_t)T[w + 1] + (T[w] >> 32);
 }
 
-template <int D, class Src>
+template <int D, bool kSingle, class Src>
 __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
   pdl_enter();
   constexpr int WPT = Geo<D>::WPT, CPT = Geo<D>::CPT, BACK = Geo<D>::BACK;
@@ -138,11 +172,21 @@ __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
   __shared__ int64_t s_c1[kStage];
   __shared__ int64_t s_c2[kStage];
   __shared__ uint32_t s_warp[kThreads / 32];
+  __shared__ uint32_t s_idx;
+  __shared__ int s_cin[2];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int64_t bid;
   const NormArgs &a = src.locate(blockIdx.x, bid);
-  const int64_t group = bid / a.ntiles;
-  const int64_t tile = bid - group * a.ntiles;
+  // single pass: tiles go to CTAs in the order the CTAs start (a counter
+  // after the flags), so every tile's predecessors have started before it
+  // looks back at them
+  if (kSingle) {
+    if (tid == 0) s_idx = atomicAdd(a.job[0].flags + (int64_t)a.njobs * a.ntiles, 1u);
+    __syncthreads();
+  }
+  const int64_t idx = kSingle ? (int64_t)s_idx : bid;
+  const int64_t group = idx / a.ntiles;
+  const int64_t tile = idx - group * a.ntiles;
   const int nsub = a.paired ? 2 : 1;
   const NormJob &J0 = a.job[nsub * group];
   const int64_t W0 = tile * TW;
@@ -237,23 +281,60 @@ __global__ void __launch_bounds__(kThreads) norm_tiles(Src src) {
     pre = compose2(excl, wpre);
   }
 
-  // the tile's transfer functions, for the carry pass
-  if (tid == 0)
-    for (int u = 0; u < nsub; u++) a.job[nsub * group + u].flags[tile] = (total >> (8 * u)) & 63u;
+  // the carry into the tile: publish the tile's functions, then compose the
+  // predecessors' back to the first one that is constant or already holds its
+  // carry out (usually the previous tile alone), and publish that carry out
+  if (!kSingle) {
+    // two passes: the tile's functions for norm_carry, and carry 0 here
+    if (tid == 0) {
+      for (int u = 0; u < nsub; u++) a.job[nsub * group + u].flags[tile] = (total >> (8 * u)) & 63u;
+      s_cin[0] = 0;
+      s_cin[1] = 0;
+    }
+  } else if (tid == 0) {
+    uint32_t *fl = a.job[nsub * group].flags;
+    const uint32_t used = nsub == 2 ? kFnMask : 63u;
+    flag_store(fl + tile, (total & used) | kFlagAgg);
+    uint32_t acc = kIdentity | (kIdentity << 8);
+    bool ok = true;
+    for (int64_t j = tile - 1; j >= 0; j--) {
+      uint32_t v = flag_load(fl + j);
+      if ((v & (kFlagAgg | kFlagPrefix)) == 0) {
+        const uint64_t t0 = now_ns();
+        while (((v = flag_load(fl + j)) & (kFlagAgg | kFlagPrefix)) == 0)
+          if (now_ns() - t0 > kFlagWaitNs) {
+            ok = false;
+            break;
+          }
+        if (!ok) break;
+      }
+      acc = compose2(acc, (v & used) | (~used & (kIdentity | (kIdentity << 8))));
+      if ((v & kFlagPrefix) || (is_const(acc & 63u) && (nsub == 1 || is_const((acc >> 8) & 63u))))
+        break;
+    }
+    if (!ok && a.status != nullptr) atomicCAS(a.status, 0, 1);
+    const int c0 = apply_fn(acc & 63u, 0), c1 = apply_fn((acc >> 8) & 63u, 0);
+    const int o0 = apply_fn(total & 63u, c0), o1 = apply_fn((total >> 8) & 63u, c1);
+    flag_store(fl + tile, ((const_fn(o0) | (const_fn(o1) << 8)) & used) | kFlagPrefix);
+    s_cin[0] = c0;
+    s_cin[1] = c1;
+  }
+  __syncthreads();
 
   // predecessor's functions (fast path): the previous lane, or the previous
-  // warp's last lane; thread 0 takes carry 0 (norm_carry adds the true one)
+  // warp's last lane; thread 0 takes the tile's carry in
   const uint32_t prev_lane = __shfl_up_sync(0xffffffffu, agg, 1);
   const uint32_t prev = lane > 0 ? prev_lane : (wid > 0 ? s_warp[wid - 1] : 0u);
 #pragma unroll
   for (int u = 0; u < 2; u++) {
     if (u >= nsub) break;
     const NormJob &J = a.job[nsub * group + u];
+    const int cin = s_cin[u];
     int c;
     if (fast)
-      c = tid == 0 ? 0 : apply_fn((prev >> (8 * u)) & 63u, 0);
+      c = tid == 0 ? cin : apply_fn((prev >> (8 * u)) & 63u, 0);
     else
-      c = apply_fn((pre >> (8 * u)) & 63u, 0);
+      c = apply_fn((pre >> (8 * u)) & 63u, cin);
     uint32_t o[WPT];
 #pragma unroll
     for (int w = 0; w < WPT; w++) {
@@ -357,16 +438,18 @@ int64_t norm_tiles_for(int64_t nwords, int d) {
 }
 
 int make_norm_args(const NormJob *jobs, int njobs, int d, int64_t nwords, int64_t ntiles,
-                   NormArgs &a) {
+                   int *status, NormArgs &a) {
   if (njobs < 1 || njobs > 4) return -1;
   if (d != 16 && d != 32) return -1;
   if (ntiles * norm_tile_words(d) < nwords || (nwords & 3) != 0) return -1;
+  if (ntiles * 2 > 0x7fffffffLL) return -1;  // the tile counter is 32 bits
   a = NormArgs{};
   for (int i = 0; i < njobs; i++) a.job[i] = jobs[i];
   a.njobs = njobs;
   a.d = d;
   a.nwords = nwords;
   a.ntiles = ntiles;
+  a.status = status;
   // the +- pairs of Sec. 3.3 / 3.4 share their inputs
   bool paired = njobs % 2 == 0;
   for (int i = 0; paired && i < njobs; i += 2) {
@@ -385,20 +468,31 @@ int64_t norm_carry_blocks(const NormArgs &a) {
   return (a.paired ? a.njobs / 2 : a.njobs) * ((a.ntiles + kCarryThreads - 1) / kCarryThreads);
 }
 
+bool norm_single_pass(int64_t tile_blocks) { return tile_blocks <= kSinglePassCtas; }
+
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
-                             int64_t ntiles, cudaStream_t s) {
+                             int64_t ntiles, int *status, cudaStream_t s) {
   NormArgs a;
-  if (make_norm_args(jobs, njobs, d, nwords, ntiles, a) != 0) return cudaErrorInvalidValue;
+  if (make_norm_args(jobs, njobs, d, nwords, ntiles, status, a) != 0)
+    return cudaErrorInvalidValue;
   const One<NormArgs> one{a};
   const unsigned g1 = (unsigned)norm_blocks(a), g2 = (unsigned)norm_carry_blocks(a);
-  if (d == 32) {
-    (void)launch_k(norm_tiles<32, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
-    (void)launch_k(norm_carry<32, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
+  if (norm_single_pass(g1)) {
+    if (d == 32)
+      (void)launch_k(norm_tiles<32, true, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+    else
+      (void)launch_k(norm_tiles<16, true, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+    note_launches(1);
   } else {
-    (void)launch_k(norm_tiles<16, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
-    (void)launch_k(norm_carry<16, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
+    if (d == 32) {
+      (void)launch_k(norm_tiles<32, false, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+      (void)launch_k(norm_carry<32, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
+    } else {
+      (void)launch_k(norm_tiles<16, false, One<NormArgs>>, dim3(g1), dim3(kThreads), 0, s, one);
+      (void)launch_k(norm_carry<16, One<NormArgs>>, dim3(g2), dim3(kCarryThreads), 0, s, one);
+    }
+    note_launches(2);
   }
-  note_launches(2);
   return cudaGetLastError();
 }
 
@@ -407,20 +501,29 @@ cudaError_t launch_normalize_batch(int d, const NormArgs *da, const int64_t *pre
                                    int64_t carry_blocks, cudaStream_t s) {
   if (n == 0 || tile_blocks == 0) return cudaSuccess;
   const Many<NormArgs> t{da, prefix_tiles, n}, c{da, prefix_carry, n};
-  if (d == 32) {
-    (void)launch_k(norm_tiles<32, Many<NormArgs>>, dim3((unsigned)tile_blocks), dim3(kThreads), 0, s, t);
-    (void)launch_k(norm_carry<32, Many<NormArgs>>, dim3((unsigned)carry_blocks), dim3(kCarryThreads), 0, s, c);
+  const dim3 g1((unsigned)tile_blocks), g2((unsigned)carry_blocks);
+  if (norm_single_pass(tile_blocks)) {
+    if (d == 32)
+      (void)launch_k(norm_tiles<32, true, Many<NormArgs>>, g1, dim3(kThreads), 0, s, t);
+    else
+      (void)launch_k(norm_tiles<16, true, Many<NormArgs>>, g1, dim3(kThreads), 0, s, t);
+    note_launches(1);
   } else {
-    (void)launch_k(norm_tiles<16, Many<NormArgs>>, dim3((unsigned)tile_blocks), dim3(kThreads), 0, s, t);
-    (void)launch_k(norm_carry<16, Many<NormArgs>>, dim3((unsigned)carry_blocks), dim3(kCarryThreads), 0, s, c);
+    if (d == 32) {
+      (void)launch_k(norm_tiles<32, false, Many<NormArgs>>, g1, dim3(kThreads), 0, s, t);
+      (void)launch_k(norm_carry<32, Many<NormArgs>>, g2, dim3(kCarryThreads), 0, s, c);
+    } else {
+      (void)launch_k(norm_tiles<16, false, Many<NormArgs>>, g1, dim3(kThreads), 0, s, t);
+      (void)launch_k(norm_carry<16, Many<NormArgs>>, g2, dim3(kCarryThreads), 0, s, c);
+    }
+    note_launches(2);
   }
-  note_launches(2);
   return cudaGetLastError();
 }
 
-// flag words of a product: one transfer function per tile per job
+// flag words of a product: one per tile per job, then the tile counter
 int64_t norm_flag_bytes(int njobs, int64_t ntiles) {
-  return ((4 * (int64_t)njobs * ntiles) + 7) & ~(int64_t)7;
+  return ((4 * (int64_t)njobs * ntiles + 4) + 7) & ~(int64_t)7;
 }
 
 }  // namespace ks
