@@ -405,6 +405,18 @@ void ks_debug_fail_allocs(int n);
 void ks_debug_tc_stall(int on, int64_t wait_ns);
 
 /*
+ * Test hook, host only: how the tensor-core engine would split the work of
+ * one product (this variant, engine KS_ENGINE_TC) over `grid` <= 160 CTAs.
+ * The work is the sequence of (sub-product, output tile, block offset), total
+ * entries in all; CTA k takes [at[k], at[k + 1]) (at: grid + 1 entries) and
+ * its first item lies in tile first_tile[k] of sub-product first_q[k].
+ * (The paper has no counterpart: this is the engine's own scheduling.)
+ */
+int ks_debug_tc_split(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+                      int variant, int grid, int64_t *at, int32_t *first_q,
+                      int32_t *first_tile, int64_t *total);
+
+/*
  * The plan ks_mul_ex would run, as int64 fields (n of them are written):
  * 0 variant, 1 engine, 2 N, 3 digit bits d, 4 sub-products, 5 digits of each
  * f-side operand, 6 digits of each g-side operand, 7 column sums per

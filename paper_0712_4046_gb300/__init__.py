@@ -63,6 +63,8 @@ _sig("ks_plan_destroy", None, _vp)
 _sig("ks_plan_status", _ci, _vp)
 _sig("ks_debug_fail_allocs", None, _ci)
 _sig("ks_debug_tc_stall", None, _ci, _i64)
+_sig("ks_debug_tc_split", _ci, _i64, _i64, _ci, _ci, _ci, _ci, ctypes.POINTER(_i64),
+     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64))
 _sig("ks_set_pdl", None, _ci)
 
 DISPATCH_AUTO, DISPATCH_KS1, DISPATCH_TABLE, DISPATCH_MLP = 0, 1, 2, 3
@@ -418,6 +420,18 @@ def profile_collect() -> dict:
     cnt = (ctypes.c_longlong * N_PHASES)()
     _check(lib.ks_profile_collect(ms, cnt, N_PHASES), "ks_profile_collect")
     return {lib.ks_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES)}
+
+
+def tc_split(len_f, len_g, coeff_bits, is_signed, variant, grid) -> dict:
+    """The tensor-core engine's split of one product's work over `grid` CTAs
+    (host only): {"at": grid + 1 positions, "first_q", "first_tile", "total"}."""
+    at = (_i64 * (grid + 1))()
+    fq = (ctypes.c_int32 * grid)()
+    ft = (ctypes.c_int32 * grid)()
+    tot = _i64(0)
+    _check(lib.ks_debug_tc_split(len_f, len_g, coeff_bits, int(is_signed), variant, grid, at, fq,
+                                 ft, ctypes.byref(tot)), "ks_debug_tc_split")
+    return {"at": list(at), "first_q": list(fq), "first_tile": list(ft), "total": tot.value}
 
 
 def plan_info(len_f, len_g, coeff_bits, is_signed, variant=KS_AUTO, engine=ENGINE_AUTO,

@@ -954,3 +954,32 @@ extern "C" void ks_debug_tc_stall(int on, int64_t wait_ns) {
   ks::g_tc_wait_ns.store(wait_ns > 0 ? (unsigned long long)wait_ns : ks::kWaitNs);
   ks::bump_epoch();
 }
+
+// The host's split of one product's tensor-core work over `grid` CTAs (host
+// only: plans it without touching the device).
+extern "C" int ks_debug_tc_split(int64_t len_f, int64_t len_g, int coeff_bits, int is_signed,
+                                 int variant, int grid, int64_t *at, int32_t *first_q,
+                                 int32_t *first_tile, int64_t *total) {
+  if (!at || !first_q || !first_tile || !total || grid < 1 || grid > ks::kTcMaxCtas)
+    return KS_EINVAL;
+  ks::Plan p;
+  const int rc = ks::make_plan(p, len_f, len_g, coeff_bits, is_signed, variant, KS_ENGINE_TC);
+  if (rc != KS_OK) return rc;
+  // operand and column-sum addresses are only recorded here, never used
+  char *base = reinterpret_cast<char *>(static_cast<uintptr_t>(1) << 20);
+  int64_t *C[4];
+  for (int q = 0; q < p.nprod; q++) C[q] = reinterpret_cast<int64_t *>(base);
+  ks::TcArgs a;
+  ks::make_tc_args(p.tg, p.nprod, base, C, nullptr, a);
+  const int64_t prefix[2] = {0, a.work_prefix[p.nprod]};
+  ks::TcSplit sp;
+  ks::tc_make_split(&a, prefix, 1, grid, sp);
+  if (sp.n != grid) return KS_ERANGE;
+  for (int k = 0; k <= grid; k++) at[k] = sp.at[k];
+  for (int k = 0; k < grid; k++) {
+    first_q[k] = sp.q[k];
+    first_tile[k] = sp.tile[k];
+  }
+  *total = prefix[1];
+  return KS_OK;
+}

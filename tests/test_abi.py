@@ -144,3 +144,46 @@ def test_binding_refuses_wrong_layouts_before_any_device_call():
         ks.ks_mul_mod(torch.zeros((lf + lg - 1, 2), dtype=torch.int64),
                       torch.zeros((lf, 1), dtype=torch.int64),
                       torch.zeros((lg, 1), dtype=torch.int64), 97)
+
+
+def _tile_offsets(dmax, R):
+    """Block offsets of each output tile of one sub-product (tile t meets the
+    offsets max(0, 128 t - R + 1) .. min(128 t + 127, dmax))."""
+    T = (dmax + R + 127) // 128
+    return [min(128 * t + 127, dmax) - max(0, 128 * t - R + 1) + 1 for t in range(T)]
+
+
+@pytest.mark.parametrize("shape", [(16384, 16384, 48, True, 4), (2500, 2300, 48, True, 1),
+                                   (4000, 1000, 20, False, 3), (65536, 65536, 8, False, 2)])
+@pytest.mark.parametrize("grid", [152, 37])
+def test_tensor_core_split(ks, shape, grid):
+    # the host's split of the tensor-core work: it covers every offset once, in
+    # order; each CTA's first item is the tile holding its first offset; a share
+    # that runs into a further tile is charged two offsets, and with that charge
+    # the shares cost the same to within the charge and the rounding
+    lf, lg, b, sg, v = shape
+    info = ks.plan_info(lf, lg, b, sg, v, ks.ENGINE_TC)
+    sp = ks.tc_split(lf, lg, b, sg, v, grid)
+    dmax, R = (info["nA"] + 126) // 128, (info["nB"] + 127) // 128
+    per_tile = _tile_offsets(dmax, R)
+    starts, tiles = [], []  # every tile's first position, with (q, t)
+    pos = 0
+    for q in range(info["nprod"]):
+        for t, n in enumerate(per_tile):
+            starts.append(pos)
+            tiles.append((q, t))
+            pos += n
+    assert sp["total"] == pos
+    at = sp["at"]
+    assert at[0] == 0 and at[-1] == pos
+    assert all(x <= y for x, y in zip(at, at[1:]))
+    import bisect
+    costs = []
+    for k in range(grid):
+        if at[k] < pos:
+            j = bisect.bisect_right(starts, at[k]) - 1
+            assert (sp["first_q"][k], sp["first_tile"][k]) == tiles[j], k
+        inside = sum(1 for s in starts if at[k] < s < at[k + 1])
+        costs.append(at[k + 1] - at[k] + 2 * inside)
+    V = pos + 2 * (len(starts) - 1)
+    assert max(costs) <= V / grid + 2 + 1, (max(costs), V / grid)
