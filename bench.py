@@ -49,11 +49,11 @@ METRIC = "Z[x] products/s and output Gbit/s, KS4 vs KS1, bit-exact, 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_kernel
 # launch on this workload's KS4 product, from an ncu capture of the current
-# kernel (the tc_kernel summary under profiles/: 5.21 MB read, no DRAM
+# kernel (the tc_kernel summary under profiles/: 5.22 MB read, no DRAM
 # writes); set to None whenever the kernel changes until it is captured again
 TC_KERNEL_DRAM_BYTES = 5.22e6
-TC_KERNEL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                            "profiles/tc_kernel_zx_product_16384_s48_ks4.md")
+TC_KERNEL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                            "(the tc_kernel capture of this workload under profiles/)")
 # 32-bit IMAD issue rate per SM per clock (the INT32 multiply-add pipe), x2 ops per MAC
 IMAD_PER_SM_CLK = 64
 SMS = 152
