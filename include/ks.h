@@ -405,6 +405,15 @@ void ks_debug_fail_allocs(int n);
 void ks_debug_tc_stall(int on, int64_t wait_ns);
 
 /*
+ * Test hook: which form the carry normalization takes (no counterpart in the
+ * paper).  0: by size (one single-pass launch up to 2048 tile CTAs, else a
+ * tile pass and a carry pass), 1: always the single pass, 2: always the two
+ * passes.  Both give the same words; a captured plan keeps the form it was
+ * captured with.
+ */
+void ks_debug_norm_form(int form);
+
+/*
  * Test hook, host only: how the tensor-core engine would split the work of
  * one product (this variant, engine KS_ENGINE_TC) over `grid` <= 160 CTAs.
  * The work is the sequence of (sub-product, output tile, block offset), total

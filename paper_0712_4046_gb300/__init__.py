@@ -63,6 +63,7 @@ _sig("ks_plan_destroy", None, _vp)
 _sig("ks_plan_status", _ci, _vp)
 _sig("ks_debug_fail_allocs", None, _ci)
 _sig("ks_debug_tc_stall", None, _ci, _i64)
+_sig("ks_debug_norm_form", None, _ci)
 _sig("ks_debug_tc_split", _ci, _i64, _i64, _ci, _ci, _ci, _ci, ctypes.POINTER(_i64),
      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64))
 _sig("ks_set_pdl", None, _ci)

@@ -46,6 +46,8 @@
 // constant, usually one step), scans its own 256, and adds each tile's carry
 // in to its stored words -- an exact increment or decrement of the tile's
 // value, which stops at the first word that absorbs it.
+#include <atomic>
+
 #include "ks_internal.cuh"
 #include "ks_src.cuh"
 
@@ -468,7 +470,13 @@ int64_t norm_carry_blocks(const NormArgs &a) {
   return (a.paired ? a.njobs / 2 : a.njobs) * ((a.ntiles + kCarryThreads - 1) / kCarryThreads);
 }
 
-bool norm_single_pass(int64_t tile_blocks) { return tile_blocks <= kSinglePassCtas; }
+// test hook: 0 by size, 1 always the single pass, 2 always the two passes
+static std::atomic<int> g_norm_form{0};
+
+bool norm_single_pass(int64_t tile_blocks) {
+  const int f = g_norm_form.load(std::memory_order_relaxed);
+  return f == 1 || (f == 0 && tile_blocks <= kSinglePassCtas);
+}
 
 cudaError_t launch_normalize(const NormJob *jobs, int njobs, int d, int64_t nwords,
                              int64_t ntiles, int *status, cudaStream_t s) {
@@ -527,3 +535,8 @@ int64_t norm_flag_bytes(int njobs, int64_t ntiles) {
 }
 
 }  // namespace ks
+
+extern "C" void ks_debug_norm_form(int form) {
+  ks::g_norm_form.store(form == 1 || form == 2 ? form : 0);
+  ks::bump_epoch();  // host-call graphs captured the other form
+}
