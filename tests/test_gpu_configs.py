@@ -1,10 +1,15 @@
 """The five workload configurations at full size, through the C ABI.
 
 Where the CPU oracle finishes in seconds the comparison is exact and complete;
-above that (the 2^20 x 256-bit product, long sweep points, the 64 products
-mod 2^61 - 1, the 4096-product batch) every product is checked by modular
-fingerprints h(r) = f(r) g(r) mod q at random points, and sampled
-coefficients are compared exactly with the oracle's dot products."""
+above that (long sweep points, the 64 products mod 2^61 - 1, the 4096-product
+batch) every product is checked by modular fingerprints h(r) = f(r) g(r) mod q
+at random points, and sampled coefficients are compared exactly with the
+oracle's dot products.  The 2^20 x 256-bit product is compared in full with
+the oracle's complete schoolbook product, run once offline: its SHA-256 is in
+tests/golden/config5a_product.txt (written by make_config5a_hash.py there)."""
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
@@ -102,11 +107,26 @@ def test_config4_uneven_batch(ks):
             fingerprint_check(got, f, g, q["is_signed"], i, nchecks=1)
 
 
+def _golden_5a():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "config5a_product.txt")
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    return tuple(int(x) for x in kv["shape"].split()), kv["sha256"]
+
+
 def test_config5a_2pow20_u256(ks):
     L, b = 1 << 20, 256
     f, g = random_case(L, L, b, False, 55)
+    shape, digest = _golden_5a()
     for variant in (1, 4):
         got = gpu_mul(ks, f, g, b, False, variant)
+        # every coefficient, against the oracle's full product
+        assert got.shape == shape
+        assert hashlib.sha256(np.ascontiguousarray(got).tobytes()).hexdigest() == digest, variant
         fingerprint_check(got, f, g, False, variant, nchecks=2)
         sampled_check(got, f, g, b, False, 12, variant)
 
