@@ -187,3 +187,17 @@ def test_tensor_core_split(ks, shape, grid):
         costs.append(at[k + 1] - at[k] + 2 * inside)
     V = pos + 2 * (len(starts) - 1)
     assert max(costs) <= V / grid + 2 + 1, (max(costs), V / grid)
+
+
+def test_tensor_core_split_edges(ks):
+    # one coefficient each: a single tile with two offsets; more CTAs than
+    # offsets leave the extra shares empty; a long thin product stays ordered
+    sp = ks.tc_split(1, 1, 1, False, 1, 1)
+    assert sp["at"] == [0, sp["total"]] and sp["first_tile"] == [0]
+    sp = ks.tc_split(1, 1, 1, False, 1, 152)
+    assert sp["at"][0] == 0 and sp["at"][-1] == sp["total"]
+    assert all(x <= y for x, y in zip(sp["at"], sp["at"][1:]))
+    sp = ks.tc_split(3, 200000, 8, True, 4, 152)
+    assert sp["at"][-1] == sp["total"] and all(x <= y for x, y in zip(sp["at"], sp["at"][1:]))
+    with pytest.raises(ks.KSError):
+        ks.tc_split(100, 100, 8, False, 1, 161)  # more CTAs than the split holds
