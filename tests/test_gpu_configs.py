@@ -1,12 +1,12 @@
 """The five workload configurations at full size, through the C ABI.
 
 Where the CPU oracle finishes in seconds the comparison is exact and complete;
-above that (long sweep points, the 64 products mod 2^61 - 1, the 4096-product
-batch) every product is checked by modular fingerprints h(r) = f(r) g(r) mod q
-at random points, and sampled coefficients are compared exactly with the
-oracle's dot products.  The 2^20 x 256-bit product is compared in full with
-the oracle's complete schoolbook product, run once offline: its SHA-256 is in
-tests/golden/config5a_product.txt (written by make_config5a_hash.py there)."""
+above that (long sweep points, the 4096-product batch) every product is
+checked by modular fingerprints h(r) = f(r) g(r) mod q at random points, and
+sampled coefficients are compared exactly with the oracle's dot products.  The
+2^20 x 256-bit product and the 64 products mod 2^61 - 1 are compared in full
+with the oracle's complete products, run once offline: their SHA-256 digests
+are in tests/golden/ (written by the make_config5*_hash.py scripts there)."""
 import hashlib
 import os
 
@@ -131,17 +131,33 @@ def test_config5a_2pow20_u256(ks):
         sampled_check(got, f, g, b, False, 12, variant)
 
 
+def _golden_5b():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "config5b_products.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            i, digest = line.split()
+            out[int(i)] = digest
+    return out
+
+
 def test_config5b_64_products_mod_mersenne61(ks):
     import torch
     p = (1 << 61) - 1
     L = 1 << 16
     rng = np.random.default_rng(61)
+    digests = _golden_5b()
+    assert sorted(digests) == list(range(64))
     for i in range(64):
         f = gen.random_residues(L, p, 900 + 2 * i)
         g = gen.random_residues(L, p, 901 + 2 * i)
         h = torch.empty((2 * L - 1, 1), dtype=torch.int64, device="cuda")
         ks.ks_mul_mod(h, to_dev(f), to_dev(g), p, 4 if i % 2 else 1)
-        got = [int(x) for x in to_host(h).reshape(-1)]
+        hh = to_host(h)
+        # every residue, against the oracle's full product
+        assert hashlib.sha256(np.ascontiguousarray(hh).tobytes()).hexdigest() == digests[i], i
+        got = [int(x) for x in hh.reshape(-1)]
         fi = [int(x) for x in f.reshape(-1)]
         gi = [int(x) for x in g.reshape(-1)]
         assert all(0 <= x < p for x in got)
