@@ -166,3 +166,43 @@ def test_rejects_bad_arguments():
         oracle.mul_mod(np.array([[5]], dtype=np.uint64), np.array([[1]], dtype=np.uint64), 5)
     with pytest.raises(ValueError):
         oracle.mul(f, f, 0, False)
+
+
+def test_stored_config5b_digests_are_the_oracles():
+    # the golden digests of the 64 products mod 2^61 - 1 were written by
+    # tests/golden/make_config5b_hash.py from the oracle alone; two of them are
+    # recomputed here (a few seconds each), and the file lists all 64
+    import hashlib
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "config5b_products.txt")
+    digests = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            i, d = line.split()
+            digests[int(i)] = d
+    assert sorted(digests) == list(range(64))
+    p, L = (1 << 61) - 1, 1 << 16
+    for i in (0, 63):
+        h = oracle.mul_mod(gen.random_residues(L, p, 900 + 2 * i),
+                           gen.random_residues(L, p, 901 + 2 * i), p)
+        assert hashlib.sha256(np.ascontiguousarray(h, dtype=np.uint64).tobytes()).hexdigest() \
+            == digests[i], i
+
+
+def test_stored_config5a_digest_format():
+    # the full 2^20 x 256-bit product takes the oracle about 1.5 hours, so only
+    # the stored record's shape is checked here: 2^21 - 1 coefficients of the
+    # library's output limb count, and a SHA-256
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "config5a_product.txt")
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    L = 1 << 20
+    assert tuple(int(x) for x in kv["shape"].split()) == (2 * L - 1, oracle.out_limbs(L, L, 256,
+                                                                                    False))
+    assert len(kv["sha256"]) == 64 and int(kv["sha256"], 16) >= 0
