@@ -201,3 +201,28 @@ def test_tensor_core_split_edges(ks):
     assert sp["at"][-1] == sp["total"] and all(x <= y for x, y in zip(sp["at"], sp["at"][1:]))
     with pytest.raises(ks.KSError):
         ks.tc_split(100, 100, 8, False, 1, 161)  # more CTAs than the split holds
+
+
+def test_binding_checks_unequal_size_layouts():
+    # ks_mul_bits: f and g with their own limb counts, h with the limbs of
+    # bf + bg (not of 2 max(bf, bg)); plan problems with coeff_bits_g likewise
+    import torch
+
+    import paper_0712_4046_gb300 as ks
+    lf, lg, bf, bg = 40, 30, 130, 20
+    ol = ks.out_limbs_bits(lf, lg, bf, bg, True)
+    assert ol < ks.out_limbs(lf, lg, max(bf, bg), True)
+    f = torch.zeros((lf, 3), dtype=torch.int64)
+    g = torch.zeros((lg, 1), dtype=torch.int64)
+    with pytest.raises(ValueError, match="shape"):  # h sized for 2 max(bf, bg)
+        ks.ks_mul_bits(torch.zeros((lf + lg - 1, ks.out_limbs(lf, lg, bf, True)),
+                                   dtype=torch.int64), f, bf, g, bg, True)
+    with pytest.raises(ValueError, match="shape"):  # g with f's limb count
+        ks.ks_mul_bits(torch.zeros((lf + lg - 1, ol), dtype=torch.int64), f, bf,
+                       torch.zeros((lg, 3), dtype=torch.int64), bg, True)
+    with pytest.raises(ValueError, match="CUDA"):  # right layouts, host tensors
+        ks.ks_mul_bits(torch.zeros((lf + lg - 1, ol), dtype=torch.int64), f, bf, g, bg, True)
+    with pytest.raises(ValueError, match="shape"):
+        ks.Plan([dict(h=torch.zeros((lf + lg - 1, ol), dtype=torch.int64), f=f,
+                      g=torch.zeros((lg, 3), dtype=torch.int64), coeff_bits=bf,
+                      coeff_bits_g=bg, is_signed=True)])
